@@ -1,0 +1,124 @@
+"""Level-set geometry and cell classification (oracle).
+
+Test infrastructure only (see ``oracle/__init__``).
+
+FCM embeds the physical domain in a box and marks it by an indicator alpha
+(Sec. 2.1, Eq. weakform): alpha = 1 in Omega_phys, alpha = eps << 1 in
+Omega_fict.  Geometry is given by a level set psi with Omega_phys = {psi <= 0}
+(the popcorn convention of Sec. 4.4, points on the surface count as
+physical).
+
+Kinds:
+  none       psi = -1 everywhere (body-fitted box)
+  ball       psi = |x - c| - r                         (circle / sphere)
+  voids      psi = max_k (r_k - |x - c_k|)             (block minus balls)
+  ellipsoid  psi = |diag(1/a) R^T (x - c)| - 1
+
+Box classification (the paper leaves the cut test open; this is the
+reading): balls and voids use exact nearest/farthest point distances, the
+ellipsoid a sign test of psi on a 5^d lattice including the corners.
+Floating-point operations are written out in a fixed order so that a second
+implementation performing the same operations gets identical results.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+INSIDE, OUTSIDE, CUT = 0, 1, 2
+
+
+def levelset(geom: dict, x: np.ndarray) -> np.ndarray:
+    """psi at points x of shape (..., d)."""
+    x = np.asarray(x, dtype=np.float64)
+    d = x.shape[-1]
+    kind = geom["kind"]
+    if kind == "none":
+        return -np.ones(x.shape[:-1])
+    if kind == "ball":
+        c = geom["center"]
+        s = (x[..., 0] - c[0]) * (x[..., 0] - c[0])
+        for a in range(1, d):
+            s = s + (x[..., a] - c[a]) * (x[..., a] - c[a])
+        return np.sqrt(s) - geom["radius"]
+    if kind == "voids":
+        out = None
+        for (cx, cy, cz, r) in geom["balls"]:
+            c = (cx, cy, cz)
+            s = (x[..., 0] - c[0]) * (x[..., 0] - c[0])
+            for a in range(1, d):
+                s = s + (x[..., a] - c[a]) * (x[..., a] - c[a])
+            v = r - np.sqrt(s)
+            out = v if out is None else np.maximum(out, v)
+        return out
+    if kind == "ellipsoid":
+        c, ax, R = geom["center"], geom["axes"], geom["rot"]
+        dx = [x[..., a] - c[a] for a in range(3)]
+        q = None
+        for i in range(3):
+            y = R[0][i] * dx[0] + R[1][i] * dx[1] + R[2][i] * dx[2]
+            t = y / ax[i]
+            q = t * t if q is None else q + t * t
+        return np.sqrt(q) - 1.0
+    raise ValueError(kind)
+
+
+def _ball_dist2(lo, hi, c):
+    """(nearest, farthest) squared distance from c to the box [lo, hi]."""
+    dmin2 = 0.0
+    dmax2 = 0.0
+    for a in range(len(lo)):
+        l = lo[a] - c[a]
+        u = hi[a] - c[a]
+        near = 0.0
+        if l > 0.0:
+            near = l
+        elif u < 0.0:
+            near = -u
+        far = max(abs(l), abs(u))
+        dmin2 = dmin2 + near * near
+        dmax2 = dmax2 + far * far
+    return dmin2, dmax2
+
+
+def classify_box(geom: dict, lo, hi) -> int:
+    """INSIDE (all physical), OUTSIDE (all fictitious) or CUT."""
+    kind = geom["kind"]
+    if kind == "none":
+        return INSIDE
+    if kind == "ball":
+        r = geom["radius"]
+        dmin2, dmax2 = _ball_dist2(lo, hi, geom["center"])
+        r2 = r * r
+        if dmax2 <= r2:
+            return INSIDE
+        if dmin2 >= r2:
+            return OUTSIDE
+        return CUT
+    if kind == "voids":
+        all_clear = True
+        for (cx, cy, cz, r) in geom["balls"]:
+            dmin2, dmax2 = _ball_dist2(lo, hi, (cx, cy, cz))
+            r2 = r * r
+            if dmax2 <= r2:
+                return OUTSIDE
+            if dmin2 < r2:
+                all_clear = False
+        return INSIDE if all_clear else CUT
+    if kind == "ellipsoid":
+        d = len(lo)
+        ts = [k * 0.25 for k in range(5)]
+        pts = []
+        for kz in range(5):
+            for ky in range(5):
+                for kx in range(5):
+                    k = (kx, ky, kz)
+                    pts.append([lo[a] + ts[k[a]] * (hi[a] - lo[a]) for a in range(d)])
+        psi = levelset(geom, np.array(pts))
+        if np.all(psi <= 0.0):
+            return INSIDE
+        if np.all(psi > 0.0):
+            return OUTSIDE
+        return CUT
+    raise ValueError(kind)

@@ -1,0 +1,185 @@
+"""Pins of the oracle's multigrid hierarchy, smoother, V-cycle and PCG.
+
+* Hierarchical levels (Eq. hierarchicalMatrices): the level p-1 matrix is the
+  matrix assembled directly at degree p-1.
+* Galerkin Q1 h-levels equal direct assembly on the coarse grid (nested
+  spaces, exact quadrature).
+* AS blocks have the sizes of Table tab::upperbound (n = 1) and
+  lambda_max(M^{-1} A) stays below the overlap 3^d of the block supports.
+* The V-cycle (Algorithm 1) is symmetric positive definite.
+* PCG agrees with a direct sparse solve.
+* CG+MG iteration counts of Table tab:testcaseA are reproduced.
+* Iteration counts stay bounded under h-refinement on cut grids (Sec. 4).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import fcm_inputs as fi
+from oracle import multigrid as mg
+from oracle.assembly import assemble
+from oracle.grid import m_1d
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_p_levels_are_direct_assemblies():
+    prob = fi.square_mms(cells=4, p=3)
+    H = mg.Hierarchy(prob)
+    for lv in H.levels:
+        if lv.cells == (4, 4) and lv.p < 3:
+            q = dict(prob, p=lv.p)
+            A, _, _ = assemble(q)
+            assert abs(A - lv.A).max() < 1e-12 * abs(A).max()
+
+
+def test_restriction_is_prefix_subbox():
+    sel = mg.p_selection(2, (3, 3), 3, 2)
+    m3, m2 = m_1d(3, 3), m_1d(3, 2)
+    assert len(sel) == m2 * m2
+    for k, g in enumerate(sel):
+        ix, iy = k % m2, k // m2
+        assert g == ix + m3 * iy
+
+
+def test_galerkin_h_level_equals_coarse_assembly():
+    fine = fi.square_mms(cells=8, p=1)
+    fine["dirichlet"] = dict(kind="faces", g="zero", faces=[0, 3])
+    coarse = dict(fine, cells=(4, 4))
+    Af, _, _ = assemble(fine)
+    Ac, _, _ = assemble(coarse)
+    P = mg.q1_prolongation(2, (8, 8))
+    G = P.T @ Af @ P
+    assert abs(G - Ac).max() < 1e-12 * abs(Ac).max()
+
+
+def test_q1_prolongation_reproduces_linears():
+    for Cf in (4, 5, 7):
+        P = mg.q1_prolongation(3, (Cf, Cf, Cf))
+        Cc = (Cf + 1) // 2
+        # coarse nodes at 2h spacing (the last one may lie outside)
+        xc = np.arange(Cc + 1) * 2.0
+        xf = np.arange(Cf + 1) * 1.0
+        X, Y, Z = np.meshgrid(xc, xc, xc, indexing="ij")
+        u = (1 + 2 * X - Y + 0.5 * Z).transpose(2, 1, 0).ravel()
+        Xf, Yf, Zf = np.meshgrid(xf, xf, xf, indexing="ij")
+        uf = (1 + 2 * Xf - Yf + 0.5 * Zf).transpose(2, 1, 0).ravel()
+        assert np.allclose(P @ u, uf)
+
+
+@pytest.mark.parametrize("dim,p,nf", [(3, 2, 1), (3, 3, 1), (3, 2, 3), (2, 4, 1)])
+def test_block_sizes_match_upper_bound_table(dim, p, nf):
+    """Table tab::upperbound, tensor product space, elementwise (n = 1):
+    m_max = n_f (n p + 1)^3 (the 2D analogue has exponent 2)."""
+    from oracle.grid import cell_dofs
+    idx = cell_dofs(dim, (3,) * dim, p, (1,) * dim, nf)
+    assert len(idx) == nf * (p + 1) ** dim == len(set(idx))
+
+
+@pytest.fixture(scope="module")
+def circle_h():
+    return mg.Hierarchy(fi.poisson2d_circle(cells=8, p=2))
+
+
+def _dense(op, n):
+    return np.column_stack([op(e) for e in np.eye(n)])
+
+
+def test_smoother_eigen_bound(circle_h):
+    for lv in circle_h.levels[1:]:
+        A = lv.A.toarray()
+        Minv = _dense(lv.smoother, lv.N)
+        assert np.allclose(Minv, Minv.T, atol=1e-10 * np.abs(Minv).max())
+        lam = np.linalg.eigvals(Minv @ A).real
+        assert lam.min() > 0
+        assert lam.max() <= 3 ** lv.dim + 1e-9
+        # the estimate used for omega is a lower bound close to lambda_max
+        assert lv.lam <= lam.max() * (1 + 1e-9)
+        assert lv.lam > 0.9 * lam.max()
+        # and the chosen omega keeps the fixed-point iteration stable
+        assert lv.omega * lam.max() < 2.0
+
+
+def test_vcycle_symmetric_positive_definite(circle_h):
+    N = circle_h.A.shape[0]
+    V = _dense(circle_h.vcycle, N)
+    assert np.abs(V - V.T).max() < 1e-9 * np.abs(V).max()
+    ev = np.linalg.eigvalsh((V + V.T) / 2)
+    assert ev.min() > 0
+
+
+def test_vcycle_is_linear_and_nested(circle_h):
+    rng = np.random.default_rng(0)
+    N = circle_h.A.shape[0]
+    u, v = rng.standard_normal(N), rng.standard_normal(N)
+    a = circle_h.vcycle(2 * u - 3 * v)
+    b = 2 * circle_h.vcycle(u) - 3 * circle_h.vcycle(v)
+    assert np.abs(a - b).max() < 1e-10 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("make", [
+    lambda: fi.poisson2d_circle(cells=16, p=2),
+    lambda: fi.poisson3d_sphere(cells=3, p=2),
+])
+def test_pcg_matches_direct_solve(make):
+    prob = make()
+    H = mg.Hierarchy(prob)
+    x, k, hist = mg.pcg(H.A, H.b, H.vcycle, rtol=1e-13, maxit=200)
+    xd = spla.spsolve(H.A.tocsc(), H.b)
+    # kappa(A) ~ 1e10..1e12 (alpha = 1e-6..1e-8): coefficient vectors agree
+    # only to ~kappa * eps in the fictitious part, the energy norm tightly
+    e = x - xd
+    assert np.sqrt(e @ (H.A @ e)) / np.sqrt(xd @ (H.A @ xd)) < 1e-10
+    assert np.linalg.norm(e) / np.linalg.norm(xd) < 1e-6
+    assert np.linalg.norm(H.b - H.A @ x) / np.linalg.norm(H.b) <= 1e-13
+
+
+def test_square_iteration_table():
+    """Table tab:testcaseA, CG with multigrid preconditioner, elementwise AS
+    (5,5), tolerance 1e-9, h = 1/8 and 1/16 (h = 1/32, 1/64 in the slow
+    test).  Tolerance +-1: the coarse solver differs from the paper's."""
+    g = json.load(open(os.path.join(GOLDEN, "square_mms_cg_mg_elementwise.json")))
+    for p in (2, 3, 4, 5):
+        for j, C in enumerate(g["cells"][:2]):
+            H, x, k, hist = mg.solve(fi.square_mms(cells=C, p=p), rtol=g["rtol"])
+            assert abs(k - g["iterations"][str(p)][j]) <= 1, (p, C, k)
+
+
+@pytest.mark.slow
+def test_square_iteration_table_fine():
+    g = json.load(open(os.path.join(GOLDEN, "square_mms_cg_mg_elementwise.json")))
+    for p in (2, 3):
+        H, x, k, hist = mg.solve(fi.square_mms(cells=32, p=p), rtol=g["rtol"])
+        assert abs(k - g["iterations"][str(p)][2]) <= 1, (p, k)
+
+
+def test_mg_solver_contraction_close_to_paper():
+    """MG as a stand-alone solver (Eq. contraction): rho_max at h = 1/8 stays
+    within 0.1 of Table tab::squareCont (which is for h = 1/32) for p = 2, 3,
+    and the iteration counts within 2 of Table tab:testcaseA."""
+    g = json.load(open(os.path.join(GOLDEN, "square_mms_cg_mg_elementwise.json")))
+    for p in (2, 3):
+        H = mg.Hierarchy(fi.square_mms(cells=8, p=p))
+        x, k, rho = mg.mg_solve(H.A, H.b, H.vcycle, rtol=1e-9)
+        assert abs(max(rho) - g["rho_max_h32_elementwise"][str(p)]) < 0.1
+        assert abs(k - g["mg_solver_iterations"][str(p)][0]) <= 2
+
+
+def test_iterations_bounded_under_refinement():
+    """Sec. 4.1.2: with AS smoothing the CG+MG iteration count does not grow
+    with h on immersed grids."""
+    ks = []
+    for C in (8, 16, 32):
+        H, x, k, hist = mg.solve(fi.poisson2d_circle(cells=C), rtol=1e-8)
+        ks.append(k)
+    assert max(ks) - min(ks) <= 3 and max(ks) <= 20, ks
+
+
+def test_pcg_flexible_equals_standard_for_symmetric_preconditioner(circle_h):
+    x1, k1, _ = mg.pcg(circle_h.A, circle_h.b, circle_h.vcycle, rtol=1e-10)
+    x2, k2, _ = mg.pcg(circle_h.A, circle_h.b, circle_h.vcycle, rtol=1e-10, flexible=True)
+    assert abs(k1 - k2) <= 1
+    assert np.linalg.norm(x1 - x2) <= 1e-8 * np.linalg.norm(x1)
