@@ -1,0 +1,208 @@
+/*
+ * fcm.h - C ABI of the GB300 hierarchical multigrid solver for the finite
+ * cell method (Jomo et al., "Hierarchical multigrid approaches for the finite
+ * cell method on uniform and multi-level hp-refined grids", arXiv 2010.00881).
+ *
+ * Problem (Sec. 2.1, Eq. weakform): find u_h with
+ *   int (B v)^T alpha C B u dOmega + int beta (N v)^T N u dGamma_D
+ *     = int alpha (N v)^T f dOmega + int (N v)^T g_N dGamma_N
+ *       + int beta (N v)^T g_D dGamma_D
+ * on a uniform Cartesian grid of integrated Legendre elements of degree p
+ * (tensor-product space), alpha = 1 in the physical domain {psi <= 0} and
+ * alpha = eps << 1 in the fictitious domain.
+ *
+ * Solver (Sec. 3 and 4): conjugate gradients preconditioned by one
+ * hierarchical multigrid V-cycle (Algorithm 1) per iteration: elementwise
+ * additive Schwarz smoothing (Eq. AdditiveSchwarz) with n_pre / n_post steps,
+ * binary p-transfers (Eq. restrictionoperation) down the arithmetic
+ * p-sequence, nested Q1 h-coarsening below p = 1 (the Remark of Sec. 3.2)
+ * and a dense Cholesky solve on the coarsest grid.
+ *
+ * Conventions (all entry points):
+ *  - Every vector is a caller-owned buffer of `ndofs` doubles in the
+ *    hierarchical layout: per axis the 1D index of node k is k and that of
+ *    the degree-q bubble of cell c is (C+1) + (q-2) C + c; the scalar index
+ *    is ix + m_x (iy + m_y iz) with m = C p + 1; vector fields (elasticity)
+ *    stack whole scalar fields.  `_dev` pointers are device memory of the
+ *    device current at setup, `_host` pointers host memory.
+ *  - The handle owns all device state (matrices, inverses, work vectors,
+ *    captured graphs) and frees it in fcm_destroy.  All work is ordered on
+ *    the CUDA stream given at setup; calls return after that stream has
+ *    finished the call's work unless stated otherwise.
+ *  - No exception or C++ object crosses the ABI.  On failure the status is
+ *    returned and fcm_last_error() describes it (thread-local string, valid
+ *    until the next call on the same thread).  A NULL handle or pointer, an
+ *    invalid enum or size gives FCM_E_INVALID; CUDA failures FCM_E_CUDA.
+ */
+#ifndef FCM_H
+#define FCM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FCM_OK = 0,
+  FCM_E_INVALID = 1,       /* bad argument, NaN input, inconsistent descriptor */
+  FCM_E_OOM = 2,           /* device allocation failed */
+  FCM_E_CUDA = 3,          /* CUDA runtime error (message in fcm_last_error) */
+  FCM_E_UNSUPPORTED = 4,   /* valid request this build does not implement */
+  FCM_E_NOT_CONVERGED = 5, /* maxit reached; x holds the last iterate */
+  FCM_E_BREAKDOWN = 6,     /* CG breakdown: p^T A p <= 0 or non-finite scalar */
+  FCM_E_TIMEOUT = 7        /* a bounded device-side wait expired */
+} fcm_status;
+
+/* Arithmetic of the preconditioner (the outer CG is always FP64). */
+typedef enum {
+  FCM_FP64 = 0,  /* everything in FP64 */
+  FCM_MIXED = 1  /* FP32 V-cycle with FP64 islands inside FP64 flexible CG */
+} fcm_precision;
+
+enum { FCM_GEOM_NONE = 0, FCM_GEOM_BALL = 1, FCM_GEOM_VOIDS = 2, FCM_GEOM_ELLIPSOID = 3 };
+enum { FCM_PDE_POISSON = 0, FCM_PDE_ELASTICITY = 1 };
+enum { FCM_SRC_CONST = 0, FCM_SRC_SIN3 = 1, FCM_SRC_SQUARE_MMS = 2 };
+enum { FCM_DIR_NONE = 0, FCM_DIR_LEVELSET = 1, FCM_DIR_FACES = 2 };
+enum { FCM_G_ZERO = 0, FCM_G_SIN3 = 1, FCM_G_SQUARE_MMS = 2 };
+enum { FCM_SMOOTHER_ELEMENTWISE = 0, FCM_SMOOTHER_PATCHWISE = 1 };
+
+/* Grid: dim in {2,3}; cells per axis (>= 1); box [lo, hi]; degree p in
+ * [1, 8].  overlay_levels > 0 (multi-level hp) is FCM_E_UNSUPPORTED. */
+typedef struct {
+  int dim;
+  int cells[3];
+  double lo[3], hi[3];
+  int p;
+  int overlay_levels;
+  int overlay_p;
+} fcm_grid;
+
+/* Level-set geometry, Omega_phys = {psi <= 0}.  params (host memory, read
+ * during fcm_setup only):
+ *   BALL       cx cy [cz] r                          psi = |x-c| - r
+ *   VOIDS      n_params/4 balls (cx cy cz r)          psi = max_k (r_k - |x-c_k|)
+ *   ELLIPSOID  cx cy cz a0 a1 a2 R00 R01 ... R22      psi = |diag(1/a) R^T (x-c)| - 1
+ * Cell and sub-cell classification: exact nearest/farthest distances for
+ * balls and voids, a 5^d lattice sign test for the ellipsoid. */
+typedef struct {
+  int kind;
+  int n_params;
+  const double* params;
+} fcm_geometry;
+
+/* Physics of Eq. (weakform).  Poisson: kappa scales the stiffness.
+ * Elasticity: isotropic E, nu (3D).  alpha: fictitious factor; beta:
+ * penalty.  source: CONST (f = f0), SIN3 (f = kappa d pi^2 prod sin(pi x_a)),
+ * SQUARE_MMS (f = cos(a x') sin(a y'), x' = x - 1/2, y' = y - 1/2, a = src_a).
+ * dirichlet: LEVELSET (penalty on {psi = 0}) or FACES (bit 2a+s of
+ * dirichlet_faces: face of axis a, lower s = 0 / upper s = 1); g selects
+ * g_D.  traction_face (-1: none) carries the constant traction vector.
+ * quad_depth: space-tree depth on cut cells (0..4). */
+typedef struct {
+  int pde;
+  double kappa, E, nu;
+  double alpha, beta;
+  int source;
+  double f0;
+  double src_a;
+  int dirichlet;
+  int g;
+  unsigned dirichlet_faces;
+  int traction_face;
+  double traction[3];
+  int quad_depth;
+} fcm_physics;
+
+/* Solver options.  omega <= 0 selects the paper's values (Sec. 3.3.2),
+ * clamped per level to 1.75 / lambda_max(M^{-1} A) where that value would
+ * break the stability condition rho(I - omega M^{-1} A) < 1.  n_pre, n_post:
+ * smoothing steps (paper: 5, 5).  coarse_cells: h-coarsening stops once
+ * every axis has at most this many cells (>= 1).  build_mixed: also build
+ * the FP32 data of FCM_MIXED. */
+typedef struct {
+  int smoother;
+  double omega;
+  int n_pre, n_post;
+  int coarse_cells;
+  int build_mixed;
+} fcm_solver_opts;
+
+typedef struct {
+  int iters;                 /* CG iterations (= V-cycles after the first) */
+  double relres_recursive;   /* ||r_k|| / ||b|| of the CG recurrence */
+  double relres_true;        /* ||b - A x|| / ||b|| recomputed at the end */
+  double setup_ms;           /* wall time of fcm_setup */
+  double solve_ms;           /* wall time of this solve (host clock) */
+  long long ndofs;
+} fcm_info;
+
+/* Per-level description (test and benchmark introspection). */
+typedef struct {
+  int cells[3];
+  int p;
+  int is_h_level;            /* 1: Q1 Galerkin level below p = 1 */
+  long long ndofs;
+  int nloc;                  /* DOFs per cell */
+  int n_own_cells;           /* cells with a stored matrix (the rest share s K_ref) */
+  int n_own_blocks;          /* AS blocks with a stored inverse */
+  int n_fp64_blocks;         /* of those, kept in FP64 by FCM_MIXED */
+  double omega;              /* relaxation used on this level (0 on level 0) */
+  double lambda_est;         /* estimate of lambda_max(M^{-1} A) */
+} fcm_level_info;
+
+typedef struct fcm_handle fcm_handle;
+
+/* Discretise, assemble on the device, build the multigrid hierarchy (level
+ * matrices, AS inverses, Galerkin h-levels, coarse Cholesky) and capture the
+ * V-cycle graphs.  `stream` is a cudaStream_t (NULL: legacy default stream).
+ * Setup itself uses a few temporary buffers freed before returning. */
+fcm_status fcm_setup(const fcm_grid* grid, const fcm_geometry* geom,
+                     const fcm_physics* phys, const fcm_solver_opts* opts,
+                     void* stream, fcm_handle** out);
+
+fcm_status fcm_ndofs(const fcm_handle* h, long long* n);
+
+/* Copy the assembled load vector b into b_dev (ndofs doubles). */
+fcm_status fcm_rhs(const fcm_handle* h, double* b_dev);
+
+/* y = A x on the finest level (prec FCM_FP64: FP64 matrices; FCM_MIXED: the
+ * FP32 copies the V-cycle uses, computed in FP32 and widened). */
+fcm_status fcm_apply(fcm_handle* h, const double* x_dev, double* y_dev, int prec);
+
+/* z = V(r): one V-cycle with zero initial guess (Algorithm 1). */
+fcm_status fcm_vcycle(fcm_handle* h, const double* r_dev, double* z_dev, int prec);
+
+/* Level hooks for tests: op 0: y = A_l x; op 1: y = M_l^{-1} x (AS sum of
+ * block inverses, no omega); op 2: y = R_l x (to level l-1); op 3: y = R_l^T x
+ * (from level l-1); op 4: y = A_0^{-1} x (level 0 only).  Level 0 is the
+ * coarsest, fcm_num_levels()-1 the finest.  Vectors have that level's size. */
+fcm_status fcm_num_levels(const fcm_handle* h, int* n);
+fcm_status fcm_level_info_get(const fcm_handle* h, int level, fcm_level_info* info);
+fcm_status fcm_level_op(fcm_handle* h, int level, int op, const double* x_dev,
+                        double* y_dev);
+
+/* Cell classes of the finest grid (0 inside, 1 outside, 2 cut), linear cell
+ * order (x fastest), into a host array of prod(cells) bytes. */
+fcm_status fcm_cell_classes(const fcm_handle* h, signed char* cls_host);
+
+/* V-cycle-preconditioned CG from x = 0 (Sec. 4): stops when the recursive
+ * relative residual falls below rtol and the recomputed true residual
+ * confirms it.  b_dev NULL uses the assembled load.  prec FCM_MIXED runs
+ * the FP32 V-cycle inside flexible (Polak-Ribiere) CG.  Returns
+ * FCM_E_NOT_CONVERGED after maxit iterations (x_dev holds the last
+ * iterate), FCM_E_BREAKDOWN on p^T A p <= 0 or a non-finite scalar. */
+fcm_status fcm_pcg_solve(fcm_handle* h, const double* b_dev, double* x_dev, double rtol,
+                         int maxit, int prec, fcm_info* info);
+
+/* Same solve through host buffers: b_host (NULL: assembled load) is copied
+ * to the device and x is copied back into x_host (ndofs doubles each). */
+fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_host,
+                              double rtol, int maxit, int prec, fcm_info* info);
+
+void fcm_destroy(fcm_handle* h);
+
+const char* fcm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCM_H */

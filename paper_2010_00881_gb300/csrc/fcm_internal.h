@@ -1,0 +1,208 @@
+// Internal declarations of the GB300 FCM multigrid library (not part of the
+// C ABI).  Layout conventions follow include/fcm.h: hierarchical per-axis 1D
+// indices (nodes, then bubbles by degree), x fastest, fields stacked.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fcm.h"
+
+namespace fcm {
+
+constexpr int kMaxP = 8;
+constexpr int kMaxDepth = 4;
+
+// Geometry of one multigrid level as seen by the kernels.
+struct LevelGeom {
+  int dim, nf, p;
+  int C[3];        // cells per axis (1 for unused axes)
+  int m[3];        // 1D indices per axis, C p + 1 (1 for unused axes)
+  long long M;     // scalar DOFs
+  long long N;     // nf * M
+  int nloc_s;      // (p+1)^dim
+  int nloc;        // nf * nloc_s
+  int ncells;
+};
+
+LevelGeom make_geom(int dim, int nf, int p, const int* C);
+
+__host__ __device__ inline int dof1(int C, int c, int j) {
+  return j == 0 ? c : (j == 1 ? c + 1 : (C + 1) + (j - 2) * C + c);
+}
+
+// Global index of local DOF l of cell (cx, cy, cz).
+__host__ __device__ inline long long cell_dof(const LevelGeom& g, int cx, int cy, int cz, int l) {
+  int f = l / g.nloc_s;
+  int s = l - f * g.nloc_s;
+  int P1 = g.p + 1;
+  int jx = s % P1;
+  int jy = g.dim > 1 ? (s / P1) % P1 : 0;
+  int jz = g.dim > 2 ? s / (P1 * P1) : 0;
+  long long ix = dof1(g.C[0], cx, jx);
+  long long iy = g.dim > 1 ? dof1(g.C[1], cy, jy) : 0;
+  long long iz = g.dim > 2 ? dof1(g.C[2], cz, jz) : 0;
+  return (long long)f * g.M + ix + (long long)g.m[0] * (iy + (long long)g.m[1] * iz);
+}
+
+__host__ __device__ inline void cell_coords(const LevelGeom& g, int c, int& cx, int& cy, int& cz) {
+  cx = c % g.C[0];
+  int t = c / g.C[0];
+  cy = t % g.C[1];
+  cz = t / g.C[1];
+}
+
+// ----------------------------------------------------------------------------
+// Problem description copied from the C ABI descriptors (device-friendly).
+struct Problem {
+  int dim, nf, p, pde;
+  int C[3];
+  double lo[3], hi[3], h[3];
+  int geom_kind;
+  int n_gparams;
+  double* d_gparams;            // device copy of geometry parameters
+  double kappa, E, nu, alpha, beta;
+  int source;
+  double f0, src_a;
+  int dirichlet, g;
+  unsigned dir_faces;
+  int traction_face;
+  double traction[3];
+  int quad_depth;
+};
+
+// Cell classes.
+enum { CLS_INSIDE = 0, CLS_OUTSIDE = 1, CLS_CUT = 2 };
+
+// ----------------------------------------------------------------------------
+// Per-level operator and smoother data.
+template <typename T>
+struct CellSet {
+  int n = 0;                 // cells in the set
+  int* cells = nullptr;      // linear cell ids (device)
+  T* mats = nullptr;         // own matrices [n][nloc][nloc] (device)
+};
+
+struct TileList {
+  int ntiles = 0;
+  int4* tiles = nullptr;     // {matrix id, start, count, 0} (device)
+  int* cells = nullptr;      // cells grouped by matrix (device)
+  int ncells = 0;
+};
+
+template <typename T>
+struct SharedSet {
+  TileList tl;
+  T* scale = nullptr;        // per entry of tl.cells
+  T* mats = nullptr;         // [nmats][nloc][nloc]
+  int nmats = 0;
+};
+
+template <typename TV>
+struct OpData {
+  CellSet<TV> own;           // matrices in the vector precision
+  CellSet<double> own64;     // FP64 islands (only used when TV = float)
+  SharedSet<TV> sh;
+};
+
+// Launch a cell operation Y[c] = S_c x_c for every cell in `op`.
+template <typename TV>
+void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y,
+                    cudaStream_t s);
+
+// DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
+enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };
+template <typename TV>
+void launch_gather(const LevelGeom& g, int mode, const TV* Y, const TV* b, TV* out, double w,
+                   cudaStream_t s);
+
+template <typename TV>
+void launch_p_restrict(const LevelGeom& gc, const LevelGeom& gf, const TV* rf, TV* bc,
+                       cudaStream_t s);
+template <typename TV>
+void launch_p_prolong_add(const LevelGeom& gc, const LevelGeom& gf, const TV* xc, TV* xf,
+                          cudaStream_t s);
+template <typename TV>
+void launch_h_restrict(const LevelGeom& gc, const LevelGeom& gf, const TV* rf, TV* bc,
+                       cudaStream_t s);
+template <typename TV>
+void launch_h_prolong_add(const LevelGeom& gc, const LevelGeom& gf, const TV* xc, TV* xf,
+                          cudaStream_t s);
+// x = L^{-T} L^{-1} b with the dense lower Cholesky factor L (n x n, FP64).
+template <typename TV>
+void launch_coarse_solve(int n, const double* L, const TV* b, TV* x, cudaStream_t s);
+
+// CG helpers (FP64).
+constexpr int kDotBlocks = 592;  // fixed: 4 x 148, keeps reductions deterministic
+void launch_dot_partials(const double* a, const double* b, long long n, double* partials,
+                         cudaStream_t s);
+void launch_dot2_partials(const double* a, const double* b, const double* c, long long n,
+                          double* partials, cudaStream_t s);
+void launch_reduce(const double* partials, int count, double* out, cudaStream_t s);
+struct CGScalars {
+  double rz;        // r_k^T z_k
+  double pq;        // p^T A p
+  double alpha, beta;
+  double rr;        // ||r||^2 after the update
+  double rz_new, rzold_new;
+  int flag;         // nonzero: breakdown detected
+};
+void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, long long n,
+                         const double* pq_partials, CGScalars* sc, double* rr_partials,
+                         cudaStream_t s);
+void launch_cg_update_p(double* p, const double* z, long long n, const double* rz_partials,
+                        int flexible, CGScalars* sc, cudaStream_t s);
+void launch_cg_init(const double* r, const double* z, long long n, const double* rz_partials,
+                    double* p, CGScalars* sc, cudaStream_t s);
+void launch_copy_d2f(const double* a, float* b, long long n, cudaStream_t s);
+void launch_copy_f2d(const float* a, double* b, long long n, cudaStream_t s);
+void launch_axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+void launch_scale_copy(const double* x, double* y, double a, long long n, cudaStream_t s);
+void launch_fill_sin(double* v, long long n, cudaStream_t s);
+void launch_d2f_mats(const double* a, float* b, long long n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Setup kernels.
+void launch_gauss_table(int n, double* nodes_weights, cudaStream_t s);
+void launch_classify(const Problem& P, signed char* cls, unsigned char* faces, cudaStream_t s);
+// Element matrices and loads of `ncell` own cells (cells[i] < 0: the
+// reference uncut cell with alpha = 1, no surface and no faces).
+void launch_element_own(const Problem& P, const double* gauss, int ncell, const int* cells,
+                        double* K, double* bvec, int* leaf_scratch, int max_leaves,
+                        cudaStream_t s);
+// Load vectors of uncut cells: B[c][:] = alpha_c int f N.
+void launch_load_uncut(const Problem& P, const double* gauss, int ncell, const int* cells,
+                       const signed char* cls, double* Bcells, cudaStream_t s);
+// Scatter per-own-cell loads into the per-cell load array.
+void launch_scatter_rows(int n, const int* cells, const double* src, int nloc, double* Bcells,
+                         cudaStream_t s);
+// Sub-block extraction: the level-(pc) cell matrix of a level-(pf) matrix.
+void launch_extract_sub(int nmat, int dim, int nf, int pf, int pc, const double* Kf,
+                        double* Kc, cudaStream_t s);
+// Galerkin Q1 coarse cells.
+struct FineCellSource {
+  const int* own_index;      // per fine cell: index into own mats or -1
+  const double* own_mats;
+  const double* shared_scale_by_cell;  // per fine cell scale of K_ref when own_index < 0
+  const double* Kref;
+};
+void launch_galerkin(const LevelGeom& gc, const LevelGeom& gf, FineCellSource src,
+                     double* Kc, cudaStream_t s);
+// AS block assembly for a list of blocks; cell >= 0: real cell, cell < 0:
+// reference signature -(sig+1) on an all-shared grid.
+void launch_block_assemble(const LevelGeom& g, int nblk, const int* blk_cells,
+                           FineCellSource src, double* Ablk, cudaStream_t s);
+// In-place Cholesky inverse of nblk SPD blocks; pivots[2*i] = min, [2*i+1] =
+// max of diag(L)^2; info[i] != 0 on a non-positive pivot.
+void launch_chol_inverse(int nblk, int n, double* A, double* pivots, int* info,
+                         cudaStream_t s);
+void launch_chol_factor(int n, double* A, int* info, cudaStream_t s);
+void launch_dense_assemble(const LevelGeom& g, const double* own_mats, double* A,
+                           cudaStream_t s);
+
+std::string cuda_msg(cudaError_t e);
+
+}  // namespace fcm

@@ -1,0 +1,275 @@
+"""Thin ctypes binding of the C ABI in include/fcm.h.
+
+Argument marshalling only: problem dicts (see ``fcm_inputs``) become the C
+descriptors, torch CUDA tensors are passed by data pointer, and every step
+of the discretisation and the solve runs in libfcm.so.  There is no CPU
+fallback: loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfcm.so")
+
+FCM_OK, FCM_E_INVALID, FCM_E_OOM, FCM_E_CUDA, FCM_E_UNSUPPORTED = 0, 1, 2, 3, 4
+FCM_E_NOT_CONVERGED, FCM_E_BREAKDOWN, FCM_E_TIMEOUT = 5, 6, 7
+FCM_FP64, FCM_MIXED = 0, 1
+GEOM = {"none": 0, "ball": 1, "voids": 2, "ellipsoid": 3}
+PDE = {"poisson": 0, "elasticity": 1}
+SRC = {"const": 0, "sin3": 1, "square_mms": 2}
+DIR = {"none": 0, "levelset": 1, "faces": 2}
+GVAL = {"zero": 0, "sin3": 1, "square_mms": 2}
+OP_APPLY, OP_SMOOTHER, OP_RESTRICT, OP_PROLONG, OP_COARSE = 0, 1, 2, 3, 4
+
+EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_num_levels",
+           "fcm_level_info_get", "fcm_level_op", "fcm_cell_classes", "fcm_pcg_solve",
+           "fcm_pcg_solve_host", "fcm_destroy", "fcm_last_error"]
+
+
+class fcm_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("cells", C.c_int * 3), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("p", C.c_int), ("overlay_levels", C.c_int),
+                ("overlay_p", C.c_int)]
+
+
+class fcm_geometry(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_params", C.c_int), ("params", C.POINTER(C.c_double))]
+
+
+class fcm_physics(C.Structure):
+    _fields_ = [("pde", C.c_int), ("kappa", C.c_double), ("E", C.c_double), ("nu", C.c_double),
+                ("alpha", C.c_double), ("beta", C.c_double), ("source", C.c_int),
+                ("f0", C.c_double), ("src_a", C.c_double), ("dirichlet", C.c_int),
+                ("g", C.c_int), ("dirichlet_faces", C.c_uint), ("traction_face", C.c_int),
+                ("traction", C.c_double * 3), ("quad_depth", C.c_int)]
+
+
+class fcm_solver_opts(C.Structure):
+    _fields_ = [("smoother", C.c_int), ("omega", C.c_double), ("n_pre", C.c_int),
+                ("n_post", C.c_int), ("coarse_cells", C.c_int), ("build_mixed", C.c_int)]
+
+
+class fcm_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("relres_recursive", C.c_double),
+                ("relres_true", C.c_double), ("setup_ms", C.c_double),
+                ("solve_ms", C.c_double), ("ndofs", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fcm_level_info(C.Structure):
+    _fields_ = [("cells", C.c_int * 3), ("p", C.c_int), ("is_h_level", C.c_int),
+                ("ndofs", C.c_longlong), ("nloc", C.c_int), ("n_own_cells", C.c_int),
+                ("n_own_blocks", C.c_int), ("n_fp64_blocks", C.c_int), ("omega", C.c_double),
+                ("lambda_est", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["cells"] = tuple(self.cells)
+        return d
+
+
+_lib = None
+
+
+def load():
+    """Load libfcm.so (built by paper_2010_00881_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2010_00881_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.fcm_setup.argtypes = [C.POINTER(fcm_grid), C.POINTER(fcm_geometry), C.POINTER(fcm_physics),
+                              C.POINTER(fcm_solver_opts), P, C.POINTER(P)]
+    lib.fcm_ndofs.argtypes = [P, C.POINTER(C.c_longlong)]
+    lib.fcm_rhs.argtypes = [P, P]
+    lib.fcm_apply.argtypes = [P, P, P, C.c_int]
+    lib.fcm_vcycle.argtypes = [P, P, P, C.c_int]
+    lib.fcm_num_levels.argtypes = [P, C.POINTER(C.c_int)]
+    lib.fcm_level_info_get.argtypes = [P, C.c_int, C.POINTER(fcm_level_info)]
+    lib.fcm_level_op.argtypes = [P, C.c_int, C.c_int, P, P]
+    lib.fcm_cell_classes.argtypes = [P, P]
+    lib.fcm_pcg_solve.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, C.POINTER(fcm_info)]
+    lib.fcm_pcg_solve_host.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, C.POINTER(fcm_info)]
+    lib.fcm_destroy.argtypes = [P]
+    lib.fcm_destroy.restype = None
+    lib.fcm_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("fcm_destroy", "fcm_last_error"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class FcmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fcm status {status}: {msg}")
+        self.status = status
+
+
+def _check(st, allow=()):
+    if st != FCM_OK and st not in allow:
+        raise FcmError(st, load().fcm_last_error().decode())
+    return st
+
+
+def descriptors(prob: dict, build_mixed: bool = True):
+    """C descriptors for a problem dict of ``fcm_inputs``."""
+    d = prob["dim"]
+    g = fcm_grid()
+    g.dim = d
+    for a in range(3):
+        g.cells[a] = prob["cells"][a] if a < d else 1
+        g.lo[a] = prob["lo"][a] if a < d else 0.0
+        g.hi[a] = prob["hi"][a] if a < d else 0.0
+    g.p = prob["p"]
+    geo = prob["geometry"]
+    kind = geo["kind"]
+    if kind == "ball":
+        params = list(geo["center"]) + [geo["radius"]]
+    elif kind == "voids":
+        params = [v for ball in geo["balls"] for v in ball]
+    elif kind == "ellipsoid":
+        params = list(geo["center"]) + list(geo["axes"]) + [v for row in geo["rot"] for v in row]
+    else:
+        params = []
+    arr = (C.c_double * max(1, len(params)))(*params)
+    gm = fcm_geometry(GEOM[kind], len(params), arr)
+    ph = fcm_physics()
+    ph.pde = PDE[prob["pde"]]
+    ph.kappa = prob["kappa"]
+    ph.E = prob["E"]
+    ph.nu = prob["nu"]
+    ph.alpha = prob["alpha"]
+    ph.beta = prob["beta"]
+    src = prob["source"]
+    ph.source = SRC[src["kind"]]
+    ph.f0 = src.get("f0", 0.0)
+    ph.src_a = src.get("a", 0.0)
+    dr = prob["dirichlet"]
+    ph.dirichlet = DIR[dr["kind"]]
+    ph.g = GVAL[dr.get("g", "zero")]
+    mask = 0
+    for f in dr.get("faces", []):
+        mask |= 1 << f
+    ph.dirichlet_faces = mask
+    tr = prob.get("traction")
+    ph.traction_face = tr["face"] if tr else -1
+    if tr:
+        for a in range(3):
+            ph.traction[a] = tr["t"][a] if a < len(tr["t"]) else 0.0
+    ph.quad_depth = prob["quad_depth"]
+    op = fcm_solver_opts()
+    op.smoother = 0
+    op.omega = prob["omega"] if prob.get("omega") else 0.0
+    op.n_pre = prob["n_pre"]
+    op.n_post = prob["n_post"]
+    op.coarse_cells = prob["coarse_cells"]
+    op.build_mixed = 1 if build_mixed else 0
+    return g, gm, ph, op, arr
+
+
+def _ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One FCM problem set up on the current CUDA device (fcm_setup)."""
+
+    def __init__(self, prob: dict, build_mixed: bool = True, stream=None):
+        import torch
+        lib = load()
+        self.prob = prob
+        g, gm, ph, op, self._keep = descriptors(prob, build_mixed)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        h = C.c_void_p()
+        _check(lib.fcm_setup(C.byref(g), C.byref(gm), C.byref(ph), C.byref(op),
+                             C.c_void_p(s.cuda_stream), C.byref(h)))
+        self.h = h
+        n = C.c_longlong()
+        _check(lib.fcm_ndofs(h, C.byref(n)))
+        self.ndofs = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fcm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, n=None):
+        import torch
+        return torch.empty(self.ndofs if n is None else n, dtype=torch.float64, device="cuda")
+
+    def rhs(self):
+        b = self._empty()
+        _check(load().fcm_rhs(self.h, _ptr(b)))
+        return b
+
+    def apply(self, x, prec=FCM_FP64):
+        y = self._empty()
+        _check(load().fcm_apply(self.h, _ptr(x), _ptr(y), prec))
+        return y
+
+    def vcycle(self, r, prec=FCM_FP64):
+        z = self._empty()
+        _check(load().fcm_vcycle(self.h, _ptr(r), _ptr(z), prec))
+        return z
+
+    def num_levels(self):
+        n = C.c_int()
+        _check(load().fcm_num_levels(self.h, C.byref(n)))
+        return n.value
+
+    def level_info(self, level):
+        inf = fcm_level_info()
+        _check(load().fcm_level_info_get(self.h, level, C.byref(inf)))
+        return inf.as_dict()
+
+    def level_op(self, level, op, x, out_size):
+        y = self._empty(out_size)
+        _check(load().fcm_level_op(self.h, level, op, _ptr(x), _ptr(y)))
+        return y
+
+    def cell_classes(self):
+        n = int(np.prod(self.prob["cells"]))
+        out = np.empty(n, dtype=np.int8)
+        _check(load().fcm_cell_classes(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def pcg(self, b=None, rtol=1e-8, maxit=500, prec=FCM_FP64, x=None, allow_fail=False):
+        x = self._empty() if x is None else x
+        inf = fcm_info()
+        st = load().fcm_pcg_solve(self.h, _ptr(b) if b is not None else None, _ptr(x),
+                                  rtol, maxit, prec, C.byref(inf))
+        _check(st, allow=(FCM_E_NOT_CONVERGED, FCM_E_BREAKDOWN) if allow_fail else ())
+        d = inf.as_dict()
+        d["status"] = st
+        return x, d
+
+    def pcg_host(self, b=None, rtol=1e-8, maxit=500, prec=FCM_FP64, x_host=None):
+        """Solve through host buffers (numpy float64)."""
+        x = np.empty(self.ndofs) if x_host is None else x_host
+        bp = None
+        if b is not None:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            bp = b.ctypes.data_as(C.c_void_p)
+        inf = fcm_info()
+        _check(load().fcm_pcg_solve_host(self.h, bp, x.ctypes.data_as(C.c_void_p), rtol, maxit,
+                                         prec, C.byref(inf)))
+        return x, inf.as_dict()

@@ -1,0 +1,152 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars:
+* integer work (cell classes, level structure): bit-exact;
+* FP64 operator apply A x, load vector: relative error <= 1e-12 (the
+  tolerance stated for FP64 applies);
+* transfers: <= 1e-14 (same weights, different summation order);
+* smoother M^{-1} x, V-cycle: the block inverses come from two different
+  factorisation orders, so they agree to about kappa(A_i) * eps; with
+  alpha = 1e-6..1e-8 the worst blocks have kappa ~ 1e8, hence 1e-7;
+* PCG: iteration counts equal to the oracle's +-1, true relative residual
+  below the tolerance, energy-norm difference of the solutions <= 1e-7.
+Problems span several tiles of 32 cells, odd cell counts (ragged h-levels),
+2D and 3D, cut and body-fitted cells.
+"""
+import numpy as np
+import pytest
+
+import fcm_inputs as fi
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("CUDA not available", allow_module_level=True)
+
+from oracle import multigrid as mg  # noqa: E402
+from oracle.assembly import classify_cells  # noqa: E402
+from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, Solver  # noqa: E402
+from paper_2010_00881_gb300 import fcm as F  # noqa: E402
+
+
+def _ellipsoid_case():
+    prob = fi.batch_instance(3)
+    prob["cells"] = (6, 6, 6)
+    prob["p"] = 2
+    return prob
+
+
+CASES = {
+    "circle16_p2": lambda: fi.poisson2d_circle(),
+    "square8_p4": lambda: fi.square_mms(cells=8, p=4),
+    "sphere5_p3": lambda: fi.poisson3d_sphere(cells=5, p=3),
+    "sphere7_p2": lambda: fi.poisson3d_sphere(cells=7, p=2),
+    "ellipsoid6_p2": _ellipsoid_case,
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    prob = CASES[request.param]()
+    H = mg.Hierarchy(prob)
+    s = Solver(prob)
+    yield request.param, prob, H, s
+    s.close()
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_cell_classes_bit_exact(case):
+    name, prob, H, s = case
+    assert np.array_equal(s.cell_classes(), classify_cells(prob))
+
+
+def test_level_structure(case):
+    name, prob, H, s = case
+    assert s.num_levels() == len(H.levels)
+    for l, lv in enumerate(H.levels):
+        info = s.level_info(l)
+        assert info["ndofs"] == lv.N
+        assert info["p"] == lv.p
+        assert tuple(info["cells"][: prob["dim"]]) == lv.cells
+        if l > 0:
+            assert abs(info["omega"] - lv.omega) <= 1e-6 * lv.omega, (l, info["omega"], lv.omega)
+
+
+def test_rhs(case):
+    name, prob, H, s = case
+    b = s.rhs().cpu().numpy()
+    assert np.abs(b - H.b).max() <= 1e-12 * np.abs(H.b).max()
+
+
+def test_apply_fp64(case):
+    name, prob, H, s = case
+    x = fi.random_vector(s.ndofs, seed=1)
+    y = s.apply(_t(x)).cpu().numpy()
+    assert _rel(y, H.A @ x) <= 1e-12
+
+
+def test_apply_fp32(case):
+    name, prob, H, s = case
+    x = fi.random_vector(s.ndofs, seed=1)
+    y = s.apply(_t(x), prec=FCM_MIXED).cpu().numpy()
+    assert _rel(y, H.A @ x) <= 1e-5
+
+
+def test_level_operators(case):
+    name, prob, H, s = case
+    for l, lv in enumerate(H.levels):
+        x = fi.random_vector(lv.N, seed=10 + l)
+        y = s.level_op(l, F.OP_APPLY, _t(x), lv.N).cpu().numpy()
+        assert _rel(y, lv.A @ x) <= 1e-12, ("A", l)
+        if l == 0:
+            z = s.level_op(0, F.OP_COARSE, _t(x), lv.N).cpu().numpy()
+            import scipy.linalg as sla
+            ref = sla.cho_solve(lv.chol, x)
+            assert _rel(z, ref) <= 1e-7, ("coarse", _rel(z, ref))
+            continue
+        z = s.level_op(l, F.OP_SMOOTHER, _t(x), lv.N).cpu().numpy()
+        assert _rel(z, lv.smoother(x)) <= 1e-7, ("M", l, _rel(z, lv.smoother(x)))
+        Nc = H.levels[l - 1].N
+        rc = s.level_op(l, F.OP_RESTRICT, _t(x), Nc).cpu().numpy()
+        assert _rel(rc, H.restrict(l, x)) <= 1e-14, ("R", l)
+        xc = fi.random_vector(Nc, seed=20 + l)
+        pf = s.level_op(l, F.OP_PROLONG, _t(xc), lv.N).cpu().numpy()
+        assert _rel(pf, H.prolong_add(l, np.zeros(lv.N), xc)) <= 1e-14, ("P", l)
+
+
+def test_vcycle_fp64(case):
+    name, prob, H, s = case
+    r = fi.random_vector(s.ndofs, seed=2)
+    z = s.vcycle(_t(r)).cpu().numpy()
+    assert _rel(z, H.vcycle(r)) <= 1e-7
+
+
+def test_pcg_fp64_and_mixed(case):
+    name, prob, H, s = case
+    xo, ko, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=1e-8)
+    A = H.A
+    en = np.sqrt(xo @ (A @ xo))
+    for prec in (FCM_FP64, FCM_MIXED):
+        x, info = s.pcg(rtol=1e-8, prec=prec)
+        x = x.cpu().numpy()
+        assert info["relres_true"] <= 1e-8
+        assert np.linalg.norm(H.b - A @ x) / np.linalg.norm(H.b) <= 1.01e-8
+        assert abs(info["iters"] - ko) <= 1, (prec, info["iters"], ko)
+        e = x - xo
+        assert np.sqrt(e @ (A @ e)) / en <= 1e-7
+
+
+def test_host_buffer_solve_matches_device_solve(case):
+    name, prob, H, s = case
+    xd, infd = s.pcg(rtol=1e-8)
+    xh, infh = s.pcg_host(rtol=1e-8)
+    assert infh["iters"] == infd["iters"]
+    assert np.array_equal(xh, xd.cpu().numpy())
