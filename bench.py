@@ -1,0 +1,304 @@
+"""Benchmark: DOFs solved per second to relative residual 1e-8 by
+V-cycle-preconditioned CG, mixed precision (FP32 V-cycle with FP64 islands
+inside FP64 flexible CG) against the plain FP64 GPU path, on one GB300.
+
+Workload: 3D Poisson on the unit cube embedding a sphere r = 0.45, 32^3
+cells, integrated Legendre p = 3 (912,673 DOFs), alpha = 1e-8, manufactured
+solution sin(pi x) sin(pi y) sin(pi z) (synthetic, built on the device).
+One step = one complete solve from x = 0 to ||b - A x|| / ||b|| <= 1e-8.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fcm|reference]
+
+N > 1 (torchrun): every rank solves its own replica (the path has no
+exchange step), value = DOFs solved by all ranks / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload family.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import fcm_inputs as fi  # noqa: E402
+
+METRIC = "DOFs solved/s to rel. residual 1e-8: mixed-prec vs FP64 V-cycle PCG, 1 GB300"
+RTOL = 1e-8
+MAXIT = 500
+WORKLOAD = "poisson3d_sphere_32^3_p3"
+
+
+def workload():
+    return fi.poisson3d_sphere(cells=32, p=3)
+
+
+def oracle_sample():
+    """Bounded CPU sample of the same family: 8^3 cells, p = 3."""
+    return fi.poisson3d_sphere(cells=8, p=3)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fcm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_reference(args, rank):
+    """The oracle as it stands, on the host cores, one bounded sample per step."""
+    import numpy as np  # noqa: F401
+    from oracle import multigrid as mg
+
+    if rank != 0:
+        return
+    prob = oracle_sample()
+    t0 = time.perf_counter()
+    H = mg.Hierarchy(prob)
+    setup_s = time.perf_counter() - t0
+    N = H.A.shape[0]
+    for _ in range(args.warmup):
+        mg.pcg(H.A, H.b, H.vcycle, rtol=RTOL, maxit=MAXIT)
+    times, iters = [], []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        _, k, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=RTOL, maxit=MAXIT)
+        times.append(time.perf_counter() - t)
+        iters.append(k)
+    tot = sum(times)
+    value = N * args.steps / tot
+    sample = (f"oracle V-cycle PCG solve (setup excluded, {setup_s:.1f} s) of the same "
+              f"workload family at 8^3 cells, p = 3 ({N} DOFs), {iters[0]} iterations")
+    out = {"metric": METRIC, "value": value, "unit": "DOFs/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "sample": "poisson3d_sphere_8^3_p3", "rtol": RTOL},
+           "cpu_baseline": {"value": value, "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "DOFs/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def cpu_baseline(seconds_cap=30.0):
+    """Oracle timed on one bounded sample (rank 0, N = 1)."""
+    from oracle import multigrid as mg
+    prob = oracle_sample()
+    t0 = time.perf_counter()
+    H = mg.Hierarchy(prob)
+    setup_s = time.perf_counter() - t0
+    t = time.perf_counter()
+    _, k, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=RTOL, maxit=MAXIT)
+    dt = time.perf_counter() - t
+    N = H.A.shape[0]
+    return {"value": N / dt, "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one oracle solve of the same workload family at 8^3 cells, p = 3 "
+                       f"({N} DOFs, {k} iterations, {dt:.1f} s; setup {setup_s:.1f} s excluded)")}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, Solver
+    from paper_2010_00881_gb300 import build as fbuild
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fbuild.build()
+    prob = workload()
+    s = Solver(prob, build_mixed=True)
+    N = s.ndofs
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(prec, steps, tag):
+        ms, infos = [], []
+        for _ in range(steps):
+            flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push(tag)
+            e0.record(stream)
+            x, info = s.pcg(rtol=RTOL, maxit=MAXIT, prec=prec)
+            e1.record(stream)
+            torch.cuda.nvtx.range_pop()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+        return ms, infos
+
+    for _ in range(args.warmup):
+        s.pcg(rtol=RTOL, maxit=MAXIT, prec=FCM_MIXED)
+        s.pcg(rtol=RTOL, maxit=MAXIT, prec=FCM_FP64)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ms_mixed, inf_mixed = timed(FCM_MIXED, args.steps, "timed_mixed")
+    barrier()
+    ms_fp64, inf_fp64 = timed(FCM_FP64, args.steps, "timed_fp64")
+    barrier()
+    # end to end through the host-buffer entry point (H2D of b, D2H of x)
+    import numpy as np
+    b_host = s.rhs().cpu().numpy()
+    x_host = np.empty(N)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s.pcg_host(b=b_host, rtol=RTOL, maxit=MAXIT, prec=FCM_MIXED, x_host=x_host)
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+    barrier()
+    clk = clocks.stop()
+
+    tot = sum(ms_mixed)
+    tot64 = sum(ms_fp64)
+    tot_e2e = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([tot, tot64, tot_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot, tot64, tot_e2e = t.tolist()
+    value = world * N * args.steps / (tot / 1e3)
+    value64 = world * N * args.steps / (tot64 / 1e3)
+    value_e2e = world * N * args.steps / (tot_e2e / 1e3)
+
+    # roofline of the dominant kernel: the finest-level smoother cell kernel
+    # of the mixed path, replayed with CUDA events on its own stream
+    peaks, peak_src = load_peaks()
+    L = s.num_levels() - 1
+    roof = {}
+    prof = {}
+    for which, name in ((0, "operator"), (1, "smoother"), (2, "gather")):
+        for prec, pn in ((FCM_MIXED, "mixed"), (FCM_FP64, "fp64")):
+            t_ms = s.profile_op(L, which, prec=prec, reps=20)
+            byt = s.op_bytes(L, which, prec=prec)
+            prof[f"{name}_{pn}"] = {"ms": t_ms, "bytes": byt, "GBps": byt / (t_ms * 1e-3) / 1e9}
+    dom = prof["smoother_mixed"]
+    achieved = dom["GBps"]
+    peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "cell_op_kernel<float> (finest-level additive Schwarz smoother)",
+            "peak_source": peak_src}
+
+    if rank == 0:
+        levels = [s.level_info(l) for l in range(s.num_levels())]
+        out = {
+            "metric": METRIC, "value": value, "unit": "DOFs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "ndofs": N, "rtol": RTOL,
+                       "precision": "mixed: FP32 V-cycle, FP64 cut-cell matrices and "
+                                    "ill-conditioned block inverses, FP64 flexible CG",
+                       "l2": "256 MB buffer written between timed solves",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "iterations": inf_mixed[-1]["iters"],
+            "relres_true": inf_mixed[-1]["relres_true"],
+            "fp64": {"value": value64, "unit": "DOFs/s", "ms_per_step": tot64 / args.steps,
+                     "iterations": inf_fp64[-1]["iters"],
+                     "relres_true": inf_fp64[-1]["relres_true"]},
+            "speedup_mixed_vs_fp64": value / value64,
+            "vcycles_per_s": (inf_mixed[-1]["iters"] + 1) * args.steps / (tot / 1e3),
+            "setup_ms": inf_mixed[-1]["setup_ms"],
+            "e2e": {"value": value_e2e, "unit": "DOFs/s", "h2d_bytes_per_step": 8 * N,
+                    "d2h_bytes_per_step": 8 * N},
+            "gpu_launches": int(sum(i["kernel_launches"] for i in inf_mixed)),
+            "roofline": roof,
+            "kernels": prof,
+            "levels": [{"cells": lv["cells"][0], "p": lv["p"], "h": lv["is_h_level"],
+                        "ndofs": lv["ndofs"], "own_cells": lv["n_own_cells"],
+                        "own_blocks": lv["n_own_blocks"], "fp64_blocks": lv["n_fp64_blocks"],
+                        "omega": round(lv["omega"], 5)} for lv in levels],
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

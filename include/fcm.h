@@ -133,6 +133,7 @@ typedef struct {
   double setup_ms;           /* wall time of fcm_setup */
   double solve_ms;           /* wall time of this solve (host clock) */
   long long ndofs;
+  long long kernel_launches; /* device kernels this solve launched (graph nodes included) */
 } fcm_info;
 
 /* Per-level description (test and benchmark introspection). */
@@ -197,6 +198,21 @@ fcm_status fcm_pcg_solve(fcm_handle* h, const double* b_dev, double* x_dev, doub
  * to the device and x is copied back into x_host (ndofs doubles each). */
 fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_host,
                               double rtol, int maxit, int prec, fcm_info* info);
+
+/* Benchmark hook: replay one kernel of level `level` `reps` times on the
+ * handle's stream and return its mean duration from CUDA events (ms).
+ * which 0: operator cell kernel (y_c = K_c x_c over all cells), 1: smoother
+ * cell kernel (A_i^{-1} over all blocks), 2: the DOF gather that follows
+ * them.  prec selects the FP64 or the FCM_MIXED data.  Inputs are the level's
+ * work vectors (their current contents); results are discarded. */
+fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int reps,
+                          double* avg_ms);
+
+/* Bytes the level kernel `which` (as in fcm_profile_op) must move at least
+ * once per launch: stored cell matrices or block inverses, one read of
+ * every input coefficient per cell and one write of every per-cell result. */
+fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec,
+                        long long* bytes);
 
 void fcm_destroy(fcm_handle* h);
 

@@ -106,6 +106,8 @@ struct fcm_handle {
   double* d_scalar = nullptr;      // reductions for the host
   double* h_scalar = nullptr;      // pinned
   cudaGraphExec_t g_vc64 = nullptr, g_vc32 = nullptr;
+  long long vc_nodes64 = 0, vc_nodes32 = 0;  // kernel nodes per V-cycle graph
+  long long launches = 0;                    // kernels launched by the current solve
 
   template <typename T>
   T* alloc(size_t count) {
@@ -200,6 +202,7 @@ void check_status(Handle* h, const int* d_info, int n, const char* what) {
 }
 
 double host_dot(Handle* h, const double* a, const double* b, long long n) {
+  h->launches += 2;
   launch_dot_partials(a, b, n, h->part, h->s);
   launch_reduce(h->part, kDotBlocks, h->d_scalar, h->s);
   CKL();
@@ -209,6 +212,7 @@ double host_dot(Handle* h, const double* a, const double* b, long long n) {
 }
 
 void apply_A64(Handle* h, Level& L, const double* x, double* y, int mode, const double* b) {
+  h->launches += 2;
   launch_cell_op<double>(L.g, L.A64, x, L.Y, h->s);
   launch_gather<double>(L.g, mode, L.Y, b, y, 1.0, h->s);
   CKL();
@@ -292,7 +296,7 @@ void record_vcycle(Handle* h, int l) {
 }
 
 template <typename TV>
-cudaGraphExec_t capture_vcycle(Handle* h) {
+cudaGraphExec_t capture_vcycle(Handle* h, long long* nodes) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
   try {
@@ -302,6 +306,17 @@ cudaGraphExec_t capture_vcycle(Handle* h) {
     throw;
   }
   CK(cudaStreamEndCapture(h->s, &g));
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nv(nn);
+  if (nn) CK(cudaGraphGetNodes(g, nv.data(), &nn));
+  long long kn = 0;
+  for (auto nd : nv) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++kn;
+  }
+  *nodes = kn;
   cudaGraphExec_t ex;
   CK(cudaGraphInstantiate(&ex, g, 0));
   CK(cudaGraphDestroy(g));
@@ -764,8 +779,8 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     estimate_omega(h, L, omega_paper);
   }
   CK(cudaStreamSynchronize(h->s));
-  h->g_vc64 = capture_vcycle<double>(h);
-  if (h->mixed) h->g_vc32 = capture_vcycle<float>(h);
+  h->g_vc64 = capture_vcycle<double>(h, &h->vc_nodes64);
+  if (h->mixed) h->g_vc32 = capture_vcycle<float>(h, &h->vc_nodes32);
   CK(cudaStreamSynchronize(h->s));
 }
 
@@ -779,9 +794,11 @@ void run_vcycle(Handle* h, const double* r, double* z, int prec) {
     CK(cudaGraphLaunch(h->g_vc32, h->s));
     launch_copy_f2d(T.x32, z, T.g.N, h->s);
     CKL();
+    h->launches += 2 + h->vc_nodes32;
   } else {
     if (r != T.b) CK(cudaMemcpyAsync(T.b, r, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     CK(cudaGraphLaunch(h->g_vc64, h->s));
+    h->launches += h->vc_nodes64;
     if (z != T.x) CK(cudaMemcpyAsync(z, T.x, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   }
 }
@@ -789,6 +806,7 @@ void run_vcycle(Handle* h, const double* r, double* z, int prec) {
 fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int maxit, int prec,
                     fcm_info* info) {
   double t0 = now_ms();
+  h->launches = 0;
   Level& T = h->levels.back();
   const long long N = T.g.N;
   const double* b = b_in ? b_in : h->b;
@@ -818,6 +836,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   launch_dot_partials(r, z, N, h->part, h->s);
   launch_cg_init(r, z, N, h->part, p, h->sc, h->s);
   CKL();
+  h->launches += 2;
   int k = 0;
   double rel = 1.0;
   fcm_status st = FCM_E_NOT_CONVERGED;
@@ -828,6 +847,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
     launch_cg_update_xr(x, r, p, q, N, h->part, h->sc, h->part + kDotBlocks, h->s);
     launch_reduce(h->part + kDotBlocks, kDotBlocks, h->d_scalar, h->s);
     CKL();
+    h->launches += 3;
     CK(cudaMemcpyAsync(h->h_scalar, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
     double rr = h->h_scalar[0];
@@ -856,6 +876,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
       launch_dot_partials(r, z, N, h->part, h->s);
     launch_cg_update_p(p, z, N, h->part, flexible ? 1 : 0, h->sc, h->s);
     CKL();
+    h->launches += 3;
   }
   CGScalars sc;
   CK(cudaMemcpyAsync(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, h->s));
@@ -866,6 +887,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
     inf.relres_true = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / nb;
   }
   inf.iters = k;
+  inf.kernel_launches = h->launches;
   inf.relres_recursive = rel;
   inf.solve_ms = now_ms() - t0;
   if (info) *info = inf;
@@ -1091,6 +1113,73 @@ fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_hos
     cs.finish();
     return st;
   });
+}
+
+fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int reps,
+                          double* avg_ms) {
+  if (!h || !avg_ms || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 2 ||
+      reps < 1 || (prec != FCM_FP64 && prec != FCM_MIXED) || (prec == FCM_MIXED && !h->mixed)) {
+    g_last_error = "invalid argument";
+    return FCM_E_INVALID;
+  }
+  return guarded([&]() {
+    CallScope cs(h);
+    Level& L = h->levels[level];
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto once = [&]() {
+      if (prec == FCM_FP64) {
+        if (which == 0) launch_cell_op<double>(L.g, L.A64, L.x, L.Y, h->s);
+        else if (which == 1) launch_cell_op<double>(L.g, L.M64, L.r, L.Y, h->s);
+        else launch_gather<double>(L.g, GATHER_RESID, L.Y, L.b, L.r, 1.0, h->s);
+      } else {
+        if (which == 0) launch_cell_op<float>(L.g, L.A32, L.x32, L.Y32, h->s);
+        else if (which == 1) launch_cell_op<float>(L.g, L.M32, L.r32, L.Y32, h->s);
+        else launch_gather<float>(L.g, GATHER_RESID, L.Y32, L.b32, L.r32, 1.0, h->s);
+      }
+    };
+    once();
+    CK(cudaEventRecord(e0, h->s));
+    for (int i = 0; i < reps; ++i) once();
+    CK(cudaEventRecord(e1, h->s));
+    CKL();
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *avg_ms = ms / reps;
+    cs.finish();
+    return FCM_OK;
+  });
+}
+
+fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, long long* bytes) {
+  if (!h || !bytes || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 2 ||
+      (prec != FCM_FP64 && prec != FCM_MIXED)) {
+    g_last_error = "invalid argument";
+    return FCM_E_INVALID;
+  }
+  const Level& L = h->levels[level];
+  const long long n = L.g.nloc, nc = L.g.ncells;
+  const long long sv = prec == FCM_FP64 ? 8 : 4;
+  long long b = 0;
+  if (which == 2) {
+    b = nc * n * sv + 2 * L.g.N * sv + L.g.N * sv;  // Y, b, r(out)
+  } else {
+    const OpData<double>& d64 = which == 0 ? L.A64 : L.M64;
+    const OpData<float>& d32 = which == 0 ? L.A32 : L.M32;
+    long long mats;
+    if (prec == FCM_FP64)
+      mats = (long long)d64.own.n * n * n * 8 + (long long)d64.sh.nmats * n * n * 8;
+    else
+      mats = (long long)d32.own.n * n * n * 4 + (long long)d32.own64.n * n * n * 8 +
+             (long long)d32.sh.nmats * n * n * 4;
+    b = mats + 2 * nc * n * sv;  // gathered coefficients + per-cell results
+  }
+  *bytes = b;
+  return FCM_OK;
 }
 
 void fcm_destroy(fcm_handle* h) { delete h; }

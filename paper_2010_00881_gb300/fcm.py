@@ -27,7 +27,8 @@ OP_APPLY, OP_SMOOTHER, OP_RESTRICT, OP_PROLONG, OP_COARSE = 0, 1, 2, 3, 4
 
 EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_num_levels",
            "fcm_level_info_get", "fcm_level_op", "fcm_cell_classes", "fcm_pcg_solve",
-           "fcm_pcg_solve_host", "fcm_destroy", "fcm_last_error"]
+           "fcm_pcg_solve_host", "fcm_profile_op", "fcm_op_bytes", "fcm_destroy",
+           "fcm_last_error"]
 
 
 class fcm_grid(C.Structure):
@@ -56,7 +57,8 @@ class fcm_solver_opts(C.Structure):
 class fcm_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("relres_recursive", C.c_double),
                 ("relres_true", C.c_double), ("setup_ms", C.c_double),
-                ("solve_ms", C.c_double), ("ndofs", C.c_longlong)]
+                ("solve_ms", C.c_double), ("ndofs", C.c_longlong),
+                ("kernel_launches", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -98,6 +100,8 @@ def load():
     lib.fcm_cell_classes.argtypes = [P, P]
     lib.fcm_pcg_solve.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, C.POINTER(fcm_info)]
     lib.fcm_pcg_solve_host.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, C.POINTER(fcm_info)]
+    lib.fcm_profile_op.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
+    lib.fcm_op_bytes.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
     lib.fcm_destroy.argtypes = [P]
     lib.fcm_destroy.restype = None
     lib.fcm_last_error.restype = C.c_char_p
@@ -261,6 +265,16 @@ class Solver:
         d = inf.as_dict()
         d["status"] = st
         return x, d
+
+    def profile_op(self, level, which, prec=FCM_FP64, reps=20):
+        ms = C.c_double()
+        _check(load().fcm_profile_op(self.h, level, which, prec, reps, C.byref(ms)))
+        return ms.value
+
+    def op_bytes(self, level, which, prec=FCM_FP64):
+        b = C.c_longlong()
+        _check(load().fcm_op_bytes(self.h, level, which, prec, C.byref(b)))
+        return b.value
 
     def pcg_host(self, b=None, rtol=1e-8, maxit=500, prec=FCM_FP64, x_host=None):
         """Solve through host buffers (numpy float64)."""
