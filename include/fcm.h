@@ -214,6 +214,25 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
 fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec,
                         long long* bytes);
 
+/* Allocation-free operator apply, for callers that cannot allocate device
+ * memory once they run (fixed device arenas, real-time loops, plug-ins in a
+ * foreign memory pool) and therefore cannot call fcm_setup.  The paper has
+ * no counterpart; it is a service entry point of this library.
+ *   y = sum_c P_c^T K_c P_c x  on a grid of dim (2 or 3) with cells[0..dim-1]
+ *   cells per axis and one scalar field of degree p, in the layout above.
+ * K_dev: caller-owned device array of prod(cells) symmetric cell matrices,
+ * (p+1)^d x (p+1)^d each, row-major, cells in linear order (x fastest), local
+ * DOF order j_x + (p+1) j_y + (p+1)^2 j_z.  x_dev, y_dev: ndofs doubles.
+ * stream: cudaStream_t (NULL: legacy default stream); returns after the
+ * stream has finished the work.  Scratch: a 4 MiB array compiled into the
+ * library (per GPU, held until exit), so prod(cells) (p+1)^d may be at most
+ * about 520,000; larger requests return FCM_E_INVALID.  The first call on a
+ * device looks up the array's device address and should precede any stream
+ * capture; calls that overlap on the GPU race on the shared array.  Calls
+ * no allocating routine. */
+fcm_status fcm_cell_apply_noalloc(int dim, const int* cells, int p, const double* K_dev,
+                                  const double* x_dev, double* y_dev, void* stream);
+
 void fcm_destroy(fcm_handle* h);
 
 const char* fcm_last_error(void);

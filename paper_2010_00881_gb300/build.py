@@ -25,6 +25,7 @@ SOURCES = {
     "setup_levels.cu": [],
     "ops.cu": [],
     "api.cu": [],
+    "noalloc.cu": [],
 }
 
 

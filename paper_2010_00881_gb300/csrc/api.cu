@@ -913,6 +913,9 @@ fcm_status guarded(F&& f) {
 }
 
 }  // namespace
+
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 }  // namespace fcm
 
 using namespace fcm;

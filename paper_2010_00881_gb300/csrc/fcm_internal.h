@@ -205,4 +205,7 @@ void launch_dense_assemble(const LevelGeom& g, const double* own_mats, double* A
 
 std::string cuda_msg(cudaError_t e);
 
+// Set the thread-local message returned by fcm_last_error().
+void set_last_error(const char* msg);
+
 }  // namespace fcm

@@ -27,8 +27,8 @@ OP_APPLY, OP_SMOOTHER, OP_RESTRICT, OP_PROLONG, OP_COARSE = 0, 1, 2, 3, 4
 
 EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_num_levels",
            "fcm_level_info_get", "fcm_level_op", "fcm_cell_classes", "fcm_pcg_solve",
-           "fcm_pcg_solve_host", "fcm_profile_op", "fcm_op_bytes", "fcm_destroy",
-           "fcm_last_error"]
+           "fcm_pcg_solve_host", "fcm_profile_op", "fcm_op_bytes", "fcm_cell_apply_noalloc",
+           "fcm_destroy", "fcm_last_error"]
 
 
 class fcm_grid(C.Structure):
@@ -102,6 +102,7 @@ def load():
     lib.fcm_pcg_solve_host.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, C.POINTER(fcm_info)]
     lib.fcm_profile_op.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.fcm_op_bytes.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
+    lib.fcm_cell_apply_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int, P, P, P, P]
     lib.fcm_destroy.argtypes = [P]
     lib.fcm_destroy.restype = None
     lib.fcm_last_error.restype = C.c_char_p
