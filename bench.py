@@ -160,6 +160,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="setup, W warm-up and K timed mixed solves only (for profilers)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -206,6 +208,16 @@ def main():
             infos.append(info)
         return ms, infos
 
+    if args.profile_run:
+        for _ in range(args.warmup):
+            s.pcg(rtol=RTOL, maxit=MAXIT, prec=FCM_MIXED)
+        barrier()
+        ms, infos = timed(FCM_MIXED, args.steps, "timed_mixed")
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": sum(ms) / len(ms),
+                              "iterations": infos[-1]["iters"]}))
+        s.close()
+        return
     for _ in range(args.warmup):
         s.pcg(rtol=RTOL, maxit=MAXIT, prec=FCM_MIXED)
         s.pcg(rtol=RTOL, maxit=MAXIT, prec=FCM_FP64)

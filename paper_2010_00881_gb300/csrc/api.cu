@@ -67,6 +67,7 @@ struct Level {
   int* d_own_index = nullptr;       // per cell: own matrix index or -1
   double* d_scale_cell = nullptr;   // per cell: scale of K_ref for shared cells
   double* Kref = nullptr;           // shared operator matrix (nloc x nloc)
+  double* Kown_c = nullptr;         // canonical n x n own cell matrices (setup only)
   std::vector<int> h_own_index;
   std::vector<double> h_scale_cell;
   // work vectors
@@ -77,7 +78,7 @@ struct Level {
   FineCellSource source() const {
     FineCellSource s;
     s.own_index = d_own_index;
-    s.own_mats = A64.own.mats;
+    s.own_mats = Kown_c;
     s.shared_scale_by_cell = d_scale_cell;
     s.Kref = Kref;
     return s;
@@ -430,13 +431,22 @@ void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, doub
                     double* Kref, const std::vector<int>& sh_cells,
                     const std::vector<double>& sh_scale) {
   const int n = L.g.nloc;
-  L.A64.own.n = (int)own_cells.size();
+  const int ld = padded_ld(n);
+  const int nown = (int)own_cells.size();
+  L.Kown_c = own_mats;
+  L.A64.ld = ld;
+  L.A64.own.n = nown;
   L.A64.own.cells = own_cells.empty() ? nullptr : h->upload(own_cells);
-  L.A64.own.mats = own_mats;
+  if (nown) {
+    double* m = h->alloc<double>((size_t)nown * n * ld);
+    launch_repack(nown, n, ld, own_mats, nullptr, 0, m, h->s);
+    CKL();
+    L.A64.own.mats = m;
+  }
   L.Kref = Kref;
   std::vector<int> mat0(sh_cells.size(), 0);
   build_shared<double>(h, L.A64.sh, mat0, sh_cells, sh_scale, Kref, Kref ? 1 : 0);
-  L.n_own_cells = (int)own_cells.size();
+  L.n_own_cells = nown;
   L.h_own_index.assign(L.g.ncells, -1);
   L.h_scale_cell.assign(L.g.ncells, 0.0);
   for (size_t i = 0; i < own_cells.size(); ++i) L.h_own_index[own_cells[i]] = (int)i;
@@ -445,13 +455,19 @@ void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, doub
   L.d_scale_cell = h->upload(L.h_scale_cell);
   if (h->mixed) {
     // Cell matrices with their own entries (cut cells, penalty faces, all
-    // Galerkin h-level cells) stay FP64 in the FP32 V-cycle: rounding their
-    // entries to FP32 loses the alpha-weighted part and makes the residual
-    // inconsistent with the FP64 block inverses of the smoother.  Products
-    // are formed in FP64 from FP32 inputs and rounded on output.
-    L.A32.own64.n = L.A64.own.n;
-    L.A32.own64.cells = L.A64.own.cells;
-    L.A32.own64.mats = own_mats;
+    // Galerkin h-level cells) keep FP64 accuracy in the FP32 V-cycle (df32
+    // pairs with compensated accumulation): rounding their entries to FP32
+    // loses the alpha-weighted part and makes the residual inconsistent with
+    // the block inverses of the smoother.
+    L.A32.ld = ld;
+    L.A32.own_x.n = nown;
+    L.A32.own_x.cells = L.A64.own.cells;
+    if (nown) {
+      float2* m = h->alloc<float2>((size_t)nown * n * ld);
+      launch_repack(nown, n, ld, own_mats, nullptr, 2, m, h->s);
+      CKL();
+      L.A32.own_x.mats = m;
+    }
     float* K32 = Kref ? to_f32(h, Kref, (size_t)n * n) : nullptr;
     L.A32.sh.tl = L.A64.sh.tl;
     std::vector<float> sc32(sh_scale.begin(), sh_scale.end());
@@ -461,9 +477,12 @@ void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, doub
   }
 }
 
-// Threshold on the pivot ratio of a block's Cholesky factorisation above
-// which FCM_MIXED keeps the block inverse in FP64.
-constexpr double kFp64PivotRatio = 1e4;
+// FCM_MIXED keeps a block inverse at FP64 accuracy (df32) when some row of the
+// block is close to linear dependence on the rows before it:
+// max_k A_kk / (Cholesky pivot)_k above this threshold.  The ratio is
+// invariant under diagonal scaling, unlike the plain pivot ratio, which also
+// grows with the hierarchical basis's mode scaling.
+constexpr double kDfDependence = 1e3;
 
 void build_smoother(Handle* h, Level& L) {
   const LevelGeom& g = L.g;
@@ -536,8 +555,12 @@ void build_smoother(Handle* h, Level& L) {
     CK(cudaStreamSynchronize(h->s));
     L.M64.own.n = nown;
     L.M64.own.cells = d_cells;
-    L.M64.own.mats = inv;
+    double* m = h->alloc<double>((size_t)nown * n * padded_ld(n));
+    launch_repack(nown, n, padded_ld(n), inv, nullptr, 0, m, h->s);
+    CKL();
+    L.M64.own.mats = m;
   }
+  L.M64.ld = padded_ld(n);
   L.n_own_blocks = nown;
   // shared signatures
   std::vector<int> order(shared.size());
@@ -570,34 +593,36 @@ void build_smoother(Handle* h, Level& L) {
   build_shared<double>(h, L.M64.sh, mat_of, cells, scale, sinv, (int)sigs.size());
   // mixed precision copies
   if (h->mixed) {
-    std::vector<int> c32, c64, i32, i64;
+    const int ld = padded_ld(n);
+    std::vector<int> c32, cx, i32, ix;
     for (int i = 0; i < nown; ++i) {
-      double ratio = piv[2 * i + 1] / piv[2 * i];
-      if (ratio > kFp64PivotRatio) {
-        c64.push_back(own_blocks[i]);
-        i64.push_back(i);
+      if (piv[2 * i + 1] > kDfDependence) {
+        cx.push_back(own_blocks[i]);
+        ix.push_back(i);
       } else {
         c32.push_back(own_blocks[i]);
         i32.push_back(i);
       }
     }
-    L.n_fp64_blocks = (int)c64.size();
-    auto gather_mats = [&](const std::vector<int>& idx) -> double* {
-      if (idx.empty()) return nullptr;
-      double* d = h->alloc<double>(idx.size() * (size_t)n * n);
-      for (size_t k = 0; k < idx.size(); ++k)
-        CK(cudaMemcpyAsync(d + k * (size_t)n * n, inv + (size_t)idx[k] * n * n,
-                           (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-      return d;
-    };
-    double* m32src = gather_mats(i32);
-    double* m64 = gather_mats(i64);
+    L.n_fp64_blocks = (int)cx.size();
+    L.M32.ld = ld;
     L.M32.own.n = (int)c32.size();
     L.M32.own.cells = c32.empty() ? nullptr : h->upload(c32);
-    L.M32.own.mats = m32src ? to_f32(h, m32src, c32.size() * (size_t)n * n) : nullptr;
-    L.M32.own64.n = (int)c64.size();
-    L.M32.own64.cells = c64.empty() ? nullptr : h->upload(c64);
-    L.M32.own64.mats = m64;
+    if (!c32.empty()) {
+      int* sel = h->upload(i32);
+      float* m = h->alloc<float>(c32.size() * (size_t)n * ld);
+      launch_repack((int)c32.size(), n, ld, inv, sel, 1, m, h->s);
+      L.M32.own.mats = m;
+    }
+    L.M32.own_x.n = (int)cx.size();
+    L.M32.own_x.cells = cx.empty() ? nullptr : h->upload(cx);
+    if (!cx.empty()) {
+      int* sel = h->upload(ix);
+      float2* m = h->alloc<float2>(cx.size() * (size_t)n * ld);
+      launch_repack((int)cx.size(), n, ld, inv, sel, 2, m, h->s);
+      L.M32.own_x.mats = m;
+    }
+    CKL();
     L.M32.sh.tl = L.M64.sh.tl;
     std::vector<float> sc32(scale.begin(), scale.end());
     L.M32.sh.scale = sc32.empty() ? nullptr : h->upload(sc32);
@@ -678,7 +703,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   double* Bcells = h->alloc<double>((size_t)ncell * n);
   int* d_sh = sh_cells.empty() ? nullptr : h->upload(sh_cells);
   launch_load_uncut(P, gauss, (int)sh_cells.size(), d_sh, d_cls, Bcells, h->s);
-  launch_scatter_rows((int)own_cells.size(), d_elist, bown, n, Bcells, h->s);
+  launch_scatter_rows((int)own_cells.size(), d_elist, bown, n, ncell, Bcells, h->s);
   h->b = h->alloc<double>(gt.N);
   launch_gather<double>(gt, GATHER_SET, Bcells, nullptr, h->b, 1.0, h->s);
   CKL();
@@ -743,7 +768,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     for (int c = 0; c < L0.g.ncells; ++c) {
       int oi = L0.h_own_index[c];
       if (oi >= 0) {
-        CK(cudaMemcpyAsync(Kall + (size_t)c * nl * nl, L0.A64.own.mats + (size_t)oi * nl * nl,
+        CK(cudaMemcpyAsync(Kall + (size_t)c * nl * nl, L0.Kown_c + (size_t)oi * nl * nl,
                            (size_t)nl * nl * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
       } else {
         launch_scale_copy(L0.Kref, Kall + (size_t)c * nl * nl, L0.h_scale_cell[c],
@@ -1173,11 +1198,12 @@ fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, lon
   } else {
     const OpData<double>& d64 = which == 0 ? L.A64 : L.M64;
     const OpData<float>& d32 = which == 0 ? L.A32 : L.M32;
+    const long long ld = padded_ld((int)n);
     long long mats;
     if (prec == FCM_FP64)
-      mats = (long long)d64.own.n * n * n * 8 + (long long)d64.sh.nmats * n * n * 8;
+      mats = (long long)d64.own.n * n * ld * 8 + (long long)d64.sh.nmats * n * n * 8;
     else
-      mats = (long long)d32.own.n * n * n * 4 + (long long)d32.own64.n * n * n * 8 +
+      mats = (long long)d32.own.n * n * ld * 4 + (long long)d32.own_x.n * n * ld * 8 +
              (long long)d32.sh.nmats * n * n * 4;
     b = mats + 2 * nc * n * sv;  // gathered coefficients + per-cell results
   }

@@ -78,12 +78,17 @@ struct Problem {
 enum { CLS_INSIDE = 0, CLS_OUTSIDE = 1, CLS_CUT = 2 };
 
 // ----------------------------------------------------------------------------
-// Per-level operator and smoother data.
-template <typename T>
+// Per-level operator and smoother data (solve layout).
+//
+// Stored cell matrices are symmetric and kept with rows padded to `ld`
+// entries (a multiple of 4) so that every row starts on a 16-byte boundary.
+// Element types: the vector precision TV (FP64 path: double, mixed path:
+// float) or, for the mixed path's extended-precision islands, pairs of
+// floats (hi, lo) with hi = fl32(a), lo = fl32(a - hi) ("df32").
 struct CellSet {
   int n = 0;                 // cells in the set
   int* cells = nullptr;      // linear cell ids (device)
-  T* mats = nullptr;         // own matrices [n][nloc][nloc] (device)
+  void* mats = nullptr;      // [n][nloc][ld] (device)
 };
 
 struct TileList {
@@ -97,18 +102,28 @@ template <typename T>
 struct SharedSet {
   TileList tl;
   T* scale = nullptr;        // per entry of tl.cells
-  T* mats = nullptr;         // [nmats][nloc][nloc]
+  T* mats = nullptr;         // [nmats][nloc][nloc] (canonical, unpadded)
   int nmats = 0;
 };
 
 template <typename TV>
 struct OpData {
-  CellSet<TV> own;           // matrices in the vector precision
-  CellSet<double> own64;     // FP64 islands (only used when TV = float)
+  int ld = 0;                // padded row length of stored matrices
+  CellSet own;               // stored matrices in precision TV
+  CellSet own_x;             // df32 islands (mixed path only)
   SharedSet<TV> sh;
 };
 
-// Launch a cell operation Y[c] = S_c x_c for every cell in `op`.
+// Padded row length of stored cell matrices.
+inline int padded_ld(int n) { return (n + 3) & ~3; }
+
+// Repack canonical FP64 n x n matrices (optionally selected by index) into
+// the solve layout [count][n][ld]: kind 0 = double, 1 = float, 2 = df32.
+void launch_repack(int count, int n, int ld, const double* src, const int* sel, int kind,
+                   void* dst, cudaStream_t s);
+
+// Launch a cell operation Y[l][c] = (S_c x_c)[l] for every cell in `op`
+// (Y is stored local-index-major: Y[l * ncells + cell]).
 template <typename TV>
 void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y,
                     cudaStream_t s);
@@ -173,12 +188,12 @@ void launch_classify(const Problem& P, signed char* cls, unsigned char* faces, c
 void launch_element_own(const Problem& P, const double* gauss, int ncell, const int* cells,
                         double* K, double* bvec, int* leaf_scratch, int max_leaves,
                         cudaStream_t s);
-// Load vectors of uncut cells: B[c][:] = alpha_c int f N.
+// Load vectors of uncut cells: B[l][c] = alpha_c int f N_l ([local][cell]).
 void launch_load_uncut(const Problem& P, const double* gauss, int ncell, const int* cells,
                        const signed char* cls, double* Bcells, cudaStream_t s);
 // Scatter per-own-cell loads into the per-cell load array.
-void launch_scatter_rows(int n, const int* cells, const double* src, int nloc, double* Bcells,
-                         cudaStream_t s);
+void launch_scatter_rows(int n, const int* cells, const double* src, int nloc, long long ncells,
+                         double* Bcells, cudaStream_t s);
 // Sub-block extraction: the level-(pc) cell matrix of a level-(pf) matrix.
 void launch_extract_sub(int nmat, int dim, int nf, int pf, int pc, const double* Kf,
                         double* Kc, cudaStream_t s);

@@ -106,6 +106,7 @@ extern "C" fcm_status fcm_cell_apply_noalloc(int dim, const int* cells, int p, c
   int blocks = (g.ncells + 255) / 256;
   iota_kernel<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(ids, g.ncells);
   fcm::OpData<double> op;
+  op.ld = g.nloc;  // caller matrices are unpadded n x n
   op.own.n = g.ncells;
   op.own.cells = ids;
   op.own.mats = const_cast<double*>(K_dev);

@@ -16,6 +16,7 @@
 // using the matrix symmetry so that every lane accumulates its own output
 // columns without a reduction.
 #include <cmath>
+#include <type_traits>
 
 #include "fcm_internal.h"
 
@@ -46,56 +47,188 @@ namespace {
 constexpr int kOpThreads = 256;
 constexpr int kWarpsPerBlock = kOpThreads / 32;
 constexpr int kTileCells = 32;
-constexpr int kMaxCols = 4;  // nloc <= 128
+constexpr int kRowUnroll = 4;
 
 // ---------------------------------------------------------------------------
-// Own matrices: one warp per cell.  Lane l accumulates output j = l + 32 k;
-// row s of the symmetric matrix equals column s, so y_j += K[s][j] x_s.
+// Stored matrices: one warp per cell.  Rows are padded to ld entries so a
+// row is ld / V 16-byte vectors (V entries each).  Lanes are split into R
+// row groups of ncv = ld / V lanes; lane (rg, cv) streams rows rg, rg + R, ...
+// and accumulates the V output columns [cv V, cv V + V): the matrix is
+// symmetric, so row s is column s and y_j += K[s][j] x_s needs no
+// reduction across columns.  The R partial sums are added at the end.
+template <typename TM>
+struct Elem;
+template <>
+struct Elem<float> {
+  static constexpr int V = 4;
+};
+template <>
+struct Elem<double> {
+  static constexpr int V = 2;
+};
+template <>
+struct Elem<float2> {  // df32 pair
+  static constexpr int V = 2;
+};
+
+template <typename TM>
+struct Acc {
+  TM v[Elem<TM>::V * 2];
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < Elem<TM>::V * 2; ++k) v[k] = 0;
+  }
+};
+// Compensated accumulator for df32 entries: value = s + c, with the exact
+// product error and the rounding error of every addition collected in c
+// (TwoProduct via fma, TwoSum; Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005).
+template <>
+struct Acc<float2> {
+  float s[4], c[4];
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] = c[k] = 0.f;
+  }
+};
+
+__device__ __forceinline__ void fma_row(Acc<float>& a, int slot, const float* row, float xs) {
+  float4 v = *reinterpret_cast<const float4*>(row);
+  a.v[slot * 4 + 0] += v.x * xs;
+  a.v[slot * 4 + 1] += v.y * xs;
+  a.v[slot * 4 + 2] += v.z * xs;
+  a.v[slot * 4 + 3] += v.w * xs;
+}
+__device__ __forceinline__ void fma_row(Acc<double>& a, int slot, const double* row, double xs) {
+  double2 v = *reinterpret_cast<const double2*>(row);
+  a.v[slot * 2 + 0] += v.x * xs;
+  a.v[slot * 2 + 1] += v.y * xs;
+}
+__device__ __forceinline__ void df_term(float& s, float& c, float hi, float lo, float x) {
+  float p = hi * x;
+  float e = fmaf(hi, x, -p);
+  float t = s + p;
+  float bb = t - s;
+  float err = (s - (t - bb)) + (p - bb);
+  s = t;
+  c += err + e + lo * x;
+}
+__device__ __forceinline__ void fma_row(Acc<float2>& a, int slot, const float2* row, float xs) {
+  float4 v = *reinterpret_cast<const float4*>(row);  // (hi0, lo0, hi1, lo1)
+  df_term(a.s[slot * 2 + 0], a.c[slot * 2 + 0], v.x, v.y, xs);
+  df_term(a.s[slot * 2 + 1], a.c[slot * 2 + 1], v.z, v.w, xs);
+}
+__device__ __forceinline__ double acc_value(const Acc<float>& a, int k) { return a.v[k]; }
+__device__ __forceinline__ double acc_value(const Acc<double>& a, int k) { return a.v[k]; }
+__device__ __forceinline__ double acc_value(const Acc<float2>& a, int k) {
+  return (double)a.s[k] + (double)a.c[k];
+}
+
 template <typename TV, typename TM>
-__device__ void own_role(const LevelGeom& g, int n_own, const int* cells, const TM* mats,
-                         const TV* __restrict__ x, TV* __restrict__ Y, int vblock, int nvblocks,
-                         TM* xw_all) {
+__device__ void own_role(const LevelGeom& g, int ld, int n_own, const int* __restrict__ cells,
+                         const TM* __restrict__ mats, const TV* __restrict__ x,
+                         TV* __restrict__ Y, int vblock, int nvblocks, unsigned char* smem) {
+  constexpr int V = Elem<TM>::V;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = g.nloc;
-  TM* xw = xw_all + warp * 128;
+  const long long ncells = g.ncells;
+  TV* xw = reinterpret_cast<TV*>(smem) + warp * 128;
+  double* red = reinterpret_cast<double*>(smem + kWarpsPerBlock * 128 * sizeof(TV)) + warp * 128;
+  const int ncv = ld / V;
+  int R, NV;
+  if (ncv <= 32) {
+    R = 32 / ncv;
+    NV = 1;
+  } else {
+    R = 1;
+    NV = 2;  // ld <= 64 V
+  }
+  const int rg = ncv <= 32 ? lane / ncv : 0;
+  const int cv = ncv <= 32 ? lane % ncv : lane;
+  const bool active = rg < R;
+  const bool second = NV > 1 && cv + 32 < ncv;  // second column vector of this lane
   for (int ci = vblock * kWarpsPerBlock + warp; ci < n_own; ci += nvblocks * kWarpsPerBlock) {
     const int cell = cells[ci];
     int cx, cy, cz;
     cell_coords(g, cell, cx, cy, cz);
-    for (int l = lane; l < n; l += 32) xw[l] = (TM)x[cell_dof(g, cx, cy, cz, l)];
+    for (int l = lane; l < n; l += 32) xw[l] = x[cell_dof(g, cx, cy, cz, l)];
     __syncwarp();
-    TM acc[kMaxCols];
+    Acc<TM> acc;
+    acc.zero();
+    const TM* K = mats + (size_t)ci * n * ld;
+    if (active) {
+      int s = rg;
+      for (; s + (kRowUnroll - 1) * R < n; s += kRowUnroll * R) {
 #pragma unroll
-    for (int k = 0; k < kMaxCols; ++k) acc[k] = 0;
-    const TM* K = mats + (size_t)ci * n * n;
-    int s = 0;
-    for (; s + 4 <= n; s += 4) {
-      TM x0 = xw[s], x1 = xw[s + 1], x2 = xw[s + 2], x3 = xw[s + 3];
-      const TM* r0 = K + (size_t)s * n;
-#pragma unroll
-      for (int k = 0; k < kMaxCols; ++k) {
-        int j = lane + 32 * k;
-        if (j < n) {
-          TM a0 = __ldg(r0 + j), a1 = __ldg(r0 + n + j), a2 = __ldg(r0 + 2 * n + j),
-             a3 = __ldg(r0 + 3 * n + j);
-          acc[k] += a0 * x0 + a1 * x1 + a2 * x2 + a3 * x3;
+        for (int u = 0; u < kRowUnroll; ++u) {
+          const int sr = s + u * R;
+          const TV xs = xw[sr];
+          const TM* row = K + (size_t)sr * ld;
+          fma_row(acc, 0, row + cv * V, xs);
+          if (second) fma_row(acc, 1, row + (cv + 32) * V, xs);
         }
       }
-    }
-    for (; s < n; ++s) {
-      TM xs = xw[s];
-      const TM* r0 = K + (size_t)s * n;
-#pragma unroll
-      for (int k = 0; k < kMaxCols; ++k) {
-        int j = lane + 32 * k;
-        if (j < n) acc[k] += __ldg(r0 + j) * xs;
+      for (; s < n; s += R) {
+        const TV xs = xw[s];
+        const TM* row = K + (size_t)s * ld;
+        fma_row(acc, 0, row + cv * V, xs);
+        if (second) fma_row(acc, 1, row + (cv + 32) * V, xs);
       }
     }
-    TV* y = Y + (size_t)cell * n;
+    if (R == 1) {
 #pragma unroll
-    for (int k = 0; k < kMaxCols; ++k) {
+      for (int k = 0; k < 2 * V; ++k) {
+        int j = (k < V ? cv * V + k : (cv + 32) * V + (k - V));
+        if (k >= V && !second) break;
+        if (j < n) Y[(size_t)j * ncells + cell] = (TV)acc_value(acc, k);
+      }
+    } else {
+      if (active) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) red[rg * ld + cv * V + k] = acc_value(acc, k);
+      }
+      __syncwarp();
+      for (int j = lane; j < n; j += 32) {
+        double t = 0.0;
+        for (int r = 0; r < R; ++r) t += red[r * ld + j];
+        Y[(size_t)j * ncells + cell] = (TV)t;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Unpadded rows (ld = n not a multiple of 4): scalar loads, lane j owns the
+// output columns j, j + 32, ... (row s is column s by symmetry).
+__device__ void own_role_scalar(const LevelGeom& g, int n_own, const int* __restrict__ cells,
+                                const double* __restrict__ mats, const double* __restrict__ x,
+                                double* __restrict__ Y, int vblock, int nvblocks,
+                                unsigned char* smem) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = g.nloc;
+  const long long ncells = g.ncells;
+  double* xw = reinterpret_cast<double*>(smem) + warp * 128;
+  for (int ci = vblock * kWarpsPerBlock + warp; ci < n_own; ci += nvblocks * kWarpsPerBlock) {
+    const int cell = cells[ci];
+    int cx, cy, cz;
+    cell_coords(g, cell, cx, cy, cz);
+    for (int l = lane; l < n; l += 32) xw[l] = x[cell_dof(g, cx, cy, cz, l)];
+    __syncwarp();
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const double* K = mats + (size_t)ci * n * n;
+    for (int s = 0; s < n; ++s) {
+      const double xs = xw[s];
+      const double* row = K + (size_t)s * n;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int j = lane + 32 * k;
+        if (j < n) acc[k] += row[j] * xs;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
       int j = lane + 32 * k;
-      if (j < n) y[j] = (TV)acc[k];
+      if (j < n) Y[(size_t)j * ncells + cell] = acc[k];
     }
     __syncwarp();
   }
@@ -145,13 +278,13 @@ __device__ void tile_role(const LevelGeom& g, const int4 tile, const int* cells,
       if (r < R) acc[r] += krow[r] * xv;
   }
   if (c < cnt) {
+    const long long ncells = g.ncells;
     int cell = cells[tile.y + c];
     TV s = scale[tile.y + c];
-    TV* y = Y + (size_t)cell * n;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       int i = i0 + r;
-      if (r < R && i < n) y[i] = s * acc[r];
+      if (r < R && i < n) Y[(size_t)i * ncells + cell] = s * acc[r];
     }
   }
   __syncthreads();
@@ -160,20 +293,21 @@ __device__ void tile_role(const LevelGeom& g, const int4 tile, const int* cells,
 template <typename TV>
 struct CellOpArgs {
   LevelGeom g;
+  int ld;
   const TV* x;
   TV* Y;
   int n_own;
   const int* own_cells;
   const TV* own_mats;
-  int n_own64;
-  const int* own64_cells;
-  const double* own64_mats;
+  int n_own_x;
+  const int* own_x_cells;
+  const float2* own_x_mats;
   int ntiles;
   const int4* tiles;
   const int* sh_cells;
   const TV* sh_scale;
   const TV* sh_mats;
-  int nb_own, nb_own64;
+  int nb_own, nb_own_x;
 };
 
 template <typename TV>
@@ -181,74 +315,88 @@ __global__ void __launch_bounds__(kOpThreads) cell_op_kernel(CellOpArgs<TV> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int b = blockIdx.x;
   if (b < A.nb_own) {
-    own_role<TV, TV>(A.g, A.n_own, A.own_cells, A.own_mats, A.x, A.Y, b, A.nb_own,
-                     reinterpret_cast<TV*>(smem_raw));
+    if constexpr (std::is_same<TV, double>::value) {
+      if ((A.ld & 3) || (reinterpret_cast<uintptr_t>(A.own_mats) & 15)) {
+        own_role_scalar(A.g, A.n_own, A.own_cells, A.own_mats, A.x, A.Y, b, A.nb_own, smem_raw);
+        return;
+      }
+    }
+    own_role<TV, TV>(A.g, A.ld, A.n_own, A.own_cells, A.own_mats, A.x, A.Y, b, A.nb_own,
+                     smem_raw);
     return;
   }
   b -= A.nb_own;
-  if (b < A.nb_own64) {
-    own_role<TV, double>(A.g, A.n_own64, A.own64_cells, A.own64_mats, A.x, A.Y, b, A.nb_own64,
-                         reinterpret_cast<double*>(smem_raw));
+  if (b < A.nb_own_x) {
+    if constexpr (std::is_same<TV, float>::value)
+      own_role<float, float2>(A.g, A.ld, A.n_own_x, A.own_x_cells, A.own_x_mats, A.x, A.Y, b,
+                              A.nb_own_x, smem_raw);
     return;
   }
-  b -= A.nb_own64;
+  b -= A.nb_own_x;
   if (b < A.ntiles)
     tile_role<TV>(A.g, A.tiles[b], A.sh_cells, A.sh_scale, A.sh_mats, A.x, A.Y,
                   reinterpret_cast<TV*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------
-// DOF-centric gather of per-cell contributions.
+// DOF-centric gather of per-cell contributions (Y local-index-major).
+__device__ __forceinline__ int axis_pairs(int C, int i, int& c0, int& j0, int& c1, int& j1) {
+  if (i <= C) {
+    if (i == 0) {
+      c0 = 0;
+      j0 = 0;
+      return 1;
+    }
+    if (i == C) {
+      c0 = C - 1;
+      j0 = 1;
+      return 1;
+    }
+    c0 = i - 1;
+    j0 = 1;
+    c1 = i;
+    j1 = 0;
+    return 2;
+  }
+  int t = i - (C + 1);
+  int q = t / C;
+  c0 = t - q * C;
+  j0 = q + 2;
+  return 1;
+}
+
 template <typename TV, int MODE>
 __global__ void gather_kernel(LevelGeom g, const TV* __restrict__ Y, const TV* __restrict__ b,
                               TV* __restrict__ out, TV w) {
   const int P1 = g.p + 1;
+  const long long ncells = g.ncells;
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < g.N;
        I += (long long)gridDim.x * blockDim.x) {
-    long long f = I / g.M;
-    long long r = I - f * g.M;
-    int idx[3];
-    idx[0] = (int)(r % g.m[0]);
-    long long t = r / g.m[0];
-    idx[1] = (int)(t % g.m[1]);
-    idx[2] = (int)(t / g.m[1]);
-    int cs[3][2], js[3][2], nc[3];
-    for (int a = 0; a < 3; ++a) {
-      if (a >= g.dim) {
-        nc[a] = 1;
-        cs[a][0] = 0;
-        js[a][0] = 0;
-        continue;
-      }
-      int C = g.C[a], i = idx[a];
-      if (i <= C) {
-        int k = 0;
-        if (i >= 1) {
-          cs[a][k] = i - 1;
-          js[a][k] = 1;
-          ++k;
+    const long long f = I / g.M;
+    const long long r = I - f * g.M;
+    const int ix = (int)(r % g.m[0]);
+    const long long t = r / g.m[0];
+    const int iy = (int)(t % g.m[1]);
+    const int iz = (int)(t / g.m[1]);
+    int cx0 = 0, jx0 = 0, cx1 = 0, jx1 = 0, cy0 = 0, jy0 = 0, cy1 = 0, jy1 = 0, cz0 = 0, jz0 = 0,
+        cz1 = 0, jz1 = 0;
+    const int nx = axis_pairs(g.C[0], ix, cx0, jx0, cx1, jx1);
+    const int ny = g.dim > 1 ? axis_pairs(g.C[1], iy, cy0, jy0, cy1, jy1) : 1;
+    const int nz = g.dim > 2 ? axis_pairs(g.C[2], iz, cz0, jz0, cz1, jz1) : 1;
+    TV sum = 0;
+    const int lf = (int)f * g.nloc_s;
+    for (int kz = 0; kz < nz; ++kz) {
+      const int cz = kz ? cz1 : cz0, jz = kz ? jz1 : jz0;
+      for (int ky = 0; ky < ny; ++ky) {
+        const int cy = ky ? cy1 : cy0, jy = ky ? jy1 : jy0;
+        for (int kx = 0; kx < nx; ++kx) {
+          const int cx = kx ? cx1 : cx0, jx = kx ? jx1 : jx0;
+          const int cell = cx + g.C[0] * (cy + g.C[1] * cz);
+          const int l = lf + jx + P1 * (jy + P1 * jz);
+          sum += Y[(size_t)l * ncells + cell];
         }
-        if (i < C) {
-          cs[a][k] = i;
-          js[a][k] = 0;
-          ++k;
-        }
-        nc[a] = k;
-      } else {
-        int q = (i - (C + 1)) / C;
-        cs[a][0] = (i - (C + 1)) - q * C;
-        js[a][0] = q + 2;
-        nc[a] = 1;
       }
     }
-    TV sum = 0;
-    for (int kz = 0; kz < nc[2]; ++kz)
-      for (int ky = 0; ky < nc[1]; ++ky)
-        for (int kx = 0; kx < nc[0]; ++kx) {
-          int cell = cs[0][kx] + g.C[0] * (cs[1][ky] + g.C[1] * cs[2][kz]);
-          int l = (int)f * g.nloc_s + js[0][kx] + P1 * (js[1][ky] + P1 * js[2][kz]);
-          sum += Y[(size_t)cell * g.nloc + l];
-        }
     if (MODE == GATHER_SET)
       out[I] = sum;
     else if (MODE == GATHER_RESID)
@@ -257,6 +405,29 @@ __global__ void gather_kernel(LevelGeom g, const TV* __restrict__ Y, const TV* _
       out[I] = out[I] + w * sum;
     else
       out[I] = w * sum;
+  }
+}
+
+// Canonical FP64 matrices -> padded solve layout.
+__global__ void repack_kernel(int count, int n, int ld, const double* __restrict__ src,
+                              const int* __restrict__ sel, int kind, void* dst) {
+  long long tot = (long long)count * n * ld;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    int m = (int)(t / ((long long)n * ld));
+    int r = (int)(t % ((long long)n * ld));
+    int i = r / ld, j = r % ld;
+    int sm = sel ? sel[m] : m;
+    double v = j < n ? src[(size_t)sm * n * n + (size_t)i * n + j] : 0.0;
+    if (kind == 0) {
+      reinterpret_cast<double*>(dst)[t] = v;
+    } else if (kind == 1) {
+      reinterpret_cast<float*>(dst)[t] = (float)v;
+    } else {
+      float hi = (float)v;
+      float lo = (float)(v - (double)hi);
+      reinterpret_cast<float2*>(dst)[t] = make_float2(hi, lo);
+    }
   }
 }
 
@@ -533,14 +704,15 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
                     cudaStream_t s) {
   CellOpArgs<TV> A;
   A.g = g;
+  A.ld = op.ld;
   A.x = x;
   A.Y = Y;
   A.n_own = op.own.n;
   A.own_cells = op.own.cells;
-  A.own_mats = op.own.mats;
-  A.n_own64 = op.own64.n;
-  A.own64_cells = op.own64.cells;
-  A.own64_mats = op.own64.mats;
+  A.own_mats = static_cast<const TV*>(op.own.mats);
+  A.n_own_x = op.own_x.n;
+  A.own_x_cells = op.own_x.cells;
+  A.own_x_mats = static_cast<const float2*>(op.own_x.mats);
   A.ntiles = op.sh.tl.ntiles;
   A.tiles = op.sh.tl.tiles;
   A.sh_cells = op.sh.tl.cells;
@@ -548,15 +720,15 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   A.sh_mats = op.sh.mats;
   auto nb = [](int n) {
     int b = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    return b > 2048 ? 2048 : b;
+    return b > 4096 ? 4096 : b;
   };
   A.nb_own = op.own.n ? nb(op.own.n) : 0;
-  A.nb_own64 = op.own64.n ? nb(op.own64.n) : 0;
-  int grid = A.nb_own + A.nb_own64 + A.ntiles;
+  A.nb_own_x = op.own_x.n ? nb(op.own_x.n) : 0;
+  int grid = A.nb_own + A.nb_own_x + A.ntiles;
   if (grid == 0) return;
   int n = g.nloc, npad = (n + 7) & ~7;
   size_t sm_tile = op.sh.tl.ntiles ? ((size_t)n * npad + (size_t)n * kTileCells) * sizeof(TV) : 0;
-  size_t sm_own = (size_t)kWarpsPerBlock * 128 * sizeof(double);
+  size_t sm_own = (size_t)kWarpsPerBlock * 128 * (sizeof(TV) + sizeof(double));
   size_t smem = sm_tile > sm_own ? sm_tile : sm_own;
   static size_t attr_set = 0;
   if (smem > 48 * 1024 && smem > attr_set) {
@@ -565,6 +737,13 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
     attr_set = smem;
   }
   cell_op_kernel<TV><<<grid, kOpThreads, smem, s>>>(A);
+}
+
+void launch_repack(int count, int n, int ld, const double* src, const int* sel, int kind,
+                   void* dst, cudaStream_t s) {
+  if (count == 0) return;
+  long long tot = (long long)count * n * ld;
+  repack_kernel<<<grid_for(tot), 256, 0, s>>>(count, n, ld, src, sel, kind, dst);
 }
 
 template <typename TV>

@@ -769,18 +769,19 @@ __global__ void load_uncut_kernel(Problem P, const double* gauss, int ncell, con
         }
         s += (w * alpha) * source_f(P, x) * v;
       }
-      Bcells[(size_t)cell * n + i] = s;
+      Bcells[(size_t)i * (P.C[0] * P.C[1] * P.C[2]) + cell] = s;  // [local][cell]
     }
   }
 }
 
+// Rows src[r][l] of own cells into the [local][cell] per-cell array.
 __global__ void scatter_rows_kernel(int nrows, const int* cells, const double* src, int nloc,
-                                    double* dst) {
+                                    long long ncells, double* dst) {
   long long tot = (long long)nrows * nloc;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
        t += (long long)gridDim.x * blockDim.x) {
     int r = (int)(t / nloc), l = (int)(t % nloc);
-    dst[(size_t)cells[r] * nloc + l] = src[t];
+    dst[(size_t)l * ncells + cells[r]] = src[t];
   }
 }
 
@@ -826,13 +827,13 @@ void launch_load_uncut(const Problem& P, const double* gauss, int ncell, const i
   load_uncut_kernel<<<blocks, 256, 0, s>>>(P, gauss, ncell, cells, cls, Bcells);
 }
 
-void launch_scatter_rows(int n, const int* cells, const double* src, int nloc, double* Bcells,
-                         cudaStream_t s) {
+void launch_scatter_rows(int n, const int* cells, const double* src, int nloc, long long ncells,
+                         double* Bcells, cudaStream_t s) {
   if (n == 0) return;
   long long tot = (long long)n * nloc;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 8192) blocks = 8192;
-  scatter_rows_kernel<<<blocks, 256, 0, s>>>(n, cells, src, nloc, Bcells);
+  scatter_rows_kernel<<<blocks, 256, 0, s>>>(n, cells, src, nloc, ncells, Bcells);
 }
 
 }  // namespace fcm

@@ -192,18 +192,22 @@ __global__ void block_assemble_kernel(LevelGeom g, int nblk, const int* blk_cell
 
 // In-place inverse of SPD blocks via A = L L^T, L^{-1} (in place) and
 // A^{-1} = L^{-T} L^{-1}.  One block per matrix, matrix staged in shared
-// memory (n <= 128).
-__global__ void chol_inverse_kernel(int nblk, int n, double* Aall, double* pivots, int* info) {
+// memory (n <= 128).  Per block: stats[2i] = smallest Cholesky pivot,
+// stats[2i+1] = max_k A_kk / pivot_k (how close a row comes to linear
+// dependence on the rows before it).
+__global__ void chol_inverse_kernel(int nblk, int n, double* Aall, double* stats, int* info) {
   extern __shared__ double Ls[];  // n * n
   double* tmp = Ls + n * n;       // n
-  __shared__ double pmin, pmax;
+  double* diag = tmp + n;         // n
+  __shared__ double pmin, dep;
   __shared__ int bad;
   for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
     double* A = Aall + (size_t)bi * n * n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) Ls[e] = A[e];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) diag[i] = A[(size_t)i * n + i];
     if (threadIdx.x == 0) {
       pmin = INFINITY;
-      pmax = 0.0;
+      dep = 0.0;
       bad = 0;
     }
     __syncthreads();
@@ -216,7 +220,7 @@ __global__ void chol_inverse_kernel(int nblk, int n, double* Aall, double* pivot
           d = 1.0;
         }
         pmin = fmin(pmin, d);
-        pmax = fmax(pmax, d);
+        dep = fmax(dep, diag[k] / d);
         Ls[k * n + k] = sqrt(d);
       }
       __syncthreads();
@@ -253,9 +257,9 @@ __global__ void chol_inverse_kernel(int nblk, int n, double* Aall, double* pivot
       A[e] = s;
     }
     if (threadIdx.x == 0) {
-      if (pivots) {
-        pivots[2 * bi] = pmin;
-        pivots[2 * bi + 1] = pmax;
+      if (stats) {
+        stats[2 * bi] = pmin;
+        stats[2 * bi + 1] = dep;
       }
       if (info) info[bi] = bad;
     }
@@ -359,7 +363,7 @@ void launch_block_assemble(const LevelGeom& g, int nblk, const int* blk_cells,
 
 void launch_chol_inverse(int nblk, int n, double* A, double* pivots, int* info, cudaStream_t s) {
   if (nblk == 0) return;
-  size_t smem = ((size_t)n * n + n) * sizeof(double);
+  size_t smem = ((size_t)n * n + 2 * n) * sizeof(double);
   cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   int grid = nblk < 4096 ? nblk : 4096;
