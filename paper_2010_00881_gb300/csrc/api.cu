@@ -159,7 +159,7 @@ struct CallScope {
   }
 };
 
-// Build tiles of <= 32 cells for entries grouped by matrix id.
+// Build tiles of <= 64 cells for entries grouped by matrix id.
 template <typename T>
 void build_shared(Handle* h, SharedSet<T>& S, const std::vector<int>& mat_of,
                   const std::vector<int>& cells, const std::vector<T>& scale, T* mats,
@@ -171,7 +171,7 @@ void build_shared(Handle* h, SharedSet<T>& S, const std::vector<int>& mat_of,
   while (i < n) {
     int m = mat_of[i];
     int j = i;
-    while (j < n && mat_of[j] == m && j - i < 32) ++j;
+    while (j < n && mat_of[j] == m && j - i < 64) ++j;  // tiles of <= 64 cells
     tiles.push_back(make_int4(m, i, j - i, 0));
     i = j;
   }
@@ -200,6 +200,14 @@ void check_status(Handle* h, const int* d_info, int n, const char* what) {
   CK(cudaStreamSynchronize(h->s));
   for (int i = 0; i < n; ++i)
     if (info[i]) throw Error(FCM_E_INVALID, std::string(what) + ": matrix not positive definite");
+}
+
+// A streaming kernel whose bounded wait on a bulk copy expired sets a device
+// flag; report it instead of returning numbers computed from stale data.
+void check_timeout(Handle* h) {
+  int flag = 0;
+  CK(read_and_clear_timeout(&flag, h->s));
+  if (flag) throw Error(FCM_E_TIMEOUT, "a bounded device wait on a bulk copy expired");
 }
 
 double host_dot(Handle* h, const double* a, const double* b, long long n) {
@@ -804,6 +812,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     estimate_omega(h, L, omega_paper);
   }
   CK(cudaStreamSynchronize(h->s));
+  check_timeout(h);
   h->g_vc64 = capture_vcycle<double>(h, &h->vc_nodes64);
   if (h->mixed) h->g_vc32 = capture_vcycle<float>(h, &h->vc_nodes32);
   CK(cudaStreamSynchronize(h->s));
@@ -906,6 +915,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   CGScalars sc;
   CK(cudaMemcpyAsync(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
+  check_timeout(h);
   if (sc.flag && st != FCM_OK) st = FCM_E_BREAKDOWN;
   if (st != FCM_OK) {
     apply_A64(h, T, x, h->cz_old, GATHER_RESID, b);
@@ -1013,6 +1023,7 @@ fcm_status fcm_apply(fcm_handle* h, const double* x, double* y, int prec) {
       CKL();
     }
     cs.finish();
+    check_timeout(h);
     return FCM_OK;
   });
 }
@@ -1026,6 +1037,7 @@ fcm_status fcm_vcycle(fcm_handle* h, const double* r, double* z, int prec) {
     CallScope cs(h);
     run_vcycle(h, r, z, prec);
     cs.finish();
+    check_timeout(h);
     return FCM_OK;
   });
 }

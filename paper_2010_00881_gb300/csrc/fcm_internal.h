@@ -220,6 +220,10 @@ void launch_dense_assemble(const LevelGeom& g, const double* own_mats, double* A
 
 std::string cuda_msg(cudaError_t e);
 
+// Read (and reset) the flag the streaming kernels set when a bounded wait on
+// a bulk copy expired.
+cudaError_t read_and_clear_timeout(int* flag, cudaStream_t s);
+
 // Set the thread-local message returned by fcm_last_error().
 void set_last_error(const char* msg);
 

@@ -46,8 +46,33 @@ namespace {
 
 constexpr int kOpThreads = 256;
 constexpr int kWarpsPerBlock = kOpThreads / 32;
-constexpr int kTileCells = 32;
+constexpr int kTileCells = 64;
 constexpr int kRowUnroll = 4;
+constexpr int kOwnBlocksCap = 152 * 6;  // own-kernel blocks: several cells per warp
+
+// Per-block table of local indices l -> (f, jx, jy, jz), packed into one
+// int, so coefficient gathers avoid runtime integer division.
+__device__ __forceinline__ void build_local_table(const LevelGeom& g, int* tab) {
+  const int P1 = g.p + 1;
+  for (int l = threadIdx.x; l < g.nloc; l += blockDim.x) {
+    int f = l / g.nloc_s;
+    int t = l - f * g.nloc_s;
+    int jx = t % P1;
+    int jy = g.dim > 1 ? (t / P1) % P1 : 0;
+    int jz = g.dim > 2 ? t / (P1 * P1) : 0;
+    tab[l] = (f << 24) | (jz << 16) | (jy << 8) | jx;
+  }
+}
+
+// Global index of the local DOF with packed modes `pk` of cell (cx, cy, cz).
+__device__ __forceinline__ long long dof_packed(const LevelGeom& g, int cx, int cy, int cz,
+                                                int pk) {
+  const int jx = pk & 255, jy = (pk >> 8) & 255, jz = (pk >> 16) & 255, f = pk >> 24;
+  long long ix = dof1(g.C[0], cx, jx);
+  long long iy = dof1(g.C[1], cy, jy);
+  long long iz = dof1(g.C[2], cz, jz);
+  return (long long)f * g.M + ix + (long long)g.m[0] * (iy + (long long)g.m[1] * iz);
+}
 
 // ---------------------------------------------------------------------------
 // Stored matrices: one warp per cell.  Rows are padded to ld entries so a
@@ -127,7 +152,8 @@ __device__ __forceinline__ double acc_value(const Acc<float2>& a, int k) {
 template <typename TV, typename TM>
 __device__ void own_role(const LevelGeom& g, int ld, int n_own, const int* __restrict__ cells,
                          const TM* __restrict__ mats, const TV* __restrict__ x,
-                         TV* __restrict__ Y, int vblock, int nvblocks, unsigned char* smem) {
+                         TV* __restrict__ Y, int vblock, int nvblocks, unsigned char* smem,
+                         const int* tab) {
   constexpr int V = Elem<TM>::V;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = g.nloc;
@@ -147,12 +173,38 @@ __device__ void own_role(const LevelGeom& g, int ld, int n_own, const int* __res
   const int cv = ncv <= 32 ? lane % ncv : lane;
   const bool active = rg < R;
   const bool second = NV > 1 && cv + 32 < ncv;  // second column vector of this lane
-  for (int ci = vblock * kWarpsPerBlock + warp; ci < n_own; ci += nvblocks * kWarpsPerBlock) {
-    const int cell = cells[ci];
+  const int stride = nvblocks * kWarpsPerBlock;
+  int ci = vblock * kWarpsPerBlock + warp;
+  // coefficients of the first cell; later cells are prefetched into
+  // registers while the previous cell's matrix streams
+  TV xn[4];
+  if (ci < n_own) {
     int cx, cy, cz;
-    cell_coords(g, cell, cx, cy, cz);
-    for (int l = lane; l < n; l += 32) xw[l] = x[cell_dof(g, cx, cy, cz, l)];
+    cell_coords(g, cells[ci], cx, cy, cz);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int l = lane + 32 * k;
+      xn[k] = l < n ? x[dof_packed(g, cx, cy, cz, tab[l])] : (TV)0;
+    }
+  }
+  for (; ci < n_own; ci += stride) {
+    const int cell = cells[ci];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int l = lane + 32 * k;
+      if (l < n) xw[l] = xn[k];
+    }
     __syncwarp();
+    const int cnext = ci + stride;
+    if (cnext < n_own) {
+      int cx, cy, cz;
+      cell_coords(g, cells[cnext], cx, cy, cz);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int l = lane + 32 * k;
+        if (l < n) xn[k] = x[dof_packed(g, cx, cy, cz, tab[l])];
+      }
+    }
     Acc<TM> acc;
     acc.zero();
     const TM* K = mats + (size_t)ci * n * ld;
@@ -234,60 +286,107 @@ __device__ void own_role_scalar(const LevelGeom& g, int n_own, const int* __rest
   }
 }
 
-// Shared matrices: a tile of up to 32 cells against one n x n matrix held in
-// shared memory.  Thread (c = t % 32, rgroup = t / 32) computes the rows
-// [rgroup R, rgroup R + R) of cell c, R = ceil(n / 8).
-template <typename TV>
+// Shared matrices: a tile of up to 64 cells against one n x n matrix held in
+// shared memory.  npad = next power of two >= max(16, n); thread
+// (cg = t % 16, rg = t / 16) computes rows [rg RB, rg RB + RB) of the four
+// cells 4 cg .. 4 cg + 3 (RB = npad / 16), so every k step reads RB matrix
+// entries and 4 coefficients from shared memory for 4 RB multiply-adds.
+__host__ __device__ inline int tile_npad(int n) {
+  int p2 = 16;
+  while (p2 < n) p2 <<= 1;
+  return p2;
+}
+
+template <typename TV, int RB>
 __device__ void tile_role(const LevelGeom& g, const int4 tile, const int* cells, const TV* scale,
                           const TV* mats, const TV* __restrict__ x, TV* __restrict__ Y,
-                          TV* smem) {
+                          TV* smem, const int* tab, int* ccell) {
   const int n = g.nloc;
-  const int npad = (n + 7) & ~7;
-  const int R = npad / 8;
-  TV* Ks = smem;                 // n x npad
-  TV* Xs = smem + n * npad;      // n x 32
+  constexpr int npad = 16 * RB;
+  constexpr int lgp = RB == 1 ? 4 : RB == 2 ? 5 : RB == 4 ? 6 : 7;
+  TV* Ks = smem;                 // n x npad, row k = column k (K symmetric)
+  TV* Xs = smem + n * npad;      // n x 64
+  const int cnt = tile.z;
+  // cell ids and coordinates of the tile, once
+  if (threadIdx.x < kTileCells) {
+    int c = threadIdx.x;
+    int cell = c < cnt ? cells[tile.y + c] : 0;
+    int cx, cy, cz;
+    cell_coords(g, cell, cx, cy, cz);
+    ccell[c] = cell;
+    ccell[kTileCells + c] = cx;
+    ccell[2 * kTileCells + c] = cy;
+    ccell[3 * kTileCells + c] = cz;
+  }
   const TV* K = mats + (size_t)tile.x * n * n;
   for (int e = threadIdx.x; e < n * npad; e += blockDim.x) {
-    int i = e / npad, j = e % npad;
+    int i = e >> lgp, j = e & (npad - 1);
     Ks[e] = j < n ? K[(size_t)i * n + j] : (TV)0;
   }
-  const int cnt = tile.z;
+  __syncthreads();
   for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
-    int k = e / kTileCells, c = e % kTileCells;
+    int k = e >> 6, c = e & (kTileCells - 1);
     TV v = 0;
-    if (c < cnt) {
-      int cell = cells[tile.y + c];
-      int cx, cy, cz;
-      cell_coords(g, cell, cx, cy, cz);
-      v = x[cell_dof(g, cx, cy, cz, k)];
-    }
+    if (c < cnt)
+      v = x[dof_packed(g, ccell[kTileCells + c], ccell[2 * kTileCells + c],
+                       ccell[3 * kTileCells + c], tab[k])];
     Xs[e] = v;
   }
   __syncthreads();
-  const int c = threadIdx.x % kTileCells;
-  const int rg = threadIdx.x / kTileCells;
-  const int i0 = rg * R;
-  TV acc[16];
+  const int cg = threadIdx.x & 15;
+  const int rg = threadIdx.x >> 4;
+  const int i0 = rg * RB;
+  TV acc[RB][4];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) acc[r] = 0;
-  for (int k = 0; k < n; ++k) {
-    TV xv = Xs[k * kTileCells + c];
-    const TV* krow = Ks + k * npad + i0;  // K symmetric: K[i][k] = K[k][i]
+  for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int r = 0; r < 16; ++r)
-      if (r < R) acc[r] += krow[r] * xv;
-  }
-  if (c < cnt) {
-    const long long ncells = g.ncells;
-    int cell = cells[tile.y + c];
-    TV s = scale[tile.y + c];
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+  if (i0 < n) {
+#pragma unroll 2
+    for (int k = 0; k < n; ++k) {
+      TV xv[4];
+      const TV* xr = Xs + k * kTileCells + 4 * cg;
+      TV kv[RB];
+      const TV* kr = Ks + k * npad + i0;
+      if constexpr (std::is_same<TV, float>::value) {
+        float4 t = *reinterpret_cast<const float4*>(xr);
+        xv[0] = t.x; xv[1] = t.y; xv[2] = t.z; xv[3] = t.w;
+        if constexpr (RB >= 4) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      int i = i0 + r;
-      if (r < R && i < n) Y[(size_t)i * ncells + cell] = s * acc[r];
+          for (int r4 = 0; r4 < RB / 4; ++r4) {
+            float4 u = *reinterpret_cast<const float4*>(kr + 4 * r4);
+            kv[4 * r4] = u.x; kv[4 * r4 + 1] = u.y; kv[4 * r4 + 2] = u.z; kv[4 * r4 + 3] = u.w;
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < RB; ++r) kv[r] = kr[r];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xv[c] = xr[c];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) kv[r] = kr[r];
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] += kv[r] * xv[c];
     }
   }
-  __syncthreads();
+  const long long ncells = g.ncells;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int cc = 4 * cg + c;
+    if (cc < cnt) {
+      const int cell = ccell[cc];
+      const TV sc = scale[tile.y + cc];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int i = i0 + r;
+        if (i < n) Y[(size_t)i * ncells + cell] = sc * acc[r][c];
+      }
+    }
+  }
 }
 
 template <typename TV>
@@ -310,32 +409,261 @@ struct CellOpArgs {
   int nb_own, nb_own_x;
 };
 
-template <typename TV>
-__global__ void __launch_bounds__(kOpThreads) cell_op_kernel(CellOpArgs<TV> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  int b = blockIdx.x;
-  if (b < A.nb_own) {
-    if constexpr (std::is_same<TV, double>::value) {
-      if ((A.ld & 3) || (reinterpret_cast<uintptr_t>(A.own_mats) & 15)) {
-        own_role_scalar(A.g, A.n_own, A.own_cells, A.own_mats, A.x, A.Y, b, A.nb_own, smem_raw);
-        return;
+// ---------------------------------------------------------------------------
+// Stored matrices streamed through shared memory by the bulk-copy (TMA)
+// engine.  Every warp owns a contiguous range of cells, whose matrices are
+// contiguous in memory, and walks it in chunks of RC rows (RC divides n,
+// chunk <= 8 KB).  Lane 0 issues cp.async.bulk copies into three per-warp
+// stages completed through mbarriers; the warp computes from shared memory
+// with the same (row group, column vector) lane mapping as own_role, so the
+// only loads in flight that registers must cover are the coefficient
+// gathers.  Waits are bounded: on expiry the kernel records a timeout flag,
+// drains its own copies (again bounded) and returns.
+constexpr int kStages = 2;
+constexpr int kChunkBytes = 8192;
+constexpr int kStreamWarps = 12;
+constexpr long long kSpinLimit = 1LL << 26;
+
+__device__ int g_stream_timeout = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename TV, typename TM>
+struct StreamArgs {
+  LevelGeom g;
+  int ld, rc;  // padded row length, rows per chunk
+  int n_own;
+  const int* cells;
+  const TM* mats;
+  const TV* x;
+  TV* Y;
+};
+
+struct StreamWarpSmem {
+  uint64_t bar[kStages];
+};
+
+template <typename TV, typename TM>
+__global__ void __launch_bounds__(kStreamWarps * 32, 1) stream_kernel(StreamArgs<TV, TM> A) {
+  constexpr int V = Elem<TM>::V;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int tab[128];
+  __shared__ uint64_t bars[kStreamWarps][kStages];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const LevelGeom& g = A.g;
+  const int n = g.nloc, ld = A.ld, RC = A.rc;
+  const long long ncells = g.ncells;
+  build_local_table(g, tab);
+  // per-warp shared memory: stages, coefficients, row-group partial sums
+  unsigned char* wbase = smem_raw + (size_t)warp * (kStages * kChunkBytes + 128 * sizeof(TV) +
+                                                    128 * sizeof(double));
+  TM* stage[kStages];
+#pragma unroll
+  for (int k = 0; k < kStages; ++k) stage[k] = reinterpret_cast<TM*>(wbase + k * kChunkBytes);
+  TV* xw = reinterpret_cast<TV*>(wbase + kStages * kChunkBytes);
+  double* red = reinterpret_cast<double*>(wbase + kStages * kChunkBytes + 128 * sizeof(TV));
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kStages; ++k) mbar_init(&bar[k], 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  const long long GW = (long long)gridDim.x * kStreamWarps;
+  const long long gw = (long long)blockIdx.x * kStreamWarps + warp;
+  const int c0 = (int)(gw * A.n_own / GW), c1 = (int)((gw + 1) * A.n_own / GW);
+  if (c0 >= c1) return;
+  const int cpc = n / RC;
+  const long long nq = (long long)(c1 - c0) * cpc;
+  const uint32_t chunk_bytes = (uint32_t)(RC * ld * sizeof(TM));
+  const TM* base = A.mats + (size_t)c0 * n * ld;
+  auto issue = [&](long long q) {
+    if (lane == 0 && q < nq)
+      bulk_load(stage[q % kStages], base + (size_t)q * RC * ld, chunk_bytes, &bar[q % kStages]);
+  };
+#pragma unroll
+  for (int k = 0; k < kStages; ++k) issue(k);
+
+  const int ncv = ld / V;
+  const int R = ncv <= 32 ? 32 / ncv : 1;
+  const bool two = ncv > 32;
+  const int rg = ncv <= 32 ? lane / ncv : 0;
+  const int cv = ncv <= 32 ? lane % ncv : lane;
+  const bool active = rg < R;
+  const bool second = two && cv + 32 < ncv;
+
+  TV xn[4];
+  {
+    int cx, cy, cz;
+    cell_coords(g, A.cells[c0], cx, cy, cz);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      int l = lane + 32 * k;
+      xn[k] = l < n ? A.x[dof_packed(g, cx, cy, cz, tab[l])] : (TV)0;
+    }
+  }
+  Acc<TM> acc;
+  acc.zero();
+  bool ok = true;
+  long long q = 0;
+  for (; q < nq; ++q) {
+    const int ci = c0 + (int)(q / cpc);
+    const int part = (int)(q % cpc);
+    if (part == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int l = lane + 32 * k;
+        if (l < n) xw[l] = xn[k];
+      }
+      __syncwarp();
+      if (ci + 1 < c1) {
+        int cx, cy, cz;
+        cell_coords(g, A.cells[ci + 1], cx, cy, cz);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          int l = lane + 32 * k;
+          if (l < n) xn[k] = A.x[dof_packed(g, cx, cy, cz, tab[l])];
+        }
       }
     }
-    own_role<TV, TV>(A.g, A.ld, A.n_own, A.own_cells, A.own_mats, A.x, A.Y, b, A.nb_own,
-                     smem_raw);
-    return;
+    if (!mbar_wait(&bar[q % kStages], (uint32_t)((q / kStages) & 1))) {
+      ok = false;
+      break;
+    }
+    const TM* K = stage[q % kStages];
+    const int s0 = part * RC;
+    if (active) {
+      int r = rg;
+      for (; r + 3 * R < RC; r += 4 * R) {
+        const TV x0 = xw[s0 + r], x1 = xw[s0 + r + R], x2 = xw[s0 + r + 2 * R],
+                 x3 = xw[s0 + r + 3 * R];
+        const TM* row = K + (size_t)r * ld + cv * V;
+        const size_t st = (size_t)R * ld;
+        fma_row(acc, 0, row, x0);
+        fma_row(acc, 0, row + st, x1);
+        fma_row(acc, 0, row + 2 * st, x2);
+        fma_row(acc, 0, row + 3 * st, x3);
+        if (second) {
+          fma_row(acc, 1, row + 32 * V, x0);
+          fma_row(acc, 1, row + st + 32 * V, x1);
+          fma_row(acc, 1, row + 2 * st + 32 * V, x2);
+          fma_row(acc, 1, row + 3 * st + 32 * V, x3);
+        }
+      }
+      for (; r < RC; r += R) {
+        const TV xs = xw[s0 + r];
+        const TM* row = K + (size_t)r * ld;
+        fma_row(acc, 0, row + cv * V, xs);
+        if (second) fma_row(acc, 1, row + (cv + 32) * V, xs);
+      }
+    }
+    __syncwarp();
+    issue(q + kStages);
+    if (part == cpc - 1) {
+      const int cell = A.cells[ci];
+      if (R == 1) {
+#pragma unroll
+        for (int k = 0; k < 2 * V; ++k) {
+          int j = (k < V ? cv * V + k : (cv + 32) * V + (k - V));
+          if (k >= V && !second) break;
+          if (j < n) A.Y[(size_t)j * ncells + cell] = (TV)acc_value(acc, k);
+        }
+      } else {
+        if (active) {
+#pragma unroll
+          for (int k = 0; k < V; ++k) red[rg * ld + cv * V + k] = acc_value(acc, k);
+        }
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+          double t = 0.0;
+          for (int r = 0; r < R; ++r) t += red[r * ld + j];
+          A.Y[(size_t)j * ncells + cell] = (TV)t;
+        }
+      }
+      acc.zero();
+      __syncwarp();
+    }
   }
-  b -= A.nb_own;
-  if (b < A.nb_own_x) {
-    if constexpr (std::is_same<TV, float>::value)
-      own_role<float, float2>(A.g, A.ld, A.n_own_x, A.own_x_cells, A.own_x_mats, A.x, A.Y, b,
-                              A.nb_own_x, smem_raw);
-    return;
+  if (!ok) {
+    // expired wait: record it, then let this warp's copies in flight land
+    // before the block (and its shared memory) goes away
+    if (lane == 0) atomicExch(&g_stream_timeout, 1);
+    for (long long k = q; k < q + kStages && k < nq; ++k)
+      mbar_wait(&bar[k % kStages], (uint32_t)((k / kStages) & 1));
   }
-  b -= A.nb_own_x;
-  if (b < A.ntiles)
-    tile_role<TV>(A.g, A.tiles[b], A.sh_cells, A.sh_scale, A.sh_mats, A.x, A.Y,
-                  reinterpret_cast<TV*>(smem_raw));
+}
+
+// Stored matrices in the vector precision (FP64 path: double; mixed: float).
+template <typename TV>
+__global__ void __launch_bounds__(kOpThreads) own_kernel(CellOpArgs<TV> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int tab[128];
+  build_local_table(A.g, tab);
+  __syncthreads();
+  if constexpr (std::is_same<TV, double>::value) {
+    if ((A.ld & 3) || (reinterpret_cast<uintptr_t>(A.own_mats) & 15)) {
+      own_role_scalar(A.g, A.n_own, A.own_cells, A.own_mats, A.x, A.Y, blockIdx.x, gridDim.x,
+                      smem_raw);
+      return;
+    }
+  }
+  own_role<TV, TV>(A.g, A.ld, A.n_own, A.own_cells, A.own_mats, A.x, A.Y, blockIdx.x, gridDim.x,
+                   smem_raw, tab);
+}
+
+// Stored df32 islands of the mixed path (float vectors).
+__global__ void __launch_bounds__(kOpThreads) own_x_kernel(CellOpArgs<float> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int tab[128];
+  build_local_table(A.g, tab);
+  __syncthreads();
+  own_role<float, float2>(A.g, A.ld, A.n_own_x, A.own_x_cells, A.own_x_mats, A.x, A.Y,
+                          blockIdx.x, gridDim.x, smem_raw, tab);
+}
+
+// Shared matrices: one tile of up to 64 cells per block.
+template <typename TV, int RB>
+__global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int tab[128];
+  __shared__ int ccell[4 * kTileCells];
+  build_local_table(A.g, tab);
+  tile_role<TV, RB>(A.g, A.tiles[blockIdx.x], A.sh_cells, A.sh_scale, A.sh_mats, A.x, A.Y,
+                    reinterpret_cast<TV*>(smem_raw), tab, ccell);
 }
 
 // ---------------------------------------------------------------------------
@@ -365,38 +693,43 @@ __device__ __forceinline__ int axis_pairs(int C, int i, int& c0, int& j0, int& c
   return 1;
 }
 
+// One block row per line (f, iy, iz) of the level's DOF array, threads along
+// x: the y/z decomposition is uniform per block and the x index needs no
+// division except inside the bubble range.
 template <typename TV, int MODE>
-__global__ void gather_kernel(LevelGeom g, const TV* __restrict__ Y, const TV* __restrict__ b,
-                              TV* __restrict__ out, TV w) {
+__global__ void __launch_bounds__(128) gather_kernel(LevelGeom g, const TV* __restrict__ Y,
+                                                     const TV* __restrict__ b,
+                                                     TV* __restrict__ out, TV w) {
   const int P1 = g.p + 1;
   const long long ncells = g.ncells;
-  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < g.N;
-       I += (long long)gridDim.x * blockDim.x) {
-    const long long f = I / g.M;
-    const long long r = I - f * g.M;
-    const int ix = (int)(r % g.m[0]);
-    const long long t = r / g.m[0];
-    const int iy = (int)(t % g.m[1]);
-    const int iz = (int)(t / g.m[1]);
-    int cx0 = 0, jx0 = 0, cx1 = 0, jx1 = 0, cy0 = 0, jy0 = 0, cy1 = 0, jy1 = 0, cz0 = 0, jz0 = 0,
-        cz1 = 0, jz1 = 0;
+  const int myz = g.m[1] * g.m[2];
+  const int nlines = g.nf * myz;
+  for (int line = blockIdx.y; line < nlines; line += gridDim.y) {
+  const int f = line / myz;
+  const int rem = line - f * myz;
+  const int iy = rem % g.m[1];
+  const int iz = rem / g.m[1];
+  int cy0 = 0, jy0 = 0, cy1 = 0, jy1 = 0, cz0 = 0, jz0 = 0, cz1 = 0, jz1 = 0;
+  const int ny = g.dim > 1 ? axis_pairs(g.C[1], iy, cy0, jy0, cy1, jy1) : 1;
+  const int nz = g.dim > 2 ? axis_pairs(g.C[2], iz, cz0, jz0, cz1, jz1) : 1;
+  const long long rowbase = (long long)f * g.M + (long long)g.m[0] * (iy + (long long)g.m[1] * iz);
+  const int lf = f * g.nloc_s;
+  for (int ix = blockIdx.x * blockDim.x + threadIdx.x; ix < g.m[0]; ix += gridDim.x * blockDim.x) {
+    int cx0 = 0, jx0 = 0, cx1 = 0, jx1 = 0;
     const int nx = axis_pairs(g.C[0], ix, cx0, jx0, cx1, jx1);
-    const int ny = g.dim > 1 ? axis_pairs(g.C[1], iy, cy0, jy0, cy1, jy1) : 1;
-    const int nz = g.dim > 2 ? axis_pairs(g.C[2], iz, cz0, jz0, cz1, jz1) : 1;
     TV sum = 0;
-    const int lf = (int)f * g.nloc_s;
     for (int kz = 0; kz < nz; ++kz) {
       const int cz = kz ? cz1 : cz0, jz = kz ? jz1 : jz0;
       for (int ky = 0; ky < ny; ++ky) {
         const int cy = ky ? cy1 : cy0, jy = ky ? jy1 : jy0;
-        for (int kx = 0; kx < nx; ++kx) {
-          const int cx = kx ? cx1 : cx0, jx = kx ? jx1 : jx0;
-          const int cell = cx + g.C[0] * (cy + g.C[1] * cz);
-          const int l = lf + jx + P1 * (jy + P1 * jz);
-          sum += Y[(size_t)l * ncells + cell];
-        }
+        const int cyz = g.C[0] * (cy + g.C[1] * cz);
+        const int lyz = lf + P1 * (jy + P1 * jz);
+        const TV* Yl0 = Y + (size_t)(lyz + jx0) * ncells + cyz;
+        sum += Yl0[cx0];
+        if (nx > 1) sum += Y[(size_t)(lyz + jx1) * ncells + cyz + cx1];
       }
     }
+    const long long I = rowbase + ix;
     if (MODE == GATHER_SET)
       out[I] = sum;
     else if (MODE == GATHER_RESID)
@@ -405,6 +738,7 @@ __global__ void gather_kernel(LevelGeom g, const TV* __restrict__ Y, const TV* _
       out[I] = out[I] + w * sum;
     else
       out[I] = w * sum;
+  }
   }
 }
 
@@ -699,6 +1033,46 @@ inline int grid_for(long long n, int threads = 256, int cap = 8192) {
 
 }  // namespace
 
+template <typename TV, int RB>
+void launch_tile(const CellOpArgs<TV>& A, size_t sm_tile, cudaStream_t s) {
+  static size_t attr_set = 0;
+  // the opt-in is needed once dynamic + static shared memory exceeds 48 KB
+  if (sm_tile + 2048 > 48 * 1024 && sm_tile > attr_set) {
+    cudaFuncSetAttribute(tile_kernel<TV, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm_tile);
+    attr_set = sm_tile;
+  }
+  tile_kernel<TV, RB><<<A.ntiles, kOpThreads, sm_tile, s>>>(A);
+}
+
+// Rows per streamed chunk: the largest divisor of n whose rows fit in one
+// 8 KB stage; 0 when streaming does not pay (small matrices) or does not fit.
+int stream_rows(int n, int ld, size_t es) {
+  const size_t row = (size_t)ld * es;
+  if (n < 16 || n > 128 || row > (size_t)kChunkBytes) return 0;
+  for (int rc = n; rc >= 1; --rc)
+    if (n % rc == 0 && rc * row <= (size_t)kChunkBytes) return rc;
+  return 0;
+}
+
+template <typename TV, typename TM>
+void launch_stream(const StreamArgs<TV, TM>& S, cudaStream_t s) {
+  const size_t smem = (size_t)kStreamWarps *
+                      (kStages * kChunkBytes + 128 * sizeof(TV) + 128 * sizeof(double));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(stream_kernel<TV, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = (S.n_own + kStreamWarps - 1) / kStreamWarps;
+  if (grid > sms) grid = sms;
+  stream_kernel<TV, TM><<<grid, kStreamWarps * 32, smem, s>>>(S);
+}
+
 template <typename TV>
 void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y,
                     cudaStream_t s) {
@@ -720,23 +1094,47 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   A.sh_mats = op.sh.mats;
   auto nb = [](int n) {
     int b = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    return b > 4096 ? 4096 : b;
+    return b > kOwnBlocksCap ? kOwnBlocksCap : b;
   };
   A.nb_own = op.own.n ? nb(op.own.n) : 0;
   A.nb_own_x = op.own_x.n ? nb(op.own_x.n) : 0;
-  int grid = A.nb_own + A.nb_own_x + A.ntiles;
-  if (grid == 0) return;
-  int n = g.nloc, npad = (n + 7) & ~7;
-  size_t sm_tile = op.sh.tl.ntiles ? ((size_t)n * npad + (size_t)n * kTileCells) * sizeof(TV) : 0;
-  size_t sm_own = (size_t)kWarpsPerBlock * 128 * (sizeof(TV) + sizeof(double));
-  size_t smem = sm_tile > sm_own ? sm_tile : sm_own;
-  static size_t attr_set = 0;
-  if (smem > 48 * 1024 && smem > attr_set) {
-    cudaFuncSetAttribute(cell_op_kernel<TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr_set = smem;
+  int n = g.nloc;
+  const size_t sm_own = (size_t)kWarpsPerBlock * 128 * (sizeof(TV) + sizeof(double));
+  const int ld = op.ld;
+  if (A.nb_own) {
+    const int rc = stream_rows(n, ld, sizeof(TV));
+    const bool aligned = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(op.own.mats) & 15) == 0;
+    if (rc > 0 && aligned) {
+      StreamArgs<TV, TV> S{g, ld, rc, op.own.n, op.own.cells, static_cast<const TV*>(op.own.mats),
+                           x, Y};
+      launch_stream<TV, TV>(S, s);
+    } else {
+      own_kernel<TV><<<A.nb_own, kOpThreads, sm_own, s>>>(A);
+    }
   }
-  cell_op_kernel<TV><<<grid, kOpThreads, smem, s>>>(A);
+  if constexpr (std::is_same<TV, float>::value) {
+    if (A.nb_own_x) {
+      const int rc = stream_rows(n, ld, sizeof(float2));
+      if (rc > 0) {
+        StreamArgs<float, float2> S{g, ld, rc, op.own_x.n, op.own_x.cells,
+                                    static_cast<const float2*>(op.own_x.mats), x, Y};
+        launch_stream<float, float2>(S, s);
+      } else {
+        const size_t smx = (size_t)kWarpsPerBlock * 128 * (sizeof(float) + sizeof(double));
+        own_x_kernel<<<A.nb_own_x, kOpThreads, smx, s>>>(A);
+      }
+    }
+  }
+  if (A.ntiles) {
+    const int npad = tile_npad(n);
+    size_t sm_tile = ((size_t)n * npad + (size_t)n * kTileCells) * sizeof(TV);
+    switch (npad / 16) {
+      case 1: launch_tile<TV, 1>(A, sm_tile, s); break;
+      case 2: launch_tile<TV, 2>(A, sm_tile, s); break;
+      case 4: launch_tile<TV, 4>(A, sm_tile, s); break;
+      default: launch_tile<TV, 8>(A, sm_tile, s); break;
+    }
+  }
 }
 
 void launch_repack(int count, int n, int ld, const double* src, const int* sel, int kind,
@@ -749,13 +1147,14 @@ void launch_repack(int count, int n, int ld, const double* src, const int* sel, 
 template <typename TV>
 void launch_gather(const LevelGeom& g, int mode, const TV* Y, const TV* b, TV* out, double w,
                    cudaStream_t s) {
-  int grid = grid_for(g.N);
+  long long lines = (long long)g.nf * g.m[1] * g.m[2];
+  dim3 grid((g.m[0] + 127) / 128, (unsigned)(lines < 65535 ? lines : 65535));
   TV tw = (TV)w;
   switch (mode) {
-    case GATHER_SET: gather_kernel<TV, GATHER_SET><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
-    case GATHER_RESID: gather_kernel<TV, GATHER_RESID><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
-    case GATHER_ADD: gather_kernel<TV, GATHER_ADD><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
-    default: gather_kernel<TV, GATHER_SCALE><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
+    case GATHER_SET: gather_kernel<TV, GATHER_SET><<<grid, 128, 0, s>>>(g, Y, b, out, tw); break;
+    case GATHER_RESID: gather_kernel<TV, GATHER_RESID><<<grid, 128, 0, s>>>(g, Y, b, out, tw); break;
+    case GATHER_ADD: gather_kernel<TV, GATHER_ADD><<<grid, 128, 0, s>>>(g, Y, b, out, tw); break;
+    default: gather_kernel<TV, GATHER_SCALE><<<grid, 128, 0, s>>>(g, Y, b, out, tw); break;
   }
 }
 
@@ -848,5 +1247,17 @@ FCM_INST(double)
 FCM_INST(float)
 
 std::string cuda_msg(cudaError_t e) { return std::string(cudaGetErrorString(e)); }
+
+cudaError_t read_and_clear_timeout(int* flag, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyFromSymbolAsync(flag, g_stream_timeout, sizeof(int), 0,
+                                            cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || *flag == 0) return e;
+  const int zero = 0;
+  e = cudaMemcpyToSymbolAsync(g_stream_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
 
 }  // namespace fcm
