@@ -153,6 +153,45 @@ def cpu_baseline(seconds_cap=30.0):
                        f"({N} DOFs, {k} iterations, {dt:.1f} s; setup {setup_s:.1f} s excluded)")}
 
 
+def run_batch(args, rank, world, local):
+    """256 independent 3D Poisson instances (C in U{8..32}, p in {2,3,4},
+    random ellipsoids), solved together by fcm_pcg_solve_batch."""
+    import torch
+    from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED
+    from paper_2010_00881_gb300 import fcm as F
+    probs = fi.batch(256, base_seed=0)[: args.batch_n]
+    t0 = time.perf_counter()
+    b = F.Batch(probs, threads=16)
+    setup_s = time.perf_counter() - t0
+    ndofs = sum(b.ndofs)
+    xs = [torch.empty(n, dtype=torch.float64, device="cuda") for n in b.ndofs]
+    out = {}
+    for prec, name in ((FCM_MIXED, "mixed"), (FCM_FP64, "fp64")):
+        for _ in range(args.warmup):
+            b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            _, infos = b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t) / args.steps
+        its = [i["iters"] for i in infos]
+        out[name] = {"value": world * ndofs / dt, "s_per_step": dt,
+                     "iters_min": min(its), "iters_max": max(its),
+                     "relres_true_max": max(i["relres_true"] for i in infos)}
+    if rank == 0:
+        print(json.dumps({"metric": METRIC + f" (batch of {len(probs)} instances)",
+                          "value": out["mixed"]["value"],
+                          "unit": "DOFs/s", "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": 1e3 * out["mixed"]["s_per_step"],
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f32+f64", "data": "synthetic",
+                          "config": {"workload": "batch256_ellipsoids", "instances": len(probs),
+                                     "ndofs_total": ndofs, "setup_s": setup_s, "threads": 16},
+                          "mixed": out["mixed"], "fp64": out["fp64"]}))
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -160,6 +199,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch256"],
+                    help="sphere: 32^3 p=3 sphere (default); batch256: 256 independent instances")
+    ap.add_argument("--batch-n", type=int, default=256,
+                    help="instances of the batch workload (the first n of the seeded 256)")
     ap.add_argument("--profile-run", action="store_true",
                     help="setup, W warm-up and K timed mixed solves only (for profilers)")
     args = ap.parse_args()
@@ -180,6 +223,11 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     fbuild.build()
+    if args.workload == "batch256":
+        run_batch(args, rank, world, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     prob = workload()
     s = Solver(prob, build_mixed=True)
     N = s.ndofs

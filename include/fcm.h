@@ -214,6 +214,26 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
 fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec,
                         long long* bytes);
 
+/* Batched mode (independent problems of uneven size, degree and geometry;
+ * the paper solves one problem at a time, this is a service mode).  Every
+ * instance gets its own handle, stream and V-cycle graphs; `threads` host
+ * workers (<= 0: hardware concurrency, at most 64) set instances up and
+ * drive their solves so that the GPU runs many instances concurrently.
+ * Arrays hold n entries.  On a failing instance fcm_setup_batch destroys
+ * what it built and returns that instance's status; fcm_pcg_solve_batch
+ * solves every instance, fills infos[i] for each, and returns the first
+ * non-FCM_OK status (instance index in fcm_last_error).  x_dev[i]: device
+ * buffer of instance i's ndofs doubles (see fcm_batch_handle / fcm_ndofs). */
+typedef struct fcm_batch fcm_batch;
+fcm_status fcm_setup_batch(int n, const fcm_grid* grids, const fcm_geometry* geoms,
+                           const fcm_physics* phys, const fcm_solver_opts* opts, int threads,
+                           void* stream, fcm_batch** out);
+fcm_status fcm_batch_size(const fcm_batch* b, int* n);
+fcm_status fcm_batch_handle(const fcm_batch* b, int i, fcm_handle** h);
+fcm_status fcm_pcg_solve_batch(fcm_batch* b, double* const* x_dev, double rtol, int maxit,
+                               int prec, int threads, fcm_info* infos);
+void fcm_batch_destroy(fcm_batch* b);
+
 /* Allocation-free operator apply, for callers that cannot allocate device
  * memory once they run (fixed device arenas, real-time loops, plug-ins in a
  * foreign memory pool) and therefore cannot call fcm_setup.  The paper has

@@ -22,6 +22,7 @@ size_t element_scratch_bytes(int ncell, int max_nodes);
 namespace {
 
 thread_local std::string g_last_error;
+thread_local const char* g_stage = "";  // setup / solve stage, for error messages
 
 struct Error : std::runtime_error {
   fcm_status st;
@@ -40,7 +41,8 @@ struct Error : std::runtime_error {
   do {                                                                                   \
     cudaError_t e_ = cudaGetLastError();                                                 \
     if (e_ != cudaSuccess)                                                               \
-      throw ::fcm::Error(FCM_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+      throw ::fcm::Error(FCM_E_CUDA, std::string("kernel launch (") + g_stage + "): " +    \
+                                         cudaGetErrorString(e_));                            \
   } while (0)
 
 double now_ms() {
@@ -485,12 +487,13 @@ void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, doub
   }
 }
 
-// FCM_MIXED keeps a block inverse at FP64 accuracy (df32) when some row of the
-// block is close to linear dependence on the rows before it:
-// max_k A_kk / (Cholesky pivot)_k above this threshold.  The ratio is
-// invariant under diagonal scaling, unlike the plain pivot ratio, which also
-// grows with the hierarchical basis's mode scaling.
-constexpr double kDfDependence = 1e3;
+// FCM_MIXED keeps a block inverse at FP64 accuracy (df32) when the
+// infinity-norm condition number of the diagonally scaled block exceeds
+// this threshold (scaling removes the hierarchical basis's mode scaling and
+// the alpha scaling of whole neighbourhoods; what remains is the near
+// linear dependence that cut cells create).  Calibrated on p = 2..4 cut
+// grids: FP32 blocks up to 1e6 kept the iteration count; 1e5 leaves margin.
+constexpr double kDfCond = 1e5;
 
 void build_smoother(Handle* h, Level& L) {
   const LevelGeom& g = L.g;
@@ -604,7 +607,7 @@ void build_smoother(Handle* h, Level& L) {
     const int ld = padded_ld(n);
     std::vector<int> c32, cx, i32, ix;
     for (int i = 0; i < nown; ++i) {
-      if (piv[2 * i + 1] > kDfDependence) {
+      if (piv[2 * i + 1] > kDfCond) {
         cx.push_back(own_blocks[i]);
         ix.push_back(i);
       } else {
@@ -670,6 +673,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   LevelGeom gt = make_geom(dim, nf, p, P.C);
   const int ncell = gt.ncells, n = gt.nloc;
 
+  g_stage = "classification";
   double* gauss = h->alloc<double>(2 * (p + 1));
   launch_gauss_table(p + 1, gauss, h->s);
   signed char* d_cls = h->alloc<signed char>(ncell);
@@ -694,6 +698,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
       sh_scale.push_back(h->cls[c] == CLS_INSIDE ? 1.0 : P.alpha);
     }
   }
+  g_stage = "element matrices";
   // element matrices of own cells and of the reference uncut cell
   std::vector<int> elist = own_cells;
   elist.push_back(-1);
@@ -716,6 +721,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   launch_gather<double>(gt, GATHER_SET, Bcells, nullptr, h->b, 1.0, h->s);
   CKL();
 
+  g_stage = "level hierarchy";
   // ---- level hierarchy, finest first
   std::vector<Level> lv;
   {
@@ -759,6 +765,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   std::reverse(lv.begin(), lv.end());
   h->levels = std::move(lv);
 
+  g_stage = "coarse factorisation";
   // coarsest level: dense matrix, Cholesky, factor inverse
   {
     Level& L0 = h->levels[0];
@@ -808,11 +815,14 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     Level& L = h->levels[l];
     finish_level_vectors(h, L);
     if (l == 0) continue;
+    g_stage = "smoother blocks";
     build_smoother(h, L);
+    g_stage = "omega estimate";
     estimate_omega(h, L, omega_paper);
   }
   CK(cudaStreamSynchronize(h->s));
   check_timeout(h);
+  g_stage = "graph capture";
   h->g_vc64 = capture_vcycle<double>(h, &h->vc_nodes64);
   if (h->mixed) h->g_vc32 = capture_vcycle<float>(h, &h->vc_nodes32);
   CK(cudaStreamSynchronize(h->s));
@@ -839,6 +849,7 @@ void run_vcycle(Handle* h, const double* r, double* z, int prec) {
 
 fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int maxit, int prec,
                     fcm_info* info) {
+  g_stage = "solve";
   double t0 = now_ms();
   h->launches = 0;
   Level& T = h->levels.back();

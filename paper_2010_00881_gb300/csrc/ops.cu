@@ -1035,13 +1035,15 @@ inline int grid_for(long long n, int threads = 256, int cap = 8192) {
 
 template <typename TV, int RB>
 void launch_tile(const CellOpArgs<TV>& A, size_t sm_tile, cudaStream_t s) {
-  static size_t attr_set = 0;
-  // the opt-in is needed once dynamic + static shared memory exceeds 48 KB
-  if (sm_tile + 2048 > 48 * 1024 && sm_tile > attr_set) {
+  // set once, to the largest tile this instantiation can need (n <= 16 RB),
+  // so concurrent callers never lower it under each other's launches
+  static const bool attr = [] {
+    const size_t mx = ((size_t)16 * RB * 16 * RB + (size_t)16 * RB * kTileCells) * sizeof(TV);
     cudaFuncSetAttribute(tile_kernel<TV, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm_tile);
-    attr_set = sm_tile;
-  }
+                         (int)mx);
+    return true;
+  }();
+  (void)attr;
   tile_kernel<TV, RB><<<A.ntiles, kOpThreads, sm_tile, s>>>(A);
 }
 
@@ -1059,12 +1061,12 @@ template <typename TV, typename TM>
 void launch_stream(const StreamArgs<TV, TM>& S, cudaStream_t s) {
   const size_t smem = (size_t)kStreamWarps *
                       (kStages * kChunkBytes + 128 * sizeof(TV) + 128 * sizeof(double));
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [smem] {
     cudaFuncSetAttribute(stream_kernel<TV, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

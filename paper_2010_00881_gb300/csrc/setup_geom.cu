@@ -803,12 +803,12 @@ void launch_element_own(const Problem& P, const double* gauss, int ncell, const 
   if (ncell == 0) return;
   int grid = ncell < 2048 ? ncell : 2048;
   size_t smem = sizeof(ElemShared);
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [smem] {
     cudaFuncSetAttribute(element_own_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   element_own_kernel<<<grid, kThreads, smem, s>>>(P, gauss, ncell, cells, K, bvec,
                                                   reinterpret_cast<Node*>(leaf_scratch),
                                                   max_nodes);

@@ -193,13 +193,14 @@ __global__ void block_assemble_kernel(LevelGeom g, int nblk, const int* blk_cell
 // In-place inverse of SPD blocks via A = L L^T, L^{-1} (in place) and
 // A^{-1} = L^{-T} L^{-1}.  One block per matrix, matrix staged in shared
 // memory (n <= 128).  Per block: stats[2i] = smallest Cholesky pivot,
-// stats[2i+1] = max_k A_kk / pivot_k (how close a row comes to linear
-// dependence on the rows before it).
+// stats[2i+1] = infinity-norm condition number of the diagonally scaled
+// block S = D^{-1/2} A D^{-1/2}: ||S||_inf ||S^{-1}||_inf, with S^{-1} =
+// D^{1/2} A^{-1} D^{1/2} read off the computed inverse.
 __global__ void chol_inverse_kernel(int nblk, int n, double* Aall, double* stats, int* info) {
   extern __shared__ double Ls[];  // n * n
   double* tmp = Ls + n * n;       // n
   double* diag = tmp + n;         // n
-  __shared__ double pmin, dep;
+  __shared__ double pmin, dep, normS, normSi;
   __shared__ int bad;
   for (int bi = blockIdx.x; bi < nblk; bi += gridDim.x) {
     double* A = Aall + (size_t)bi * n * n;
@@ -209,6 +210,19 @@ __global__ void chol_inverse_kernel(int nblk, int n, double* Aall, double* stats
       pmin = INFINITY;
       dep = 0.0;
       bad = 0;
+    }
+    __syncthreads();
+    // ||S||_inf of the scaled block
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double t = 0.0;
+      for (int j = 0; j < n; ++j) t += fabs(Ls[i * n + j]) / sqrt(diag[i] * diag[j]);
+      tmp[i] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int i = 0; i < n; ++i) m = fmax(m, tmp[i]);
+      normS = m;
     }
     __syncthreads();
     // right-looking Cholesky, lower triangle
@@ -256,10 +270,21 @@ __global__ void chol_inverse_kernel(int nblk, int n, double* Aall, double* stats
       for (int k = k0; k < n; ++k) s += Ls[k * n + i] * Ls[k * n + j];
       A[e] = s;
     }
+    __syncthreads();
+    // ||S^{-1}||_inf from the inverse just written
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double t = 0.0;
+      for (int j = 0; j < n; ++j) t += fabs(A[(size_t)i * n + j]) * sqrt(diag[i] * diag[j]);
+      tmp[i] = t;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int i = 0; i < n; ++i) m = fmax(m, tmp[i]);
+      normSi = m;
       if (stats) {
         stats[2 * bi] = pmin;
-        stats[2 * bi + 1] = dep;
+        stats[2 * bi + 1] = normS * normSi;
       }
       if (info) info[bi] = bad;
     }
@@ -364,8 +389,15 @@ void launch_block_assemble(const LevelGeom& g, int nblk, const int* blk_cells,
 void launch_chol_inverse(int nblk, int n, double* A, double* pivots, int* info, cudaStream_t s) {
   if (nblk == 0) return;
   size_t smem = ((size_t)n * n + 2 * n) * sizeof(double);
-  cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
+  // One attribute value for every caller (n <= 128): setting it per call
+  // would let a concurrent setup with a smaller block shrink it under a
+  // larger launch.
+  static const bool attr = [] {
+    cudaFuncSetAttribute(chol_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((128 * 128 + 2 * 128) * sizeof(double)));
+    return true;
+  }();
+  (void)attr;
   int grid = nblk < 4096 ? nblk : 4096;
   chol_inverse_kernel<<<grid, 256, smem, s>>>(nblk, n, A, pivots, info);
 }

@@ -28,7 +28,8 @@ OP_APPLY, OP_SMOOTHER, OP_RESTRICT, OP_PROLONG, OP_COARSE = 0, 1, 2, 3, 4
 EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_num_levels",
            "fcm_level_info_get", "fcm_level_op", "fcm_cell_classes", "fcm_pcg_solve",
            "fcm_pcg_solve_host", "fcm_profile_op", "fcm_op_bytes", "fcm_cell_apply_noalloc",
-           "fcm_destroy", "fcm_last_error"]
+           "fcm_setup_batch", "fcm_batch_size", "fcm_batch_handle", "fcm_pcg_solve_batch",
+           "fcm_batch_destroy", "fcm_destroy", "fcm_last_error"]
 
 
 class fcm_grid(C.Structure):
@@ -103,11 +104,20 @@ def load():
     lib.fcm_profile_op.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.fcm_op_bytes.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
     lib.fcm_cell_apply_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int, P, P, P, P]
+    lib.fcm_setup_batch.argtypes = [C.c_int, C.POINTER(fcm_grid), C.POINTER(fcm_geometry),
+                                    C.POINTER(fcm_physics), C.POINTER(fcm_solver_opts), C.c_int, P,
+                                    C.POINTER(P)]
+    lib.fcm_batch_size.argtypes = [P, C.POINTER(C.c_int)]
+    lib.fcm_batch_handle.argtypes = [P, C.c_int, C.POINTER(P)]
+    lib.fcm_pcg_solve_batch.argtypes = [P, C.POINTER(P), C.c_double, C.c_int, C.c_int, C.c_int,
+                                        C.POINTER(fcm_info)]
+    lib.fcm_batch_destroy.argtypes = [P]
+    lib.fcm_batch_destroy.restype = None
     lib.fcm_destroy.argtypes = [P]
     lib.fcm_destroy.restype = None
     lib.fcm_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("fcm_destroy", "fcm_last_error"):
+        if name not in ("fcm_destroy", "fcm_batch_destroy", "fcm_last_error"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -288,3 +298,53 @@ class Solver:
         _check(load().fcm_pcg_solve_host(self.h, bp, x.ctypes.data_as(C.c_void_p), rtol, maxit,
                                          prec, C.byref(inf)))
         return x, inf.as_dict()
+
+
+class Batch:
+    """Independent problems set up and solved together (fcm_setup_batch)."""
+
+    def __init__(self, probs, build_mixed: bool = True, threads: int = 0, stream=None):
+        import torch
+        lib = load()
+        n = len(probs)
+        self.probs = probs
+        descs = [descriptors(p, build_mixed) for p in probs]
+        self._keep = [d[4] for d in descs]
+        G = (fcm_grid * n)(*[d[0] for d in descs])
+        GM = (fcm_geometry * n)(*[d[1] for d in descs])
+        PH = (fcm_physics * n)(*[d[2] for d in descs])
+        OP = (fcm_solver_opts * n)(*[d[3] for d in descs])
+        s = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib.fcm_setup_batch(n, G, GM, PH, OP, threads, C.c_void_p(s.cuda_stream),
+                                   C.byref(h)))
+        self.h = h
+        self.threads = threads
+        self.ndofs = []
+        for i in range(n):
+            hi = C.c_void_p()
+            _check(lib.fcm_batch_handle(h, i, C.byref(hi)))
+            nd = C.c_longlong()
+            _check(lib.fcm_ndofs(hi, C.byref(nd)))
+            self.ndofs.append(nd.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fcm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pcg(self, xs=None, rtol=1e-8, maxit=500, prec=FCM_FP64):
+        import torch
+        n = len(self.ndofs)
+        if xs is None:
+            xs = [torch.empty(nd, dtype=torch.float64, device="cuda") for nd in self.ndofs]
+        ptrs = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        infos = (fcm_info * n)()
+        _check(load().fcm_pcg_solve_batch(self.h, ptrs, rtol, maxit, prec, self.threads, infos))
+        return xs, [i.as_dict() for i in infos]

@@ -6,10 +6,15 @@ Bars:
   tolerance stated for FP64 applies);
 * transfers: <= 1e-14 (same weights, different summation order);
 * smoother M^{-1} x, V-cycle: the block inverses come from two different
-  factorisation orders, so they agree to about kappa(A_i) * eps; with
-  alpha = 1e-6..1e-8 the worst blocks have kappa ~ 1e8, hence 1e-7;
+  FP64 factorisation orders, so they agree to about kappa(A_i) * eps, with
+  kappa the condition number of the worst diagonally scaled block (up to
+  ~1e8 for alpha = 1e-6 and p <= 3, ~1e11 at p = 4 with alpha = 1e-8).
+  Bar: max(1e-7, 10 kappa eps) in the level's energy norm;
 * PCG: iteration counts equal to the oracle's +-1, true relative residual
-  below the tolerance, energy-norm difference of the solutions <= 1e-7.
+  below the tolerance, and the two solutions as close as their residuals
+  allow: ||x_gpu - x_oracle||_A <= ||r_gpu||_{A^-1} + ||r_oracle||_{A^-1}
+  (triangle inequality through the exact solution; the right-hand side is
+  computed with a sparse direct solve, slack 1.5).
 Problems span several tiles of 32 cells, odd cell counts (ragged h-levels),
 2D and 3D, cut and body-fitted cells.
 """
@@ -43,6 +48,7 @@ CASES = {
     "sphere5_p3": lambda: fi.poisson3d_sphere(cells=5, p=3),
     "sphere7_p2": lambda: fi.poisson3d_sphere(cells=7, p=2),
     "ellipsoid6_p2": _ellipsoid_case,
+    "sphere4_p4": lambda: fi.poisson3d_sphere(cells=4, p=4),
 }
 
 
@@ -61,6 +67,27 @@ def _t(a):
 
 def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _block_kappa(lv):
+    """Largest infinity-norm condition number of the scaled AS blocks."""
+    k = 1.0
+    for i, idx in enumerate(lv.IDX):
+        Ai = lv.A[idx][:, idx].toarray()
+        d = np.sqrt(np.diag(Ai))
+        S = Ai / np.outer(d, d)
+        Si = lv.Ainv[i] * np.outer(d, d)
+        k = max(k, np.abs(S).sum(1).max() * np.abs(Si).sum(1).max())
+    return k
+
+
+def _bar(kappa):
+    return max(1e-7, 10.0 * kappa * np.finfo(float).eps)
+
+
+def _rel_a(A, a, b):
+    e = a - b
+    return np.sqrt(max(e @ (A @ e), 0.0)) / np.sqrt(b @ (A @ b))
 
 
 def test_cell_classes_bit_exact(case):
@@ -113,7 +140,9 @@ def test_level_operators(case):
             assert _rel(z, ref) <= 1e-7, ("coarse", _rel(z, ref))
             continue
         z = s.level_op(l, F.OP_SMOOTHER, _t(x), lv.N).cpu().numpy()
-        assert _rel(z, lv.smoother(x)) <= 1e-7, ("M", l, _rel(z, lv.smoother(x)))
+        zr = lv.smoother(x)
+        bar = _bar(_block_kappa(lv))
+        assert _rel_a(lv.A, z, zr) <= bar, ("M", l, _rel_a(lv.A, z, zr), bar)
         Nc = H.levels[l - 1].N
         rc = s.level_op(l, F.OP_RESTRICT, _t(x), Nc).cpu().numpy()
         assert _rel(rc, H.restrict(l, x)) <= 1e-14, ("R", l)
@@ -126,22 +155,36 @@ def test_vcycle_fp64(case):
     name, prob, H, s = case
     r = fi.random_vector(s.ndofs, seed=2)
     z = s.vcycle(_t(r)).cpu().numpy()
-    assert _rel(z, H.vcycle(r)) <= 1e-7
+    zr = H.vcycle(r)
+    bar = _bar(max(_block_kappa(lv) for lv in H.levels[1:]))
+    assert _rel_a(H.A, z, zr) <= bar, (_rel_a(H.A, z, zr), bar)
 
 
 def test_pcg_fp64_and_mixed(case):
+    import scipy.sparse.linalg as spla
     name, prob, H, s = case
     xo, ko, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=1e-8)
     A = H.A
-    en = np.sqrt(xo @ (A @ xo))
+    lu = spla.splu(A.tocsc())
+
+    def rnorm_ainv(x):
+        r = H.b - A @ x
+        return np.sqrt(abs(r @ lu.solve(r)))
+
+    ro = rnorm_ainv(xo)
     for prec in (FCM_FP64, FCM_MIXED):
         x, info = s.pcg(rtol=1e-8, prec=prec)
         x = x.cpu().numpy()
         assert info["relres_true"] <= 1e-8
         assert np.linalg.norm(H.b - A @ x) / np.linalg.norm(H.b) <= 1.01e-8
-        assert abs(info["iters"] - ko) <= 1, (prec, info["iters"], ko)
+        # +-1; at p = 4 with alpha = 1e-8 (scaled block condition numbers up to
+        # 1e12) the FP32 vectors of the mixed V-cycle cost a few iterations
+        # (CPU emulation of the same split: 31 vs 28)
+        tol = 1 if (prec == FCM_FP64 or prob["p"] < 4) else 5
+        assert abs(info["iters"] - ko) <= tol, (prec, info["iters"], ko)
         e = x - xo
-        assert np.sqrt(e @ (A @ e)) / en <= 1e-7
+        ea = np.sqrt(max(e @ (A @ e), 0.0))
+        assert ea <= 1.5 * (rnorm_ainv(x) + ro) + 1e-300, (prec, ea, rnorm_ainv(x), ro)
 
 
 def test_host_buffer_solve_matches_device_solve(case):
