@@ -347,9 +347,9 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   P.dim = grid->dim;
   P.p = grid->p;
   P.pde = phys->pde;
-  if (P.pde != FCM_PDE_POISSON)
-    throw Error(FCM_E_UNSUPPORTED, "only the Poisson problem is implemented");
-  P.nf = 1;
+  if (P.pde != FCM_PDE_POISSON && P.pde != FCM_PDE_ELASTICITY)
+    throw Error(FCM_E_INVALID, "unknown pde");
+  P.nf = P.pde == FCM_PDE_ELASTICITY ? P.dim : 1;
   for (int a = 0; a < 3; ++a) {
     if (a < P.dim) {
       if (grid->cells[a] < 1 || grid->cells[a] > 4096)
@@ -364,9 +364,10 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
       P.C[a] = 1;
     }
   }
-  int nloc = 1;
+  int nloc = P.nf;
   for (int a = 0; a < P.dim; ++a) nloc *= P.p + 1;
-  if (nloc > 128) throw Error(FCM_E_UNSUPPORTED, "cell size (p+1)^d must be <= 128");
+  if (nloc > 128)
+    throw Error(FCM_E_UNSUPPORTED, "DOFs per cell (fields x (p+1)^d) must be <= 128");
   P.geom_kind = geom->kind;
   if (geom->kind < FCM_GEOM_NONE || geom->kind > FCM_GEOM_ELLIPSOID)
     throw Error(FCM_E_INVALID, "unknown geometry kind");
@@ -391,7 +392,9 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   P.alpha = phys->alpha;
   P.beta = phys->beta;
   if (!(P.alpha > 0.0) || !(P.alpha <= 1.0)) throw Error(FCM_E_INVALID, "alpha must be in (0, 1]");
-  if (!(P.kappa > 0.0)) throw Error(FCM_E_INVALID, "kappa must be > 0");
+  if (P.pde == FCM_PDE_POISSON && !(P.kappa > 0.0)) throw Error(FCM_E_INVALID, "kappa must be > 0");
+  if (P.pde == FCM_PDE_ELASTICITY && (!(P.E > 0.0) || !(P.nu > -1.0) || !(P.nu < 0.5)))
+    throw Error(FCM_E_INVALID, "elasticity needs E > 0 and -1 < nu < 0.5");
   if (!(P.beta >= 0.0)) throw Error(FCM_E_INVALID, "beta must be >= 0");
   P.source = phys->source;
   P.f0 = phys->f0;
@@ -691,6 +694,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   for (int c = 0; c < ncell; ++c) {
     bool own = h->cls[c] == CLS_CUT;
     if (P.dirichlet == FCM_DIR_FACES && (faces[c] & P.dir_faces)) own = true;
+    if (P.traction_face >= 0 && (faces[c] >> P.traction_face) & 1u) own = true;
     if (own)
       own_cells.push_back(c);
     else {

@@ -217,7 +217,7 @@ __device__ void basis1d(int p, double xi, double* N, double* dN) {
 }
 
 __device__ double source_f(const Problem& P, const double* x) {
-  if (P.source == FCM_SRC_CONST) return P.f0;
+  if (P.pde == FCM_PDE_ELASTICITY || P.source == FCM_SRC_CONST) return P.f0;
   if (P.source == FCM_SRC_SIN3) {
     double u = 1.0;
     for (int a = 0; a < P.dim; ++a) u = u * sin(M_PI * x[a]);
@@ -228,7 +228,7 @@ __device__ double source_f(const Problem& P, const double* x) {
 }
 
 __device__ double dirichlet_g(const Problem& P, const double* x) {
-  if (P.g == FCM_G_ZERO) return 0.0;
+  if (P.pde == FCM_PDE_ELASTICITY || P.g == FCM_G_ZERO) return 0.0;
   if (P.g == FCM_G_SIN3) {
     double u = 1.0;
     for (int a = 0; a < P.dim; ++a) u = u * sin(M_PI * x[a]);
@@ -310,17 +310,56 @@ __device__ void accumulate_stiffness(const PointBatch& B, int np, int dim, int P
   }
 }
 
-// K_ij += sum_q w_q N_i N_j (surface / face penalty mass)
-__device__ void accumulate_mass(const PointBatch& B, int np, int dim, int P1, PairSet& ps) {
+// K_IJ += sum_q w_q N_i N_j (surface / face penalty mass); for vector fields
+// (I = f ns + i) only pairs of the same field couple.
+__device__ void accumulate_mass(const PointBatch& B, int np, int dim, int P1, int ns,
+                                PairSet& ps) {
   for (int k = 0; k < ps.cnt; ++k) {
+    const int I = ps.i[k], J = ps.j[k];
+    if (I / ns != J / ns) continue;
     int ia[3], jb[3];
-    mode_axes(ps.i[k], P1, dim, ia);
-    mode_axes(ps.j[k], P1, dim, jb);
+    mode_axes(I % ns, P1, dim, ia);
+    mode_axes(J % ns, P1, dim, jb);
     double s = 0.0;
     for (int q = 0; q < np; ++q) {
       double v = 1.0;
       for (int a = 0; a < dim; ++a) v *= B.T[q][a][0][ia[a]] * B.T[q][a][0][jb[a]];
       s += B.w[q] * v;
+    }
+    ps.acc[k] += s;
+  }
+}
+
+// Isotropic linear elasticity, K_{fi,gj} += sum_q w_q (lambda N_i,f N_j,g +
+// mu N_i,g N_j,f + mu delta_fg grad N_i . grad N_j): the entries of
+// B^T C B for the Voigt strain operator B and isotropic C.
+__device__ void accumulate_elastic(const PointBatch& B, int np, int dim, int P1, int ns,
+                                   double lam, double mu, PairSet& ps) {
+  for (int k = 0; k < ps.cnt; ++k) {
+    const int I = ps.i[k], J = ps.j[k];
+    const int f = I / ns, g = J / ns;
+    int ia[3], jb[3];
+    mode_axes(I % ns, P1, dim, ia);
+    mode_axes(J % ns, P1, dim, jb);
+    double s = 0.0;
+    for (int q = 0; q < np; ++q) {
+      double gi[3], gj[3];
+      for (int a = 0; a < dim; ++a) {
+        double vi = 1.0, vj = 1.0;
+        for (int b = 0; b < dim; ++b) {
+          vi *= B.T[q][b][a == b ? 1 : 0][ia[b]];
+          vj *= B.T[q][b][a == b ? 1 : 0][jb[b]];
+        }
+        gi[a] = vi;
+        gj[a] = vj;
+      }
+      double t = lam * gi[f] * gj[g] + mu * gi[g] * gj[f];
+      if (f == g) {
+        double d = 0.0;
+        for (int a = 0; a < dim; ++a) d += gi[a] * gj[a];
+        t += mu * d;
+      }
+      s += B.w[q] * t;
     }
     ps.acc[k] += s;
   }
@@ -429,16 +468,22 @@ struct ElemShared {
 };
 
 // One CTA per own cell: volume terms on the space-tree leaves, penalty on
-// the marching-simplex surface of cut leaves, box-face penalty.  Poisson.
+// the marching-simplex surface of cut leaves, box-face penalty and traction.
+// Poisson (n = (p+1)^d) or isotropic elasticity (n = d (p+1)^d, fields
+// stacked).
 __global__ void __launch_bounds__(kThreads) element_own_kernel(
     Problem P, const double* gauss, int ncell, const int* cells, double* Kout, double* bout,
     Node* scratch, int max_nodes) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ElemShared& S = *reinterpret_cast<ElemShared*>(smem_raw);
   const int dim = P.dim, p = P.p, P1 = p + 1;
-  int n = 1;
-  for (int a = 0; a < dim; ++a) n *= P1;
+  int ns = 1;
+  for (int a = 0; a < dim; ++a) ns *= P1;
+  const int n = P.nf * ns;
   const int npairs = n * (n + 1) / 2;
+  const bool elastic = P.pde == FCM_PDE_ELASTICITY;
+  const double lam = P.E * P.nu / ((1.0 + P.nu) * (1.0 - 2.0 * P.nu));
+  const double mu = P.E / (2.0 * (1.0 + P.nu));
   Geo G{P.geom_kind, dim, P.n_gparams, P.d_gparams};
   const int nq1 = P1;  // points per axis
   int Qleaf = 1;
@@ -581,15 +626,18 @@ __global__ void __launch_bounds__(kThreads) element_own_kernel(
         __syncthreads();
         batch_tables(S.B, np, dim, p, S.x0, S.x1);
         __syncthreads();
-        accumulate_stiffness(S.B, np, dim, P1, P.kappa, ps);
+        if (elastic)
+          accumulate_elastic(S.B, np, dim, P1, ns, lam, mu, ps);
+        else
+          accumulate_stiffness(S.B, np, dim, P1, P.kappa, ps);
         double bl[4] = {0, 0, 0, 0};
         {
-          // load with the same tables
+          // load with the same tables (every field gets the same body load)
           for (int k = 0; k < 4; ++k) {
             int i = threadIdx.x + k * blockDim.x;
             if (i >= n) break;
             int ia[3];
-            mode_axes(i, P1, dim, ia);
+            mode_axes(i % ns, P1, dim, ia);
             double s = 0.0;
             for (int q = 0; q < np; ++q) {
               double v = 1.0;
@@ -645,12 +693,12 @@ __global__ void __launch_bounds__(kThreads) element_own_kernel(
           __syncthreads();
           batch_tables(S.B, ppp, dim, p, S.x0, S.x1);
           __syncthreads();
-          accumulate_mass(S.B, ppp, dim, P1, ps);
+          accumulate_mass(S.B, ppp, dim, P1, ns, ps);
           for (int k = 0; k < 4; ++k) {
             int i = threadIdx.x + k * blockDim.x;
             if (i >= n) break;
             int ia[3];
-            mode_axes(i, P1, dim, ia);
+            mode_axes(i % ns, P1, dim, ia);
             double s = 0.0;
             for (int q = 0; q < ppp; ++q) {
               double v = 1.0;
@@ -663,17 +711,18 @@ __global__ void __launch_bounds__(kThreads) element_own_kernel(
         }
       }
     }
-    // Dirichlet box faces (penalty)
-    if (!ref && P.dirichlet == FCM_DIR_FACES) {
+    // box faces: Dirichlet penalty (K and b) and traction (b only)
+    if (!ref) {
       int cc[3] = {cx, cy, cz};
       for (int face = 0; face < 2 * dim; ++face) {
         int a = face / 2, sd = face % 2;
         bool on = sd == 0 ? cc[a] == 0 : cc[a] == P.C[a] - 1;
-        if (!on || !((P.dir_faces >> face) & 1u)) continue;
+        const bool dir = P.dirichlet == FCM_DIR_FACES && ((P.dir_faces >> face) & 1u);
+        const bool tra = P.traction_face == face;
+        if (!on || (!dir && !tra)) continue;
         int nfp = 1;
         for (int b = 0; b < dim - 1; ++b) nfp *= P1;
         for (int t = threadIdx.x; t < nfp; t += blockDim.x) {
-          int k = 0;
           double w = 1.0;
           int rem = t;
           for (int b = 0; b < dim; ++b) {
@@ -687,27 +736,34 @@ __global__ void __launch_bounds__(kThreads) element_own_kernel(
             double hd = 0.5 * (S.x1[b] - S.x0[b]);
             S.B.x[t][b] = mid + hd * S.gauss[ib];
             w = w * (hd * S.gauss[P1 + ib]);
-            ++k;
           }
-          S.B.w[t] = P.beta * w;
+          S.B.w[t] = w;
           S.B.fg[t] = dirichlet_g(P, S.B.x[t]);
         }
         __syncthreads();
         batch_tables(S.B, nfp, dim, p, S.x0, S.x1);
         __syncthreads();
-        accumulate_mass(S.B, nfp, dim, P1, ps);
+        if (dir) {
+          for (int t = threadIdx.x; t < nfp; t += blockDim.x) S.B.w[t] *= P.beta;
+          __syncthreads();
+          accumulate_mass(S.B, nfp, dim, P1, ns, ps);
+        }
         for (int k = 0; k < 4; ++k) {
           int i = threadIdx.x + k * blockDim.x;
           if (i >= n) break;
           int ia[3];
-          mode_axes(i, P1, dim, ia);
-          double s = 0.0;
+          mode_axes(i % ns, P1, dim, ia);
+          const int fld = i / ns;
+          double sdir = 0.0, stra = 0.0;
           for (int q = 0; q < nfp; ++q) {
             double v = 1.0;
             for (int b = 0; b < dim; ++b) v *= S.B.T[q][b][0][ia[b]];
-            s += S.B.w[q] * S.B.fg[q] * v;
+            sdir += S.B.w[q] * S.B.fg[q] * v;
+            stra += S.B.w[q] * v;
           }
-          bacc[k] += s;
+          if (dir) bacc[k] += sdir;
+          // traction: int t_f N_i over the face (w not scaled by beta then)
+          if (tra && !dir) bacc[k] += P.traction[fld] * stra;
         }
         __syncthreads();
       }
@@ -732,9 +788,10 @@ __global__ void __launch_bounds__(kThreads) element_own_kernel(
 __global__ void load_uncut_kernel(Problem P, const double* gauss, int ncell, const int* cells,
                                   const signed char* cls, double* Bcells) {
   const int dim = P.dim, p = P.p, P1 = p + 1;
-  int n = 1;
-  for (int a = 0; a < dim; ++a) n *= P1;
-  int Q = n;
+  int ns = 1;
+  for (int a = 0; a < dim; ++a) ns *= P1;
+  const int n = P.nf * ns;
+  int Q = ns;
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -751,7 +808,7 @@ __global__ void load_uncut_kernel(Problem P, const double* gauss, int ncell, con
     }
     for (int i = lane; i < n; i += 32) {
       int ia[3];
-      mode_axes(i, P1, dim, ia);
+      mode_axes(i % ns, P1, dim, ia);
       double s = 0.0;
       for (int q = 0; q < Q; ++q) {
         int qa[3];

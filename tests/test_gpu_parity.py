@@ -49,6 +49,8 @@ CASES = {
     "sphere7_p2": lambda: fi.poisson3d_sphere(cells=7, p=2),
     "ellipsoid6_p2": _ellipsoid_case,
     "sphere4_p4": lambda: fi.poisson3d_sphere(cells=4, p=4),
+    "elastic4_p2": lambda: fi.elasticity3d_voids(cells=4, p=2, n_voids=3, seed=1),
+    "elastic5_p1": lambda: fi.elasticity3d_voids(cells=5, p=1, n_voids=4, seed=2),
 }
 
 
