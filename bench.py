@@ -199,8 +199,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch256"],
-                    help="sphere: 32^3 p=3 sphere (default); batch256: 256 independent instances")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch256", "elasticity64"],
+                    help="sphere: 32^3 p=3 sphere (default); batch256: independent instances; "
+                         "elasticity64: 64^3 block with 64 voids, p = 2")
     ap.add_argument("--batch-n", type=int, default=256,
                     help="instances of the batch workload (the first n of the seeded 256)")
     ap.add_argument("--profile-run", action="store_true",
@@ -228,7 +229,8 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    prob = workload()
+    prob = workload() if args.workload == "sphere" else fi.elasticity3d_voids(cells=64, p=2)
+    wl_name = WORKLOAD if args.workload == "sphere" else "elasticity3d_voids_64^3_p2"
     s = Solver(prob, build_mixed=True)
     N = s.ndofs
     dev = torch.device("cuda", local)
@@ -328,7 +330,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "ndofs": N, "rtol": RTOL,
+            "config": {"workload": wl_name, "ndofs": N, "rtol": RTOL,
                        "precision": "mixed: FP32 V-cycle, FP64 cut-cell matrices and "
                                     "ill-conditioned block inverses, FP64 flexible CG",
                        "l2": "256 MB buffer written between timed solves",
@@ -352,7 +354,7 @@ def main():
                         "omega": round(lv["omega"], 5)} for lv in levels],
             "clocks": clk,
         }
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == "sphere":
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out))
     s.close()
