@@ -297,96 +297,25 @@ __host__ __device__ inline int tile_npad(int n) {
   return p2;
 }
 
-template <typename TV, int RB>
-__device__ void tile_role(const LevelGeom& g, const int4 tile, const int* cells, const TV* scale,
-                          const TV* mats, const TV* __restrict__ x, TV* __restrict__ Y,
-                          TV* smem, const int* tab, int* ccell) {
-  const int n = g.nloc;
-  constexpr int npad = 16 * RB;
-  constexpr int lgp = RB == 1 ? 4 : RB == 2 ? 5 : RB == 4 ? 6 : 7;
-  TV* Ks = smem;                 // n x npad, row k = column k (K symmetric)
-  TV* Xs = smem + n * npad;      // n x 64
-  const int cnt = tile.z;
-  // cell ids and coordinates of the tile, once
-  if (threadIdx.x < kTileCells) {
-    int c = threadIdx.x;
-    int cell = c < cnt ? cells[tile.y + c] : 0;
-    int cx, cy, cz;
-    cell_coords(g, cell, cx, cy, cz);
-    ccell[c] = cell;
-    ccell[kTileCells + c] = cx;
-    ccell[2 * kTileCells + c] = cy;
-    ccell[3 * kTileCells + c] = cz;
-  }
-  const TV* K = mats + (size_t)tile.x * n * n;
-  for (int e = threadIdx.x; e < n * npad; e += blockDim.x) {
-    int i = e >> lgp, j = e & (npad - 1);
-    Ks[e] = j < n ? K[(size_t)i * n + j] : (TV)0;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
-    int k = e >> 6, c = e & (kTileCells - 1);
-    TV v = 0;
-    if (c < cnt)
-      v = x[dof_packed(g, ccell[kTileCells + c], ccell[2 * kTileCells + c],
-                       ccell[3 * kTileCells + c], tab[k])];
-    Xs[e] = v;
-  }
-  __syncthreads();
-  const int cg = threadIdx.x & 15;
-  const int rg = threadIdx.x >> 4;
-  const int i0 = rg * RB;
-  TV acc[RB][4];
-#pragma unroll
-  for (int r = 0; r < RB; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0;
-  if (i0 < n) {
-#pragma unroll 2
-    for (int k = 0; k < n; ++k) {
-      TV xv[4];
-      const TV* xr = Xs + k * kTileCells + 4 * cg;
-      TV kv[RB];
-      const TV* kr = Ks + k * npad + i0;
-      if constexpr (std::is_same<TV, float>::value) {
-        float4 t = *reinterpret_cast<const float4*>(xr);
-        xv[0] = t.x; xv[1] = t.y; xv[2] = t.z; xv[3] = t.w;
-        if constexpr (RB >= 4) {
-#pragma unroll
-          for (int r4 = 0; r4 < RB / 4; ++r4) {
-            float4 u = *reinterpret_cast<const float4*>(kr + 4 * r4);
-            kv[4 * r4] = u.x; kv[4 * r4 + 1] = u.y; kv[4 * r4 + 2] = u.z; kv[4 * r4 + 3] = u.w;
-          }
-        } else {
-#pragma unroll
-          for (int r = 0; r < RB; ++r) kv[r] = kr[r];
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) xv[c] = xr[c];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) kv[r] = kr[r];
-      }
-#pragma unroll
-      for (int r = 0; r < RB; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] += kv[r] * xv[c];
-    }
-  }
-  const long long ncells = g.ncells;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int cc = 4 * cg + c;
-    if (cc < cnt) {
-      const int cell = ccell[cc];
-      const TV sc = scale[tile.y + cc];
-#pragma unroll
-      for (int r = 0; r < RB; ++r) {
-        const int i = i0 + r;
-        if (i < n) Y[(size_t)i * ncells + cell] = sc * acc[r][c];
-      }
-    }
-  }
+__device__ __forceinline__ uint32_t smem_addr32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async_4(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr32(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_addr32(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
 }
 
 template <typename TV>
@@ -645,6 +574,125 @@ __global__ void __launch_bounds__(kOpThreads) own_kernel(CellOpArgs<TV> A) {
                    smem_raw, tab);
 }
 
+// Small stored matrices (n <= 16: the Q1 levels, 2D low degree): one thread
+// per cell, coefficients and N accumulators in registers, rows read as
+// 16-byte vectors of the padded layout (row s = column s by symmetry).
+template <typename TM>
+struct SmallAcc;
+template <>
+struct SmallAcc<float> {
+  float v[16];
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = 0.f;
+  }
+  __device__ double get(int k) const { return v[k]; }
+};
+template <>
+struct SmallAcc<double> {
+  double v[16];
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = 0.0;
+  }
+  __device__ double get(int k) const { return v[k]; }
+};
+template <>
+struct SmallAcc<float2> {
+  float s[16], c[16];
+  __device__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s[k] = c[k] = 0.f;
+  }
+  __device__ double get(int k) const { return (double)s[k] + (double)c[k]; }
+};
+
+template <int N, typename TV>
+__device__ __forceinline__ void small_row(SmallAcc<float>& a, const float* row, TV xs) {
+  constexpr int LD = (N + 3) & ~3;
+#pragma unroll
+  for (int v = 0; v < LD / 4; ++v) {
+    float4 t = *reinterpret_cast<const float4*>(row + 4 * v);
+    if (4 * v + 0 < N) a.v[4 * v + 0] += t.x * xs;
+    if (4 * v + 1 < N) a.v[4 * v + 1] += t.y * xs;
+    if (4 * v + 2 < N) a.v[4 * v + 2] += t.z * xs;
+    if (4 * v + 3 < N) a.v[4 * v + 3] += t.w * xs;
+  }
+}
+template <int N, typename TV>
+__device__ __forceinline__ void small_row(SmallAcc<double>& a, const double* row, TV xs) {
+  constexpr int LD = (N + 3) & ~3;
+#pragma unroll
+  for (int v = 0; v < LD / 2; ++v) {
+    double2 t = *reinterpret_cast<const double2*>(row + 2 * v);
+    if (2 * v + 0 < N) a.v[2 * v + 0] += t.x * xs;
+    if (2 * v + 1 < N) a.v[2 * v + 1] += t.y * xs;
+  }
+}
+template <int N, typename TV>
+__device__ __forceinline__ void small_row(SmallAcc<float2>& a, const float2* row, TV xs) {
+  constexpr int LD = (N + 3) & ~3;
+#pragma unroll
+  for (int v = 0; v < LD / 2; ++v) {
+    float4 t = *reinterpret_cast<const float4*>(row + 2 * v);
+    if (2 * v + 0 < N) df_term(a.s[2 * v + 0], a.c[2 * v + 0], t.x, t.y, xs);
+    if (2 * v + 1 < N) df_term(a.s[2 * v + 1], a.c[2 * v + 1], t.z, t.w, xs);
+  }
+}
+
+template <int N, typename TV, typename TM>
+__global__ void __launch_bounds__(kOpThreads) small_kernel(LevelGeom g, int n_own,
+                                                           const int* __restrict__ cells,
+                                                           const TM* __restrict__ mats,
+                                                           const TV* __restrict__ x,
+                                                           TV* __restrict__ Y) {
+  constexpr int LD = (N + 3) & ~3;
+  __shared__ int tab[128];
+  build_local_table(g, tab);
+  __syncthreads();
+  const long long ncells = g.ncells;
+  for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_own;
+       ci += gridDim.x * blockDim.x) {
+    const int cell = cells[ci];
+    int cx, cy, cz;
+    cell_coords(g, cell, cx, cy, cz);
+    TV xv[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) xv[j] = x[dof_packed(g, cx, cy, cz, tab[j])];
+    SmallAcc<TM> acc;
+    acc.zero();
+    const TM* K = mats + (size_t)ci * N * LD;
+#pragma unroll
+    for (int r = 0; r < N; ++r) small_row<N, TV>(acc, K + r * LD, xv[r]);
+#pragma unroll
+    for (int j = 0; j < N; ++j) Y[(size_t)j * ncells + cell] = (TV)acc.get(j);
+  }
+}
+
+template <int N, typename TV, typename TM>
+void launch_small(const LevelGeom& g, int n_own, const int* cells, const TM* mats, const TV* x,
+                  TV* Y, cudaStream_t s) {
+  int blocks = (n_own + kOpThreads - 1) / kOpThreads;
+  small_kernel<N, TV, TM><<<blocks, kOpThreads, 0, s>>>(g, n_own, cells, mats, x, Y);
+}
+
+// n in {4, 8, 9, 16} with padded rows: thread-per-cell kernel; false: not
+// handled here.
+template <typename TV, typename TM>
+bool dispatch_small(const LevelGeom& g, int ld, int n_own, const int* cells, const void* mats,
+                    const TV* x, TV* Y, cudaStream_t s) {
+  const int n = g.nloc;
+  if (ld != padded_ld(n) || (reinterpret_cast<uintptr_t>(mats) & 15)) return false;
+  const TM* m = static_cast<const TM*>(mats);
+  switch (n) {
+    case 4: launch_small<4, TV, TM>(g, n_own, cells, m, x, Y, s); return true;
+    case 8: launch_small<8, TV, TM>(g, n_own, cells, m, x, Y, s); return true;
+    case 9: launch_small<9, TV, TM>(g, n_own, cells, m, x, Y, s); return true;
+    case 16: launch_small<16, TV, TM>(g, n_own, cells, m, x, Y, s); return true;
+    default: return false;
+  }
+}
+
 // Stored df32 islands of the mixed path (float vectors).
 __global__ void __launch_bounds__(kOpThreads) own_x_kernel(CellOpArgs<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -655,15 +703,149 @@ __global__ void __launch_bounds__(kOpThreads) own_x_kernel(CellOpArgs<float> A) 
                           blockIdx.x, gridDim.x, smem_raw, tab);
 }
 
-// Shared matrices: one tile of up to 64 cells per block.
-template <typename TV, int RB>
+// Shared matrices: persistent blocks walk the tile list (tiles of up to 64
+// cells against one n x n matrix, K symmetric so row k = column k).  The
+// matrix stays in shared memory while consecutive tiles use it; the
+// coefficients of the next tile are gathered with cp.async into the second
+// buffer while the current tile is multiplied.  npad = next power of two >=
+// max(16, n); thread (cg = t % 16, rg = t / 16) computes rows
+// [rg RB, rg RB + RB) of the cells 4 cg .. 4 cg + 3.
+template <typename TV, int RB, int NB>
 __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int tab[128];
-  __shared__ int ccell[4 * kTileCells];
-  build_local_table(A.g, tab);
-  tile_role<TV, RB>(A.g, A.tiles[blockIdx.x], A.sh_cells, A.sh_scale, A.sh_mats, A.x, A.Y,
-                    reinterpret_cast<TV*>(smem_raw), tab, ccell);
+  __shared__ int ccell[2][4][kTileCells];
+  constexpr int npad = 16 * RB;
+  constexpr int lgp = RB == 1 ? 4 : RB == 2 ? 5 : RB == 4 ? 6 : 7;
+  const LevelGeom& g = A.g;
+  const int n = g.nloc;
+  TV* Ks = reinterpret_cast<TV*>(smem_raw);
+  TV* Xb[2] = {Ks + n * npad, Ks + n * npad + (NB == 2 ? n * kTileCells : 0)};
+  build_local_table(g, tab);
+  const int T = A.ntiles;
+  int t = blockIdx.x;
+  if (t >= T) return;
+  auto coords = [&](int tt, int buf) {
+    if (threadIdx.x < kTileCells) {
+      const int4 tl = A.tiles[tt];
+      const int c = threadIdx.x;
+      const int cell = c < tl.z ? A.sh_cells[tl.y + c] : 0;
+      int cx, cy, cz;
+      cell_coords(g, cell, cx, cy, cz);
+      ccell[buf][0][c] = c < tl.z ? cell : -1;
+      ccell[buf][1][c] = cx;
+      ccell[buf][2][c] = cy;
+      ccell[buf][3][c] = cz;
+    }
+  };
+  auto gather = [&](int buf) {
+    TV* X = Xb[buf];
+    for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
+      const int k = e >> 6, c = e & (kTileCells - 1);
+      const bool live = ccell[buf][0][c] >= 0;
+      const TV* src = live ? A.x + dof_packed(g, ccell[buf][1][c], ccell[buf][2][c],
+                                              ccell[buf][3][c], tab[k])
+                           : A.x;
+      if constexpr (sizeof(TV) == 4)
+        cp_async_4(X + e, src, live ? 4 : 0);
+      else
+        cp_async_8(X + e, src, live ? 8 : 0);
+    }
+    cp_async_commit();
+  };
+  if (NB == 2) {
+    coords(t, 0);
+    __syncthreads();
+    gather(0);
+  }
+  int cur_mat = -1;
+  const int cg = threadIdx.x & 15;
+  const int rg = threadIdx.x >> 4;
+  const int i0 = rg * RB;
+  const long long ncells = g.ncells;
+  for (int it = 0; t < T; t += gridDim.x, ++it) {
+    const int buf = NB == 2 ? (it & 1) : 0;
+    const int tn = t + gridDim.x;
+    const int4 tile = A.tiles[t];
+    if (NB == 2) {
+      if (tn < T) coords(tn, buf ^ 1);
+    } else {
+      coords(t, 0);
+    }
+    if (tile.x != cur_mat) {
+      const TV* K = A.sh_mats + (size_t)tile.x * n * n;
+      for (int e = threadIdx.x; e < n * npad; e += blockDim.x) {
+        const int i = e >> lgp, j = e & (npad - 1);
+        Ks[e] = j < n ? K[(size_t)i * n + j] : (TV)0;
+      }
+      cur_mat = tile.x;
+    }
+    __syncthreads();
+    if (NB == 2) {
+      if (tn < T) {
+        gather(buf ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+    } else {
+      gather(0);
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const TV* Xs = Xb[buf];
+    TV acc[RB][4];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+    if (i0 < n) {
+#pragma unroll 2
+      for (int k = 0; k < n; ++k) {
+        TV xv[4];
+        const TV* xr = Xs + k * kTileCells + 4 * cg;
+        TV kv[RB];
+        const TV* kr = Ks + k * npad + i0;
+        if constexpr (std::is_same<TV, float>::value) {
+          float4 q = *reinterpret_cast<const float4*>(xr);
+          xv[0] = q.x; xv[1] = q.y; xv[2] = q.z; xv[3] = q.w;
+          if constexpr (RB >= 4) {
+#pragma unroll
+            for (int r4 = 0; r4 < RB / 4; ++r4) {
+              float4 u = *reinterpret_cast<const float4*>(kr + 4 * r4);
+              kv[4 * r4] = u.x; kv[4 * r4 + 1] = u.y; kv[4 * r4 + 2] = u.z; kv[4 * r4 + 3] = u.w;
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < RB; ++r) kv[r] = kr[r];
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) xv[c] = xr[c];
+#pragma unroll
+          for (int r = 0; r < RB; ++r) kv[r] = kr[r];
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] += kv[r] * xv[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int cc = 4 * cg + c;
+      const int cell = ccell[buf][0][cc];
+      if (cell >= 0) {
+        const TV sc = A.sh_scale[tile.y + cc];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const int i = i0 + r;
+          if (i < n) A.Y[(size_t)i * ncells + cell] = sc * acc[r][c];
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1034,17 +1216,33 @@ inline int grid_for(long long n, int threads = 256, int cap = 8192) {
 }  // namespace
 
 template <typename TV, int RB>
-void launch_tile(const CellOpArgs<TV>& A, size_t sm_tile, cudaStream_t s) {
+void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t s) {
+  // FP32: two coefficient buffers; as many persistent blocks as shared
+  // memory keeps resident (at most four per SM), each walking several tiles
+  // so the next tile's gather overlaps the current product.  FP64: the
+  // product is FMA-bound on this GPU; one tile per block, single buffer.
+  constexpr int NB = sizeof(TV) == 8 ? 1 : 2;
+  const int n = A.g.nloc;
+  const size_t smem = ((size_t)n * 16 * RB + (size_t)NB * n * kTileCells) * sizeof(TV);
   // set once, to the largest tile this instantiation can need (n <= 16 RB),
   // so concurrent callers never lower it under each other's launches
   static const bool attr = [] {
-    const size_t mx = ((size_t)16 * RB * 16 * RB + (size_t)16 * RB * kTileCells) * sizeof(TV);
-    cudaFuncSetAttribute(tile_kernel<TV, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t mx =
+        ((size_t)16 * RB * 16 * RB + (size_t)NB * 16 * RB * kTileCells) * sizeof(TV);
+    cudaFuncSetAttribute(tile_kernel<TV, RB, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)mx);
     return true;
   }();
   (void)attr;
-  tile_kernel<TV, RB><<<A.ntiles, kOpThreads, sm_tile, s>>>(A);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = (int)((200 * 1024) / (smem + 4096));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 4) per_sm = 4;
+  int grid = NB == 2 ? sms * per_sm : A.ntiles;
+  if (grid > A.ntiles) grid = A.ntiles;
+  tile_kernel<TV, RB, NB><<<grid, kOpThreads, smem, s>>>(A);
 }
 
 // Rows per streamed chunk: the largest divisor of n whose rows fit in one
@@ -1106,7 +1304,8 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   if (A.nb_own) {
     const int rc = stream_rows(n, ld, sizeof(TV));
     const bool aligned = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(op.own.mats) & 15) == 0;
-    if (rc > 0 && aligned) {
+    if (dispatch_small<TV, TV>(g, ld, op.own.n, op.own.cells, op.own.mats, x, Y, s)) {
+    } else if (rc > 0 && aligned) {
       StreamArgs<TV, TV> S{g, ld, rc, op.own.n, op.own.cells, static_cast<const TV*>(op.own.mats),
                            x, Y};
       launch_stream<TV, TV>(S, s);
@@ -1117,7 +1316,9 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   if constexpr (std::is_same<TV, float>::value) {
     if (A.nb_own_x) {
       const int rc = stream_rows(n, ld, sizeof(float2));
-      if (rc > 0) {
+      if (dispatch_small<float, float2>(g, ld, op.own_x.n, op.own_x.cells, op.own_x.mats, x, Y,
+                                        s)) {
+      } else if (rc > 0) {
         StreamArgs<float, float2> S{g, ld, rc, op.own_x.n, op.own_x.cells,
                                     static_cast<const float2*>(op.own_x.mats), x, Y};
         launch_stream<float, float2>(S, s);
