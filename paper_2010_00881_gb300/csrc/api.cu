@@ -94,6 +94,7 @@ struct fcm_handle {
   cudaStream_t user = nullptr;
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  fcm::SideStream side;  // tiles beside stored-matrix kernels
   std::vector<void*> allocs;
   std::vector<fcm::Level> levels;  // 0 = coarsest
   int n_pre = 5, n_post = 5;
@@ -137,6 +138,9 @@ struct fcm_handle {
     if (h_scalar) cudaFreeHost(h_scalar);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
+    if (side.fork) cudaEventDestroy(side.fork);
+    if (side.join) cudaEventDestroy(side.join);
+    if (side.s2) cudaStreamDestroy(side.s2);
     if (s) cudaStreamDestroy(s);
   }
 };
@@ -224,13 +228,13 @@ double host_dot(Handle* h, const double* a, const double* b, long long n) {
 
 void apply_A64(Handle* h, Level& L, const double* x, double* y, int mode, const double* b) {
   h->launches += 2;
-  launch_cell_op<double>(L.g, L.A64, x, L.Y, h->s);
+  launch_cell_op<double>(L.g, L.A64, x, L.Y, h->s, &h->side);
   launch_gather<double>(L.g, mode, L.Y, b, y, 1.0, h->s);
   CKL();
 }
 
 void apply_M64(Handle* h, Level& L, const double* r, double* y) {
-  launch_cell_op<double>(L.g, L.M64, r, L.Y, h->s);
+  launch_cell_op<double>(L.g, L.M64, r, L.Y, h->s, &h->side);
   launch_gather<double>(L.g, GATHER_SET, L.Y, nullptr, y, 1.0, h->s);
   CKL();
 }
@@ -273,18 +277,18 @@ void record_vcycle(Handle* h, int l) {
   if (h->n_pre == 0) CK(cudaMemsetAsync(x, 0, L.g.N * sizeof(TV), s));
   for (int k = 0; k < h->n_pre; ++k) {
     if (k == 0) {
-      launch_cell_op<TV>(L.g, V::M(L), b, Y, s);
+      launch_cell_op<TV>(L.g, V::M(L), b, Y, s, &h->side);
       launch_gather<TV>(L.g, GATHER_SCALE, Y, nullptr, x, w, s);
     } else {
-      launch_cell_op<TV>(L.g, V::A(L), x, Y, s);
+      launch_cell_op<TV>(L.g, V::A(L), x, Y, s, &h->side);
       launch_gather<TV>(L.g, GATHER_RESID, Y, b, r, 1.0, s);
-      launch_cell_op<TV>(L.g, V::M(L), r, Y, s);
+      launch_cell_op<TV>(L.g, V::M(L), r, Y, s, &h->side);
       launch_gather<TV>(L.g, GATHER_ADD, Y, nullptr, x, w, s);
     }
   }
   const TV* rr = b;
   if (h->n_pre > 0) {
-    launch_cell_op<TV>(L.g, V::A(L), x, Y, s);
+    launch_cell_op<TV>(L.g, V::A(L), x, Y, s, &h->side);
     launch_gather<TV>(L.g, GATHER_RESID, Y, b, r, 1.0, s);
     rr = r;
   }
@@ -298,9 +302,9 @@ void record_vcycle(Handle* h, int l) {
   else
     launch_p_prolong_add<TV>(Lc.g, L.g, V::x(Lc), x, s);
   for (int k = 0; k < h->n_post; ++k) {
-    launch_cell_op<TV>(L.g, V::A(L), x, Y, s);
+    launch_cell_op<TV>(L.g, V::A(L), x, Y, s, &h->side);
     launch_gather<TV>(L.g, GATHER_RESID, Y, b, r, 1.0, s);
-    launch_cell_op<TV>(L.g, V::M(L), r, Y, s);
+    launch_cell_op<TV>(L.g, V::M(L), r, Y, s, &h->side);
     launch_gather<TV>(L.g, GATHER_ADD, Y, nullptr, x, w, s);
   }
   CKL();
@@ -368,6 +372,16 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   for (int a = 0; a < P.dim; ++a) nloc *= P.p + 1;
   if (nloc > 128)
     throw Error(FCM_E_UNSUPPORTED, "DOFs per cell (fields x (p+1)^d) must be <= 128");
+  {
+    long long ndof = P.nf, ncell = 1;
+    for (int a = 0; a < P.dim; ++a) {
+      ndof *= (long long)P.C[a] * P.p + 1;
+      ncell *= P.C[a];
+    }
+    // vector and per-cell buffer indices are 32-bit in the solve kernels
+    if (ndof >= 2147483647LL || ncell * nloc >= 2147483647LL)
+      throw Error(FCM_E_UNSUPPORTED, "problem too large: DOFs and cells x local DOFs must be < 2^31");
+  }
   P.geom_kind = geom->kind;
   if (geom->kind < FCM_GEOM_NONE || geom->kind > FCM_GEOM_ELLIPSOID)
     throw Error(FCM_E_INVALID, "unknown geometry kind");
@@ -986,6 +1000,9 @@ fcm_status fcm_setup(const fcm_grid* grid, const fcm_geometry* geom, const fcm_p
     CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&h->side.s2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming));
     CallScope cs(h.get());
     setup_impl(h.get(), grid, geom, phys, opts);
     cs.finish();

@@ -17,6 +17,31 @@ constexpr int kMaxP = 8;
 constexpr int kMaxDepth = 4;
 
 // Geometry of one multigrid level as seen by the kernels.
+// n / d for 0 <= n < 2^31 and 1 <= d < 2^31 by a multiply-high and a shift
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): with s = ceil(log2 d) and
+// mul = floor(2^32 (2^s - d) / d) + 1, n / d = (mulhi(n, mul) + n) >> s.
+struct FastDiv {
+  unsigned mul;
+  int shift;
+};
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  int s = 0;
+  while ((1LL << s) < d) ++s;
+  f.shift = s;
+  f.mul = (unsigned)((((1ULL << s) - (unsigned long long)d) << 32) / (unsigned long long)d + 1);
+  return f;
+}
+__host__ __device__ inline int fdiv(const FastDiv& f, int n) {
+#ifdef __CUDA_ARCH__
+  const unsigned hi = __umulhi((unsigned)n, f.mul);
+#else
+  const unsigned hi = (unsigned)(((unsigned long long)(unsigned)n * f.mul) >> 32);
+#endif
+  return (int)((hi + (unsigned)n) >> f.shift);
+}
+
 struct LevelGeom {
   int dim, nf, p;
   int C[3];        // cells per axis (1 for unused axes)
@@ -26,6 +51,9 @@ struct LevelGeom {
   int nloc_s;      // (p+1)^dim
   int nloc;        // nf * nloc_s
   int ncells;
+  FastDiv dC[3];   // division by C[a]
+  FastDiv dm[2];   // division by m[0], m[1]
+  FastDiv dM;      // division by M
 };
 
 LevelGeom make_geom(int dim, int nf, int p, const int* C);
@@ -122,11 +150,21 @@ inline int padded_ld(int n) { return (n + 3) & ~3; }
 void launch_repack(int count, int n, int ld, const double* src, const int* sel, int kind,
                    void* dst, cudaStream_t s);
 
+// A second stream on which the shared-matrix tiles of a cell operation run
+// beside the stored-matrix kernels (one is bound by FMA issue, the other by
+// HBM bandwidth); `fork` and `join` order it against the main stream, also
+// under stream capture, where they become parallel graph branches.
+struct SideStream {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 // Launch a cell operation Y[l][c] = (S_c x_c)[l] for every cell in `op`
-// (Y is stored local-index-major: Y[l * ncells + cell]).
+// (Y is stored local-index-major: Y[l * ncells + cell]).  With `side`, the
+// tiles run on side->s2 and the main stream waits for them before returning.
 template <typename TV>
 void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y,
-                    cudaStream_t s);
+                    cudaStream_t s, const SideStream* side = nullptr);
 
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };

@@ -39,6 +39,10 @@ LevelGeom make_geom(int dim, int nf, int p, const int* C) {
   }
   g.N = g.M * nf;
   g.nloc = g.nloc_s * nf;
+  for (int a = 0; a < 3; ++a) g.dC[a] = make_fastdiv(g.C[a]);
+  g.dm[0] = make_fastdiv(g.m[0]);
+  g.dm[1] = make_fastdiv(g.m[1]);
+  g.dM = make_fastdiv(g.M < 2147483647LL ? (int)g.M : 2147483647);
   return g;
 }
 
@@ -50,8 +54,12 @@ constexpr int kTileCells = 64;
 constexpr int kRowUnroll = 4;
 constexpr int kOwnBlocksCap = 152 * 6;  // own-kernel blocks: several cells per warp
 
-// Per-block table of local indices l -> (f, jx, jy, jz), packed into one
-// int, so coefficient gathers avoid runtime integer division.
+// Per axis the global index of mode j of cell c is c + off1(C, j): nodes
+// j = 0, 1 are c and c + 1, bubble j >= 2 is (C + 1) + (j - 2) C + c.  So
+// the global index of local DOF l of a cell is cell_base(cell) + tab[l],
+// with tab[l] = f M + off1_x + m0 (off1_y + m1 off1_z) built once per block.
+__device__ __forceinline__ int off1(int C, int j) { return j < 2 ? j : (C + 1) + (j - 2) * C; }
+
 __device__ __forceinline__ void build_local_table(const LevelGeom& g, int* tab) {
   const int P1 = g.p + 1;
   for (int l = threadIdx.x; l < g.nloc; l += blockDim.x) {
@@ -60,18 +68,18 @@ __device__ __forceinline__ void build_local_table(const LevelGeom& g, int* tab) 
     int jx = t % P1;
     int jy = g.dim > 1 ? (t / P1) % P1 : 0;
     int jz = g.dim > 2 ? t / (P1 * P1) : 0;
-    tab[l] = (f << 24) | (jz << 16) | (jy << 8) | jx;
+    tab[l] = f * (int)g.M + off1(g.C[0], jx) +
+             g.m[0] * (off1(g.C[1], jy) + g.m[1] * off1(g.C[2], jz));
   }
 }
 
-// Global index of the local DOF with packed modes `pk` of cell (cx, cy, cz).
-__device__ __forceinline__ long long dof_packed(const LevelGeom& g, int cx, int cy, int cz,
-                                                int pk) {
-  const int jx = pk & 255, jy = (pk >> 8) & 255, jz = (pk >> 16) & 255, f = pk >> 24;
-  long long ix = dof1(g.C[0], cx, jx);
-  long long iy = dof1(g.C[1], cy, jy);
-  long long iz = dof1(g.C[2], cz, jz);
-  return (long long)f * g.M + ix + (long long)g.m[0] * (iy + (long long)g.m[1] * iz);
+__device__ __forceinline__ int cell_base(const LevelGeom& g, int cx, int cy, int cz) {
+  return cx + g.m[0] * (cy + g.m[1] * cz);
+}
+
+// Global index of the local DOF with table entry `ko` of cell (cx, cy, cz).
+__device__ __forceinline__ int dof_packed(const LevelGeom& g, int cx, int cy, int cz, int ko) {
+  return cell_base(g, cx, cy, cz) + ko;
 }
 
 // ---------------------------------------------------------------------------
@@ -313,6 +321,10 @@ __device__ __forceinline__ void cp_async_8(void* dst, const void* src, int bytes
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr32(dst)), "l"(src)
+               : "memory");
+}
 template <int K>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
@@ -350,7 +362,7 @@ struct CellOpArgs {
 // drains its own copies (again bounded) and returns.
 constexpr int kStages = 2;
 constexpr int kChunkBytes = 8192;
-constexpr int kStreamWarps = 12;
+constexpr int kStreamWarps = 8;
 constexpr long long kSpinLimit = 1LL << 26;
 
 __device__ int g_stream_timeout = 0;
@@ -705,18 +717,22 @@ __global__ void __launch_bounds__(kOpThreads) own_x_kernel(CellOpArgs<float> A) 
 
 // Shared matrices: persistent blocks walk the tile list (tiles of up to 64
 // cells against one n x n matrix, K symmetric so row k = column k).  The
-// matrix stays in shared memory while consecutive tiles use it; the
-// coefficients of the next tile are gathered with cp.async into the second
-// buffer while the current tile is multiplied.  npad = next power of two >=
-// max(16, n); thread (cg = t % 16, rg = t / 16) computes rows
-// [rg RB, rg RB + RB) of the cells 4 cg .. 4 cg + 3.
+// matrix stays in shared memory while consecutive tiles use it; matrix and
+// coefficients arrive by cp.async (the next tile's coefficients are
+// gathered into the second buffer while the current tile is multiplied).
+// npad = next power of two >= max(16, n); thread (cg = t % 16, rg = t / 16)
+// computes rows [rg RB, rg RB + RB) of the cells 4 cg .. 4 cg + 3.  The
+// products are staged through shared memory so each row of Y is written as
+// one coalesced run over the tile's cells.
 template <typename TV, int RB, int NB>
 __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int tab[128];
-  __shared__ int ccell[2][4][kTileCells];
+  __shared__ int ccell[2][2][kTileCells];  // cell (-1: empty slot), cell_base
+  __shared__ TV cscale[2][kTileCells];
   constexpr int npad = 16 * RB;
   constexpr int lgp = RB == 1 ? 4 : RB == 2 ? 5 : RB == 4 ? 6 : 7;
+  constexpr int V16 = 16 / (int)sizeof(TV);  // entries per 16-byte copy
   const LevelGeom& g = A.g;
   const int n = g.nloc;
   TV* Ks = reinterpret_cast<TV*>(smem_raw);
@@ -733,9 +749,8 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
       int cx, cy, cz;
       cell_coords(g, cell, cx, cy, cz);
       ccell[buf][0][c] = c < tl.z ? cell : -1;
-      ccell[buf][1][c] = cx;
-      ccell[buf][2][c] = cy;
-      ccell[buf][3][c] = cz;
+      ccell[buf][1][c] = cell_base(g, cx, cy, cz);
+      cscale[buf][c] = c < tl.z ? A.sh_scale[tl.y + c] : (TV)0;
     }
   };
   auto gather = [&](int buf) {
@@ -743,13 +758,32 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
     for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
       const int k = e >> 6, c = e & (kTileCells - 1);
       const bool live = ccell[buf][0][c] >= 0;
-      const TV* src = live ? A.x + dof_packed(g, ccell[buf][1][c], ccell[buf][2][c],
-                                              ccell[buf][3][c], tab[k])
-                           : A.x;
+      const TV* src = live ? A.x + (ccell[buf][1][c] + tab[k]) : A.x;
       if constexpr (sizeof(TV) == 4)
         cp_async_4(X + e, src, live ? 4 : 0);
       else
         cp_async_8(X + e, src, live ? 8 : 0);
+    }
+    cp_async_commit();
+  };
+  // rows of K into Ks[k][0 .. n); 16-byte copies when rows start aligned
+  auto load_matrix = [&](int m) {
+    const TV* K = A.sh_mats + (size_t)m * n * n;
+    if (n % V16 == 0 && (reinterpret_cast<uintptr_t>(A.sh_mats) & 15) == 0) {
+      const int nv = n / V16;
+      for (int e = threadIdx.x; e < n * nv; e += blockDim.x) {
+        const int k = e / nv, v = e - k * nv;
+        cp_async_16(Ks + k * npad + v * V16, K + (size_t)k * n + v * V16);
+      }
+    } else {
+      for (int e = threadIdx.x; e < n * npad; e += blockDim.x) {
+        const int i = e >> lgp, j = e & (npad - 1);
+        const TV* src = j < n ? K + (size_t)i * n + j : K;
+        if constexpr (sizeof(TV) == 4)
+          cp_async_4(Ks + e, src, j < n ? 4 : 0);
+        else
+          cp_async_8(Ks + e, src, j < n ? 8 : 0);
+      }
     }
     cp_async_commit();
   };
@@ -773,14 +807,11 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
       coords(t, 0);
     }
     if (tile.x != cur_mat) {
-      const TV* K = A.sh_mats + (size_t)tile.x * n * n;
-      for (int e = threadIdx.x; e < n * npad; e += blockDim.x) {
-        const int i = e >> lgp, j = e & (npad - 1);
-        Ks[e] = j < n ? K[(size_t)i * n + j] : (TV)0;
-      }
+      load_matrix(tile.x);
       cur_mat = tile.x;
     }
     __syncthreads();
+    // groups complete in issue order: [this tile's X] [K] [next tile's X]
     if (NB == 2) {
       if (tn < T) {
         gather(buf ^ 1);
@@ -793,7 +824,7 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const TV* Xs = Xb[buf];
+    TV* Xs = Xb[buf];
     TV acc[RB][4];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
@@ -831,18 +862,20 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
           for (int c = 0; c < 4; ++c) acc[r][c] += kv[r] * xv[c];
       }
     }
+    __syncthreads();  // every thread is done reading Xs
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int cc = 4 * cg + c;
-      const int cell = ccell[buf][0][cc];
-      if (cell >= 0) {
-        const TV sc = A.sh_scale[tile.y + cc];
+    for (int r = 0; r < RB; ++r) {
+      const int i = i0 + r;
+      if (i < n) {
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          const int i = i0 + r;
-          if (i < n) A.Y[(size_t)i * ncells + cell] = sc * acc[r][c];
-        }
+        for (int c = 0; c < 4; ++c) Xs[i * kTileCells + 4 * cg + c] = acc[r][c];
       }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
+      const int i = e >> 6, c = e & (kTileCells - 1);
+      const int cell = ccell[buf][0][c];
+      if (cell >= 0) A.Y[(size_t)i * ncells + cell] = cscale[buf][c] * Xs[e];
     }
     __syncthreads();
   }
@@ -850,7 +883,8 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
 
 // ---------------------------------------------------------------------------
 // DOF-centric gather of per-cell contributions (Y local-index-major).
-__device__ __forceinline__ int axis_pairs(int C, int i, int& c0, int& j0, int& c1, int& j1) {
+__device__ __forceinline__ int axis_pairs(int C, const FastDiv& dC, int i, int& c0, int& j0,
+                                          int& c1, int& j1) {
   if (i <= C) {
     if (i == 0) {
       c0 = 0;
@@ -868,50 +902,62 @@ __device__ __forceinline__ int axis_pairs(int C, int i, int& c0, int& j0, int& c
     j1 = 0;
     return 2;
   }
-  int t = i - (C + 1);
-  int q = t / C;
+  const int t = i - (C + 1);
+  const int q = fdiv(dC, t);
   c0 = t - q * C;
   j0 = q + 2;
   return 1;
 }
 
-// One block row per line (f, iy, iz) of the level's DOF array, threads along
-// x: the y/z decomposition is uniform per block and the x index needs no
-// division except inside the bubble range.
+// One thread per DOF I = f M + ix + m0 (iy + m1 iz): the (up to 2 per axis)
+// cells that share the DOF and its local index in each are found per axis
+// (divisions by multiply-high), and the contributions are summed in the
+// fixed order (z, y, x) of the cells.
 template <typename TV, int MODE>
-__global__ void __launch_bounds__(128) gather_kernel(LevelGeom g, const TV* __restrict__ Y,
+__global__ void __launch_bounds__(256) gather_kernel(LevelGeom g, const TV* __restrict__ Y,
                                                      const TV* __restrict__ b,
                                                      TV* __restrict__ out, TV w) {
   const int P1 = g.p + 1;
-  const long long ncells = g.ncells;
-  const int myz = g.m[1] * g.m[2];
-  const int nlines = g.nf * myz;
-  for (int line = blockIdx.y; line < nlines; line += gridDim.y) {
-  const int f = line / myz;
-  const int rem = line - f * myz;
-  const int iy = rem % g.m[1];
-  const int iz = rem / g.m[1];
-  int cy0 = 0, jy0 = 0, cy1 = 0, jy1 = 0, cz0 = 0, jz0 = 0, cz1 = 0, jz1 = 0;
-  const int ny = g.dim > 1 ? axis_pairs(g.C[1], iy, cy0, jy0, cy1, jy1) : 1;
-  const int nz = g.dim > 2 ? axis_pairs(g.C[2], iz, cz0, jz0, cz1, jz1) : 1;
-  const long long rowbase = (long long)f * g.M + (long long)g.m[0] * (iy + (long long)g.m[1] * iz);
-  const int lf = f * g.nloc_s;
-  for (int ix = blockIdx.x * blockDim.x + threadIdx.x; ix < g.m[0]; ix += gridDim.x * blockDim.x) {
+  const int ncells = g.ncells;
+  const int N = (int)g.N;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += gridDim.x * blockDim.x) {
+    const int f = g.nf > 1 ? fdiv(g.dM, I) : 0;
+    const int r = I - f * (int)g.M;
+    const int t = fdiv(g.dm[0], r);
+    const int ix = r - t * g.m[0];
+    const int iz = fdiv(g.dm[1], t);
+    const int iy = t - iz * g.m[1];
     int cx0 = 0, jx0 = 0, cx1 = 0, jx1 = 0;
-    const int nx = axis_pairs(g.C[0], ix, cx0, jx0, cx1, jx1);
-    TV sum = 0;
-    for (int kz = 0; kz < nz; ++kz) {
+    int cy0 = 0, jy0 = 0, cy1 = 0, jy1 = 0, cz0 = 0, jz0 = 0, cz1 = 0, jz1 = 0;
+    const int nx = axis_pairs(g.C[0], g.dC[0], ix, cx0, jx0, cx1, jx1);
+    const int ny = g.dim > 1 ? axis_pairs(g.C[1], g.dC[1], iy, cy0, jy0, cy1, jy1) : 1;
+    const int nz = g.dim > 2 ? axis_pairs(g.C[2], g.dC[2], iz, cz0, jz0, cz1, jz1) : 1;
+    const int lf = f * g.nloc_s;
+    // all (up to 8) contributions are loaded before any is added, so the
+    // loads overlap; absent ones read as 0 and leave the sum unchanged
+    TV v[2][2][2];
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz) {
       const int cz = kz ? cz1 : cz0, jz = kz ? jz1 : jz0;
-      for (int ky = 0; ky < ny; ++ky) {
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky) {
         const int cy = ky ? cy1 : cy0, jy = ky ? jy1 : jy0;
+        const bool on = kz < nz && ky < ny;
         const int cyz = g.C[0] * (cy + g.C[1] * cz);
         const int lyz = lf + P1 * (jy + P1 * jz);
-        const TV* Yl0 = Y + (size_t)(lyz + jx0) * ncells + cyz;
-        sum += Yl0[cx0];
-        if (nx > 1) sum += Y[(size_t)(lyz + jx1) * ncells + cyz + cx1];
+        const TV* Yb = Y + (size_t)lyz * ncells + cyz;
+        v[kz][ky][0] = on ? Yb[(size_t)jx0 * ncells + cx0] : (TV)0;
+        v[kz][ky][1] = (on && nx > 1) ? Yb[(size_t)jx1 * ncells + cx1] : (TV)0;
       }
     }
-    const long long I = rowbase + ix;
+    TV sum = 0;
+#pragma unroll
+    for (int kz = 0; kz < 2; ++kz)
+#pragma unroll
+      for (int ky = 0; ky < 2; ++ky) {
+        sum += v[kz][ky][0];
+        sum += v[kz][ky][1];
+      }
     if (MODE == GATHER_SET)
       out[I] = sum;
     else if (MODE == GATHER_RESID)
@@ -920,7 +966,6 @@ __global__ void __launch_bounds__(128) gather_kernel(LevelGeom g, const TV* __re
       out[I] = out[I] + w * sum;
     else
       out[I] = w * sum;
-  }
   }
 }
 
@@ -1040,22 +1085,28 @@ __global__ void h_prolong_kernel(LevelGeom gc, LevelGeom gf, const TV* xc, TV* x
 
 // x = Linv^T (Linv b), one block.
 template <typename TV>
-__global__ void coarse_solve_kernel(int n, const double* Linv, const TV* b, TV* x) {
+__global__ void __launch_bounds__(1024) coarse_solve_kernel(int n, const double* Linv, const TV* b,
+                                                           TV* x) {
+  // one warp per row of each triangular product; lanes stride the row and
+  // a butterfly adds their partial sums (fixed order: deterministic)
   extern __shared__ double cs[];
   double* bs = cs;
   double* ys = cs + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = (double)b[i];
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = w; i < n; i += nw) {
     double s = 0.0;
-    for (int k = 0; k <= i; ++k) s += Linv[(size_t)i * n + k] * bs[k];
-    ys[i] = s;
+    for (int k = l; k <= i; k += 32) s += Linv[(size_t)i * n + k] * bs[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) ys[i] = s;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  for (int j = w; j < n; j += nw) {
     double s = 0.0;
-    for (int i = j; i < n; ++i) s += Linv[(size_t)i * n + j] * ys[i];
-    x[j] = (TV)s;
+    for (int i = j + l; i < n; i += 32) s += Linv[(size_t)i * n + j] * ys[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) x[j] = (TV)s;
   }
 }
 
@@ -1216,7 +1267,8 @@ inline int grid_for(long long n, int threads = 256, int cap = 8192) {
 }  // namespace
 
 template <typename TV, int RB>
-void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t s) {
+void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t s,
+                 bool one_per_sm) {
   // FP32: two coefficient buffers; as many persistent blocks as shared
   // memory keeps resident (at most four per SM), each walking several tiles
   // so the next tile's gather overlaps the current product.  FP64: the
@@ -1231,6 +1283,9 @@ void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t
         ((size_t)16 * RB * 16 * RB + (size_t)NB * 16 * RB * kTileCells) * sizeof(TV);
     cudaFuncSetAttribute(tile_kernel<TV, RB, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)mx);
+    // full shared-memory carveout, so tile blocks fit beside stream blocks
+    cudaFuncSetAttribute(tile_kernel<TV, RB, NB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
     return true;
   }();
   (void)attr;
@@ -1240,7 +1295,7 @@ void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t
   int per_sm = (int)((200 * 1024) / (smem + 4096));
   if (per_sm < 1) per_sm = 1;
   if (per_sm > 4) per_sm = 4;
-  int grid = NB == 2 ? sms * per_sm : A.ntiles;
+  int grid = one_per_sm ? sms : (NB == 2 ? sms * per_sm : A.ntiles);
   if (grid > A.ntiles) grid = A.ntiles;
   tile_kernel<TV, RB, NB><<<grid, kOpThreads, smem, s>>>(A);
 }
@@ -1262,6 +1317,8 @@ void launch_stream(const StreamArgs<TV, TM>& S, cudaStream_t s) {
   static const bool attr = [smem] {
     cudaFuncSetAttribute(stream_kernel<TV, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
+    cudaFuncSetAttribute(stream_kernel<TV, TM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
     return true;
   }();
   (void)attr;
@@ -1275,7 +1332,7 @@ void launch_stream(const StreamArgs<TV, TM>& S, cudaStream_t s) {
 
 template <typename TV>
 void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y,
-                    cudaStream_t s) {
+                    cudaStream_t s, const SideStream* side) {
   CellOpArgs<TV> A;
   A.g = g;
   A.ld = op.ld;
@@ -1301,6 +1358,12 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   int n = g.nloc;
   const size_t sm_own = (size_t)kWarpsPerBlock * 128 * (sizeof(TV) + sizeof(double));
   const int ld = op.ld;
+  // With stored-matrix work to overlap them with, the tiles go on the side
+  // stream, forked before and issued after the stored-matrix kernels (whose
+  // persistent blocks then hold one slot per SM), as one persistent block
+  // per SM that fits beside them.
+  const bool fork = side && side->s2 && A.ntiles && (A.nb_own || A.nb_own_x);
+  if (fork) cudaEventRecord(side->fork, s);
   if (A.nb_own) {
     const int rc = stream_rows(n, ld, sizeof(TV));
     const bool aligned = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(op.own.mats) & 15) == 0;
@@ -1329,13 +1392,22 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
     }
   }
   if (A.ntiles) {
+    cudaStream_t st = s;
+    if (fork) {
+      cudaStreamWaitEvent(side->s2, side->fork, 0);
+      st = side->s2;
+    }
     const int npad = tile_npad(n);
     size_t sm_tile = ((size_t)n * npad + (size_t)n * kTileCells) * sizeof(TV);
     switch (npad / 16) {
-      case 1: launch_tile<TV, 1>(A, sm_tile, s); break;
-      case 2: launch_tile<TV, 2>(A, sm_tile, s); break;
-      case 4: launch_tile<TV, 4>(A, sm_tile, s); break;
-      default: launch_tile<TV, 8>(A, sm_tile, s); break;
+      case 1: launch_tile<TV, 1>(A, sm_tile, st, fork); break;
+      case 2: launch_tile<TV, 2>(A, sm_tile, st, fork); break;
+      case 4: launch_tile<TV, 4>(A, sm_tile, st, fork); break;
+      default: launch_tile<TV, 8>(A, sm_tile, st, fork); break;
+    }
+    if (fork) {
+      cudaEventRecord(side->join, side->s2);
+      cudaStreamWaitEvent(s, side->join, 0);
     }
   }
 }
@@ -1350,14 +1422,14 @@ void launch_repack(int count, int n, int ld, const double* src, const int* sel, 
 template <typename TV>
 void launch_gather(const LevelGeom& g, int mode, const TV* Y, const TV* b, TV* out, double w,
                    cudaStream_t s) {
-  long long lines = (long long)g.nf * g.m[1] * g.m[2];
-  dim3 grid((g.m[0] + 127) / 128, (unsigned)(lines < 65535 ? lines : 65535));
+  const long long nb = (g.N + 255) / 256;
+  const int grid = (int)(nb < 65535 * 16 ? nb : 65535 * 16);
   TV tw = (TV)w;
   switch (mode) {
-    case GATHER_SET: gather_kernel<TV, GATHER_SET><<<grid, 128, 0, s>>>(g, Y, b, out, tw); break;
-    case GATHER_RESID: gather_kernel<TV, GATHER_RESID><<<grid, 128, 0, s>>>(g, Y, b, out, tw); break;
-    case GATHER_ADD: gather_kernel<TV, GATHER_ADD><<<grid, 128, 0, s>>>(g, Y, b, out, tw); break;
-    default: gather_kernel<TV, GATHER_SCALE><<<grid, 128, 0, s>>>(g, Y, b, out, tw); break;
+    case GATHER_SET: gather_kernel<TV, GATHER_SET><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
+    case GATHER_RESID: gather_kernel<TV, GATHER_RESID><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
+    case GATHER_ADD: gather_kernel<TV, GATHER_ADD><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
+    default: gather_kernel<TV, GATHER_SCALE><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
   }
 }
 
@@ -1383,7 +1455,7 @@ void launch_h_prolong_add(const LevelGeom& gc, const LevelGeom& gf, const TV* xc
 }
 template <typename TV>
 void launch_coarse_solve(int n, const double* L, const TV* b, TV* x, cudaStream_t s) {
-  coarse_solve_kernel<TV><<<1, 512, 2 * n * sizeof(double), s>>>(n, L, b, x);
+  coarse_solve_kernel<TV><<<1, 1024, 2 * n * sizeof(double), s>>>(n, L, b, x);
 }
 
 void launch_dot_partials(const double* a, const double* b, long long n, double* partials,
@@ -1433,7 +1505,7 @@ void launch_fill_sin(double* v, long long n, cudaStream_t s) {
 
 #define FCM_INST(TV)                                                                          \
   template void launch_cell_op<TV>(const LevelGeom&, const OpData<TV>&, const TV*, TV*,        \
-                                   cudaStream_t);                                              \
+                                   cudaStream_t, const SideStream*);                           \
   template void launch_gather<TV>(const LevelGeom&, int, const TV*, const TV*, TV*, double,    \
                                   cudaStream_t);                                               \
   template void launch_p_restrict<TV>(const LevelGeom&, const LevelGeom&, const TV*, TV*,      \
