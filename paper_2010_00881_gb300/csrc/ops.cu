@@ -77,6 +77,15 @@ __device__ __forceinline__ int cell_base(const LevelGeom& g, int cx, int cy, int
   return cx + g.m[0] * (cy + g.m[1] * cz);
 }
 
+// cell_base of linear cell c (x fastest), divisions by multiply-high.
+__device__ __forceinline__ int cell_base_of(const LevelGeom& g, int c) {
+  const int t = fdiv(g.dC[0], c);
+  const int cx = c - t * g.C[0];
+  const int cz = fdiv(g.dC[1], t);
+  const int cy = t - cz * g.C[1];
+  return cell_base(g, cx, cy, cz);
+}
+
 // Global index of the local DOF with table entry `ko` of cell (cx, cy, cz).
 __device__ __forceinline__ int dof_packed(const LevelGeom& g, int cx, int cy, int cz, int ko) {
   return cell_base(g, cx, cy, cz) + ko;
@@ -236,11 +245,14 @@ __device__ void own_role(const LevelGeom& g, int ld, int n_own, const int* __res
       }
     }
     if (R == 1) {
+      // with 16 < ncv < 32 column vectors the lanes past ncv hold no columns
+      if (active) {
 #pragma unroll
-      for (int k = 0; k < 2 * V; ++k) {
-        int j = (k < V ? cv * V + k : (cv + 32) * V + (k - V));
-        if (k >= V && !second) break;
-        if (j < n) Y[(size_t)j * ncells + cell] = (TV)acc_value(acc, k);
+        for (int k = 0; k < 2 * V; ++k) {
+          int j = (k < V ? cv * V + k : (cv + 32) * V + (k - V));
+          if (k >= V && !second) break;
+          if (j < n) Y[(size_t)j * ncells + cell] = (TV)acc_value(acc, k);
+        }
       }
     } else {
       if (active) {
@@ -352,17 +364,27 @@ struct CellOpArgs {
 
 // ---------------------------------------------------------------------------
 // Stored matrices streamed through shared memory by the bulk-copy (TMA)
-// engine.  Every warp owns a contiguous range of cells, whose matrices are
-// contiguous in memory, and walks it in chunks of RC rows (RC divides n,
-// chunk <= 8 KB).  Lane 0 issues cp.async.bulk copies into three per-warp
-// stages completed through mbarriers; the warp computes from shared memory
-// with the same (row group, column vector) lane mapping as own_role, so the
-// only loads in flight that registers must cover are the coefficient
-// gathers.  Waits are bounded: on expiry the kernel records a timeout flag,
-// drains its own copies (again bounded) and returns.
-constexpr int kStages = 2;
-constexpr int kChunkBytes = 8192;
-constexpr int kStreamWarps = 8;
+// engine, one block per SM.  The matrices of a level's stored-matrix cells
+// (up to two sets of different storage type, e.g. FP32 and df32) are cut
+// into items: k whole cells when a cell fits a ring chunk, else one cell in
+// cpc chunks of rc rows.  Blocks own contiguous item ranges of equal byte
+// count.  A producer warp copies the block's chunks in order into a ring of
+// Ring<TV>::stages 16 KB stages (full/empty mbarrier pairs); consumer warp w takes
+// items w, w + kConsumers, ...: it gathers the item's coefficients with
+// cp.async one item ahead, multiplies from shared memory with the
+// (row group, column vector) lane mapping of own_role (row s = column s by
+// symmetry) and frees the stage.  Every wait is bounded: on expiry the
+// kernel records a timeout flag, and before the block exits the producer
+// waits (again bounded) for the last copy issued into every stage.
+// Stages per block: with FP32 vectors nine 16 KB stages still leave room for
+// one tile block on the SM; with FP64 vectors (larger tiles) six.
+template <typename TV>
+struct Ring {
+  static constexpr int stages = sizeof(TV) == 4 ? 9 : 6;
+};
+constexpr int kRingChunk = 16384;
+constexpr int kConsumers = 8;
+constexpr int kItemVals = 256;  // coefficient slots per item (cells x nloc)
 constexpr long long kSpinLimit = 1LL << 26;
 
 __device__ int g_stream_timeout = 0;
@@ -372,6 +394,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                : "memory");
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
@@ -402,170 +428,348 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-template <typename TV, typename TM>
+// A parity wait names the current or the preceding phase only, so a
+// consumer may wait for round r of a stage only once round r - 1 has
+// completed.  Consumers take other warps' stages out of turn, so before
+// the parity wait for chunk `seq` a consumer waits (bounded) until the
+// producer has issued it: the producer issues a stage's round r only after
+// its round r - 1 was consumed, hence completed.
+__device__ __forceinline__ bool wait_issued(const volatile int* issued, long long seq) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (*issued > seq) {
+      __threadfence_block();
+      return true;
+    }
+    __nanosleep(32);
+  }
+  return false;
+}
+
+template <typename TM>
+struct StreamSet {
+  int n;              // cells
+  const int* cells;
+  const TM* mats;     // n x nloc x ld entries, cell-major
+  int k;              // cells per item (> 1 only when cpc == 1)
+  int cpc;            // chunks per item
+  int rc;             // rows per chunk (nloc when cpc == 1)
+  int items;          // ceil(n / k)
+  int G;              // consumer warps per item (2: the warps split the columns)
+  long long w;        // bytes per (full) item, the balancing weight
+};
+
+template <typename TV, typename TM1, typename TM2>
 struct StreamArgs {
   LevelGeom g;
-  int ld, rc;  // padded row length, rows per chunk
-  int n_own;
-  const int* cells;
-  const TM* mats;
+  int ld;
+  StreamSet<TM1> s1;
+  StreamSet<TM2> s2;
   const TV* x;
   TV* Y;
 };
 
-struct StreamWarpSmem {
-  uint64_t bar[kStages];
-};
+// First item of block b: byte-balanced split of the item list [set 1, set 2].
+template <typename TM1, typename TM2>
+__device__ __forceinline__ int block_item(const StreamSet<TM1>& a, const StreamSet<TM2>& b,
+                                          int blk, int nblk) {
+  const long long W1 = (long long)a.items * a.w;
+  const long long W = W1 + (long long)b.items * b.w;
+  const long long t = W * blk / nblk;
+  long long u;
+  if (t <= W1)
+    u = a.w > 0 ? (t + a.w - 1) / a.w : 0;
+  else
+    u = a.items + (t - W1 + b.w - 1) / b.w;
+  const long long T = (long long)a.items + b.items;
+  return (int)(u < T ? u : T);
+}
 
 template <typename TV, typename TM>
-__global__ void __launch_bounds__(kStreamWarps * 32, 1) stream_kernel(StreamArgs<TV, TM> A) {
+__device__ __forceinline__ void rows_fma(Acc<TM>& acc, const TM* K, int nrows, int ld,
+                                         const TV* xs, int rg, int R, int cv, bool second) {
   constexpr int V = Elem<TM>::V;
+  int r = rg;
+  for (; r + 3 * R < nrows; r += 4 * R) {
+    const TV x0 = xs[r], x1 = xs[r + R], x2 = xs[r + 2 * R], x3 = xs[r + 3 * R];
+    const TM* row = K + (size_t)r * ld + cv * V;
+    const size_t st = (size_t)R * ld;
+    fma_row(acc, 0, row, x0);
+    fma_row(acc, 0, row + st, x1);
+    fma_row(acc, 0, row + 2 * st, x2);
+    fma_row(acc, 0, row + 3 * st, x3);
+    if (second) {
+      fma_row(acc, 1, row + 32 * V, x0);
+      fma_row(acc, 1, row + st + 32 * V, x1);
+      fma_row(acc, 1, row + 2 * st + 32 * V, x2);
+      fma_row(acc, 1, row + 3 * st + 32 * V, x3);
+    }
+  }
+  for (; r < nrows; r += R) {
+    const TV xv = xs[r];
+    const TM* row = K + (size_t)r * ld;
+    fma_row(acc, 0, row + cv * V, xv);
+    if (second) fma_row(acc, 1, row + (cv + 32) * V, xv);
+  }
+}
+
+// Y[jlo:jhi, cell] from the lanes' accumulators (R row groups summed in
+// order; red holds R rows of the warp's W = jhi0 - jlo columns).
+template <typename TV, typename TM>
+__device__ __forceinline__ void store_cell(const Acc<TM>& acc, double* red, TV* Y, int cell,
+                                           int n, int jlo, int W, int ncells, int R, int rg,
+                                           int cv, bool active, bool second, int lane) {
+  constexpr int V = Elem<TM>::V;
+  if (R == 1) {
+    // with 16 < ncv < 32 column vectors the lanes past ncv hold no columns
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < 2 * V; ++k) {
+        const int j = (k < V ? cv * V + k : (cv + 32) * V + (k - V));
+        if (k >= V && !second) break;
+        if (j < n) Y[(size_t)j * ncells + cell] = (TV)acc_value(acc, k);
+      }
+    }
+  } else {
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) red[rg * W + cv * V - jlo + k] = acc_value(acc, k);
+    }
+    __syncwarp();
+    for (int j = lane; j < W && jlo + j < n; j += 32) {
+      double t = 0.0;
+      for (int r = 0; r < R; ++r) t += red[r * W + j];
+      Y[(size_t)(jlo + j) * ncells + cell] = (TV)t;
+    }
+    __syncwarp();
+  }
+}
+
+// Cell ids of item iu of set S: lane c < cnt holds cell c (-1 past the item).
+template <typename TM>
+__device__ __forceinline__ int item_ids(const StreamSet<TM>& S, int iu, int lane) {
+  const int c0 = iu * S.k;
+  const int cnt = min(S.k, S.n - c0);
+  return lane < cnt ? S.cells[c0 + lane] : -1;
+}
+
+// Gather the coefficients of the item whose cell ids lane c holds in `ids`
+// into xs (cp.async) and keep the ids in cs for the stores.
+template <typename TV>
+__device__ __forceinline__ void gather_ids(const LevelGeom& g, int cnt, int ids, const TV* x,
+                                           TV* xs, int* cs, const int* tab, int lane) {
+  const int n = g.nloc;
+  if (lane < cnt) cs[lane] = ids;
+  for (int c = 0; c < cnt; ++c) {
+    const int cb = cell_base_of(g, __shfl_sync(0xffffffffu, ids, c));
+    for (int l = lane; l < n; l += 32) {
+      if constexpr (sizeof(TV) == 4)
+        cp_async_4(xs + c * n + l, x + (cb + tab[l]), 4);
+      else
+        cp_async_8(xs + c * n + l, x + (cb + tab[l]), 8);
+    }
+  }
+}
+
+// Item iu of set S on warp half h of G (G = 2: the two warps of a pair take
+// the column vectors [0, ceil(ncv/2)) and the rest); every warp frees each
+// stage with 2 / G arrivals (empty barriers count 2).
+template <typename TV, typename TM>
+__device__ bool consume_item(const LevelGeom& g, int ld, const StreamSet<TM>& S, int iu,
+                             int h, long long seq0, const unsigned char* ring, uint64_t* full,
+                             uint64_t* empty, const volatile int* issued, const TV* xs,
+                             const int* cs, double* red, TV* Y, int lane) {
+  constexpr int V = Elem<TM>::V;
+  constexpr int kRing = Ring<TV>::stages;
+  const int n = g.nloc;
+  const int ncv = ld / V;
+  const int half = (ncv + 1) / 2;
+  const int cv0 = S.G == 2 ? h * half : 0;
+  const int ncvw = S.G == 2 ? (h == 0 ? half : ncv - half) : ncv;
+  const bool any = ncvw > 0;
+  const int R = !any ? 1 : (ncvw <= 32 ? 32 / ncvw : 1);
+  const int rg = any && ncvw <= 32 ? lane / ncvw : 0;
+  const int cv = cv0 + (any && ncvw <= 32 ? lane % ncvw : lane);
+  const bool active = any && rg < R;
+  const bool second = ncvw > 32 && (cv - cv0) + 32 < ncvw;
+  const int jlo = cv0 * V, W = ncvw * V;
+  const uint32_t arrivals = 2 / S.G;
+  const int c0 = iu * S.k;
+  const int cnt = min(S.k, S.n - c0);
+  Acc<TM> acc;
+  if (S.cpc == 1) {
+    const int slot = (int)(seq0 % kRing);
+    if (!wait_issued(issued, seq0)) return false;
+    if (!mbar_wait(&full[slot], (uint32_t)((seq0 / kRing) & 1))) return false;
+    const TM* base = reinterpret_cast<const TM*>(ring + (size_t)slot * kRingChunk);
+    bool freed = false;
+    for (int c = 0; c < cnt && any; ++c) {
+      acc.zero();
+      if (active) rows_fma<TV, TM>(acc, base + (size_t)c * n * ld, n, ld, xs + c * n, rg, R, cv,
+                                   second);
+      if (c == cnt - 1) {  // the stage is free before the last cell's stores
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot], arrivals);
+        freed = true;
+      }
+      store_cell<TV, TM>(acc, red, Y, cs[c], n, jlo, W, g.ncells, R, rg, cv, active, second,
+                         lane);
+    }
+    if (!freed) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot], arrivals);
+    }
+  } else {
+    acc.zero();
+    for (int part = 0; part < S.cpc; ++part) {
+      const long long q = seq0 + part;
+      const int slot = (int)(q % kRing);
+      if (!wait_issued(issued, q)) return false;
+      if (!mbar_wait(&full[slot], (uint32_t)((q / kRing) & 1))) return false;
+      const TM* base = reinterpret_cast<const TM*>(ring + (size_t)slot * kRingChunk);
+      if (active) rows_fma<TV, TM>(acc, base, S.rc, ld, xs + part * S.rc, rg, R, cv, second);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot], arrivals);
+    }
+    if (any)
+      store_cell<TV, TM>(acc, red, Y, cs[0], n, jlo, W, g.ncells, R, rg, cv, active, second,
+                         lane);
+  }
+  return true;
+}
+
+template <typename TV, typename TM1, typename TM2>
+__global__ void __launch_bounds__((kConsumers + 1) * 32, 1)
+    stream_kernel(StreamArgs<TV, TM1, TM2> A) {
+  constexpr int kRing = Ring<TV>::stages;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int tab[128];
-  __shared__ uint64_t bars[kStreamWarps][kStages];
+  __shared__ uint64_t full[kRing], empty[kRing];
+  __shared__ int issued;  // chunks issued by the producer so far
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const LevelGeom& g = A.g;
-  const int n = g.nloc, ld = A.ld, RC = A.rc;
-  const long long ncells = g.ncells;
   build_local_table(g, tab);
-  // per-warp shared memory: stages, coefficients, row-group partial sums
-  unsigned char* wbase = smem_raw + (size_t)warp * (kStages * kChunkBytes + 128 * sizeof(TV) +
-                                                    128 * sizeof(double));
-  TM* stage[kStages];
-#pragma unroll
-  for (int k = 0; k < kStages; ++k) stage[k] = reinterpret_cast<TM*>(wbase + k * kChunkBytes);
-  TV* xw = reinterpret_cast<TV*>(wbase + kStages * kChunkBytes);
-  double* red = reinterpret_cast<double*>(wbase + kStages * kChunkBytes + 128 * sizeof(TV));
-  uint64_t* bar = bars[warp];
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < kStages; ++k) mbar_init(&bar[k], 1);
+  if (threadIdx.x == 0) {
+    issued = 0;
+    for (int k = 0; k < kRing; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 2);
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-
-  const long long GW = (long long)gridDim.x * kStreamWarps;
-  const long long gw = (long long)blockIdx.x * kStreamWarps + warp;
-  const int c0 = (int)(gw * A.n_own / GW), c1 = (int)((gw + 1) * A.n_own / GW);
-  if (c0 >= c1) return;
-  const int cpc = n / RC;
-  const long long nq = (long long)(c1 - c0) * cpc;
-  const uint32_t chunk_bytes = (uint32_t)(RC * ld * sizeof(TM));
-  const TM* base = A.mats + (size_t)c0 * n * ld;
-  auto issue = [&](long long q) {
-    if (lane == 0 && q < nq)
-      bulk_load(stage[q % kStages], base + (size_t)q * RC * ld, chunk_bytes, &bar[q % kStages]);
+  const int ub = block_item(A.s1, A.s2, blockIdx.x, gridDim.x);
+  const int ue = block_item(A.s1, A.s2, blockIdx.x + 1, gridDim.x);
+  const int I1 = A.s1.items;
+  const int a = ub > I1 ? ub : (ue < I1 ? ue : I1);  // first set-2 item of the range
+  auto seq_of = [&](int u) -> long long {
+    return (long long)((u < a ? u : a) - ub) * A.s1.cpc + (long long)(u > a ? u - a : 0) * A.s2.cpc;
   };
-#pragma unroll
-  for (int k = 0; k < kStages; ++k) issue(k);
-
-  const int ncv = ld / V;
-  const int R = ncv <= 32 ? 32 / ncv : 1;
-  const bool two = ncv > 32;
-  const int rg = ncv <= 32 ? lane / ncv : 0;
-  const int cv = ncv <= 32 ? lane % ncv : lane;
-  const bool active = rg < R;
-  const bool second = two && cv + 32 < ncv;
-
-  TV xn[4];
-  {
-    int cx, cy, cz;
-    cell_coords(g, A.cells[c0], cx, cy, cz);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      int l = lane + 32 * k;
-      xn[k] = l < n ? A.x[dof_packed(g, cx, cy, cz, tab[l])] : (TV)0;
-    }
-  }
-  Acc<TM> acc;
-  acc.zero();
-  bool ok = true;
-  long long q = 0;
-  for (; q < nq; ++q) {
-    const int ci = c0 + (int)(q / cpc);
-    const int part = (int)(q % cpc);
-    if (part == 0) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        int l = lane + 32 * k;
-        if (l < n) xw[l] = xn[k];
-      }
-      __syncwarp();
-      if (ci + 1 < c1) {
-        int cx, cy, cz;
-        cell_coords(g, A.cells[ci + 1], cx, cy, cz);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          int l = lane + 32 * k;
-          if (l < n) xn[k] = A.x[dof_packed(g, cx, cy, cz, tab[l])];
+  unsigned char* ring = smem_raw;
+  if (warp == kConsumers) {
+    // producer
+    if (lane != 0) return;
+    long long seq = 0;
+    bool ok = true;
+    for (int u = ub; u < ue && ok; ++u) {
+      const bool one = u < I1;
+      const int cpc = one ? A.s1.cpc : A.s2.cpc;
+      for (int part = 0; part < cpc; ++part, ++seq) {
+        const int slot = (int)(seq % kRing);
+        if (seq >= kRing && !mbar_wait(&empty[slot], (uint32_t)(((seq / kRing) - 1) & 1))) {
+          ok = false;
+          break;
         }
+        const void* src;
+        uint32_t bytes;
+        if (one) {
+          const int c0 = u * A.s1.k, cnt = min(A.s1.k, A.s1.n - c0);
+          src = A.s1.mats + ((size_t)c0 * g.nloc + (size_t)part * A.s1.rc) * A.ld;
+          bytes = (uint32_t)((A.s1.cpc > 1 ? A.s1.rc : cnt * g.nloc) * A.ld * sizeof(TM1));
+        } else {
+          const int iu = u - I1;
+          const int c0 = iu * A.s2.k, cnt = min(A.s2.k, A.s2.n - c0);
+          src = A.s2.mats + ((size_t)c0 * g.nloc + (size_t)part * A.s2.rc) * A.ld;
+          bytes = (uint32_t)((A.s2.cpc > 1 ? A.s2.rc : cnt * g.nloc) * A.ld * sizeof(TM2));
+        }
+        bulk_load(ring + (size_t)slot * kRingChunk, src, bytes, &full[slot]);
+        __threadfence_block();
+        *reinterpret_cast<volatile int*>(&issued) = (int)(seq + 1);
       }
     }
-    if (!mbar_wait(&bar[q % kStages], (uint32_t)((q / kStages) & 1))) {
-      ok = false;
+    if (!ok) atomicExch(&g_stream_timeout, 1);
+    // the last copy issued into every stage has landed before the block's
+    // shared memory goes away (consumed ones return at once)
+    for (int k = 0; k < kRing; ++k) {
+      if (seq > k) {
+        const long long last = k + ((seq - 1 - k) / kRing) * kRing;  // last seq in stage k
+        mbar_wait(&full[k], (uint32_t)((last / kRing) & 1));
+      }
+    }
+    return;
+  }
+  // consumers
+  unsigned char* wbase = smem_raw + (size_t)kRing * kRingChunk +
+                         (size_t)warp * (2 * kItemVals * sizeof(TV) + 128 * sizeof(double));
+  TV* xb[2] = {reinterpret_cast<TV*>(wbase), reinterpret_cast<TV*>(wbase) + kItemVals};
+  double* red = reinterpret_cast<double*>(wbase + 2 * kItemVals * sizeof(TV));
+  __shared__ int cbuf[kConsumers][2][32];  // cell ids of the items in xb
+  // this warp's items: set 1 in [ub, a), then set 2 in [a, ue); a set with
+  // G = 2 gives each item to a warp pair
+  const int G1 = A.s1.G, G2 = A.s2.G;
+  const int f1 = ub + (G1 == 2 ? warp / 2 : warp), st1 = kConsumers / G1;
+  const int f2 = a + (G2 == 2 ? warp / 2 : warp), st2 = kConsumers / G2;
+  const int e2 = f2 < ue ? f2 : ue;
+  auto next = [&](int v) {
+    if (v >= ue) return ue;
+    if (v < a) {
+      v += st1;
+      return v < a ? v : e2;
+    }
+    v += st2;
+    return v < ue ? v : ue;
+  };
+  auto ids_of = [&](int v) {
+    if (v >= ue) return -1;
+    return v < I1 ? item_ids(A.s1, v, lane) : item_ids(A.s2, v - I1, lane);
+  };
+  auto count_of = [&](int v) {
+    if (v < I1) return min(A.s1.k, A.s1.n - v * A.s1.k);
+    const int iu = v - I1;
+    return min(A.s2.k, A.s2.n - iu * A.s2.k);
+  };
+  // the ids of the item after next are loaded one iteration ahead, so no
+  // dependent global load sits on the path of the item being consumed
+  int u = f1 < a ? f1 : e2;
+  int un = next(u);
+  if (u < ue) gather_ids(g, count_of(u), ids_of(u), A.x, xb[0], cbuf[warp][0], tab, lane);
+  cp_async_commit();
+  int ids_n = ids_of(un);
+  for (int it = 0; u < ue; ++it) {
+    const int buf = it & 1;
+    const int unn = next(un);
+    if (un < ue) gather_ids(g, count_of(un), ids_n, A.x, xb[buf ^ 1], cbuf[warp][buf ^ 1], tab,
+                            lane);
+    cp_async_commit();
+    ids_n = ids_of(unn);
+    cp_async_wait<1>();
+    __syncwarp();
+    bool ok;
+    if (u < I1)
+      ok = consume_item<TV, TM1>(g, A.ld, A.s1, u, G1 == 2 ? (warp & 1) : 0, seq_of(u), ring,
+                                 full, empty, &issued, xb[buf], cbuf[warp][buf], red, A.Y, lane);
+    else
+      ok = consume_item<TV, TM2>(g, A.ld, A.s2, u - I1, G2 == 2 ? (warp & 1) : 0, seq_of(u),
+                                 ring, full, empty, &issued, xb[buf], cbuf[warp][buf], red, A.Y,
+                                 lane);
+    if (!ok) {
+      if (lane == 0) atomicExch(&g_stream_timeout, 1);
       break;
     }
-    const TM* K = stage[q % kStages];
-    const int s0 = part * RC;
-    if (active) {
-      int r = rg;
-      for (; r + 3 * R < RC; r += 4 * R) {
-        const TV x0 = xw[s0 + r], x1 = xw[s0 + r + R], x2 = xw[s0 + r + 2 * R],
-                 x3 = xw[s0 + r + 3 * R];
-        const TM* row = K + (size_t)r * ld + cv * V;
-        const size_t st = (size_t)R * ld;
-        fma_row(acc, 0, row, x0);
-        fma_row(acc, 0, row + st, x1);
-        fma_row(acc, 0, row + 2 * st, x2);
-        fma_row(acc, 0, row + 3 * st, x3);
-        if (second) {
-          fma_row(acc, 1, row + 32 * V, x0);
-          fma_row(acc, 1, row + st + 32 * V, x1);
-          fma_row(acc, 1, row + 2 * st + 32 * V, x2);
-          fma_row(acc, 1, row + 3 * st + 32 * V, x3);
-        }
-      }
-      for (; r < RC; r += R) {
-        const TV xs = xw[s0 + r];
-        const TM* row = K + (size_t)r * ld;
-        fma_row(acc, 0, row + cv * V, xs);
-        if (second) fma_row(acc, 1, row + (cv + 32) * V, xs);
-      }
-    }
     __syncwarp();
-    issue(q + kStages);
-    if (part == cpc - 1) {
-      const int cell = A.cells[ci];
-      if (R == 1) {
-#pragma unroll
-        for (int k = 0; k < 2 * V; ++k) {
-          int j = (k < V ? cv * V + k : (cv + 32) * V + (k - V));
-          if (k >= V && !second) break;
-          if (j < n) A.Y[(size_t)j * ncells + cell] = (TV)acc_value(acc, k);
-        }
-      } else {
-        if (active) {
-#pragma unroll
-          for (int k = 0; k < V; ++k) red[rg * ld + cv * V + k] = acc_value(acc, k);
-        }
-        __syncwarp();
-        for (int j = lane; j < n; j += 32) {
-          double t = 0.0;
-          for (int r = 0; r < R; ++r) t += red[r * ld + j];
-          A.Y[(size_t)j * ncells + cell] = (TV)t;
-        }
-      }
-      acc.zero();
-      __syncwarp();
-    }
+    u = un;
+    un = unn;
   }
-  if (!ok) {
-    // expired wait: record it, then let this warp's copies in flight land
-    // before the block (and its shared memory) goes away
-    if (lane == 0) atomicExch(&g_stream_timeout, 1);
-    for (long long k = q; k < q + kStages && k < nq; ++k)
-      mbar_wait(&bar[k % kStages], (uint32_t)((k / kStages) & 1));
-  }
+  cp_async_wait<0>();
 }
 
 // Stored matrices in the vector precision (FP64 path: double; mixed: float).
@@ -1300,34 +1504,54 @@ void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t
   tile_kernel<TV, RB, NB><<<grid, kOpThreads, smem, s>>>(A);
 }
 
-// Rows per streamed chunk: the largest divisor of n whose rows fit in one
-// 8 KB stage; 0 when streaming does not pay (small matrices) or does not fit.
-int stream_rows(int n, int ld, size_t es) {
-  const size_t row = (size_t)ld * es;
-  if (n < 16 || n > 128 || row > (size_t)kChunkBytes) return 0;
-  for (int rc = n; rc >= 1; --rc)
-    if (n % rc == 0 && rc * row <= (size_t)kChunkBytes) return rc;
-  return 0;
+// Items of a stored-matrix set: k whole cells per ring chunk when a cell
+// fits (at most kItemVals coefficients per item), else one cell in cpc
+// chunks of rc rows (rc the largest divisor of nloc whose rows fit).
+template <typename TM>
+StreamSet<TM> make_stream_set(int n, const int* cells, const void* mats, int nloc, int ld) {
+  StreamSet<TM> S;
+  S.n = n;
+  S.cells = cells;
+  S.mats = static_cast<const TM*>(mats);
+  const size_t row = (size_t)ld * sizeof(TM), cb = row * nloc;
+  if (cb <= (size_t)kRingChunk) {
+    int k = (int)(kRingChunk / cb);
+    if (k > kItemVals / nloc) k = kItemVals / nloc;
+    S.k = k < 1 ? 1 : k;
+    S.cpc = 1;
+    S.rc = nloc;
+  } else {
+    int rc = (int)(kRingChunk / row);
+    while (nloc % rc) --rc;
+    S.k = 1;
+    S.rc = rc;
+    S.cpc = nloc / rc;
+  }
+  S.items = n > 0 ? (n + S.k - 1) / S.k : 0;
+  S.G = S.cpc > 1 ? 2 : 1;
+  S.w = (long long)S.k * (long long)cb;
+  return S;
 }
 
-template <typename TV, typename TM>
-void launch_stream(const StreamArgs<TV, TM>& S, cudaStream_t s) {
-  const size_t smem = (size_t)kStreamWarps *
-                      (kStages * kChunkBytes + 128 * sizeof(TV) + 128 * sizeof(double));
+template <typename TV, typename TM1, typename TM2>
+void launch_stream(const StreamArgs<TV, TM1, TM2>& S, cudaStream_t s) {
+  const size_t smem = (size_t)Ring<TV>::stages * kRingChunk +
+                      (size_t)kConsumers * (2 * kItemVals * sizeof(TV) + 128 * sizeof(double));
   static const bool attr = [smem] {
-    cudaFuncSetAttribute(stream_kernel<TV, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(stream_kernel<TV, TM1, TM2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    cudaFuncSetAttribute(stream_kernel<TV, TM>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         100);
+    // full shared-memory carveout, so tile blocks fit beside stream blocks
+    cudaFuncSetAttribute(stream_kernel<TV, TM1, TM2>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return true;
   }();
   (void)attr;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int grid = (S.n_own + kStreamWarps - 1) / kStreamWarps;
-  if (grid > sms) grid = sms;
-  stream_kernel<TV, TM><<<grid, kStreamWarps * 32, smem, s>>>(S);
+  const int items = S.s1.items + S.s2.items;
+  const int grid = items < sms ? items : sms;
+  if (grid > 0) stream_kernel<TV, TM1, TM2><<<grid, (kConsumers + 1) * 32, smem, s>>>(S);
 }
 
 template <typename TV>
@@ -1364,30 +1588,36 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   // per SM that fits beside them.
   const bool fork = side && side->s2 && A.ntiles && (A.nb_own || A.nb_own_x);
   if (fork) cudaEventRecord(side->fork, s);
-  if (A.nb_own) {
-    const int rc = stream_rows(n, ld, sizeof(TV));
-    const bool aligned = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(op.own.mats) & 15) == 0;
-    if (dispatch_small<TV, TV>(g, ld, op.own.n, op.own.cells, op.own.mats, x, Y, s)) {
-    } else if (rc > 0 && aligned) {
-      StreamArgs<TV, TV> S{g, ld, rc, op.own.n, op.own.cells, static_cast<const TV*>(op.own.mats),
-                           x, Y};
-      launch_stream<TV, TV>(S, s);
-    } else {
-      own_kernel<TV><<<A.nb_own, kOpThreads, sm_own, s>>>(A);
-    }
-  }
-  if constexpr (std::is_same<TV, float>::value) {
-    if (A.nb_own_x) {
-      const int rc = stream_rows(n, ld, sizeof(float2));
-      if (dispatch_small<float, float2>(g, ld, op.own_x.n, op.own_x.cells, op.own_x.mats, x, Y,
-                                        s)) {
-      } else if (rc > 0) {
-        StreamArgs<float, float2> S{g, ld, rc, op.own_x.n, op.own_x.cells,
-                                    static_cast<const float2*>(op.own_x.mats), x, Y};
-        launch_stream<float, float2>(S, s);
+  if (A.nb_own || A.nb_own_x) {
+    auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const bool al = (ld & 3) == 0 && al16(op.own.mats) && al16(op.own_x.mats);
+    const bool small = (n == 4 || n == 8 || n == 9 || n == 16) && ld == padded_ld(n) && al;
+    if (small) {
+      if (A.nb_own) dispatch_small<TV, TV>(g, ld, op.own.n, op.own.cells, op.own.mats, x, Y, s);
+      if constexpr (std::is_same<TV, float>::value) {
+        if (A.nb_own_x)
+          dispatch_small<float, float2>(g, ld, op.own_x.n, op.own_x.cells, op.own_x.mats, x, Y,
+                                        s);
+      }
+    } else if (al && n <= 128) {
+      if constexpr (std::is_same<TV, float>::value) {
+        StreamArgs<float, float, float2> S{
+            g, ld, make_stream_set<float>(op.own.n, op.own.cells, op.own.mats, n, ld),
+            make_stream_set<float2>(op.own_x.n, op.own_x.cells, op.own_x.mats, n, ld), x, Y};
+        launch_stream(S, s);
       } else {
-        const size_t smx = (size_t)kWarpsPerBlock * 128 * (sizeof(float) + sizeof(double));
-        own_x_kernel<<<A.nb_own_x, kOpThreads, smx, s>>>(A);
+        StreamArgs<double, double, double> S{
+            g, ld, make_stream_set<double>(op.own.n, op.own.cells, op.own.mats, n, ld),
+            make_stream_set<double>(0, nullptr, nullptr, n, ld), x, Y};
+        launch_stream(S, s);
+      }
+    } else {
+      if (A.nb_own) own_kernel<TV><<<A.nb_own, kOpThreads, sm_own, s>>>(A);
+      if constexpr (std::is_same<TV, float>::value) {
+        if (A.nb_own_x) {
+          const size_t smx = (size_t)kWarpsPerBlock * 128 * (sizeof(float) + sizeof(double));
+          own_x_kernel<<<A.nb_own_x, kOpThreads, smx, s>>>(A);
+        }
       }
     }
   }

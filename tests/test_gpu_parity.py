@@ -162,6 +162,19 @@ def test_vcycle_fp64(case):
     assert _rel_a(H.A, z, zr) <= bar, (_rel_a(H.A, z, zr), bar)
 
 
+def test_vcycle_mixed(case):
+    """Mixed V-cycle (FP32 vectors and blocks, df32 islands) against the FP64
+    oracle V-cycle.  Blocks kept in FP32 have scaled condition kappa_inf <=
+    1e5 (the rest are df32), so each FP32 block inverse is accurate to about
+    kappa 2^-24 = 6e-3; bar 10x that in the energy norm.  A lost or doubled
+    column in any cell kernel shows up as an O(1) error."""
+    name, prob, H, s = case
+    r = fi.random_vector(s.ndofs, seed=2)
+    z = s.vcycle(_t(r), prec=FCM_MIXED).cpu().numpy()
+    zr = H.vcycle(r)
+    assert _rel_a(H.A, z, zr) <= 0.06, (name, _rel_a(H.A, z, zr))
+
+
 def test_pcg_fp64_and_mixed(case):
     import scipy.sparse.linalg as spla
     name, prob, H, s = case
