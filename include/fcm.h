@@ -203,8 +203,10 @@ fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_hos
  * handle's stream and return its mean duration from CUDA events (ms).
  * which 0: operator cell kernel (y_c = K_c x_c over all cells), 1: smoother
  * cell kernel (A_i^{-1} over all blocks), 2: the DOF gather that follows
- * them.  prec selects the FP64 or the FCM_MIXED data.  Inputs are the level's
- * work vectors (their current contents); results are discarded. */
+ * them, 3 / 4: the stored-matrix (cut-cell / irregular-block) kernel of the
+ * operator / smoother alone, without the shared-matrix tiles.  prec selects
+ * the FP64 or the FCM_MIXED data.  Inputs are the level's work vectors (their
+ * current contents); results are discarded. */
 fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int reps,
                           double* avg_ms);
 

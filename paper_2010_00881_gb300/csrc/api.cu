@@ -1189,7 +1189,7 @@ fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_hos
 
 fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int reps,
                           double* avg_ms) {
-  if (!h || !avg_ms || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 2 ||
+  if (!h || !avg_ms || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 4 ||
       reps < 1 || (prec != FCM_FP64 && prec != FCM_MIXED) || (prec == FCM_MIXED && !h->mixed)) {
     g_last_error = "invalid argument";
     return FCM_E_INVALID;
@@ -1200,15 +1200,24 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // which 3, 4: the stored-matrix kernel alone (shared tiles dropped)
+    auto stored = [](auto op) {
+      op.sh.tl.ntiles = 0;
+      return op;
+    };
     auto once = [&]() {
       if (prec == FCM_FP64) {
         if (which == 0) launch_cell_op<double>(L.g, L.A64, L.x, L.Y, h->s);
         else if (which == 1) launch_cell_op<double>(L.g, L.M64, L.r, L.Y, h->s);
-        else launch_gather<double>(L.g, GATHER_RESID, L.Y, L.b, L.r, 1.0, h->s);
+        else if (which == 2) launch_gather<double>(L.g, GATHER_RESID, L.Y, L.b, L.r, 1.0, h->s);
+        else if (which == 3) launch_cell_op<double>(L.g, stored(L.A64), L.x, L.Y, h->s);
+        else launch_cell_op<double>(L.g, stored(L.M64), L.r, L.Y, h->s);
       } else {
         if (which == 0) launch_cell_op<float>(L.g, L.A32, L.x32, L.Y32, h->s);
         else if (which == 1) launch_cell_op<float>(L.g, L.M32, L.r32, L.Y32, h->s);
-        else launch_gather<float>(L.g, GATHER_RESID, L.Y32, L.b32, L.r32, 1.0, h->s);
+        else if (which == 2) launch_gather<float>(L.g, GATHER_RESID, L.Y32, L.b32, L.r32, 1.0, h->s);
+        else if (which == 3) launch_cell_op<float>(L.g, stored(L.A32), L.x32, L.Y32, h->s);
+        else launch_cell_op<float>(L.g, stored(L.M32), L.r32, L.Y32, h->s);
       }
     };
     once();
@@ -1228,7 +1237,7 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
 }
 
 fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, long long* bytes) {
-  if (!h || !bytes || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 2 ||
+  if (!h || !bytes || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 4 ||
       (prec != FCM_FP64 && prec != FCM_MIXED)) {
     g_last_error = "invalid argument";
     return FCM_E_INVALID;
@@ -1239,6 +1248,19 @@ fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, lon
   long long b = 0;
   if (which == 2) {
     b = nc * n * sv + 2 * L.g.N * sv + L.g.N * sv;  // Y, b, r(out)
+  } else if (which >= 3) {
+    const OpData<double>& d64 = which == 3 ? L.A64 : L.M64;
+    const OpData<float>& d32 = which == 3 ? L.A32 : L.M32;
+    const long long ld = padded_ld((int)n);
+    long long mats, cells;
+    if (prec == FCM_FP64) {
+      mats = (long long)d64.own.n * n * ld * 8;
+      cells = d64.own.n;
+    } else {
+      mats = (long long)d32.own.n * n * ld * 4 + (long long)d32.own_x.n * n * ld * 8;
+      cells = (long long)d32.own.n + d32.own_x.n;
+    }
+    b = mats + 2 * cells * n * sv;  // stored matrices, their coefficients and results
   } else {
     const OpData<double>& d64 = which == 0 ? L.A64 : L.M64;
     const OpData<float>& d32 = which == 0 ? L.A32 : L.M32;
