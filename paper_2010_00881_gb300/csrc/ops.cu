@@ -400,15 +400,23 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                : "memory");
 }
+// L2 policy for data read once per launch (the streamed matrices): evict
+// first, so the vectors and per-cell products that the next kernels re-read
+// stay in L2.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
+                                          uint64_t* bar, uint64_t policy) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -668,6 +676,7 @@ __global__ void __launch_bounds__((kConsumers + 1) * 32, 1)
   if (warp == kConsumers) {
     // producer
     if (lane != 0) return;
+    const uint64_t policy = evict_first_policy();
     long long seq = 0;
     bool ok = true;
     for (int u = ub; u < ue && ok; ++u) {
@@ -691,7 +700,7 @@ __global__ void __launch_bounds__((kConsumers + 1) * 32, 1)
           src = A.s2.mats + ((size_t)c0 * g.nloc + (size_t)part * A.s2.rc) * A.ld;
           bytes = (uint32_t)((A.s2.cpc > 1 ? A.s2.rc : cnt * g.nloc) * A.ld * sizeof(TM2));
         }
-        bulk_load(ring + (size_t)slot * kRingChunk, src, bytes, &full[slot]);
+        bulk_load(ring + (size_t)slot * kRingChunk, src, bytes, &full[slot], policy);
         __threadfence_block();
         *reinterpret_cast<volatile int*>(&issued) = (int)(seq + 1);
       }
