@@ -634,7 +634,8 @@ __device__ bool consume_item(const LevelGeom& g, int ld, const StreamSet<TM>& S,
       if (!wait_issued(issued, q)) return false;
       if (!mbar_wait(&full[slot], (uint32_t)((q / kRing) & 1))) return false;
       const TM* base = reinterpret_cast<const TM*>(ring + (size_t)slot * kRingChunk);
-      if (active) rows_fma<TV, TM>(acc, base, S.rc, ld, xs + part * S.rc, rg, R, cv, second);
+      const int rows = min(S.rc, n - part * S.rc);
+      if (active) rows_fma<TV, TM>(acc, base, rows, ld, xs + part * S.rc, rg, R, cv, second);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot], arrivals);
     }
@@ -693,12 +694,14 @@ __global__ void __launch_bounds__((kConsumers + 1) * 32, 1)
         if (one) {
           const int c0 = u * A.s1.k, cnt = min(A.s1.k, A.s1.n - c0);
           src = A.s1.mats + ((size_t)c0 * g.nloc + (size_t)part * A.s1.rc) * A.ld;
-          bytes = (uint32_t)((A.s1.cpc > 1 ? A.s1.rc : cnt * g.nloc) * A.ld * sizeof(TM1));
+          const int rows = A.s1.cpc > 1 ? min(A.s1.rc, g.nloc - part * A.s1.rc) : cnt * g.nloc;
+          bytes = (uint32_t)(rows * A.ld * sizeof(TM1));
         } else {
           const int iu = u - I1;
           const int c0 = iu * A.s2.k, cnt = min(A.s2.k, A.s2.n - c0);
           src = A.s2.mats + ((size_t)c0 * g.nloc + (size_t)part * A.s2.rc) * A.ld;
-          bytes = (uint32_t)((A.s2.cpc > 1 ? A.s2.rc : cnt * g.nloc) * A.ld * sizeof(TM2));
+          const int rows = A.s2.cpc > 1 ? min(A.s2.rc, g.nloc - part * A.s2.rc) : cnt * g.nloc;
+          bytes = (uint32_t)(rows * A.ld * sizeof(TM2));
         }
         bulk_load(ring + (size_t)slot * kRingChunk, src, bytes, &full[slot], policy);
         __threadfence_block();
@@ -1122,63 +1125,75 @@ __device__ __forceinline__ int axis_pairs(int C, const FastDiv& dC, int i, int& 
   return 1;
 }
 
-// One thread per DOF I = f M + ix + m0 (iy + m1 iz): the (up to 2 per axis)
-// cells that share the DOF and its local index in each are found per axis
-// (divisions by multiply-high), and the contributions are summed in the
-// fixed order (z, y, x) of the cells.
+// Contributions of DOF I = f M + ix + m0 (iy + m1 iz): the (up to 2 per
+// axis) cells that share the DOF and its local index in each are found per
+// axis (divisions by multiply-high); all (up to 8) values are loaded before
+// any is added, absent ones read as 0.
+template <typename TV>
+__device__ __forceinline__ void gather_load(const LevelGeom& g, const TV* __restrict__ Y, int I,
+                                            bool live, TV v[8]) {
+  const int P1 = g.p + 1;
+  const int ncells = g.ncells;
+  const int f = g.nf > 1 ? fdiv(g.dM, I) : 0;
+  const int r = I - f * (int)g.M;
+  const int t = fdiv(g.dm[0], r);
+  const int ix = r - t * g.m[0];
+  const int iz = fdiv(g.dm[1], t);
+  const int iy = t - iz * g.m[1];
+  int cx0 = 0, jx0 = 0, cx1 = 0, jx1 = 0;
+  int cy0 = 0, jy0 = 0, cy1 = 0, jy1 = 0, cz0 = 0, jz0 = 0, cz1 = 0, jz1 = 0;
+  const int nx = axis_pairs(g.C[0], g.dC[0], ix, cx0, jx0, cx1, jx1);
+  const int ny = g.dim > 1 ? axis_pairs(g.C[1], g.dC[1], iy, cy0, jy0, cy1, jy1) : 1;
+  const int nz = g.dim > 2 ? axis_pairs(g.C[2], g.dC[2], iz, cz0, jz0, cz1, jz1) : 1;
+  const int lf = f * g.nloc_s;
+#pragma unroll
+  for (int kz = 0; kz < 2; ++kz) {
+    const int cz = kz ? cz1 : cz0, jz = kz ? jz1 : jz0;
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky) {
+      const int cy = ky ? cy1 : cy0, jy = ky ? jy1 : jy0;
+      const bool on = live && kz < nz && ky < ny;
+      const int cyz = g.C[0] * (cy + g.C[1] * cz);
+      const int lyz = lf + P1 * (jy + P1 * jz);
+      const TV* Yb = Y + (size_t)lyz * ncells + cyz;
+      v[4 * kz + 2 * ky] = on ? Yb[(size_t)jx0 * ncells + cx0] : (TV)0;
+      v[4 * kz + 2 * ky + 1] = (on && nx > 1) ? Yb[(size_t)jx1 * ncells + cx1] : (TV)0;
+    }
+  }
+}
+
+template <typename TV, int MODE>
+__device__ __forceinline__ void gather_store(const TV v[8], const TV* __restrict__ b,
+                                             TV* __restrict__ out, TV w, int I) {
+  TV sum = 0;  // fixed order: cells (z, y, x)
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += v[k];
+  if (MODE == GATHER_SET)
+    out[I] = sum;
+  else if (MODE == GATHER_RESID)
+    out[I] = b[I] - sum;
+  else if (MODE == GATHER_ADD)
+    out[I] = out[I] + w * sum;
+  else
+    out[I] = w * sum;
+}
+
+// Two DOFs per thread (I and I + stride), all sixteen loads in flight
+// before either sum.
 template <typename TV, int MODE>
 __global__ void __launch_bounds__(256) gather_kernel(LevelGeom g, const TV* __restrict__ Y,
                                                      const TV* __restrict__ b,
                                                      TV* __restrict__ out, TV w) {
-  const int P1 = g.p + 1;
-  const int ncells = g.ncells;
   const int N = (int)g.N;
-  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += gridDim.x * blockDim.x) {
-    const int f = g.nf > 1 ? fdiv(g.dM, I) : 0;
-    const int r = I - f * (int)g.M;
-    const int t = fdiv(g.dm[0], r);
-    const int ix = r - t * g.m[0];
-    const int iz = fdiv(g.dm[1], t);
-    const int iy = t - iz * g.m[1];
-    int cx0 = 0, jx0 = 0, cx1 = 0, jx1 = 0;
-    int cy0 = 0, jy0 = 0, cy1 = 0, jy1 = 0, cz0 = 0, jz0 = 0, cz1 = 0, jz1 = 0;
-    const int nx = axis_pairs(g.C[0], g.dC[0], ix, cx0, jx0, cx1, jx1);
-    const int ny = g.dim > 1 ? axis_pairs(g.C[1], g.dC[1], iy, cy0, jy0, cy1, jy1) : 1;
-    const int nz = g.dim > 2 ? axis_pairs(g.C[2], g.dC[2], iz, cz0, jz0, cz1, jz1) : 1;
-    const int lf = f * g.nloc_s;
-    // all (up to 8) contributions are loaded before any is added, so the
-    // loads overlap; absent ones read as 0 and leave the sum unchanged
-    TV v[2][2][2];
-#pragma unroll
-    for (int kz = 0; kz < 2; ++kz) {
-      const int cz = kz ? cz1 : cz0, jz = kz ? jz1 : jz0;
-#pragma unroll
-      for (int ky = 0; ky < 2; ++ky) {
-        const int cy = ky ? cy1 : cy0, jy = ky ? jy1 : jy0;
-        const bool on = kz < nz && ky < ny;
-        const int cyz = g.C[0] * (cy + g.C[1] * cz);
-        const int lyz = lf + P1 * (jy + P1 * jz);
-        const TV* Yb = Y + (size_t)lyz * ncells + cyz;
-        v[kz][ky][0] = on ? Yb[(size_t)jx0 * ncells + cx0] : (TV)0;
-        v[kz][ky][1] = (on && nx > 1) ? Yb[(size_t)jx1 * ncells + cx1] : (TV)0;
-      }
-    }
-    TV sum = 0;
-#pragma unroll
-    for (int kz = 0; kz < 2; ++kz)
-#pragma unroll
-      for (int ky = 0; ky < 2; ++ky) {
-        sum += v[kz][ky][0];
-        sum += v[kz][ky][1];
-      }
-    if (MODE == GATHER_SET)
-      out[I] = sum;
-    else if (MODE == GATHER_RESID)
-      out[I] = b[I] - sum;
-    else if (MODE == GATHER_ADD)
-      out[I] = out[I] + w * sum;
-    else
-      out[I] = w * sum;
+  const int stride = gridDim.x * blockDim.x;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += 2 * stride) {
+    const int I2 = I + stride;
+    const bool two = I2 < N;
+    TV v0[8], v1[8];
+    gather_load<TV>(g, Y, I, true, v0);
+    gather_load<TV>(g, Y, two ? I2 : I, two, v1);
+    gather_store<TV, MODE>(v0, b, out, w, I);
+    if (two) gather_store<TV, MODE>(v1, b, out, w, I2);
   }
 }
 
@@ -1515,7 +1530,7 @@ void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t
 
 // Items of a stored-matrix set: k whole cells per ring chunk when a cell
 // fits (at most kItemVals coefficients per item), else one cell in cpc
-// chunks of rc rows (rc the largest divisor of nloc whose rows fit).
+// chunks of rc rows (as many rows as fit; the last chunk holds the rest).
 template <typename TM>
 StreamSet<TM> make_stream_set(int n, const int* cells, const void* mats, int nloc, int ld) {
   StreamSet<TM> S;
@@ -1530,11 +1545,10 @@ StreamSet<TM> make_stream_set(int n, const int* cells, const void* mats, int nlo
     S.cpc = 1;
     S.rc = nloc;
   } else {
-    int rc = (int)(kRingChunk / row);
-    while (nloc % rc) --rc;
+    const int rc = (int)(kRingChunk / row);  // full chunks; the last one is shorter
     S.k = 1;
     S.rc = rc;
-    S.cpc = nloc / rc;
+    S.cpc = (nloc + rc - 1) / rc;
   }
   S.items = n > 0 ? (n + S.k - 1) / S.k : 0;
   S.G = S.cpc > 1 ? 2 : 1;
@@ -1594,13 +1608,28 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   // With stored-matrix work to overlap them with, the tiles go on the side
   // stream, forked before and issued after the stored-matrix kernels (whose
   // persistent blocks then hold one slot per SM), as one persistent block
-  // per SM that fits beside them.
-  const bool fork = side && side->s2 && A.ntiles && (A.nb_own || A.nb_own_x);
+  // per SM that fits beside them.  Tiles too large to fit beside a stream
+  // block (n > 64 at FP32, n > 32 at FP64) run after it with their usual
+  // grid instead.
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  const bool al = (ld & 3) == 0 && al16(op.own.mats) && al16(op.own_x.mats);
+  const bool small = (n == 4 || n == 8 || n == 9 || n == 16) && ld == padded_ld(n) && al;
+  bool fork = side && side->s2 && A.ntiles && (A.nb_own || A.nb_own_x);
+  if (fork && !small) {
+    const size_t stream_smem =
+        (size_t)Ring<TV>::stages * kRingChunk +
+        (size_t)kConsumers * (2 * kItemVals * sizeof(TV) + 128 * sizeof(double));
+    const int npad = tile_npad(n);
+    const size_t tile_smem =
+        ((size_t)n * npad + (sizeof(TV) == 4 ? 2 : 1) * (size_t)n * kTileCells) * sizeof(TV);
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // + static shared memory of both kernels and the per-block reservation
+    fork = stream_smem + tile_smem + 12 * 1024 <= (size_t)per_sm;
+  }
   if (fork) cudaEventRecord(side->fork, s);
   if (A.nb_own || A.nb_own_x) {
-    auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-    const bool al = (ld & 3) == 0 && al16(op.own.mats) && al16(op.own_x.mats);
-    const bool small = (n == 4 || n == 8 || n == 9 || n == 16) && ld == padded_ld(n) && al;
     if (small) {
       if (A.nb_own) dispatch_small<TV, TV>(g, ld, op.own.n, op.own.cells, op.own.mats, x, Y, s);
       if constexpr (std::is_same<TV, float>::value) {
@@ -1661,7 +1690,7 @@ void launch_repack(int count, int n, int ld, const double* src, const int* sel, 
 template <typename TV>
 void launch_gather(const LevelGeom& g, int mode, const TV* Y, const TV* b, TV* out, double w,
                    cudaStream_t s) {
-  const long long nb = (g.N + 255) / 256;
+  const long long nb = (g.N + 511) / 512;  // two DOFs per thread
   const int grid = (int)(nb < 65535 * 16 ? nb : 65535 * 16);
   TV tw = (TV)w;
   switch (mode) {
