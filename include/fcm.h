@@ -55,7 +55,13 @@ typedef enum {
 /* Arithmetic of the preconditioner (the outer CG is always FP64). */
 typedef enum {
   FCM_FP64 = 0,  /* everything in FP64 */
-  FCM_MIXED = 1  /* FP32 V-cycle with FP64 islands inside FP64 flexible CG */
+  FCM_MIXED = 1, /* FP32 V-cycle with FP64-accurate islands inside FP64 flexible CG */
+  /* fcm_apply only: the operator the FCM_MIXED solve uses for its FP64
+   * residuals and search directions (FP64 vectors; cut-cell and shared
+   * matrices as df32 pairs, products compensated in FP32 arithmetic, within
+   * about n 2^-48 of sum |K_ij x_j| per row).  Finest levels with at most 16
+   * DOFs per cell use the FP64 data. */
+  FCM_MIXED_OUTER = 2
 } fcm_precision;
 
 enum { FCM_GEOM_NONE = 0, FCM_GEOM_BALL = 1, FCM_GEOM_VOIDS = 2, FCM_GEOM_ELLIPSOID = 3 };
@@ -166,7 +172,8 @@ fcm_status fcm_ndofs(const fcm_handle* h, long long* n);
 fcm_status fcm_rhs(const fcm_handle* h, double* b_dev);
 
 /* y = A x on the finest level (prec FCM_FP64: FP64 matrices; FCM_MIXED: the
- * FP32 copies the V-cycle uses, computed in FP32 and widened). */
+ * FP32 copies the V-cycle uses, computed in FP32 and widened;
+ * FCM_MIXED_OUTER: the FP64-accurate operator of the mixed solve's CG). */
 fcm_status fcm_apply(fcm_handle* h, const double* x_dev, double* y_dev, int prec);
 
 /* z = V(r): one V-cycle with zero initial guess (Algorithm 1). */

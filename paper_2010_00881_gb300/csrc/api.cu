@@ -63,6 +63,10 @@ struct Level {
   // smoother (AS block inverses)
   OpData<double> M64;
   OpData<float> M32;
+  // finest level, mixed path: the outer operator of the mixed solve (FP64
+  // vectors; cut-cell matrices and shared matrices as df32 pairs)
+  OpData<double> A64df;
+  bool has_outer = false;
   double omega = 0.0, lambda = 0.0;
   int n_own_cells = 0, n_own_blocks = 0, n_fp64_blocks = 0;
   // cell sources for Galerkin / block assembly
@@ -229,6 +233,21 @@ double host_dot(Handle* h, const double* a, const double* b, long long n) {
 void apply_A64(Handle* h, Level& L, const double* x, double* y, int mode, const double* b) {
   h->launches += 2;
   launch_cell_op<double>(L.g, L.A64, x, L.Y, h->s, &h->side);
+  launch_gather<double>(L.g, mode, L.Y, b, y, 1.0, h->s);
+  CKL();
+}
+
+// The FP64 residual operator of a solve: the FP64 data, or for FCM_MIXED the
+// df32 outer operator when the finest level has one (FP64-accurate, products
+// in FP32 arithmetic).
+void apply_outer(Handle* h, Level& L, const double* x, double* y, int mode, const double* b,
+                 int prec) {
+  if (prec != FCM_MIXED || !L.has_outer) {
+    apply_A64(h, L, x, y, mode, b);
+    return;
+  }
+  h->launches += 2;
+  launch_cell_op<double>(L.g, L.A64df, x, L.Y, h->s, &h->side);
   launch_gather<double>(L.g, mode, L.Y, b, y, 1.0, h->s);
   CKL();
 }
@@ -840,6 +859,24 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   }
   CK(cudaStreamSynchronize(h->s));
   check_timeout(h);
+  // outer operator of the mixed solve on the finest level: df32 copies of the
+  // shared matrices; the df32 cut-cell matrices of the mixed operator
+  {
+    Level& T = h->levels.back();
+    const int n = T.g.nloc;
+    if (h->mixed && n > 16 && T.A32.own.n == 0) {
+      T.A64df.ld = T.A64.ld;
+      T.A64df.own_x = T.A32.own_x;
+      T.A64df.sh = T.A64.sh;
+      if (T.A64.sh.nmats && T.A64.sh.mats) {
+        float2* m = h->alloc<float2>((size_t)T.A64.sh.nmats * n * n);
+        launch_repack(T.A64.sh.nmats, n, n, T.A64.sh.mats, nullptr, 2, m, h->s);
+        CKL();
+        T.A64df.sh_df = m;
+      }
+      T.has_outer = true;
+    }
+  }
   g_stage = "graph capture";
   h->g_vc64 = capture_vcycle<double>(h, &h->vc_nodes64);
   if (h->mixed) h->g_vc32 = capture_vcycle<float>(h, &h->vc_nodes32);
@@ -905,7 +942,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   fcm_status st = FCM_E_NOT_CONVERGED;
   while (k < maxit) {
     ++k;
-    apply_A64(h, T, p, q, GATHER_SET, nullptr);
+    apply_outer(h, T, p, q, GATHER_SET, nullptr, prec);
     launch_dot_partials(p, q, N, h->part, h->s);
     launch_cg_update_xr(x, r, p, q, N, h->part, h->sc, h->part + kDotBlocks, h->s);
     launch_reduce(h->part + kDotBlocks, kDotBlocks, h->d_scalar, h->s);
@@ -921,7 +958,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
     rel = std::sqrt(rr) / nb;
     if (rel <= rtol) {
       // confirm with the true residual b - A x
-      apply_A64(h, T, x, h->cz_old, GATHER_RESID, b);
+      apply_outer(h, T, x, h->cz_old, GATHER_RESID, b, prec);
       double rt = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / nb;
       if (rt <= rtol) {
         st = FCM_OK;
@@ -947,7 +984,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   check_timeout(h);
   if (sc.flag && st != FCM_OK) st = FCM_E_BREAKDOWN;
   if (st != FCM_OK) {
-    apply_A64(h, T, x, h->cz_old, GATHER_RESID, b);
+    apply_outer(h, T, x, h->cz_old, GATHER_RESID, b, prec);
     inf.relres_true = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / nb;
   }
   inf.iters = k;
@@ -1037,7 +1074,7 @@ fcm_status fcm_rhs(const fcm_handle* hc, double* b_dev) {
 }
 
 fcm_status fcm_apply(fcm_handle* h, const double* x, double* y, int prec) {
-  if (!h || !x || !y || (prec != FCM_FP64 && prec != FCM_MIXED)) {
+  if (!h || !x || !y || (prec != FCM_FP64 && prec != FCM_MIXED && prec != FCM_MIXED_OUTER)) {
     g_last_error = "invalid argument";
     return FCM_E_INVALID;
   }
@@ -1046,6 +1083,9 @@ fcm_status fcm_apply(fcm_handle* h, const double* x, double* y, int prec) {
     Level& T = h->levels.back();
     if (prec == FCM_FP64) {
       apply_A64(h, T, x, y, GATHER_SET, nullptr);
+    } else if (prec == FCM_MIXED_OUTER) {
+      if (!h->mixed) throw Error(FCM_E_INVALID, "mixed precision data not built");
+      apply_outer(h, T, x, y, GATHER_SET, nullptr, FCM_MIXED);
     } else {
       if (!h->mixed) throw Error(FCM_E_INVALID, "mixed precision data not built");
       launch_copy_d2f(x, T.x32, T.g.N, h->s);

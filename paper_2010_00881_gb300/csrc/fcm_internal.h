@@ -138,8 +138,10 @@ template <typename TV>
 struct OpData {
   int ld = 0;                // padded row length of stored matrices
   CellSet own;               // stored matrices in precision TV
-  CellSet own_x;             // df32 islands (mixed path only)
+  CellSet own_x;             // df32 matrices (FP32 vectors: islands of the mixed V-cycle;
+                             // FP64 vectors: the mixed solve's outer operator)
   SharedSet<TV> sh;
+  const float2* sh_df = nullptr;  // FP64 vectors only: df32 copy of sh.mats (outer operator)
 };
 
 // Padded row length of stored cell matrices.

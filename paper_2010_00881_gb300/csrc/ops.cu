@@ -160,6 +160,28 @@ __device__ __forceinline__ void fma_row(Acc<float2>& a, int slot, const float2* 
   df_term(a.s[slot * 2 + 0], a.c[slot * 2 + 0], v.x, v.y, xs);
   df_term(a.s[slot * 2 + 1], a.c[slot * 2 + 1], v.z, v.w, xs);
 }
+// df32 entry times an FP64 coefficient given as its own (hi, lo) float split:
+// TwoProduct of the high parts, TwoSum into s, the cross terms
+// hi_K lo_x + lo_K hi_x and every rounding error into c (lo_K lo_x, below
+// 2^-48 of the product, is dropped).
+__device__ __forceinline__ void df_mac(float& s, float& c, float2 k, float2 x) {
+  const float p = k.x * x.x;
+  const float e = fmaf(k.x, x.x, -p);
+  const float t = s + p;
+  const float bb = t - s;
+  const float err = (s - (t - bb)) + (p - bb);
+  s = t;
+  c += err + e + fmaf(k.x, x.y, k.y * x.x);
+}
+__device__ __forceinline__ float2 split_df(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ void fma_row(Acc<float2>& a, int slot, const float2* row, float2 xs) {
+  float4 v = *reinterpret_cast<const float4*>(row);  // (hi0, lo0, hi1, lo1)
+  df_mac(a.s[slot * 2 + 0], a.c[slot * 2 + 0], make_float2(v.x, v.y), xs);
+  df_mac(a.s[slot * 2 + 1], a.c[slot * 2 + 1], make_float2(v.z, v.w), xs);
+}
 __device__ __forceinline__ double acc_value(const Acc<float>& a, int k) { return a.v[k]; }
 __device__ __forceinline__ double acc_value(const Acc<double>& a, int k) { return a.v[k]; }
 __device__ __forceinline__ double acc_value(const Acc<float2>& a, int k) {
@@ -492,13 +514,15 @@ __device__ __forceinline__ int block_item(const StreamSet<TM1>& a, const StreamS
   return (int)(u < T ? u : T);
 }
 
-template <typename TV, typename TM>
+// XV: the coefficient type in shared memory (the vector type, or a float2
+// (hi, lo) split of FP64 coefficients for df32 matrices).
+template <typename XV, typename TM>
 __device__ __forceinline__ void rows_fma(Acc<TM>& acc, const TM* K, int nrows, int ld,
-                                         const TV* xs, int rg, int R, int cv, bool second) {
+                                         const XV* xs, int rg, int R, int cv, bool second) {
   constexpr int V = Elem<TM>::V;
   int r = rg;
   for (; r + 3 * R < nrows; r += 4 * R) {
-    const TV x0 = xs[r], x1 = xs[r + R], x2 = xs[r + 2 * R], x3 = xs[r + 3 * R];
+    const XV x0 = xs[r], x1 = xs[r + R], x2 = xs[r + 2 * R], x3 = xs[r + 3 * R];
     const TM* row = K + (size_t)r * ld + cv * V;
     const size_t st = (size_t)R * ld;
     fma_row(acc, 0, row, x0);
@@ -513,7 +537,7 @@ __device__ __forceinline__ void rows_fma(Acc<TM>& acc, const TM* K, int nrows, i
     }
   }
   for (; r < nrows; r += R) {
-    const TV xv = xs[r];
+    const XV xv = xs[r];
     const TM* row = K + (size_t)r * ld;
     fma_row(acc, 0, row + cv * V, xv);
     if (second) fma_row(acc, 1, row + (cv + 32) * V, xv);
@@ -603,6 +627,19 @@ __device__ bool consume_item(const LevelGeom& g, int ld, const StreamSet<TM>& S,
   const uint32_t arrivals = 2 / S.G;
   const int c0 = iu * S.k;
   const int cnt = min(S.k, S.n - c0);
+  // df32 matrices against FP64 coefficients: split each gathered value once
+  // into (hi, lo) floats, in place
+  constexpr bool kSplit = std::is_same<TV, double>::value && std::is_same<TM, float2>::value;
+  using XV = typename std::conditional<kSplit, float2, TV>::type;
+  if constexpr (kSplit) {
+    double* xd = const_cast<double*>(reinterpret_cast<const double*>(xs));
+    for (int e = lane; e < cnt * n; e += 32) {
+      const float2 v = split_df(xd[e]);
+      reinterpret_cast<float2*>(xd)[e] = v;
+    }
+    __syncwarp();
+  }
+  const XV* xv = reinterpret_cast<const XV*>(xs);
   Acc<TM> acc;
   if (S.cpc == 1) {
     const int slot = (int)(seq0 % kRing);
@@ -612,7 +649,7 @@ __device__ bool consume_item(const LevelGeom& g, int ld, const StreamSet<TM>& S,
     bool freed = false;
     for (int c = 0; c < cnt && any; ++c) {
       acc.zero();
-      if (active) rows_fma<TV, TM>(acc, base + (size_t)c * n * ld, n, ld, xs + c * n, rg, R, cv,
+      if (active) rows_fma<XV, TM>(acc, base + (size_t)c * n * ld, n, ld, xv + c * n, rg, R, cv,
                                    second);
       if (c == cnt - 1) {  // the stage is free before the last cell's stores
         __syncwarp();
@@ -635,7 +672,7 @@ __device__ bool consume_item(const LevelGeom& g, int ld, const StreamSet<TM>& S,
       if (!mbar_wait(&full[slot], (uint32_t)((q / kRing) & 1))) return false;
       const TM* base = reinterpret_cast<const TM*>(ring + (size_t)slot * kRingChunk);
       const int rows = min(S.rc, n - part * S.rc);
-      if (active) rows_fma<TV, TM>(acc, base, rows, ld, xs + part * S.rc, rg, R, cv, second);
+      if (active) rows_fma<XV, TM>(acc, base, rows, ld, xv + part * S.rc, rg, R, cv, second);
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot], arrivals);
     }
@@ -1095,6 +1132,118 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
     }
     __syncthreads();
   }
+}
+
+// Shared matrices for the FP64 residuals of the mixed solve: K as df32
+// pairs in shared memory, the gathered FP64 coefficients split once into
+// (hi, lo) floats in place, products and sums by df_mac (value s + c, about
+// n 2^-48 of sum |K||x|).  Tile layout and thread mapping as tile_kernel.
+template <int RB>
+__global__ void __launch_bounds__(kOpThreads) tile_df_kernel(CellOpArgs<double> A,
+                                                             const float2* __restrict__ sh_df) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int tab[128];
+  __shared__ int ccell[2][kTileCells];  // cell (-1: empty slot), cell_base
+  __shared__ double cscale[kTileCells];
+  constexpr int npad = 16 * RB;
+  const LevelGeom& g = A.g;
+  const int n = g.nloc;
+  float2* Ks = reinterpret_cast<float2*>(smem_raw);        // [n][npad]
+  double* Xd = reinterpret_cast<double*>(Ks + n * npad);    // [n][64], then split in place
+  float2* Xf = reinterpret_cast<float2*>(Xd);
+  build_local_table(g, tab);
+  const long long ncells = g.ncells;
+  const int cg = threadIdx.x & 15, rg = threadIdx.x >> 4, i0 = rg * RB;
+  int cur_mat = -1;
+  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+    const int4 tile = A.tiles[t];
+    __syncthreads();  // the previous tile's stores are done with Xd and ccell
+    if (threadIdx.x < kTileCells) {
+      const int c = threadIdx.x;
+      const int cell = c < tile.z ? A.sh_cells[tile.y + c] : 0;
+      ccell[0][c] = c < tile.z ? cell : -1;
+      ccell[1][c] = cell_base_of(g, cell);
+      cscale[c] = c < tile.z ? A.sh_scale[tile.y + c] : 0.0;
+    }
+    if (tile.x != cur_mat) {
+      const float2* K = sh_df + (size_t)tile.x * n * n;
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int k = e / n, j = e - k * n;
+        cp_async_8(Ks + k * npad + j, K + e, 8);
+      }
+      cur_mat = tile.x;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
+      const int k = e >> 6, c = e & (kTileCells - 1);
+      const bool live = ccell[0][c] >= 0;
+      const double* src = live ? A.x + (ccell[1][c] + tab[k]) : A.x;
+      cp_async_8(Xd + e, src, live ? 8 : 0);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) Xf[e] = split_df(Xd[e]);
+    __syncthreads();
+    float sa[RB][4], ca[RB][4];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sa[r][c] = ca[r][c] = 0.f;
+    if (i0 < n) {
+#pragma unroll 2
+      for (int k = 0; k < n; ++k) {
+        const float4* xr = reinterpret_cast<const float4*>(Xf + k * kTileCells + 4 * cg);
+        const float4 x01 = xr[0], x23 = xr[1];
+        const float2 xv[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w),
+                              make_float2(x23.x, x23.y), make_float2(x23.z, x23.w)};
+        const float2* kr = Ks + k * npad + i0;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const float2 kv = kr[r];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) df_mac(sa[r][c], ca[r][c], kv, xv[c]);
+        }
+      }
+    }
+    __syncthreads();  // every thread is done reading Xf
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int i = i0 + r;
+      if (i < n) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          Xd[i * kTileCells + 4 * cg + c] = (double)sa[r][c] + (double)ca[r][c];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
+      const int i = e >> 6, c = e & (kTileCells - 1);
+      const int cell = ccell[0][c];
+      if (cell >= 0) A.Y[(size_t)i * ncells + cell] = cscale[c] * Xd[e];
+    }
+  }
+}
+
+template <int RB>
+void launch_tile_df(const CellOpArgs<double>& A, const float2* sh_df, cudaStream_t s,
+                    bool one_per_sm) {
+  const int n = A.g.nloc;
+  constexpr int npad = 16 * RB;
+  const size_t smem = ((size_t)n * npad + (size_t)n * kTileCells) * 8;
+  static const bool attr = [] {
+    const size_t mx = ((size_t)npad * npad + (size_t)npad * kTileCells) * 8;
+    cudaFuncSetAttribute(tile_df_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    cudaFuncSetAttribute(tile_df_kernel<RB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return true;
+  }();
+  (void)attr;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = one_per_sm ? sms : A.ntiles;
+  if (grid > A.ntiles) grid = A.ntiles;
+  tile_df_kernel<RB><<<grid, kOpThreads, smem, s>>>(A, sh_df);
 }
 
 // ---------------------------------------------------------------------------
@@ -1643,6 +1792,11 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
             g, ld, make_stream_set<float>(op.own.n, op.own.cells, op.own.mats, n, ld),
             make_stream_set<float2>(op.own_x.n, op.own_x.cells, op.own_x.mats, n, ld), x, Y};
         launch_stream(S, s);
+      } else if (op.own_x.n) {  // df32 matrices against FP64 vectors (outer operator)
+        StreamArgs<double, double, float2> S{
+            g, ld, make_stream_set<double>(op.own.n, op.own.cells, op.own.mats, n, ld),
+            make_stream_set<float2>(op.own_x.n, op.own_x.cells, op.own_x.mats, n, ld), x, Y};
+        launch_stream(S, s);
       } else {
         StreamArgs<double, double, double> S{
             g, ld, make_stream_set<double>(op.own.n, op.own.cells, op.own.mats, n, ld),
@@ -1667,11 +1821,25 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
     }
     const int npad = tile_npad(n);
     size_t sm_tile = ((size_t)n * npad + (size_t)n * kTileCells) * sizeof(TV);
-    switch (npad / 16) {
-      case 1: launch_tile<TV, 1>(A, sm_tile, st, fork); break;
-      case 2: launch_tile<TV, 2>(A, sm_tile, st, fork); break;
-      case 4: launch_tile<TV, 4>(A, sm_tile, st, fork); break;
-      default: launch_tile<TV, 8>(A, sm_tile, st, fork); break;
+    bool done = false;
+    if constexpr (std::is_same<TV, double>::value) {
+      if (op.sh_df) {  // outer operator: df32 shared matrices
+        switch (npad / 16) {
+          case 1: launch_tile_df<1>(A, op.sh_df, st, fork); break;
+          case 2: launch_tile_df<2>(A, op.sh_df, st, fork); break;
+          case 4: launch_tile_df<4>(A, op.sh_df, st, fork); break;
+          default: launch_tile_df<8>(A, op.sh_df, st, fork); break;
+        }
+        done = true;
+      }
+    }
+    if (!done) {
+      switch (npad / 16) {
+        case 1: launch_tile<TV, 1>(A, sm_tile, st, fork); break;
+        case 2: launch_tile<TV, 2>(A, sm_tile, st, fork); break;
+        case 4: launch_tile<TV, 4>(A, sm_tile, st, fork); break;
+        default: launch_tile<TV, 8>(A, sm_tile, st, fork); break;
+      }
     }
     if (fork) {
       cudaEventRecord(side->join, side->s2);

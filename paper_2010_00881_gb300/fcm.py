@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libfcm.so")
 
 FCM_OK, FCM_E_INVALID, FCM_E_OOM, FCM_E_CUDA, FCM_E_UNSUPPORTED = 0, 1, 2, 3, 4
 FCM_E_NOT_CONVERGED, FCM_E_BREAKDOWN, FCM_E_TIMEOUT = 5, 6, 7
-FCM_FP64, FCM_MIXED = 0, 1
+FCM_FP64, FCM_MIXED, FCM_MIXED_OUTER = 0, 1, 2
 GEOM = {"none": 0, "ball": 1, "voids": 2, "ellipsoid": 3}
 PDE = {"poisson": 0, "elasticity": 1}
 SRC = {"const": 0, "sin3": 1, "square_mms": 2}

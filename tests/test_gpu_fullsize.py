@@ -8,7 +8,7 @@ interior bubble DOFs (one cell) of cut, inside and outside cells, and
 vertex DOFs of cut cells (up to 2^d cells, stored and shared matrices
 mixed).  Bars, per sampled row, relative to s_I = sum_c |K_c[l, :]| |x|:
 FP64 1e-11 (two quadrature summation orders), mixed 1e-5 (FP32 shared
-matrices).
+matrices), the mixed solve's outer operator 1e-11 (df32 matrices, n 2^-48).
 
 The solves are checked by properties that hold at any size: the true
 relative residual (FP64 operator, itself checked above) below the
@@ -29,7 +29,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 from oracle.assembly import element_system, nfields  # noqa: E402
 from oracle.geometry import CUT, INSIDE, OUTSIDE  # noqa: E402
 from oracle.grid import cell_dofs  # noqa: E402
-from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, Solver  # noqa: E402
+from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, FCM_MIXED_OUTER, Solver  # noqa: E402
 
 WORKLOADS = {
     # the throughput workload: 32^3 cells, p = 3, sphere, 912,673 DOFs
@@ -97,6 +97,7 @@ def test_sampled_operator_rows(big):
     xt = torch.from_numpy(x).cuda()
     y64 = s.apply(xt).cpu().numpy()
     y32 = s.apply(xt, prec=FCM_MIXED).cpu().numpy()
+    yo = s.apply(xt, prec=FCM_MIXED_OUTER).cpu().numpy()
     cache = {}
     for I, holders in _samples(prob, cls, rng):
         ref = 0.0
@@ -110,6 +111,7 @@ def test_sampled_operator_rows(big):
             scale += np.abs(K[l]) @ np.abs(xd)
         assert abs(y64[I] - ref) <= 1e-11 * scale, (name, I, y64[I], ref, scale)
         assert abs(y32[I] - ref) <= 1e-5 * scale, (name, I, y32[I], ref, scale)
+        assert abs(yo[I] - ref) <= 1e-11 * scale, (name, I, yo[I], ref, scale)
 
 
 def test_solves(big):

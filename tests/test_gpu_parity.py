@@ -31,7 +31,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 from oracle import multigrid as mg  # noqa: E402
 from oracle.assembly import classify_cells  # noqa: E402
-from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, Solver  # noqa: E402
+from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, FCM_MIXED_OUTER, Solver  # noqa: E402
 from paper_2010_00881_gb300 import fcm as F  # noqa: E402
 
 
@@ -127,6 +127,16 @@ def test_apply_fp32(case):
     x = fi.random_vector(s.ndofs, seed=1)
     y = s.apply(_t(x), prec=FCM_MIXED).cpu().numpy()
     assert _rel(y, H.A @ x) <= 1e-5
+
+
+def test_apply_mixed_outer(case):
+    """The FP64 residual operator of the mixed solve: df32 matrices against
+    FP64 vectors, compensated FP32 arithmetic; error per row <= n 2^-48
+    sum |K||x| (~1e-13 relative), bar as for the FP64 apply."""
+    name, prob, H, s = case
+    x = fi.random_vector(s.ndofs, seed=1)
+    y = s.apply(_t(x), prec=FCM_MIXED_OUTER).cpu().numpy()
+    assert _rel(y, H.A @ x) <= 1e-12, _rel(y, H.A @ x)
 
 
 def test_level_operators(case):
