@@ -839,71 +839,34 @@ __global__ void __launch_bounds__(kOpThreads) own_kernel(CellOpArgs<TV> A) {
                    smem_raw, tab);
 }
 
-// Small stored matrices (n <= 16: the Q1 levels, 2D low degree): one thread
-// per cell, coefficients and N accumulators in registers, rows read as
-// 16-byte vectors of the padded layout (row s = column s by symmetry).
+// Small stored matrices (n <= 16: the Q1 levels, 2D low degree): a group of
+// L lanes per cell (N rounded up to 4, 8 or 16).  Lane j < N loads its own
+// coefficient x_j and row j of the cell's matrix (row j = column j by
+// symmetry; the cell's rows are one contiguous run across the group), gets
+// the other coefficients by shuffles within the group and accumulates
+// y_j = sum_r K[j][r] x_r in the order r = 0 .. N-1.  The row loads depend
+// only on the cell's position in the list, so they overlap the cell-id ->
+// coefficient chain.
 template <typename TM>
-struct SmallAcc;
+struct LaneAcc;
 template <>
-struct SmallAcc<float> {
-  float v[16];
-  __device__ void zero() {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = 0.f;
-  }
-  __device__ double get(int k) const { return v[k]; }
+struct LaneAcc<float> {
+  float v = 0.f;
+  __device__ void add(float k, float x) { v += k * x; }
+  __device__ double get() const { return v; }
 };
 template <>
-struct SmallAcc<double> {
-  double v[16];
-  __device__ void zero() {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = 0.0;
-  }
-  __device__ double get(int k) const { return v[k]; }
+struct LaneAcc<double> {
+  double v = 0.0;
+  __device__ void add(double k, double x) { v += k * x; }
+  __device__ double get() const { return v; }
 };
 template <>
-struct SmallAcc<float2> {
-  float s[16], c[16];
-  __device__ void zero() {
-#pragma unroll
-    for (int k = 0; k < 16; ++k) s[k] = c[k] = 0.f;
-  }
-  __device__ double get(int k) const { return (double)s[k] + (double)c[k]; }
+struct LaneAcc<float2> {
+  float s = 0.f, c = 0.f;
+  __device__ void add(float2 k, float x) { df_term(s, c, k.x, k.y, x); }
+  __device__ double get() const { return (double)s + (double)c; }
 };
-
-template <int N, typename TV>
-__device__ __forceinline__ void small_row(SmallAcc<float>& a, const float* row, TV xs) {
-  constexpr int LD = (N + 3) & ~3;
-#pragma unroll
-  for (int v = 0; v < LD / 4; ++v) {
-    float4 t = *reinterpret_cast<const float4*>(row + 4 * v);
-    if (4 * v + 0 < N) a.v[4 * v + 0] += t.x * xs;
-    if (4 * v + 1 < N) a.v[4 * v + 1] += t.y * xs;
-    if (4 * v + 2 < N) a.v[4 * v + 2] += t.z * xs;
-    if (4 * v + 3 < N) a.v[4 * v + 3] += t.w * xs;
-  }
-}
-template <int N, typename TV>
-__device__ __forceinline__ void small_row(SmallAcc<double>& a, const double* row, TV xs) {
-  constexpr int LD = (N + 3) & ~3;
-#pragma unroll
-  for (int v = 0; v < LD / 2; ++v) {
-    double2 t = *reinterpret_cast<const double2*>(row + 2 * v);
-    if (2 * v + 0 < N) a.v[2 * v + 0] += t.x * xs;
-    if (2 * v + 1 < N) a.v[2 * v + 1] += t.y * xs;
-  }
-}
-template <int N, typename TV>
-__device__ __forceinline__ void small_row(SmallAcc<float2>& a, const float2* row, TV xs) {
-  constexpr int LD = (N + 3) & ~3;
-#pragma unroll
-  for (int v = 0; v < LD / 2; ++v) {
-    float4 t = *reinterpret_cast<const float4*>(row + 2 * v);
-    if (2 * v + 0 < N) df_term(a.s[2 * v + 0], a.c[2 * v + 0], t.x, t.y, xs);
-    if (2 * v + 1 < N) df_term(a.s[2 * v + 1], a.c[2 * v + 1], t.z, t.w, xs);
-  }
-}
 
 template <int N, typename TV, typename TM>
 __global__ void __launch_bounds__(kOpThreads) small_kernel(LevelGeom g, int n_own,
@@ -911,37 +874,50 @@ __global__ void __launch_bounds__(kOpThreads) small_kernel(LevelGeom g, int n_ow
                                                            const TM* __restrict__ mats,
                                                            const TV* __restrict__ x,
                                                            TV* __restrict__ Y) {
+  constexpr int L = N <= 4 ? 4 : (N <= 8 ? 8 : 16);
+  constexpr int G = 32 / L;                   // cells per warp
   constexpr int LD = (N + 3) & ~3;
+  constexpr int VE = 16 / (int)sizeof(TM);   // entries per 16-byte load
   __shared__ int tab[128];
   build_local_table(g, tab);
   __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int j = lane % L;
   const long long ncells = g.ncells;
-  for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < n_own;
-       ci += gridDim.x * blockDim.x) {
-    const int cell = cells[ci];
-    int cx, cy, cz;
-    cell_coords(g, cell, cx, cy, cz);
-    TV xv[N];
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * G < n_own; w += nw) {
+    const int ci = w * G + lane / L;
+    const bool live = ci < n_own && j < N;
+    TM krow[LD];
+    if (live) {
+      const TM* row = mats + ((size_t)ci * N + j) * LD;
 #pragma unroll
-    for (int j = 0; j < N; ++j) xv[j] = x[dof_packed(g, cx, cy, cz, tab[j])];
-    SmallAcc<TM> acc;
-    acc.zero();
-    const TM* K = mats + (size_t)ci * N * LD;
+      for (int v = 0; v < LD / VE; ++v)
+        *reinterpret_cast<float4*>(&krow[v * VE]) = *reinterpret_cast<const float4*>(row + v * VE);
+    }
+    const int cell = ci < n_own ? cells[ci] : 0;
+    const TV xj = live ? x[cell_base_of(g, cell) + tab[j]] : (TV)0;
+    LaneAcc<TM> acc;
 #pragma unroll
-    for (int r = 0; r < N; ++r) small_row<N, TV>(acc, K + r * LD, xv[r]);
-#pragma unroll
-    for (int j = 0; j < N; ++j) Y[(size_t)j * ncells + cell] = (TV)acc.get(j);
+    for (int r = 0; r < N; ++r) {
+      const TV xr = __shfl_sync(0xffffffffu, xj, r, L);
+      if (live) acc.add(krow[r], xr);
+    }
+    if (live) Y[(size_t)j * ncells + cell] = (TV)acc.get();
   }
 }
 
 template <int N, typename TV, typename TM>
 void launch_small(const LevelGeom& g, int n_own, const int* cells, const TM* mats, const TV* x,
                   TV* Y, cudaStream_t s) {
-  int blocks = (n_own + kOpThreads - 1) / kOpThreads;
+  constexpr int L = N <= 4 ? 4 : (N <= 8 ? 8 : 16);
+  const long long threads = (long long)n_own * L;
+  int blocks = (int)((threads + kOpThreads - 1) / kOpThreads);
+  if (blocks < 1) blocks = 1;
   small_kernel<N, TV, TM><<<blocks, kOpThreads, 0, s>>>(g, n_own, cells, mats, x, Y);
 }
 
-// n in {4, 8, 9, 16} with padded rows: thread-per-cell kernel; false: not
+// n in {4, 8, 9, 16} with padded rows: lane-group kernel; false: not
 // handled here.
 template <typename TV, typename TM>
 bool dispatch_small(const LevelGeom& g, int ld, int n_own, const int* cells, const void* mats,
@@ -1821,24 +1797,27 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
     }
     const int npad = tile_npad(n);
     size_t sm_tile = ((size_t)n * npad + (size_t)n * kTileCells) * sizeof(TV);
+    // one block per SM only beside stream blocks; the small-cell kernels
+    // leave the SMs' shared memory free
+    const bool one = fork && !small;
     bool done = false;
     if constexpr (std::is_same<TV, double>::value) {
       if (op.sh_df) {  // outer operator: df32 shared matrices
         switch (npad / 16) {
-          case 1: launch_tile_df<1>(A, op.sh_df, st, fork); break;
-          case 2: launch_tile_df<2>(A, op.sh_df, st, fork); break;
-          case 4: launch_tile_df<4>(A, op.sh_df, st, fork); break;
-          default: launch_tile_df<8>(A, op.sh_df, st, fork); break;
+          case 1: launch_tile_df<1>(A, op.sh_df, st, one); break;
+          case 2: launch_tile_df<2>(A, op.sh_df, st, one); break;
+          case 4: launch_tile_df<4>(A, op.sh_df, st, one); break;
+          default: launch_tile_df<8>(A, op.sh_df, st, one); break;
         }
         done = true;
       }
     }
     if (!done) {
       switch (npad / 16) {
-        case 1: launch_tile<TV, 1>(A, sm_tile, st, fork); break;
-        case 2: launch_tile<TV, 2>(A, sm_tile, st, fork); break;
-        case 4: launch_tile<TV, 4>(A, sm_tile, st, fork); break;
-        default: launch_tile<TV, 8>(A, sm_tile, st, fork); break;
+        case 1: launch_tile<TV, 1>(A, sm_tile, st, one); break;
+        case 2: launch_tile<TV, 2>(A, sm_tile, st, one); break;
+        case 4: launch_tile<TV, 4>(A, sm_tile, st, one); break;
+        default: launch_tile<TV, 8>(A, sm_tile, st, one); break;
       }
     }
     if (fork) {
