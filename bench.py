@@ -126,6 +126,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def aggregate(totals_ms, world, units, steps, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank processed
+    `units` units `steps` times; the slowest rank bounds the job, so each
+    total is the max over ranks.  Returns (max totals, job throughputs)."""
+    import torch
+    tot = [float(t) for t in totals_ms]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor(tot, dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = t.tolist()
+    return tot, [world * units * steps / (x / 1e3) for x in tot]
+
+
 def run_reference(args, rank):
     """The oracle as it stands, on the host cores, one bounded sample per step."""
     import numpy as np  # noqa: F401
@@ -190,18 +204,27 @@ def run_batch(args, rank, world, local):
     setup_s = time.perf_counter() - t0
     ndofs = sum(b.ndofs)
     xs = [torch.empty(n, dtype=torch.float64, device="cuda") for n in b.ndofs]
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
     out = {}
     for prec, name in ((FCM_MIXED, "mixed"), (FCM_FP64, "fp64")):
         for _ in range(args.warmup):
             b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec)
-        torch.cuda.synchronize()
+        barrier()
         t = time.perf_counter()
         for _ in range(args.steps):
             _, infos = b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec)
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t) / args.steps
+        barrier()
+        (tot,), (value,) = aggregate([1e3 * (time.perf_counter() - t)], world, ndofs, args.steps,
+                                     dev)
         its = [i["iters"] for i in infos]
-        out[name] = {"value": world * ndofs / dt, "s_per_step": dt,
+        out[name] = {"value": value, "s_per_step": tot / 1e3 / args.steps,
                      "iters_min": min(its), "iters_max": max(its),
                      "relres_true_max": max(i["relres_true"] for i in infos)}
     if rank == 0:
@@ -318,16 +341,8 @@ def main():
     barrier()
     clk = clocks.stop()
 
-    tot = sum(ms_mixed)
-    tot64 = sum(ms_fp64)
-    tot_e2e = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([tot, tot64, tot_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot, tot64, tot_e2e = t.tolist()
-    value = world * N * args.steps / (tot / 1e3)
-    value64 = world * N * args.steps / (tot64 / 1e3)
-    value_e2e = world * N * args.steps / (tot_e2e / 1e3)
+    (tot, tot64, tot_e2e), (value, value64, value_e2e) = aggregate(
+        [sum(ms_mixed), sum(ms_fp64), sum(e2e_ms)], world, N, args.steps, dev)
 
     # roofline of the dominant kernel: the finest-level stored-matrix kernel
     # of the mixed smoother (stream_kernel), replayed alone with CUDA events
