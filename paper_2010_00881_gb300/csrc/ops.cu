@@ -1303,22 +1303,27 @@ __device__ __forceinline__ void gather_store(const TV v[8], const TV* __restrict
     out[I] = w * sum;
 }
 
-// Two DOFs per thread (I and I + stride), all sixteen loads in flight
-// before either sum.
+// kGatherDofs DOFs per thread (I, I + stride, ...), all their loads in
+// flight before any sum.
+constexpr int kGatherDofs = 2;
 template <typename TV, int MODE>
 __global__ void __launch_bounds__(256) gather_kernel(LevelGeom g, const TV* __restrict__ Y,
                                                      const TV* __restrict__ b,
                                                      TV* __restrict__ out, TV w) {
   const int N = (int)g.N;
   const int stride = gridDim.x * blockDim.x;
-  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += 2 * stride) {
-    const int I2 = I + stride;
-    const bool two = I2 < N;
-    TV v0[8], v1[8];
-    gather_load<TV>(g, Y, I, true, v0);
-    gather_load<TV>(g, Y, two ? I2 : I, two, v1);
-    gather_store<TV, MODE>(v0, b, out, w, I);
-    if (two) gather_store<TV, MODE>(v1, b, out, w, I2);
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += kGatherDofs * stride) {
+    TV v[kGatherDofs][8];
+#pragma unroll
+    for (int u = 0; u < kGatherDofs; ++u) {
+      const int Iu = I + u * stride;
+      gather_load<TV>(g, Y, Iu < N ? Iu : I, Iu < N, v[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherDofs; ++u) {
+      const int Iu = I + u * stride;
+      if (Iu < N) gather_store<TV, MODE>(v[u], b, out, w, Iu);
+    }
   }
 }
 
@@ -1389,15 +1394,35 @@ __global__ void h_restrict_kernel(LevelGeom gc, LevelGeom gf, const TV* rf, TV* 
         lo[a] = hi[a] = 0;
       }
     }
+    // the up to 3 x 3 x 3 fine nodes, loaded together, summed in (z, y, x)
+    // order; absent ones are skipped
+    TV v[3][3][3];
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int x = lo[0] + dx, y = lo[1] + dy, z = lo[2] + dz;
+          const bool on = x <= hi[0] && y <= hi[1] && z <= hi[2];
+          v[dz][dy][dx] =
+              on ? rf[f * gf.M + x + (long long)gf.m[0] * (y + (long long)gf.m[1] * z)] : (TV)0;
+        }
     TV sum = 0;
-    for (int z = lo[2]; z <= hi[2]; ++z)
-      for (int y = lo[1]; y <= hi[1]; ++y)
-        for (int x = lo[0]; x <= hi[0]; ++x) {
-          int i[3] = {x, y, z};
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int x = lo[0] + dx, y = lo[1] + dy, z = lo[2] + dz;
+          if (x > hi[0] || y > hi[1] || z > hi[2]) continue;
+          const int i[3] = {x, y, z};
           TV w = 1;
-          for (int a = 0; a < gc.dim; ++a)
-            if (i[a] != 2 * K[a]) w *= (TV)0.5;
-          sum += w * rf[f * gf.M + x + (long long)gf.m[0] * (y + (long long)gf.m[1] * z)];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (a < gc.dim && i[a] != 2 * K[a]) w *= (TV)0.5;
+          sum += w * v[dz][dy][dx];
         }
     bc[I] = sum;
   }
@@ -1437,29 +1462,75 @@ __global__ void h_prolong_kernel(LevelGeom gc, LevelGeom gf, const TV* xc, TV* x
 }
 
 // x = Linv^T (Linv b), one block.
+// x = Linv^T (Linv b), one block.  One warp per row of each triangular
+// product; lanes stride the row and a butterfly adds their partial sums
+// (fixed order: deterministic).  A warp takes kCoarseRows rows at a time and
+// each lane loads all its entries of a 128-column slab before the FMAs, so
+// the row loads overlap instead of following one another.
+constexpr int kCoarseRows = 4;
 template <typename TV>
-__global__ void __launch_bounds__(1024) coarse_solve_kernel(int n, const double* Linv, const TV* b,
-                                                           TV* x) {
-  // one warp per row of each triangular product; lanes stride the row and
-  // a butterfly adds their partial sums (fixed order: deterministic)
+__global__ void __launch_bounds__(1024) coarse_solve_kernel(int n, const double* __restrict__ Linv,
+                                                           const TV* b, TV* x) {
   extern __shared__ double cs[];
   double* bs = cs;
   double* ys = cs + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = (double)b[i];
   __syncthreads();
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = w; i < n; i += nw) {
-    double s = 0.0;
-    for (int k = l; k <= i; k += 32) s += Linv[(size_t)i * n + k] * bs[k];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (l == 0) ys[i] = s;
+  for (int i0 = w; i0 < n; i0 += nw * kCoarseRows) {
+    double s[kCoarseRows] = {};
+    for (int kb = 0; kb < n; kb += 128) {
+      double v[kCoarseRows][4];
+#pragma unroll
+      for (int r = 0; r < kCoarseRows; ++r)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = i0 + r * nw, k = kb + l + 32 * m;
+          v[r][m] = (i < n && k <= i) ? Linv[(size_t)i * n + k] : 0.0;
+        }
+#pragma unroll
+      for (int r = 0; r < kCoarseRows; ++r)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = i0 + r * nw, k = kb + l + 32 * m;
+          if (i < n && k <= i) s[r] += v[r][m] * bs[k];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kCoarseRows; ++r) {
+      double t = s[r];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      const int i = i0 + r * nw;
+      if (l == 0 && i < n) ys[i] = t;
+    }
   }
   __syncthreads();
-  for (int j = w; j < n; j += nw) {
-    double s = 0.0;
-    for (int i = j + l; i < n; i += 32) s += Linv[(size_t)i * n + j] * ys[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (l == 0) x[j] = (TV)s;
+  for (int j0 = w; j0 < n; j0 += nw * kCoarseRows) {
+    double s[kCoarseRows] = {};
+    for (int ib = 0; ib < n; ib += 128) {
+      double v[kCoarseRows][4];
+#pragma unroll
+      for (int r = 0; r < kCoarseRows; ++r)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int j = j0 + r * nw, i = j + ib + l + 32 * m;
+          v[r][m] = (j < n && i < n) ? Linv[(size_t)i * n + j] : 0.0;
+        }
+#pragma unroll
+      for (int r = 0; r < kCoarseRows; ++r)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int j = j0 + r * nw, i = j + ib + l + 32 * m;
+          if (j < n && i < n) s[r] += v[r][m] * ys[i];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kCoarseRows; ++r) {
+      double t = s[r];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      const int j = j0 + r * nw;
+      if (l == 0 && j < n) x[j] = (TV)t;
+    }
   }
 }
 
@@ -1837,7 +1908,7 @@ void launch_repack(int count, int n, int ld, const double* src, const int* sel, 
 template <typename TV>
 void launch_gather(const LevelGeom& g, int mode, const TV* Y, const TV* b, TV* out, double w,
                    cudaStream_t s) {
-  const long long nb = (g.N + 511) / 512;  // two DOFs per thread
+  const long long nb = (g.N + 256 * kGatherDofs - 1) / (256 * kGatherDofs);
   const int grid = (int)(nb < 65535 * 16 ? nb : 65535 * 16);
   TV tw = (TV)w;
   switch (mode) {
