@@ -247,9 +247,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "batch256", "elasticity64"],
+    ap.add_argument("--workload", default="sphere",
+                    choices=["sphere", "batch256", "elasticity64", "circle16"],
                     help="sphere: 32^3 p=3 sphere (default); batch256: independent instances; "
-                         "elasticity64: 64^3 block with 64 voids, p = 2")
+                         "elasticity64: 64^3 block with 64 voids, p = 2; circle16: 2D circle, "
+                         "16^2 cells, p = 2")
     ap.add_argument("--batch-n", type=int, default=256,
                     help="instances of the batch workload (the first n of the seeded 256)")
     ap.add_argument("--profile-run", action="store_true",
@@ -277,8 +279,12 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    prob = workload() if args.workload == "sphere" else fi.elasticity3d_voids(cells=64, p=2)
-    wl_name = WORKLOAD if args.workload == "sphere" else "elasticity3d_voids_64^3_p2"
+    if args.workload == "sphere":
+        prob, wl_name = workload(), WORKLOAD
+    elif args.workload == "circle16":
+        prob, wl_name = fi.poisson2d_circle(), "poisson2d_circle_16^2_p2"
+    else:
+        prob, wl_name = fi.elasticity3d_voids(cells=64, p=2), "elasticity3d_voids_64^3_p2"
     s = Solver(prob, build_mixed=True)
     N = s.ndofs
     dev = torch.device("cuda", local)
@@ -364,8 +370,10 @@ def main():
             "frac": achieved / peak,
             "traffic": measured_traffic(args.workload) if args.workload == "sphere" else None,
             "algorithmic_bytes": dom["bytes"], "launch_ms": dom["ms"],
-            "kernel": "stream_kernel<float, float, float2> (finest-level additive Schwarz "
-                      "smoother, stored block inverses: FP32 and df32)",
+            "kernel": ("small_kernel" if s.level_info(L)["nloc"] <= 16
+                       else "stream_kernel<float, float, float2>")
+                      + " (finest-level additive Schwarz smoother, stored block inverses: FP32 "
+                        "and df32)",
             "peak_source": peak_src}
 
     if rank == 0:
