@@ -1,6 +1,7 @@
 """Benchmark: DOFs solved per second to relative residual 1e-8 by
-V-cycle-preconditioned CG, mixed precision (FP32 V-cycle with FP64 islands
-inside FP64 flexible CG) against the plain FP64 GPU path, on one GB300.
+V-cycle-preconditioned CG, mixed precision (FP32 V-cycle with df32 islands
+inside FP64-accurate flexible CG) against the plain FP64 GPU path, on one
+GB300.
 
 Workload: 3D Poisson on the unit cube embedding a sphere r = 0.45, 32^3
 cells, integrated Legendre p = 3 (912,673 DOFs), alpha = 1e-8, manufactured
@@ -27,6 +28,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# the CPU oracle legs report one core: keep numpy/scipy's thread pools at one
+# thread (set before numpy is first imported; the GPU path does not use them)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import fcm_inputs as fi  # noqa: E402
 

@@ -195,7 +195,8 @@ fcm_status fcm_cell_classes(const fcm_handle* h, signed char* cls_host);
 /* V-cycle-preconditioned CG from x = 0 (Sec. 4): stops when the recursive
  * relative residual falls below rtol and the recomputed true residual
  * confirms it.  b_dev NULL uses the assembled load.  prec FCM_MIXED runs
- * the FP32 V-cycle inside flexible (Polak-Ribiere) CG.  Returns
+ * the FP32 V-cycle inside flexible (Polak-Ribiere) CG whose operator (search
+ * directions, true residual) is the FCM_MIXED_OUTER one.  Returns
  * FCM_E_NOT_CONVERGED after maxit iterations (x_dev holds the last
  * iterate), FCM_E_BREAKDOWN on p^T A p <= 0 or a non-finite scalar. */
 fcm_status fcm_pcg_solve(fcm_handle* h, const double* b_dev, double* x_dev, double rtol,
