@@ -342,6 +342,18 @@ __host__ __device__ inline int tile_npad(int n) {
 __device__ __forceinline__ uint32_t smem_addr32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization (launch_pdl) may start while its predecessor in the stream
+// still runs; pdl_wait() returns once that grid has completed and its writes
+// are visible (immediately for a normally launched kernel), and
+// pdl_trigger() lets this kernel's dependent start early.  Only reads of the
+// predecessor's results and writes to buffers it reads must follow
+// pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 __device__ __forceinline__ void cp_async_4(void* dst, const void* src, int bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr32(dst)), "l"(src),
                "r"(bytes)
@@ -756,7 +768,9 @@ __global__ void __launch_bounds__((kConsumers + 1) * 32, 1)
     }
     return;
   }
-  // consumers
+  // consumers: x comes from, and Y is read by, the preceding kernels (the
+  // producer only reads the stored matrices, so it does not wait)
+  pdl_wait();
   unsigned char* wbase = smem_raw + (size_t)kRing * kRingChunk +
                          (size_t)warp * (2 * kItemVals * sizeof(TV) + 128 * sizeof(double));
   TV* xb[2] = {reinterpret_cast<TV*>(wbase), reinterpret_cast<TV*>(wbase) + kItemVals};
@@ -881,6 +895,7 @@ __global__ void __launch_bounds__(kOpThreads) small_kernel(LevelGeom g, int n_ow
   __shared__ int tab[128];
   build_local_table(g, tab);
   __syncthreads();
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int j = lane % L;
   const long long ncells = g.ncells;
@@ -914,7 +929,8 @@ void launch_small(const LevelGeom& g, int n_own, const int* cells, const TM* mat
   const long long threads = (long long)n_own * L;
   int blocks = (int)((threads + kOpThreads - 1) / kOpThreads);
   if (blocks < 1) blocks = 1;
-  small_kernel<N, TV, TM><<<blocks, kOpThreads, 0, s>>>(g, n_own, cells, mats, x, Y);
+  launch_pdl(small_kernel<N, TV, TM>, dim3(blocks), dim3(kOpThreads), 0, s, g, n_own, cells, mats,
+             x, Y);
 }
 
 // n in {4, 8, 9, 16} with padded rows: lane-group kernel; false: not
@@ -1310,6 +1326,8 @@ template <typename TV, int MODE>
 __global__ void __launch_bounds__(256) gather_kernel(LevelGeom g, const TV* __restrict__ Y,
                                                      const TV* __restrict__ b,
                                                      TV* __restrict__ out, TV w) {
+  pdl_wait();
+  pdl_trigger();  // the next cell kernel may start streaming its matrices
   const int N = (int)g.N;
   const int stride = gridDim.x * blockDim.x;
   for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < N; I += kGatherDofs * stride) {
@@ -1752,6 +1770,23 @@ StreamSet<TM> make_stream_set(int n, const int* cells, const void* mats, int nlo
   return S;
 }
 
+// Launch with programmatic stream serialization (see pdl_wait).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename TV, typename TM1, typename TM2>
 void launch_stream(const StreamArgs<TV, TM1, TM2>& S, cudaStream_t s) {
   const size_t smem = (size_t)Ring<TV>::stages * kRingChunk +
@@ -1770,7 +1805,8 @@ void launch_stream(const StreamArgs<TV, TM1, TM2>& S, cudaStream_t s) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int items = S.s1.items + S.s2.items;
   const int grid = items < sms ? items : sms;
-  if (grid > 0) stream_kernel<TV, TM1, TM2><<<grid, (kConsumers + 1) * 32, smem, s>>>(S);
+  if (grid > 0)
+    launch_pdl(stream_kernel<TV, TM1, TM2>, dim3(grid), dim3((kConsumers + 1) * 32), smem, s, S);
 }
 
 template <typename TV>
@@ -1912,10 +1948,10 @@ void launch_gather(const LevelGeom& g, int mode, const TV* Y, const TV* b, TV* o
   const int grid = (int)(nb < 65535 * 16 ? nb : 65535 * 16);
   TV tw = (TV)w;
   switch (mode) {
-    case GATHER_SET: gather_kernel<TV, GATHER_SET><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
-    case GATHER_RESID: gather_kernel<TV, GATHER_RESID><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
-    case GATHER_ADD: gather_kernel<TV, GATHER_ADD><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
-    default: gather_kernel<TV, GATHER_SCALE><<<grid, 256, 0, s>>>(g, Y, b, out, tw); break;
+    case GATHER_SET: launch_pdl(gather_kernel<TV, GATHER_SET>, dim3(grid), dim3(256), 0, s, g, Y, b, out, tw); break;
+    case GATHER_RESID: launch_pdl(gather_kernel<TV, GATHER_RESID>, dim3(grid), dim3(256), 0, s, g, Y, b, out, tw); break;
+    case GATHER_ADD: launch_pdl(gather_kernel<TV, GATHER_ADD>, dim3(grid), dim3(256), 0, s, g, Y, b, out, tw); break;
+    default: launch_pdl(gather_kernel<TV, GATHER_SCALE>, dim3(grid), dim3(256), 0, s, g, Y, b, out, tw); break;
   }
 }
 
