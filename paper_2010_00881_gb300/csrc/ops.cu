@@ -896,6 +896,7 @@ __global__ void __launch_bounds__(kOpThreads) small_kernel(LevelGeom g, int n_ow
   build_local_table(g, tab);
   __syncthreads();
   pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int j = lane % L;
   const long long ncells = g.ncells;
@@ -1381,6 +1382,8 @@ __device__ inline void split_index(const LevelGeom& g, long long I, long long& f
 
 template <typename TV, bool PROLONG>
 __global__ void p_transfer_kernel(LevelGeom gc, LevelGeom gf, const TV* in, TV* out) {
+  pdl_wait();
+  pdl_trigger();
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < gc.N;
        I += (long long)gridDim.x * blockDim.x) {
     long long f;
@@ -1398,6 +1401,8 @@ __global__ void p_transfer_kernel(LevelGeom gc, LevelGeom gf, const TV* in, TV* 
 // with weights 1/2, 1, 1/2.
 template <typename TV>
 __global__ void h_restrict_kernel(LevelGeom gc, LevelGeom gf, const TV* rf, TV* bc) {
+  pdl_wait();
+  pdl_trigger();
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < gc.N;
        I += (long long)gridDim.x * blockDim.x) {
     long long f;
@@ -1450,6 +1455,8 @@ __global__ void h_restrict_kernel(LevelGeom gc, LevelGeom gf, const TV* rf, TV* 
 // its two coarse neighbours.
 template <typename TV>
 __global__ void h_prolong_kernel(LevelGeom gc, LevelGeom gf, const TV* xc, TV* xf) {
+  pdl_wait();
+  pdl_trigger();
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < gf.N;
        I += (long long)gridDim.x * blockDim.x) {
     long long f;
@@ -1489,6 +1496,8 @@ constexpr int kCoarseRows = 4;
 template <typename TV>
 __global__ void __launch_bounds__(1024) coarse_solve_kernel(int n, const double* __restrict__ Linv,
                                                            const TV* b, TV* x) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double cs[];
   double* bs = cs;
   double* ys = cs + n;
@@ -1958,26 +1967,26 @@ void launch_gather(const LevelGeom& g, int mode, const TV* Y, const TV* b, TV* o
 template <typename TV>
 void launch_p_restrict(const LevelGeom& gc, const LevelGeom& gf, const TV* rf, TV* bc,
                        cudaStream_t s) {
-  p_transfer_kernel<TV, false><<<grid_for(gc.N), 256, 0, s>>>(gc, gf, rf, bc);
+  launch_pdl(p_transfer_kernel<TV, false>, dim3(grid_for(gc.N)), dim3(256), 0, s, gc, gf, rf, bc);
 }
 template <typename TV>
 void launch_p_prolong_add(const LevelGeom& gc, const LevelGeom& gf, const TV* xc, TV* xf,
                           cudaStream_t s) {
-  p_transfer_kernel<TV, true><<<grid_for(gc.N), 256, 0, s>>>(gc, gf, xc, xf);
+  launch_pdl(p_transfer_kernel<TV, true>, dim3(grid_for(gc.N)), dim3(256), 0, s, gc, gf, xc, xf);
 }
 template <typename TV>
 void launch_h_restrict(const LevelGeom& gc, const LevelGeom& gf, const TV* rf, TV* bc,
                        cudaStream_t s) {
-  h_restrict_kernel<TV><<<grid_for(gc.N), 256, 0, s>>>(gc, gf, rf, bc);
+  launch_pdl(h_restrict_kernel<TV>, dim3(grid_for(gc.N)), dim3(256), 0, s, gc, gf, rf, bc);
 }
 template <typename TV>
 void launch_h_prolong_add(const LevelGeom& gc, const LevelGeom& gf, const TV* xc, TV* xf,
                           cudaStream_t s) {
-  h_prolong_kernel<TV><<<grid_for(gf.N), 256, 0, s>>>(gc, gf, xc, xf);
+  launch_pdl(h_prolong_kernel<TV>, dim3(grid_for(gf.N)), dim3(256), 0, s, gc, gf, xc, xf);
 }
 template <typename TV>
 void launch_coarse_solve(int n, const double* L, const TV* b, TV* x, cudaStream_t s) {
-  coarse_solve_kernel<TV><<<1, 1024, 2 * n * sizeof(double), s>>>(n, L, b, x);
+  launch_pdl(coarse_solve_kernel<TV>, dim3(1), dim3(1024), 2 * n * sizeof(double), s, n, L, b, x);
 }
 
 void launch_dot_partials(const double* a, const double* b, long long n, double* partials,
