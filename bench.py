@@ -62,11 +62,47 @@ TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "stream_kernel_poisson3d_sphere
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2010_00881_gb300", "csrc", "ops.cu")
 
 
+def code_digest(path):
+    """SHA-256 of a C++/CUDA source with comments, blank lines and runs of
+    whitespace removed (string and character literals kept), so that editing
+    comments does not count as a change of the kernels."""
+    import hashlib
+    with open(path) as f:
+        src = f.read()
+    out, i, n, quote = [], 0, len(src), None
+    while i < n:
+        c = src[i]
+        if quote:
+            out.append(c)
+            if c == "\\" and i + 1 < n:
+                out.append(src[i + 1])
+                i += 2
+                continue
+            if c == quote:
+                quote = None
+            i += 1
+        elif c in "\"'":
+            quote = c
+            out.append(c)
+            i += 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    lines = [" ".join(ln.split()) for ln in "".join(out).splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln).encode()).hexdigest()
+
+
 def measured_traffic(workload):
     """DRAM bytes (read + write) per launch of the dominant kernel from the
     committed ncu summary; None when the kernel source changed since the
-    counters were taken (the summary records the source's SHA-256)."""
-    import hashlib
+    counters were taken (the summary records the code digest of ops.cu)."""
     try:
         fields = {}
         with open(TRAFFIC_PROFILE) as f:
@@ -74,9 +110,7 @@ def measured_traffic(workload):
                 if ":" in line and line.startswith("- "):
                     k, v = line[2:].split(":", 1)
                     fields[k.strip()] = v.strip().strip("`")
-        with open(KERNEL_SOURCE, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
-        if fields.get("ops.cu sha256") != digest:
+        if fields.get("ops.cu code sha256") != code_digest(KERNEL_SOURCE):
             return None
         return int(fields["traffic bytes per launch"])
     except (OSError, KeyError, ValueError):
