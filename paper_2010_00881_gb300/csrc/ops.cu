@@ -4,17 +4,18 @@
 // cell (elementwise AS blocks are cells) gather the cell's coefficients,
 // multiply by a dense cell matrix (the stiffness K_c for A, the block
 // inverse A_i^{-1} for M^{-1}), and write the product into a per-cell buffer
-// Y[cell][local].  A second, DOF-centric pass sums the <= 2^d contributions
+// Y[local][cell].  A second, DOF-centric pass sums the <= 2^d contributions
 // of every DOF in a fixed order (no atomics: results are bitwise
 // reproducible) and fuses the vector update (residual b - A x, or
 // x += omega M^{-1} r).
 //
 // Cells whose matrix is a scaled shared matrix (uncut cells, s K_ref; blocks
 // of uncut neighbourhoods, s^{-1} inv(A_ref)) are processed as a tiled GEMM
-// with the shared matrix in shared memory; cells with their own matrix (cut
-// cells, irregular blocks) stream the matrix from HBM, one warp per cell,
-// using the matrix symmetry so that every lane accumulates its own output
-// columns without a reduction.
+// with the shared matrix in shared memory (tile_kernel, tile_df_kernel);
+// cells with their own matrix (cut cells, irregular blocks) are streamed from
+// HBM through a TMA ring (stream_kernel) or, for at most 16 DOFs per cell,
+// read by lane groups (small_kernel).  Every kernel uses the matrix symmetry
+// (row s = column s) so that each lane accumulates its own outputs.
 #include <cmath>
 #include <type_traits>
 
@@ -92,12 +93,13 @@ __device__ __forceinline__ int dof_packed(const LevelGeom& g, int cx, int cy, in
 }
 
 // ---------------------------------------------------------------------------
-// Stored matrices: one warp per cell.  Rows are padded to ld entries so a
-// row is ld / V 16-byte vectors (V entries each).  Lanes are split into R
-// row groups of ncv = ld / V lanes; lane (rg, cv) streams rows rg, rg + R, ...
-// and accumulates the V output columns [cv V, cv V + V): the matrix is
-// symmetric, so row s is column s and y_j += K[s][j] x_s needs no
-// reduction across columns.  The R partial sums are added at the end.
+// Lane mapping of the stored-matrix kernels (stream_kernel; own_role, the
+// one-warp-per-cell fallback): rows are padded to ld entries so a row is
+// ld / V 16-byte vectors (V entries each).  Lanes are split into R row groups
+// of ncv = ld / V lanes; lane (rg, cv) reads rows rg, rg + R, ... and
+// accumulates the V output columns [cv V, cv V + V): the matrix is
+// symmetric, so row s is column s and y_j += K[s][j] x_s needs no reduction
+// across columns.  The R partial sums are added at the end.
 template <typename TM>
 struct Elem;
 template <>
