@@ -15,7 +15,10 @@ Test infrastructure only (see ``oracle/__init__``).
   (dense Cholesky), the "exact" solve on level 0 of Algorithm 1.
 * Additive Schwarz smoother (Eq. AdditiveSchwarz) with elementwise blocks
   (Sec. 3.3.1): block i holds every DOF supported on cell i,
-  A_i = P_i^T A P_i, M^{-1} = sum_i P_i A_i^{-1} P_i^T.  Relaxation
+  A_i = P_i^T A P_i, M^{-1} = sum_i P_i A_i^{-1} P_i^T; or with patchwise
+  blocks (Sec. 3.3.1, the grouping the paper uses for multi-level hp grids
+  and compares on uniform ones in Sec. 4.1): block v holds every DOF
+  supported on the (up to 2^d) cells around mesh node v.  Relaxation
   (Sec. 3.3.2): omega = 1/3 (2D) and 2/15 (3D) elementwise, 1/6 and 1/18
   patchwise, on every level l != 0.  Sec. 3.3.2 derives omega from the
   stability condition rho(I - omega M^{-1} A) < 1, i.e. omega < 2 / lambda_max,
@@ -113,20 +116,47 @@ class Level:
         self.Ainv = None
         self.chol = None
 
-    def build_blocks(self):
-        """Elementwise additive Schwarz blocks: A_i = P_i^T A P_i, inverted
-        through its Cholesky factor."""
-        IDX = np.array([cell_dofs(self.dim, self.cells, self.p, c, self.nf)
-                        for c in all_cells(self.dim, self.cells)])
-        n = IDX.shape[1]
-        Ainv = np.empty((len(IDX), n, n))
-        for i, idx in enumerate(IDX):
-            Ai = self.A[idx][:, idx].toarray()
-            L = np.linalg.cholesky(Ai)
-            Linv = sla.solve_triangular(L, np.eye(n), lower=True)
-            Ainv[i] = Linv.T @ Linv
-        self.IDX = IDX
-        self.Ainv = Ainv
+    def block_dofs(self, smoother="elementwise"):
+        """Global DOF indices of every additive Schwarz block: one block per
+        cell (elementwise) or per mesh node (patchwise: the union of the
+        cells' DOFs around the node, sorted)."""
+        if smoother == "elementwise":
+            return [cell_dofs(self.dim, self.cells, self.p, c, self.nf)
+                    for c in all_cells(self.dim, self.cells)]
+        blocks = []
+        for v in itertools.product(*[range(self.cells[a] + 1) for a in reversed(range(self.dim))]):
+            v = tuple(reversed(v))  # x fastest
+            cs = []
+            for off in itertools.product((0, 1), repeat=self.dim):
+                c = tuple(v[a] - off[a] for a in range(self.dim))
+                if all(0 <= c[a] < self.cells[a] for a in range(self.dim)):
+                    cs.append(c)
+            blocks.append(np.unique(np.concatenate(
+                [cell_dofs(self.dim, self.cells, self.p, c, self.nf) for c in cs])))
+        return blocks
+
+    def build_blocks(self, smoother="elementwise"):
+        """Additive Schwarz blocks A_i = P_i^T A P_i, inverted through
+        their Cholesky factor.  Blocks of equal size are stacked (IDX, Ainv
+        for the elementwise case, where all have the same size; `groups`
+        holds one (IDX, Ainv) pair per block size)."""
+        by_size = {}
+        for idx in self.block_dofs(smoother):
+            by_size.setdefault(len(idx), []).append(idx)
+        self.groups = []
+        for n, lst in sorted(by_size.items()):
+            IDX = np.array(lst)
+            Ainv = np.empty((len(IDX), n, n))
+            for i, idx in enumerate(IDX):
+                Ai = self.A[idx][:, idx].toarray()
+                L = np.linalg.cholesky(Ai)
+                Linv = sla.solve_triangular(L, np.eye(n), lower=True)
+                Ainv[i] = Linv.T @ Linv
+            self.groups.append((IDX, Ainv))
+        if len(self.groups) == 1:
+            self.IDX, self.Ainv = self.groups[0]
+        else:
+            self.IDX = self.Ainv = None
 
     def lambda_max_estimate(self, iters=POWER_ITERS):
         """Power method on M^{-1} A (self-adjoint in the A inner product):
@@ -142,9 +172,11 @@ class Level:
 
     def smoother(self, r):
         """M^{-1} r = sum_i P_i A_i^{-1} P_i^T r."""
-        R = r[self.IDX]
-        Z = np.einsum("bij,bj->bi", self.Ainv, R)
-        return np.bincount(self.IDX.ravel(), weights=Z.ravel(), minlength=self.N)
+        z = np.zeros(self.N)
+        for IDX, Ainv in self.groups:
+            Z = np.einsum("bij,bj->bi", Ainv, r[IDX])
+            z += np.bincount(IDX.ravel(), weights=Z.ravel(), minlength=self.N)
+        return z
 
 
 class Hierarchy:
@@ -157,8 +189,10 @@ class Hierarchy:
         self.b = b
         d = prob["dim"]
         nf = nfields(prob)
+        self.smoother_kind = prob.get("smoother", "elementwise")
         self.omega = omega if omega is not None else (
-            prob["omega"] if prob.get("omega") is not None else default_omega(d))
+            prob["omega"] if prob.get("omega") is not None
+            else default_omega(d, self.smoother_kind))
         self.n_pre = prob["n_pre"]
         self.n_post = prob["n_post"]
         cells = tuple(prob["cells"])
@@ -181,7 +215,7 @@ class Hierarchy:
         levels.reverse()
         self.levels = levels
         for lv in levels[1:]:
-            lv.build_blocks()
+            lv.build_blocks(self.smoother_kind)
             lv.lam = lv.lambda_max_estimate()
             lv.omega = min(self.omega, THETA / lv.lam)
         c = levels[0]

@@ -183,3 +183,56 @@ def test_pcg_flexible_equals_standard_for_symmetric_preconditioner(circle_h):
     x2, k2, _ = mg.pcg(circle_h.A, circle_h.b, circle_h.vcycle, rtol=1e-10, flexible=True)
     assert abs(k1 - k2) <= 1
     assert np.linalg.norm(x1 - x2) <= 1e-8 * np.linalg.norm(x1)
+
+
+# --- patchwise additive Schwarz blocks (Sec. 3.3.1) ----------------------
+
+@pytest.mark.parametrize("dim,p,nf", [(2, 2, 1), (2, 4, 1), (3, 2, 1), (3, 1, 3)])
+def test_patchwise_block_sizes_match_upper_bound_table(dim, p, nf):
+    """Table tab::upperbound, tensor product space, patchwise (n = 2):
+    m_max = n_f (2 p + 1)^d, reached by the blocks of interior nodes; blocks
+    of boundary nodes hold the DOFs of the cells that exist."""
+    import scipy.sparse as sp
+    C = (3,) * dim
+    from oracle.grid import ndofs
+    N = ndofs(dim, C, p, nf)
+    lv = mg.Level(sp.identity(N, format="csr"), C, p, nf, dim)
+    blocks = lv.block_dofs("patchwise")
+    assert len(blocks) == 4 ** dim  # one block per mesh node
+    sizes = [len(b) for b in blocks]
+    assert max(sizes) == nf * (2 * p + 1) ** dim
+    # interior node (1, 1, ...): the 2^d cells around it
+    interior = blocks[sum(4 ** a for a in range(dim))]
+    assert len(interior) == nf * (2 * p + 1) ** dim == len(set(interior))
+
+
+@pytest.fixture(scope="module")
+def circle_patch():
+    prob = fi.poisson2d_circle(cells=8, p=2)
+    prob["smoother"] = "patchwise"
+    return mg.Hierarchy(prob)
+
+
+def test_patchwise_smoother_and_vcycle(circle_patch):
+    """Patchwise M^{-1} symmetric, M^{-1} A with positive spectrum, omega
+    inside the stability bound (paper value 1/6 in 2D, clamped as for
+    elementwise blocks), V-cycle symmetric positive definite."""
+    for lv in circle_patch.levels[1:]:
+        A = lv.A.toarray()
+        Minv = _dense(lv.smoother, lv.N)
+        assert np.allclose(Minv, Minv.T, atol=1e-10 * np.abs(Minv).max())
+        lam = np.linalg.eigvals(Minv @ A).real
+        assert lam.min() > 0
+        assert lv.omega <= 1.0 / 6.0 + 1e-15
+        assert lv.omega * lam.max() < 2.0
+    N = circle_patch.A.shape[0]
+    V = _dense(circle_patch.vcycle, N)
+    assert np.abs(V - V.T).max() < 1e-9 * np.abs(V).max()
+    assert np.linalg.eigvalsh((V + V.T) / 2).min() > 0
+
+
+def test_patchwise_pcg_matches_direct_solve(circle_patch):
+    x, k, hist = mg.pcg(circle_patch.A, circle_patch.b, circle_patch.vcycle, rtol=1e-12)
+    xd = spla.spsolve(circle_patch.A.tocsc(), circle_patch.b)
+    e = x - xd
+    assert np.sqrt(e @ (circle_patch.A @ e)) / np.sqrt(xd @ (circle_patch.A @ xd)) < 1e-9
