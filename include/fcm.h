@@ -168,6 +168,24 @@ fcm_status fcm_setup(const fcm_grid* grid, const fcm_geometry* geom,
 
 fcm_status fcm_ndofs(const fcm_handle* h, long long* n);
 
+/* The DOF layout above, for callers that hold vectors in another order
+ * (no GPU, no handle needed).  Modes follow the hierarchical basis of
+ * Sec. 2.1: nodal modes are shared by the two cells at a node, bubble
+ * modes belong to one cell.
+ * fcm_dof_layout: the 1D map of one axis with `cells` cells and degree p:
+ *   map[c (p+1) + j] = 1D index of local mode j of cell c, i.e. c for
+ *   j = 0, c + 1 for j = 1, (cells + 1) + (j - 2) cells + c for j >= 2.
+ *   map: caller array of cells (p+1) ints.
+ * fcm_cell_dofs: global indices of the nf (p+1)^dim DOFs of cell `cell`
+ *   (linear cell index, x fastest) in local order j_x + (p+1) j_y +
+ *   (p+1)^2 j_z, fields stacked (field f adds f M, M = prod_a (cells_a p + 1)).
+ *   dofs: caller array of nf (p+1)^dim long longs.
+ * Both return FCM_E_INVALID for dim not 2 or 3, cells < 1, p outside
+ * [1, 8], nf < 1, a cell outside the grid or a NULL output. */
+fcm_status fcm_dof_layout(int cells, int p, int* map);
+fcm_status fcm_cell_dofs(int dim, const int* cells, int p, int nf, long long cell,
+                         long long* dofs);
+
 /* Copy the assembled load vector b into b_dev (ndofs doubles). */
 fcm_status fcm_rhs(const fcm_handle* h, double* b_dev);
 

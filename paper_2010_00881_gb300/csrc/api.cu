@@ -1058,6 +1058,57 @@ fcm_status fcm_ndofs(const fcm_handle* h, long long* n) {
   return FCM_OK;
 }
 
+fcm_status fcm_dof_layout(int cells, int p, int* map) {
+  if (cells < 1 || p < 1 || p > kMaxP || !map) {
+    g_last_error = "fcm_dof_layout: invalid argument";
+    return FCM_E_INVALID;
+  }
+  for (int c = 0; c < cells; ++c)
+    for (int j = 0; j <= p; ++j) map[c * (p + 1) + j] = dof1(cells, c, j);
+  return FCM_OK;
+}
+
+fcm_status fcm_cell_dofs(int dim, const int* cells, int p, int nf, long long cell,
+                         long long* dofs) {
+  if ((dim != 2 && dim != 3) || !cells || p < 1 || p > kMaxP || nf < 1 || !dofs) {
+    g_last_error = "fcm_cell_dofs: invalid argument";
+    return FCM_E_INVALID;
+  }
+  long long m[3] = {1, 1, 1}, ncell = 1;
+  int c3[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) {
+    if (cells[a] < 1) {
+      g_last_error = "fcm_cell_dofs: cells must be >= 1";
+      return FCM_E_INVALID;
+    }
+    m[a] = (long long)cells[a] * p + 1;
+    ncell *= cells[a];
+  }
+  if (cell < 0 || cell >= ncell) {
+    g_last_error = "fcm_cell_dofs: cell outside the grid";
+    return FCM_E_INVALID;
+  }
+  long long t = cell;
+  for (int a = 0; a < dim; ++a) {
+    c3[a] = (int)(t % cells[a]);
+    t /= cells[a];
+  }
+  const long long M = m[0] * m[1] * m[2];
+  const int P1 = p + 1;
+  const int nls = dim == 2 ? P1 * P1 : P1 * P1 * P1;
+  for (int f = 0; f < nf; ++f)
+    for (int l = 0; l < nls; ++l) {
+      const int j[3] = {l % P1, (l / P1) % P1, dim == 3 ? l / (P1 * P1) : 0};
+      long long g = 0, stride = 1;
+      for (int a = 0; a < dim; ++a) {
+        g += dof1(cells[a], c3[a], j[a]) * stride;
+        stride *= m[a];
+      }
+      dofs[(long long)f * nls + l] = f * M + g;
+    }
+  return FCM_OK;
+}
+
 fcm_status fcm_rhs(const fcm_handle* hc, double* b_dev) {
   fcm_handle* h = const_cast<fcm_handle*>(hc);
   if (!h || !b_dev) {

@@ -29,7 +29,8 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
            "fcm_level_info_get", "fcm_level_op", "fcm_cell_classes", "fcm_pcg_solve",
            "fcm_pcg_solve_host", "fcm_profile_op", "fcm_op_bytes", "fcm_cell_apply_noalloc",
            "fcm_setup_batch", "fcm_batch_size", "fcm_batch_handle", "fcm_pcg_solve_batch",
-           "fcm_batch_destroy", "fcm_destroy", "fcm_last_error"]
+           "fcm_batch_destroy", "fcm_destroy", "fcm_last_error", "fcm_dof_layout",
+           "fcm_cell_dofs"]
 
 
 class fcm_grid(C.Structure):
@@ -115,6 +116,9 @@ def load():
     lib.fcm_batch_destroy.restype = None
     lib.fcm_destroy.argtypes = [P]
     lib.fcm_destroy.restype = None
+    lib.fcm_dof_layout.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int)]
+    lib.fcm_cell_dofs.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_longlong,
+                                  C.POINTER(C.c_longlong)]
     lib.fcm_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("fcm_destroy", "fcm_batch_destroy", "fcm_last_error"):
@@ -133,6 +137,22 @@ def _check(st, allow=()):
     if st != FCM_OK and st not in allow:
         raise FcmError(st, load().fcm_last_error().decode())
     return st
+
+
+def dof_layout(cells: int, p: int) -> np.ndarray:
+    """1D index of local mode j of cell c on one axis: map[c, j]."""
+    out = np.empty(cells * (p + 1), dtype=np.int32)
+    _check(load().fcm_dof_layout(cells, p, out.ctypes.data_as(C.POINTER(C.c_int))))
+    return out.reshape(cells, p + 1)
+
+
+def cell_dofs(dim: int, cells, p: int, nf: int, cell: int) -> np.ndarray:
+    """Global indices of the DOFs of one cell (linear index, x fastest)."""
+    cs = (C.c_int * 3)(*(list(cells) + [1] * (3 - len(cells))))
+    out = np.empty(nf * (p + 1) ** dim, dtype=np.int64)
+    _check(load().fcm_cell_dofs(dim, cs, p, nf, cell,
+                                out.ctypes.data_as(C.POINTER(C.c_longlong))))
+    return out
 
 
 def descriptors(prob: dict, build_mixed: bool = True):

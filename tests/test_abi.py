@@ -55,3 +55,29 @@ def test_descriptor_marshalling_roundtrip():
     prob = fi.square_mms(cells=8, p=2)
     g, gm, ph, op, keep = fcm.descriptors(prob)
     assert ph.dirichlet_faces == 0b1111 and ph.kappa == 10.0
+
+
+def test_dof_layout_matches_the_oracle():
+    """fcm_dof_layout / fcm_cell_dofs (host functions, no GPU) against the
+    oracle's numbering of the hierarchical basis, bit-exact."""
+    from oracle.grid import all_cells, cell_dofs as ocell, dof_1d
+    from paper_2010_00881_gb300 import fcm
+    for C_, p in ((1, 1), (5, 3), (8, 4)):
+        m = fcm.dof_layout(C_, p)
+        assert [[dof_1d(C_, c, j) for j in range(p + 1)] for c in range(C_)] == m.tolist()
+    for dim, cells, p, nf in (((2, (3, 4), 2, 1)), (3, (2, 3, 2), 3, 1), (3, (3, 2, 2), 2, 3),
+                              (2, (5, 1), 1, 2)):
+        for lin, cell in enumerate(all_cells(dim, cells)):
+            got = fcm.cell_dofs(dim, cells, p, nf, lin)
+            assert got.tolist() == ocell(dim, cells, p, cell, nf).tolist(), (dim, cells, p, cell)
+
+
+def test_dof_layout_rejects_invalid_input():
+    from paper_2010_00881_gb300 import fcm
+    import pytest as _pytest
+    with _pytest.raises(fcm.FcmError):
+        fcm.dof_layout(0, 2)
+    with _pytest.raises(fcm.FcmError):
+        fcm.cell_dofs(3, (2, 2, 2), 2, 1, 8)  # cell 8 of 8
+    with _pytest.raises(fcm.FcmError):
+        fcm.cell_dofs(4, (2, 2, 2), 2, 1, 0)
