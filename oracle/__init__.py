@@ -16,7 +16,8 @@ grids", arXiv 2010.00881):
 * ``assembly``    element matrices and the global system of Eq. (weakform)
 * ``multigrid``   level hierarchy (Eq. restrictionoperation,
                   Eq. hierarchicalMatrices), additive Schwarz smoother
-                  (Eq. AdditiveSchwarz), V-cycle (Algorithm 1), PCG (Sec. 4)
+                  (Eq. AdditiveSchwarz; elementwise or patchwise blocks,
+                  Sec. 3.3.1), V-cycle (Algorithm 1), PCG (Sec. 4)
 
 Pins (tests/test_oracle_*.py) tie each function to something other than
 itself; see the module docstrings.
