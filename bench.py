@@ -423,8 +423,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": wl_name, "ndofs": N, "rtol": RTOL,
-                       "precision": "mixed: FP32 V-cycle, FP64 cut-cell matrices and "
-                                    "ill-conditioned block inverses, FP64 flexible CG",
+                       "precision": "mixed: FP32 V-cycle with FP64-accurate (df32) cut-cell "
+                                    "matrices and ill-conditioned block inverses, flexible CG "
+                                    "in FP64 with an FP64-accurate df32 operator; fp64: plain "
+                                    "FP64 throughout",
                        "l2": "256 MB buffer written between timed solves",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iterations": inf_mixed[-1]["iters"],
