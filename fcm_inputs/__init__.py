@@ -27,6 +27,8 @@ quad_depth                  space-tree depth for cut cells
 omega, n_pre, n_post        smoother settings (omega None: paper default)
 coarse_cells                h-coarsening stops once every axis has at most
                             this many cells
+overlay_levels              multi-level hp refinement depth K (0: uniform)
+smoother                    "elementwise" | "patchwise" (optional)
 """
 from __future__ import annotations
 
@@ -157,6 +159,33 @@ def elasticity3d_voids(cells=64, p=4, alpha=1e-6, n_voids=64, seed=0, quad_depth
                  name=f"elasticity3d_voids_{cells}^3_p{p}")
 
 
+def poisson3d_sphere_mlhp(cells=16, p=2, overlay_levels=3, alpha=1e-8, radius=0.3,
+                          quad_depth=3):
+    """The sphere problem of poisson3d_sphere (manufactured sin solution,
+    Dirichlet data on the sphere by penalty) with r = 0.3 on a 16^3 base grid
+    whose cut cells are overlaid to depth 3 (multi-level hp)."""
+    d = poisson3d_sphere(cells=cells, p=p, alpha=alpha, radius=radius, quad_depth=quad_depth)
+    d.update(overlay_levels=overlay_levels, smoother="patchwise",
+             name=f"poisson3d_sphere_mlhp_{cells}^3_p{p}_k{overlay_levels}")
+    return d
+
+
+def perforated_plate(cells=32, p=2, overlay_levels=0, alpha=1e-8, quad_depth=3):
+    """Plane-strain plate [0,4]^2 with four circular cavities of radius
+    0.3 sqrt(2) centred in its quadrants, E = 2.069e5, nu = 0.29, clamped on
+    x = 0 and pulled by a unit traction on x = 4 (penalty beta = 1e8);
+    cut cells overlaid to depth `overlay_levels`."""
+    r = 0.3 * math.sqrt(2.0)
+    balls = [(1.0, 1.0, 0.0, r), (3.0, 1.0, 0.0, r), (1.0, 3.0, 0.0, r), (3.0, 3.0, 0.0, r)]
+    return _base(2, (cells, cells), p, pde="elasticity", E=2.069e5, nu=0.29, alpha=alpha,
+                 beta=1e8, lo=(0.0, 0.0), hi=(4.0, 4.0),
+                 geometry=dict(kind="voids", balls=balls), source=dict(kind="const", f0=0.0),
+                 dirichlet=dict(kind="faces", g="zero", faces=[0]),
+                 traction=dict(face=1, t=(1.0, 0.0, 0.0)), quad_depth=quad_depth,
+                 overlay_levels=overlay_levels, smoother="patchwise",
+                 name=f"perforated_plate_{cells}^2_p{p}_k{overlay_levels}")
+
+
 def random_rotation(rng: SplitMix64) -> list[list[float]]:
     """Rotation matrix of a uniform random unit quaternion (Shoemake 1992)."""
     u1, u2, u3 = rng.uniform(), rng.uniform(), rng.uniform()
@@ -202,4 +231,6 @@ CONFIGS = {
     "poisson3d_sphere": poisson3d_sphere,
     "elasticity3d_voids": elasticity3d_voids,
     "square_mms": square_mms,
+    "poisson3d_sphere_mlhp": poisson3d_sphere_mlhp,
+    "perforated_plate": perforated_plate,
 }

@@ -18,6 +18,9 @@ grids", arXiv 2010.00881):
                   Eq. hierarchicalMatrices), additive Schwarz smoother
                   (Eq. AdditiveSchwarz; elementwise or patchwise blocks,
                   Sec. 3.3.1), V-cycle (Algorithm 1), PCG (Sec. 4)
+* ``mlhp``        multi-level hp overlays (Sec. 2.2): overlay mesh, active
+                  basis, leaf assembly, hp-multigrid levels (Sec. 3.2,
+                  Fig. hpmultigrid) with patchwise blocks over base cells
 
 Pins (tests/test_oracle_*.py) tie each function to something other than
 itself; see the module docstrings.

@@ -155,8 +155,13 @@ def exact_solution(prob, pts):
 
 
 def _volume_terms(prob, x0, x1, pts, w, alpha):
-    p = prob["p"]
-    N, G = shape_functions(p, x0, x1, pts)
+    N, G = shape_functions(prob["p"], x0, x1, pts)
+    return volume_terms(prob, N, G, pts, w, alpha)
+
+
+def volume_terms(prob, N, G, pts, w, alpha):
+    """Stiffness and load of one integration domain from the scalar shape
+    functions N (Q, n) and their gradients G (Q, n, d) at its points."""
     wa = w * alpha
     f = source_values(prob, pts)
     if prob["pde"] == "poisson":
@@ -177,8 +182,12 @@ def _volume_terms(prob, x0, x1, pts, w, alpha):
 
 def _mass_terms(prob, x0, x1, pts, w, g):
     """beta-free surface mass matrix and load: (int N N^T, int g N)."""
-    p = prob["p"]
-    N, _ = shape_functions(p, x0, x1, pts)
+    N, _ = shape_functions(prob["p"], x0, x1, pts)
+    return mass_terms(prob, N, w, g)
+
+
+def mass_terms(prob, N, w, g):
+    """Surface mass matrix and load from the scalar shape functions N (Q, n)."""
     Ms = N.T @ (w[:, None] * N)
     nf = nfields(prob)
     if nf == 1:
@@ -191,12 +200,13 @@ def _mass_terms(prob, x0, x1, pts, w, g):
     return M, bb
 
 
-def boundary_faces(prob, cell):
+def boundary_faces(prob, cell, cells=None):
     """Box faces of this cell that carry Dirichlet (kind 'D') or traction
-    ('T') data: list of (face id, kind)."""
+    ('T') data: list of (face id, kind).  `cells`: cells per axis of the
+    lattice the cell index refers to (default: the problem's grid)."""
     out = []
     d = prob["dim"]
-    C = prob["cells"]
+    C = prob["cells"] if cells is None else cells
     dirf = prob["dirichlet"].get("faces", []) if prob["dirichlet"]["kind"] == "faces" else []
     tr = prob.get("traction")
     for a in range(d):

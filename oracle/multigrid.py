@@ -112,6 +112,7 @@ class Level:
         self.dim = dim
         self.N = A.shape[0]
         self.to_coarse = None   # ("p", selection) or ("h", P)
+        self.blocks = None      # explicit additive Schwarz blocks, if given
         self.IDX = None
         self.Ainv = None
         self.chol = None
@@ -141,7 +142,8 @@ class Level:
         for the elementwise case, where all have the same size; `groups`
         holds one (IDX, Ainv) pair per block size)."""
         by_size = {}
-        for idx in self.block_dofs(smoother):
+        blocks = self.blocks if self.blocks is not None else self.block_dofs(smoother)
+        for idx in blocks:
             by_size.setdefault(len(idx), []).append(idx)
         self.groups = []
         for n, lst in sorted(by_size.items()):
@@ -185,16 +187,9 @@ class Hierarchy:
     def __init__(self, prob, A=None, b=None, omega=None):
         if A is None:
             A, b, _ = assemble(prob)
-        self.prob = prob
-        self.b = b
+        self._configure(prob, b, omega)
         d = prob["dim"]
         nf = nfields(prob)
-        self.smoother_kind = prob.get("smoother", "elementwise")
-        self.omega = omega if omega is not None else (
-            prob["omega"] if prob.get("omega") is not None
-            else default_omega(d, self.smoother_kind))
-        self.n_pre = prob["n_pre"]
-        self.n_post = prob["n_post"]
         cells = tuple(prob["cells"])
         levels = [Level(A, cells, prob["p"], nf, d)]
         # arithmetic p-sequence
@@ -203,6 +198,25 @@ class Hierarchy:
             sel = p_selection(d, cells, fine.p, pc, nf)
             fine.to_coarse = ("p", sel)
             levels.append(Level(fine.A[sel][:, sel], cells, pc, nf, d))
+        self._complete(levels)
+
+    def _configure(self, prob, b, omega):
+        self.prob = prob
+        self.b = b
+        self.smoother_kind = prob.get("smoother", "elementwise")
+        self.omega = omega if omega is not None else (
+            prob["omega"] if prob.get("omega") is not None
+            else default_omega(prob["dim"], self.smoother_kind))
+        self.n_pre = prob["n_pre"]
+        self.n_post = prob["n_post"]
+
+    def _complete(self, levels):
+        """Append the nested Q1 h-levels below `levels` (ordered fine to
+        coarse, the last one a Q1 level of the base grid in grid order),
+        then build the smoothers and the coarse factor."""
+        prob = self.prob
+        d = prob["dim"]
+        nf = nfields(prob)
         # nested Q1 h-levels
         cmax = prob["coarse_cells"]
         while max(levels[-1].cells) > cmax:
