@@ -72,7 +72,8 @@ enum { FCM_G_ZERO = 0, FCM_G_SIN3 = 1, FCM_G_SQUARE_MMS = 2 };
 enum { FCM_SMOOTHER_ELEMENTWISE = 0, FCM_SMOOTHER_PATCHWISE = 1 };
 
 /* Grid: dim in {2,3}; cells per axis (>= 1); box [lo, hi]; degree p in
- * [1, 8].  overlay_levels > 0 (multi-level hp) is FCM_E_UNSUPPORTED. */
+ * [1, 8].  overlay_levels > 0 (multi-level hp) is FCM_E_UNSUPPORTED in
+ * fcm_setup; fcm_mlhp_create builds the overlay topology on the host. */
 typedef struct {
   int dim;
   int cells[3];
@@ -185,6 +186,52 @@ fcm_status fcm_ndofs(const fcm_handle* h, long long* n);
 fcm_status fcm_dof_layout(int cells, int p, int* map);
 fcm_status fcm_cell_dofs(int dim, const int* cells, int p, int nf, long long cell,
                          long long* dofs);
+
+/* Multi-level hp overlay topology (Sec. 2.2), host only (no GPU, no device
+ * memory).  Base grid: grid->dim, cells, lo, hi, degree p (all levels);
+ * depth K = grid->overlay_levels in [0, 10], with cells_a 2^K <= 2^19;
+ * overlay_p must be 0 or p.  An element of level k < K is overlaid by its
+ * 2^dim bisection children when `geom` cuts its box (the classification
+ * fcm_setup uses for cells; VOIDS is accepted in 2D here, ball (cx, cy, cz, r)
+ * with cz unused).  Every element carries the (p+1)^dim integrated Legendre
+ * modes on its own box.  A mode belongs to a component of its level's
+ * lattice with doubled coordinates t_a = 2 e_a (left node), 2 e_a + 2 (right
+ * node) or 2 e_a + 1 (bubble).  Active components:
+ *   R1  none of level k >= 1 on the boundary of the union of the level-k
+ *       elements (box faces excluded);
+ *   R2  no vertex of level k >= 1 whose lattice node indices are all even;
+ *   R3  edges, faces and interiors only if they belong to a leaf element.
+ * These functions span exactly the C0 piecewise-Q_p space on the leaves.
+ *
+ * fcm_mlhp_create: builds the topology; *out owned by the caller, released
+ *   by fcm_mlhp_destroy.  FCM_E_INVALID for a NULL argument or any limit
+ *   above; FCM_E_OOM if host memory runs out.
+ * fcm_mlhp_sizes: M scalar functions, L leaves, the total number of
+ *   (leaf, function) incidences and of (base node, function) patch entries.
+ * fcm_mlhp_functions: per function i (ordered by level, then component with
+ *   x fastest, then bubble degrees with the first odd axis fastest):
+ *   level[i], t[3 i + a] (doubled lattice coordinates, 0 on unused axes),
+ *   q[3 i + a] (bubble degree on odd axes, 0 elsewhere).  Caller arrays of
+ *   M, 3 M, 3 M ints.
+ * fcm_mlhp_leaves: per leaf l (ordered by level, then x fastest): level[l],
+ *   index[3 l + a] (lattice cell of its level), and functions[offsets[l] ..
+ *   offsets[l+1]) = the scalar functions supported on it, ancestors from
+ *   the base down, local modes x fastest (the row order of its element
+ *   matrix).  Caller arrays of L, 3 L, L + 1 and n_leaf_entries.
+ * fcm_mlhp_patches: per base node v (x fastest), functions[offsets[v] ..
+ *   offsets[v+1]) = sorted scalar functions touching one of the base cells
+ *   around v: the patchwise additive Schwarz block (Sec. 3.3.1) of field 0.
+ *   Caller arrays of prod_a (cells_a + 1) + 1 and n_patch_entries.
+ * Vector fields stack whole scalar spaces (DOF f M + i). */
+typedef struct fcm_mlhp fcm_mlhp;
+fcm_status fcm_mlhp_create(const fcm_grid* grid, const fcm_geometry* geom, fcm_mlhp** out);
+void fcm_mlhp_destroy(fcm_mlhp* m);
+fcm_status fcm_mlhp_sizes(const fcm_mlhp* m, long long* n_functions, long long* n_leaves,
+                          long long* n_leaf_entries, long long* n_patch_entries);
+fcm_status fcm_mlhp_functions(const fcm_mlhp* m, int* level, int* t, int* q);
+fcm_status fcm_mlhp_leaves(const fcm_mlhp* m, int* level, int* index, long long* offsets,
+                           long long* functions);
+fcm_status fcm_mlhp_patches(const fcm_mlhp* m, long long* offsets, long long* functions);
 
 /* Copy the assembled load vector b into b_dev (ndofs doubles). */
 fcm_status fcm_rhs(const fcm_handle* h, double* b_dev);

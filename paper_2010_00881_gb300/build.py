@@ -2,8 +2,9 @@
 
 Every translation unit is compiled by nvcc in parallel and linked into one
 shared library next to this file.  setup_geom.cu is compiled with
--fmad=false so that its geometric decisions round exactly like any plain
-IEEE-754 evaluation of the same formulas.
+-fmad=false and the host-only mlhp.cu with -ffp-contract=off, so that their
+geometric decisions round exactly like any plain IEEE-754 evaluation of the
+same formulas on either host architecture.
 """
 from __future__ import annotations
 
@@ -27,6 +28,7 @@ SOURCES = {
     "api.cu": [],
     "noalloc.cu": [],
     "batch.cu": [],
+    "mlhp.cu": ["-Xcompiler", "-ffp-contract=off"],
 }
 
 
@@ -40,7 +42,8 @@ def nvcc() -> str:
 def _compile(src: str, extra: list[str], verbose: bool) -> str:
     out = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     srcp = os.path.join(CSRC, src)
-    deps = [srcp, os.path.join(CSRC, "fcm_internal.h"), os.path.join(HERE, "..", "include", "fcm.h")]
+    deps = [srcp, os.path.join(HERE, "..", "include", "fcm.h")]
+    deps += [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
     if os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(d) for d in deps):
         return out
     cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", srcp, "-o", out]

@@ -30,7 +30,8 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
            "fcm_pcg_solve_host", "fcm_profile_op", "fcm_op_bytes", "fcm_cell_apply_noalloc",
            "fcm_setup_batch", "fcm_batch_size", "fcm_batch_handle", "fcm_pcg_solve_batch",
            "fcm_batch_destroy", "fcm_destroy", "fcm_last_error", "fcm_dof_layout",
-           "fcm_cell_dofs"]
+           "fcm_cell_dofs", "fcm_mlhp_create", "fcm_mlhp_destroy", "fcm_mlhp_sizes",
+           "fcm_mlhp_functions", "fcm_mlhp_leaves", "fcm_mlhp_patches"]
 
 
 class fcm_grid(C.Structure):
@@ -119,9 +120,18 @@ def load():
     lib.fcm_dof_layout.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_int)]
     lib.fcm_cell_dofs.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_longlong,
                                   C.POINTER(C.c_longlong)]
+    LL = C.POINTER(C.c_longlong)
+    IP = C.POINTER(C.c_int)
+    lib.fcm_mlhp_create.argtypes = [C.POINTER(fcm_grid), C.POINTER(fcm_geometry), C.POINTER(P)]
+    lib.fcm_mlhp_destroy.argtypes = [P]
+    lib.fcm_mlhp_destroy.restype = None
+    lib.fcm_mlhp_sizes.argtypes = [P, LL, LL, LL, LL]
+    lib.fcm_mlhp_functions.argtypes = [P, IP, IP, IP]
+    lib.fcm_mlhp_leaves.argtypes = [P, IP, IP, LL, LL]
+    lib.fcm_mlhp_patches.argtypes = [P, LL, LL]
     lib.fcm_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("fcm_destroy", "fcm_batch_destroy", "fcm_last_error"):
+        if name not in ("fcm_destroy", "fcm_batch_destroy", "fcm_last_error", "fcm_mlhp_destroy"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -155,6 +165,46 @@ def cell_dofs(dim: int, cells, p: int, nf: int, cell: int) -> np.ndarray:
     return out
 
 
+class Overlay:
+    """Multi-level hp overlay topology of a problem dict, built on the host
+    by the library (fcm_mlhp_*); no GPU is involved."""
+
+    def __init__(self, prob: dict):
+        g, gm, _, _, self._keep = descriptors(prob)
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.fcm_mlhp_create(C.byref(g), C.byref(gm), C.byref(h)))
+        try:
+            n = [C.c_longlong() for _ in range(4)]
+            _check(lib.fcm_mlhp_sizes(h, *[C.byref(v) for v in n]))
+            M, L, nle, npe = (v.value for v in n)
+            IP, LL = C.POINTER(C.c_int), C.POINTER(C.c_longlong)
+            self.level = np.empty(M, dtype=np.int32)
+            self.t = np.empty((M, 3), dtype=np.int32)
+            self.q = np.empty((M, 3), dtype=np.int32)
+            _check(lib.fcm_mlhp_functions(h, self.level.ctypes.data_as(IP),
+                                          self.t.ctypes.data_as(IP), self.q.ctypes.data_as(IP)))
+            self.leaf_level = np.empty(L, dtype=np.int32)
+            self.leaf_index = np.empty((L, 3), dtype=np.int32)
+            self.leaf_offsets = np.empty(L + 1, dtype=np.int64)
+            self.leaf_functions = np.empty(nle, dtype=np.int64)
+            _check(lib.fcm_mlhp_leaves(h, self.leaf_level.ctypes.data_as(IP),
+                                       self.leaf_index.ctypes.data_as(IP),
+                                       self.leaf_offsets.ctypes.data_as(LL),
+                                       self.leaf_functions.ctypes.data_as(LL)))
+            nodes = 1
+            for a in range(prob["dim"]):
+                nodes *= prob["cells"][a] + 1
+            self.patch_offsets = np.empty(nodes + 1, dtype=np.int64)
+            self.patch_functions = np.empty(npe, dtype=np.int64)
+            _check(lib.fcm_mlhp_patches(h, self.patch_offsets.ctypes.data_as(LL),
+                                        self.patch_functions.ctypes.data_as(LL)))
+        finally:
+            lib.fcm_mlhp_destroy(h)
+        self.n_functions = M
+        self.n_leaves = L
+
+
 def descriptors(prob: dict, build_mixed: bool = True):
     """C descriptors for a problem dict of ``fcm_inputs``."""
     d = prob["dim"]
@@ -165,6 +215,7 @@ def descriptors(prob: dict, build_mixed: bool = True):
         g.lo[a] = prob["lo"][a] if a < d else 0.0
         g.hi[a] = prob["hi"][a] if a < d else 0.0
     g.p = prob["p"]
+    g.overlay_levels = prob.get("overlay_levels", 0)
     geo = prob["geometry"]
     kind = geo["kind"]
     if kind == "ball":
@@ -202,7 +253,7 @@ def descriptors(prob: dict, build_mixed: bool = True):
             ph.traction[a] = tr["t"][a] if a < len(tr["t"]) else 0.0
     ph.quad_depth = prob["quad_depth"]
     op = fcm_solver_opts()
-    op.smoother = 0
+    op.smoother = {"elementwise": 0, "patchwise": 1}[prob.get("smoother", "elementwise")]
     op.omega = prob["omega"] if prob.get("omega") else 0.0
     op.n_pre = prob["n_pre"]
     op.n_post = prob["n_post"]

@@ -81,3 +81,67 @@ def test_dof_layout_rejects_invalid_input():
         fcm.cell_dofs(3, (2, 2, 2), 2, 1, 8)  # cell 8 of 8
     with _pytest.raises(fcm.FcmError):
         fcm.cell_dofs(4, (2, 2, 2), 2, 1, 0)
+
+
+def _oracle_topology(prob):
+    from oracle.mlhp import MlhpSpace, mesh_for, schwarz_blocks
+    import numpy as np
+    space = MlhpSpace(mesh_for(prob), prob["p"], 1)
+    d = prob["dim"]
+    level, t, q = [], [], []
+    for k, tt, qs in space.funcs:
+        level.append(k)
+        t.append(list(tt) + [0] * (3 - d))
+        qq, i = [0, 0, 0], 0
+        for a in range(d):
+            if tt[a] % 2:
+                qq[a] = qs[i]
+                i += 1
+        q.append(qq)
+    leaves, lf = [], []
+    for k, e in space.mesh.leaves():
+        leaves.append((k, list(e) + [0] * (3 - d)))
+        lf.append(np.concatenate([ids for _, _, _, ids in space.leaf_functions(k, e)]).tolist())
+    patches = [b.tolist() for b in schwarz_blocks(space, np.arange(space.M), "patchwise")]
+    return level, t, q, leaves, lf, patches
+
+
+@pytest.mark.parametrize("make", [
+    lambda fi: dict(fi.poisson2d_circle(cells=8, p=2), overlay_levels=3),
+    lambda fi: dict(fi.poisson2d_circle(cells=5, p=3, radius=0.3), overlay_levels=2),
+    lambda fi: fi.perforated_plate(cells=8, p=2, overlay_levels=2),
+    lambda fi: dict(fi.poisson3d_sphere(cells=4, p=2, radius=0.3), overlay_levels=2),
+    lambda fi: dict(fi.batch_instance(3), cells=(3, 3, 3), p=2, overlay_levels=1),
+])
+def test_overlay_topology_matches_the_oracle(make):
+    """fcm_mlhp_* (host functions, no GPU): refinement, active functions and
+    their numbering, the per-leaf function lists and the patches, bit-exact
+    against oracle/mlhp.py."""
+    import fcm_inputs as fi
+    from paper_2010_00881_gb300 import fcm
+    prob = make(fi)
+    ov = fcm.Overlay(prob)
+    level, t, q, leaves, lf, patches = _oracle_topology(prob)
+    assert ov.n_functions == len(level) and ov.n_leaves == len(leaves)
+    assert ov.level.tolist() == level
+    assert ov.t.tolist() == t and ov.q.tolist() == q
+    assert [(int(k), e.tolist()) for k, e in zip(ov.leaf_level, ov.leaf_index)] == leaves
+    off = ov.leaf_offsets
+    assert [ov.leaf_functions[off[i]:off[i + 1]].tolist() for i in range(len(leaves))] == lf
+    po = ov.patch_offsets
+    assert [ov.patch_functions[po[i]:po[i + 1]].tolist() for i in range(len(po) - 1)] == patches
+    assert max(ov.leaf_level) == prob["overlay_levels"]
+
+
+def test_overlay_topology_rejects_invalid_input():
+    import fcm_inputs as fi
+    from paper_2010_00881_gb300 import fcm
+    base = dict(fi.poisson2d_circle(cells=8, p=2), overlay_levels=2)
+    for bad in (dict(base, overlay_levels=11), dict(base, p=0), dict(base, p=9),
+                dict(base, cells=(1 << 18, 2), overlay_levels=2),
+                dict(base, geometry=dict(kind="ellipsoid", center=(0.5, 0.5, 0.5),
+                                         axes=(0.3, 0.3, 0.3),
+                                         rot=[[1, 0, 0], [0, 1, 0], [0, 0, 1]]))):
+        with pytest.raises(fcm.FcmError) as e:
+            fcm.Overlay(bad)
+        assert e.value.status == fcm.FCM_E_INVALID
