@@ -359,3 +359,16 @@ def test_perforated_plate_iteration_table():
     ref = g["cg_mg_elementwise"][:3]
     assert all(b > a for a, b in zip(elem, elem[1:])), elem
     assert elem[0] <= ref[0] + 3 and elem[2] >= ref[2], (elem, ref)
+
+
+def test_iterations_flat_in_the_refinement_depth_3d():
+    """Sec. 4.3 (influence of the refinement level): with patchwise blocks
+    the CG+MG count does not depend on the overlay depth in 3D either.  The
+    sphere workload with overlays (r = 0.3, p = 2) on a 4^3 base grid,
+    depths 0, 1, 2 (729, 2,353 and 8,249 DOFs)."""
+    ks = []
+    for depth in range(3):
+        H = MlhpHierarchy(fi.poisson3d_sphere_mlhp(cells=4, p=2, overlay_levels=depth))
+        _, k, _ = pcg(H.A, H.b, H.vcycle, rtol=1e-8, maxit=200)
+        ks.append(k)
+    assert max(ks) - min(ks) <= 2 and max(ks) <= 12, ks
