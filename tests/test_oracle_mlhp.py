@@ -372,3 +372,41 @@ def test_iterations_flat_in_the_refinement_depth_3d():
         _, k, _ = pcg(H.A, H.b, H.vcycle, rtol=1e-8, maxit=200)
         ks.append(k)
     assert max(ks) - min(ks) <= 2 and max(ks) <= 12, ks
+
+
+def _leaf_transform(space, k, e):
+    """T (nf (p+1)^d x nf n_L): the leaf's own modal coefficients of every
+    function supported on it (exact: each is a degree-p polynomial there)."""
+    x0, x1 = space.mesh.box(k, e)
+    pts, _ = leaf_rule(x0, x1, space.p)
+    V, _ = shape_functions(space.p, x0, x1, pts)
+    ids, N, _ = space.eval_on_leaf(k, e, pts)
+    return ids, np.kron(np.eye(space.nf), np.linalg.solve(V, N))
+
+
+@pytest.mark.parametrize("prob", [
+    dict(fi.poisson2d_circle(cells=4, p=3), overlay_levels=2),
+    fi.perforated_plate(cells=4, p=2, overlay_levels=2),
+    fi.poisson3d_sphere_mlhp(cells=2, p=2, overlay_levels=2),
+])
+def test_leaf_matrix_is_the_own_cell_matrix_in_ancestor_coordinates(prob):
+    """K_L = T^T K_own T and b_L = T^T b_own, where K_own, b_own are the
+    uniform element system of a cell with the leaf's box (same space tree,
+    surface and face rules) and T re-expresses the leaf's functions in the
+    leaf's own modes: the leaf assembly reduces to the uniform one."""
+    from oracle.assembly import element_system
+    from oracle.mlhp import leaf_system
+    A, _, space = assemble_mlhp(prob)
+    mesh = space.mesh
+    cut = 0
+    for k, e in mesh.leaves():
+        ids, KL, bL, cls = leaf_system(prob, space, k, e)
+        lat = tuple(mesh.lattice(k, a) for a in range(mesh.dim))
+        Kown, bown, cls_u = element_system(dict(prob, cells=lat), e)
+        assert cls == cls_u
+        _, T = _leaf_transform(space, k, e)
+        G = T.T @ Kown @ T
+        assert np.abs(KL - G).max() <= 1e-11 * np.abs(KL).max()
+        assert np.abs(bL - T.T @ bown).max() <= 1e-11 * max(np.abs(bL).max(), 1e-300)
+        cut += cls == CUT
+    assert cut > 0
