@@ -23,6 +23,7 @@
 // decisions (box classification of geom.h) round like a plain IEEE-754
 // evaluation.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <memory>
 #include <new>
@@ -309,7 +310,8 @@ void validate(const fcm_grid* g, const fcm_geometry* geom) {
     if (g->cells[a] < 1) throw Invalid{"fcm_mlhp_create: cells must be >= 1"};
     if (((long long)g->cells[a] << g->overlay_levels) > kMaxLattice)
       throw Invalid{"fcm_mlhp_create: cells * 2^overlay_levels exceeds 2^19 on an axis"};
-    if (!(g->hi[a] > g->lo[a])) throw Invalid{"fcm_mlhp_create: empty box"};
+    if (!std::isfinite(g->lo[a]) || !std::isfinite(g->hi[a]) || !(g->hi[a] > g->lo[a]))
+      throw Invalid{"fcm_mlhp_create: box corners must be finite with hi > lo"};
   }
   if (geom->kind < FCM_GEOM_NONE || geom->kind > FCM_GEOM_ELLIPSOID)
     throw Invalid{"fcm_mlhp_create: unknown geometry kind"};
@@ -322,6 +324,9 @@ void validate(const fcm_grid* g, const fcm_geometry* geom) {
     throw Invalid{"fcm_mlhp_create: the ellipsoid is 3D"};
   if (geom->n_params < need || (need && !geom->params))
     throw Invalid{"fcm_mlhp_create: too few geometry parameters"};
+  for (int i = 0; i < geom->n_params; ++i)
+    if (!std::isfinite(geom->params[i]))
+      throw Invalid{"fcm_mlhp_create: non-finite geometry parameter"};
 }
 
 }  // namespace

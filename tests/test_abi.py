@@ -141,7 +141,9 @@ def test_overlay_topology_rejects_invalid_input():
                 dict(base, cells=(1 << 18, 2), overlay_levels=2),
                 dict(base, geometry=dict(kind="ellipsoid", center=(0.5, 0.5, 0.5),
                                          axes=(0.3, 0.3, 0.3),
-                                         rot=[[1, 0, 0], [0, 1, 0], [0, 0, 1]]))):
+                                         rot=[[1, 0, 0], [0, 1, 0], [0, 0, 1]])),
+                dict(base, geometry=dict(kind="ball", center=(0.5, float("nan")), radius=0.3)),
+                dict(base, hi=(1.0, float("inf")))):
         with pytest.raises(fcm.FcmError) as e:
             fcm.Overlay(bad)
         assert e.value.status == fcm.FCM_E_INVALID
