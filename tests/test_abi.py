@@ -108,6 +108,8 @@ def _oracle_topology(prob):
 
 @pytest.mark.parametrize("make", [
     lambda fi: dict(fi.poisson2d_circle(cells=8, p=2), overlay_levels=3),
+    lambda fi: dict(fi.poisson2d_circle(cells=6, p=1), overlay_levels=3),
+    lambda fi: dict(fi.elasticity3d_voids(cells=4, p=1, n_voids=3), overlay_levels=1),
     lambda fi: dict(fi.poisson2d_circle(cells=5, p=3, radius=0.3), overlay_levels=2),
     lambda fi: fi.perforated_plate(cells=8, p=2, overlay_levels=2),
     lambda fi: dict(fi.poisson3d_sphere(cells=4, p=2, radius=0.3), overlay_levels=2),
