@@ -233,6 +233,28 @@ fcm_status fcm_mlhp_leaves(const fcm_mlhp* m, int* level, int* index, long long*
                            long long* functions);
 fcm_status fcm_mlhp_patches(const fcm_mlhp* m, long long* offsets, long long* functions);
 
+/* fcm_mlhp_leaf_classes: per leaf, the class of its box (0 inside, 1
+ *   outside, 2 cut; the test fcm_setup uses for cells).  Caller array of L.
+ * fcm_mlhp_levels: the hp-multigrid levels of Sec. 3.2 (Fig. hpmultigrid),
+ *   numbered from the coarsest (0, the base grid's hats) to the finest
+ *   (n_levels - 1, all functions): the degree is lowered first (p, ..., 1),
+ *   then at p = 1 the hats of overlay levels K, ..., 1 are removed, skipping
+ *   overlay levels without active hats; n_levels = p + the removals kept.
+ *   coarsest[i]: the lowest level that holds function i; level l holds
+ *   exactly the functions with coarsest <= l (nested, binary transfers).
+ *   Caller array of M ints.
+ * fcm_mlhp_restriction_1d: the 1D restriction of the p+1 modes of an
+ *   ancestor interval to its sub-interval pos (0 <= pos < 2^dk, 0 <= dk <=
+ *   10) of relative length 2^-dk, in the sub-interval's own modes:
+ *   S[i (p+1) + j] = coefficient of sub-interval mode i in ancestor mode j
+ *   (exact for these polynomials up to rounding).  The Kronecker product of
+ *   the per-axis S maps an ancestor's tensor modes to a leaf's, so a leaf
+ *   matrix is T^T K_own T with K_own the cell matrix of the leaf's box.
+ *   S: caller array of (p+1)^2 doubles; FCM_E_INVALID outside the limits. */
+fcm_status fcm_mlhp_leaf_classes(const fcm_mlhp* m, signed char* cls);
+fcm_status fcm_mlhp_levels(const fcm_mlhp* m, int* n_levels, int* coarsest);
+fcm_status fcm_mlhp_restriction_1d(int p, int dk, int pos, double* S);
+
 /* Copy the assembled load vector b into b_dev (ndofs doubles). */
 fcm_status fcm_rhs(const fcm_handle* h, double* b_dev);
 

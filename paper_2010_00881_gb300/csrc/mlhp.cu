@@ -69,6 +69,9 @@ struct fcm_mlhp {
   std::vector<std::unordered_map<uint64_t, long long>> comp;  // active component -> first id
   std::vector<int> f_level, f_t, f_q;                    // per function (t, q: 3 each)
   std::vector<int> leaf_level, leaf_index;               // per leaf (index: 3 each)
+  std::vector<signed char> leaf_cls;                     // per leaf: CLS_INSIDE/OUTSIDE/CUT
+  int n_levels = 0;                                      // hp-multigrid levels
+  std::vector<int> f_coarsest;                           // per function: coarsest level holding it
   std::vector<long long> leaf_off, leaf_fn;
   std::vector<long long> patch_off, patch_fn;
 
@@ -220,6 +223,11 @@ struct fcm_mlhp {
         unpack(key, e);
         leaf_level.push_back(k);
         for (int a = 0; a < 3; ++a) leaf_index.push_back(e[a]);
+        {
+          double x0[3], x1[3];
+          box(k, e, x0, x1);
+          leaf_cls.push_back((signed char)fcm::classify_box(geo, x0, x1));
+        }
         for (int jl = 0; jl <= k; ++jl) {
           int ae[3] = {0, 0, 0};
           for (int a = 0; a < dim; ++a) ae[a] = e[a] >> (k - jl);
@@ -240,6 +248,35 @@ struct fcm_mlhp {
         }
         leaf_off.push_back((long long)leaf_fn.size());
       }
+
+    // hp-multigrid levels (Sec. 3.2), coarsest = 0: the degree is lowered
+    // first (p, p-1, ..., 1), then at p = 1 the hats of overlay levels K..1
+    // are removed, skipping overlay levels without active hats.  A function
+    // of degree q >= 2 last appears on the level of degree q; a hat of
+    // overlay level k on the levels above the removal of level k.
+    {
+      std::vector<long long> hats(depth + 1, 0);
+      std::vector<int> deg(f_level.size(), 1);
+      for (size_t f = 0; f < f_level.size(); ++f) {
+        for (int a = 0; a < 3; ++a) deg[f] = std::max(deg[f], f_q[3 * f + a]);
+        if (deg[f] == 1) ++hats[f_level[f]];
+      }
+      std::vector<int> kept;                  // overlay levels whose removal is a level
+      for (int kk = depth; kk >= 1; --kk)
+        if (hats[kk] > 0) kept.push_back(kk);
+      const int nk = (int)kept.size();
+      n_levels = p + nk;
+      f_coarsest.resize(f_level.size());
+      for (size_t f = 0; f < f_level.size(); ++f) {
+        if (deg[f] >= 2) {
+          f_coarsest[f] = n_levels - 1 - (p - deg[f]);
+        } else {
+          int above = 0;                      // kept removals of levels above this hat's
+          for (int kk : kept) above += kk > f_level[f];
+          f_coarsest[f] = n_levels - 1 - (p - 1 + above);
+        }
+      }
+    }
 
     // patches: functions touching the base cells around each base node
     long long nbase = 1;
@@ -298,6 +335,51 @@ struct fcm_mlhp {
 };
 
 namespace {
+
+// Legendre P_0..P_n at x by the three-term recurrence.
+void legendre(int n, double x, double* P) {
+  P[0] = 1.0;
+  if (n >= 1) P[1] = x;
+  for (int k = 1; k < n; ++k) P[k + 1] = ((2 * k + 1) * x * P[k] - k * P[k - 1]) / (k + 1);
+}
+
+// Integrated Legendre modes of degree <= p at x (values and derivatives).
+void modes_1d(int p, double x, double* N, double* dN) {
+  double P[fcm::kMaxP + 1];
+  legendre(p, x, P);
+  N[0] = 0.5 * (1.0 - x);
+  N[1] = 0.5 * (1.0 + x);
+  dN[0] = -0.5;
+  dN[1] = 0.5;
+  for (int j = 2; j <= p; ++j) {
+    N[j] = (P[j] - P[j - 2]) / std::sqrt(4.0 * j - 2.0);
+    dN[j] = std::sqrt((2.0 * j - 1.0) / 2.0) * P[j - 1];
+  }
+}
+
+// n-point Gauss-Legendre rule: Newton on P_n from cos(pi (i - 1/4) / (n + 1/2)).
+void gauss(int n, double* x, double* w) {
+  for (int i = 1; i <= (n + 1) / 2; ++i) {
+    double r = std::cos(M_PI * (i - 0.25) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double P[fcm::kMaxP + 2];
+      legendre(n, r, P);
+      dp = n * (r * P[n] - P[n - 1]) / (r * r - 1.0);
+      const double dr = P[n] / dp;
+      r -= dr;
+      if (std::fabs(dr) <= 1e-17) break;
+    }
+    double P[fcm::kMaxP + 2];
+    legendre(n, r, P);
+    dp = n * (r * P[n] - P[n - 1]) / (r * r - 1.0);
+    const double wi = 2.0 / ((1.0 - r * r) * dp * dp);
+    x[i - 1] = -r;
+    w[i - 1] = wi;
+    x[n - i] = r;
+    w[n - i] = wi;
+  }
+}
 
 void validate(const fcm_grid* g, const fcm_geometry* geom) {
   if (g->dim != 2 && g->dim != 3) throw Invalid{"fcm_mlhp_create: dim must be 2 or 3"};
@@ -410,6 +492,64 @@ fcm_status fcm_mlhp_patches(const fcm_mlhp* m, long long* offsets, long long* fu
   }
   std::copy(m->patch_off.begin(), m->patch_off.end(), offsets);
   std::copy(m->patch_fn.begin(), m->patch_fn.end(), functions);
+  return FCM_OK;
+}
+
+fcm_status fcm_mlhp_leaf_classes(const fcm_mlhp* m, signed char* cls) {
+  if (!m || !cls) {
+    fcm::set_last_error("fcm_mlhp_leaf_classes: null argument");
+    return FCM_E_INVALID;
+  }
+  std::copy(m->leaf_cls.begin(), m->leaf_cls.end(), cls);
+  return FCM_OK;
+}
+
+fcm_status fcm_mlhp_levels(const fcm_mlhp* m, int* n_levels, int* coarsest) {
+  if (!m || !n_levels || !coarsest) {
+    fcm::set_last_error("fcm_mlhp_levels: null argument");
+    return FCM_E_INVALID;
+  }
+  *n_levels = m->n_levels;
+  std::copy(m->f_coarsest.begin(), m->f_coarsest.end(), coarsest);
+  return FCM_OK;
+}
+
+fcm_status fcm_mlhp_restriction_1d(int p, int dk, int pos, double* S) {
+  if (!S || p < 1 || p > fcm::kMaxP || dk < 0 || dk > kMaxOverlay || pos < 0 || pos >= (1 << dk)) {
+    fcm::set_last_error("fcm_mlhp_restriction_1d: invalid argument");
+    return FCM_E_INVALID;
+  }
+  const int P1 = p + 1;
+  if (dk == 0) {                                  // the interval itself
+    for (int i = 0; i < P1; ++i)
+      for (int j = 0; j < P1; ++j) S[i * P1 + j] = i == j ? 1.0 : 0.0;
+    return FCM_OK;
+  }
+  const double s = std::ldexp(1.0, -dk);          // leaf length / ancestor length
+  const double c = -1.0 + s * (2 * pos + 1);      // leaf centre in ancestor coordinates
+  double N[fcm::kMaxP + 1], dN[fcm::kMaxP + 1];
+  // nodal rows: the restricted mode's values at the leaf's end points
+  modes_1d(p, c - s, N, dN);
+  for (int j = 0; j < P1; ++j) S[j] = N[j];
+  modes_1d(p, c + s, N, dN);
+  for (int j = 0; j < P1; ++j) S[P1 + j] = N[j];
+  // bubble rows: bubble derivatives are orthonormal and orthogonal to the
+  // constant derivatives of the nodal modes, so the coefficient of leaf
+  // bubble i is int_{-1}^{1} d/dxi [N_j(c + s xi)] N_i'(xi) dxi (Gauss, exact
+  // for the degree 2p - 2 integrand with p points).  It vanishes exactly for
+  // i > j (the restriction of a degree-j mode has degree j), which includes
+  // the nodal columns j = 0, 1.
+  double xq[fcm::kMaxP], wq[fcm::kMaxP];
+  gauss(p, xq, wq);
+  for (int i = 2; i < P1; ++i)
+    for (int j = 0; j < P1; ++j) S[i * P1 + j] = 0.0;
+  for (int q = 0; q < p; ++q) {
+    double Na[fcm::kMaxP + 1], dNa[fcm::kMaxP + 1], Nl[fcm::kMaxP + 1], dNl[fcm::kMaxP + 1];
+    modes_1d(p, c + s * xq[q], Na, dNa);
+    modes_1d(p, xq[q], Nl, dNl);
+    for (int i = 2; i < P1; ++i)
+      for (int j = i; j < P1; ++j) S[i * P1 + j] += wq[q] * (s * dNa[j]) * dNl[i];
+  }
   return FCM_OK;
 }
 

@@ -31,7 +31,8 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
            "fcm_setup_batch", "fcm_batch_size", "fcm_batch_handle", "fcm_pcg_solve_batch",
            "fcm_batch_destroy", "fcm_destroy", "fcm_last_error", "fcm_dof_layout",
            "fcm_cell_dofs", "fcm_mlhp_create", "fcm_mlhp_destroy", "fcm_mlhp_sizes",
-           "fcm_mlhp_functions", "fcm_mlhp_leaves", "fcm_mlhp_patches"]
+           "fcm_mlhp_functions", "fcm_mlhp_leaves", "fcm_mlhp_patches",
+           "fcm_mlhp_leaf_classes", "fcm_mlhp_levels", "fcm_mlhp_restriction_1d"]
 
 
 class fcm_grid(C.Structure):
@@ -129,6 +130,9 @@ def load():
     lib.fcm_mlhp_functions.argtypes = [P, IP, IP, IP]
     lib.fcm_mlhp_leaves.argtypes = [P, IP, IP, LL, LL]
     lib.fcm_mlhp_patches.argtypes = [P, LL, LL]
+    lib.fcm_mlhp_leaf_classes.argtypes = [P, C.POINTER(C.c_byte)]
+    lib.fcm_mlhp_levels.argtypes = [P, IP, IP]
+    lib.fcm_mlhp_restriction_1d.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.fcm_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("fcm_destroy", "fcm_batch_destroy", "fcm_last_error", "fcm_mlhp_destroy"):
@@ -199,10 +203,25 @@ class Overlay:
             self.patch_functions = np.empty(npe, dtype=np.int64)
             _check(lib.fcm_mlhp_patches(h, self.patch_offsets.ctypes.data_as(LL),
                                         self.patch_functions.ctypes.data_as(LL)))
+            self.leaf_classes = np.empty(L, dtype=np.int8)
+            _check(lib.fcm_mlhp_leaf_classes(h, self.leaf_classes.ctypes.data_as(
+                C.POINTER(C.c_byte))))
+            nl = C.c_int()
+            self.coarsest = np.empty(M, dtype=np.int32)
+            _check(lib.fcm_mlhp_levels(h, C.byref(nl), self.coarsest.ctypes.data_as(IP)))
+            self.n_levels = nl.value
         finally:
             lib.fcm_mlhp_destroy(h)
         self.n_functions = M
         self.n_leaves = L
+
+
+def restriction_1d(p: int, dk: int, pos: int) -> np.ndarray:
+    """S[i, j]: coefficient of sub-interval mode i in ancestor mode j, for
+    sub-interval pos of 2^dk (fcm_mlhp_restriction_1d)."""
+    out = np.empty((p + 1) * (p + 1), dtype=np.float64)
+    _check(load().fcm_mlhp_restriction_1d(p, dk, pos, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out.reshape(p + 1, p + 1)
 
 
 def descriptors(prob: dict, build_mixed: bool = True):

@@ -149,3 +149,89 @@ def test_overlay_topology_rejects_invalid_input():
         with pytest.raises(fcm.FcmError) as e:
             fcm.Overlay(bad)
         assert e.value.status == fcm.FCM_E_INVALID
+
+
+def test_restriction_1d_matches_interpolation():
+    """fcm_mlhp_restriction_1d against the oracle's basis: the ancestor's
+    modes at the sub-interval's Gauss points, solved in the sub-interval's
+    own modes."""
+    import numpy as np
+    from oracle.basis import basis_1d, gauss_legendre
+    from paper_2010_00881_gb300 import fcm
+    for p in range(1, 7):
+        xi, _ = gauss_legendre(p + 1)
+        V = basis_1d(p, xi)[0].T
+        for dk in range(4):
+            s = 2.0 ** -dk
+            for pos in range(1 << dk):
+                c = -1.0 + s * (2 * pos + 1)
+                ref = np.linalg.solve(V, basis_1d(p, c + s * xi)[0].T)
+                S = fcm.restriction_1d(p, dk, pos)
+                assert np.abs(S - ref).max() <= 1e-12, (p, dk, pos)
+        assert np.array_equal(fcm.restriction_1d(p, 0, 0), np.eye(p + 1))
+    for bad in ((0, 0, 0), (9, 0, 0), (2, -1, 0), (2, 2, 4), (2, 11, 0)):
+        with pytest.raises(fcm.FcmError):
+            fcm.restriction_1d(*bad)
+
+
+@pytest.mark.parametrize("make", [
+    lambda fi: dict(fi.poisson2d_circle(cells=6, p=3, radius=0.3), overlay_levels=3),
+    lambda fi: fi.poisson3d_sphere_mlhp(cells=3, p=2, overlay_levels=2),
+])
+def test_leaf_transform_is_a_kronecker_product_of_restrictions(make):
+    """On every leaf, the leaf's own modal coefficients of its functions (the
+    oracle, by interpolation) are the Kronecker products of the per-axis
+    restrictions of their ancestors, columns in the leaf's function order."""
+    import numpy as np
+    import fcm_inputs as fi
+    from oracle.assembly import shape_functions
+    from oracle.mlhp import MlhpSpace, mesh_for
+    from oracle.quadrature import leaf_rule
+    from paper_2010_00881_gb300 import fcm
+    prob = make(fi)
+    space = MlhpSpace(mesh_for(prob), prob["p"], 1)
+    p, d = space.p, prob["dim"]
+    R = {(dk, pos): fcm.restriction_1d(p, dk, pos) for dk in range(4) for pos in range(1 << dk)}
+    modes = space.modes
+    for k, e in space.mesh.leaves():
+        x0, x1 = space.mesh.box(k, e)
+        pts, _ = leaf_rule(x0, x1, p)
+        V, _ = shape_functions(p, x0, x1, pts)
+        ids, N, _ = space.eval_on_leaf(k, e, pts)
+        T = np.linalg.solve(V, N)
+        cols = []
+        for j, _, mcols, _ in space.leaf_functions(k, e):
+            dk = k - j
+            S = [R[(dk, e[a] % (1 << dk))] for a in range(d)]
+            for m in mcols:
+                js = modes[m]
+                col = np.ones(1)
+                for a in reversed(range(d)):      # x fastest: kron(z, y, x)
+                    col = np.kron(col, S[a][:, js[a]])
+                cols.append(col)
+        assert np.abs(np.column_stack(cols) - T).max() <= 1e-12
+
+
+@pytest.mark.parametrize("make", [
+    lambda fi: dict(fi.poisson2d_circle(cells=8, p=3), overlay_levels=3),
+    lambda fi: dict(fi.poisson2d_circle(cells=8, p=1), overlay_levels=2),
+    lambda fi: fi.perforated_plate(cells=8, p=2, overlay_levels=3),
+    lambda fi: fi.poisson3d_sphere_mlhp(cells=4, p=2, overlay_levels=2),
+    lambda fi: dict(fi.poisson2d_circle(cells=4, p=2), overlay_levels=0),
+])
+def test_overlay_leaf_classes_and_levels_match_the_oracle(make):
+    import numpy as np
+    import fcm_inputs as fi
+    from oracle.geometry import classify_box
+    from oracle.mlhp import MlhpSpace, hp_level_sets, mesh_for
+    from paper_2010_00881_gb300 import fcm
+    prob = make(fi)
+    ov = fcm.Overlay(prob)
+    space = MlhpSpace(mesh_for(prob), prob["p"], 1)
+    cls = [classify_box(prob["geometry"], *space.mesh.box(k, e)) for k, e in space.mesh.leaves()]
+    assert ov.leaf_classes.tolist() == cls
+    sets = hp_level_sets(space)
+    n = len(sets)
+    assert ov.n_levels == n
+    for i, s in enumerate(sets):
+        assert np.flatnonzero(ov.coarsest <= n - 1 - i).tolist() == s.tolist(), i
