@@ -21,6 +21,9 @@ grids", arXiv 2010.00881):
 * ``mlhp``        multi-level hp overlays (Sec. 2.2): overlay mesh, active
                   basis, leaf assembly, hp-multigrid levels (Sec. 3.2,
                   Fig. hpmultigrid) with patchwise blocks over base cells
+* ``trunk``       trunk-space elements (the paper's 3D space, Table
+                  tab::upperbound) as a mask on the tensor layout, removal of
+                  fully fictitious cells, their p- and h-multigrid
 
 Pins (tests/test_oracle_*.py) tie each function to something other than
 itself; see the module docstrings.
