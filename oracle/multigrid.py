@@ -30,6 +30,9 @@ Test infrastructure only (see ``oracle/__init__``).
   below 2 for the estimate), in which case omega = THETA / lambda_est.
   lambda_est is the A-inner-product Rayleigh quotient after POWER_ITERS steps
   of the power method on M^{-1} A from the start vector v_i = sin(i + 1).
+* Comparison smoothers (Sec. 4.1, Table tab:testcaseA): damped Jacobi
+  (damping 2/3, not stated in the paper) and symmetric Gauss-Seidel (forward
+  sweeps before, backward sweeps after the coarse correction).
 * V-cycle: Algorithm 1.  The printed algorithm repeats
   x <- x + omega M^{-1} r without refreshing r; read literally n_s steps
   would collapse into one step with n_s omega.  The reading is that r is
@@ -46,6 +49,7 @@ import math
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from .assembly import assemble, nfields
 from .grid import all_cells, cell_dofs, m_1d, ndofs
@@ -55,10 +59,19 @@ THETA = 1.75
 POWER_ITERS = 40
 
 
+AS_KINDS = ("elementwise", "patchwise")
+
+
 def default_omega(dim, smoother="elementwise"):
     if smoother == "elementwise":
         return 1.0 / 3.0 if dim == 2 else 2.0 / 15.0
-    return 1.0 / 6.0 if dim == 2 else 1.0 / 18.0
+    if smoother == "patchwise":
+        return 1.0 / 6.0 if dim == 2 else 1.0 / 18.0
+    if smoother == "jacobi":
+        return 2.0 / 3.0
+    if smoother == "gauss_seidel":
+        return 1.0
+    raise ValueError(smoother)
 
 
 def p_selection(dim, cells, p_fine, p_coarse, nf=1):
@@ -113,6 +126,7 @@ class Level:
         self.N = A.shape[0]
         self.to_coarse = None   # ("p", selection) or ("h", P)
         self.blocks = None      # explicit additive Schwarz blocks, if given
+        self.kind = None        # smoother kind, set with the smoother
         self.IDX = None
         self.Ainv = None
         self.chol = None
@@ -159,6 +173,32 @@ class Level:
             self.IDX, self.Ainv = self.groups[0]
         else:
             self.IDX = self.Ainv = None
+
+    def build_pointwise(self, smoother):
+        """Comparison smoothers of Sec. 4.1: Jacobi (the diagonal) or
+        Gauss-Seidel (the lower and upper triangles with the diagonal)."""
+        if smoother == "jacobi":
+            self.dinv = 1.0 / self.A.diagonal()
+        else:
+            self.lower = sp.tril(self.A, 0, format="csr")
+            self.upper = sp.triu(self.A, 0, format="csr")
+
+    def pre_correction(self, r):
+        """Correction of one pre-smoothing step from the residual r:
+        omega M^{-1} r (additive Schwarz, Jacobi) or a forward Gauss-Seidel
+        sweep (D + L)^{-1} r."""
+        if self.kind == "gauss_seidel":
+            return spla.spsolve_triangular(self.lower, r, lower=True)
+        if self.kind == "jacobi":
+            return self.omega * (self.dinv * r)
+        return self.omega * self.smoother(r)
+
+    def post_correction(self, r):
+        """Post-smoothing: as pre_correction, but a backward Gauss-Seidel
+        sweep (D + U)^{-1} r, so that the V-cycle stays symmetric."""
+        if self.kind == "gauss_seidel":
+            return spla.spsolve_triangular(self.upper, r, lower=False)
+        return self.pre_correction(r)
 
     def lambda_max_estimate(self, iters=POWER_ITERS):
         """Power method on M^{-1} A (self-adjoint in the A inner product):
@@ -228,12 +268,23 @@ class Hierarchy:
             levels.append(Level(Ac, cc, 1, nf, d))
         levels.reverse()
         self.levels = levels
-        for lv in levels[1:]:
-            lv.build_blocks(self.smoother_kind)
-            lv.lam = lv.lambda_max_estimate()
-            lv.omega = min(self.omega, THETA / lv.lam)
+        self._setup_smoothers()
         c = levels[0]
         c.chol = sla.cho_factor(c.A.toarray(), lower=True)
+
+    def _setup_smoothers(self):
+        """Per level l != 0: additive Schwarz blocks with omega clamped by
+        the stability reading, or a comparison smoother (Jacobi with the
+        damping 2/3, symmetric Gauss-Seidel without damping)."""
+        for lv in self.levels[1:]:
+            lv.kind = self.smoother_kind
+            if self.smoother_kind in AS_KINDS:
+                lv.build_blocks(self.smoother_kind)
+                lv.lam = lv.lambda_max_estimate()
+                lv.omega = min(self.omega, THETA / lv.lam)
+            else:
+                lv.build_pointwise(self.smoother_kind)
+                lv.omega = self.omega
 
     @property
     def A(self):
@@ -258,17 +309,16 @@ class Hierarchy:
         lv = self.levels[l]
         if l == 0:
             return sla.cho_solve(lv.chol, b)
-        w = lv.omega
         x = np.zeros_like(b)
         for s in range(self.n_pre):
             r = b - lv.A @ x
-            x = x + w * lv.smoother(r)
+            x = x + lv.pre_correction(r)
         r = b - lv.A @ x
         xc = self.vcycle(self.restrict(l, r), l - 1)
         x = self.prolong_add(l, x, xc)
         for s in range(self.n_post):
             r = b - lv.A @ x
-            x = x + w * lv.smoother(r)
+            x = x + lv.post_correction(r)
         return x
 
 

@@ -32,7 +32,7 @@ import scipy.sparse as sp
 from .assembly import element_system, nfields
 from .geometry import OUTSIDE
 from .grid import all_cells, cell_dofs, local_modes, m_1d, ndofs
-from .multigrid import THETA, Hierarchy, Level, q1_prolongation
+from .multigrid import Hierarchy, Level, q1_prolongation
 
 
 def mode_degrees_1d(C: int, p: int) -> np.ndarray:
@@ -232,10 +232,7 @@ class TrunkHierarchy(Hierarchy):
             nodes = used
         levels.reverse()
         self.levels = levels
-        for lv in levels[1:]:
-            lv.build_blocks(self.smoother_kind)
-            lv.lam = lv.lambda_max_estimate()
-            lv.omega = min(self.omega, THETA / lv.lam)
+        self._setup_smoothers()
         levels[0].chol = sla.cho_factor(levels[0].A.toarray(), lower=True)
 
     def _q1_blocks(self, cells, nodes):

@@ -236,3 +236,35 @@ def test_patchwise_pcg_matches_direct_solve(circle_patch):
     xd = spla.spsolve(circle_patch.A.tocsc(), circle_patch.b)
     e = x - xd
     assert np.sqrt(e @ (circle_patch.A @ e)) / np.sqrt(xd @ (circle_patch.A @ xd)) < 1e-9
+
+
+# --- comparison smoothers of Sec. 4.1 ---------------------------------------
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5])
+def test_jacobi_and_gauss_seidel_iteration_tables(p):
+    """Table tab:testcaseA (psi = 0), h = 1/8: CG with multigrid counts within
+    1 of the paper for damped Jacobi (damping 2/3, a reading) and symmetric
+    Gauss-Seidel; multigrid as a solver within 3 (Jacobi) and 2
+    (Gauss-Seidel); the largest contraction number within 0.1 of Table
+    tab::squareCont (printed for h = 1/32)."""
+    g = json.load(open(os.path.join(GOLDEN, "square_mms_jacobi_gauss_seidel.json")))
+    P = str(p)
+    for kind, cg_key, mg_key, tol in (("jacobi", "cg_mg_jacobi", "mg_solver_jacobi", 3),
+                                      ("gauss_seidel", "cg_mg_symmetric_gauss_seidel",
+                                       "mg_solver_gauss_seidel", 2)):
+        H = mg.Hierarchy(dict(fi.square_mms(cells=g["cells"][0], p=p), smoother=kind))
+        _, k, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=g["rtol"])
+        assert abs(k - g[cg_key][P][0]) <= 1, (kind, p, k)
+        _, ks, rho = mg.mg_solve(H.A, H.b, H.vcycle, rtol=g["rtol"])
+        assert abs(ks - g[mg_key][P][0]) <= tol, (kind, p, ks)
+        assert abs(max(rho) - g["rho_max_h32"][kind][P]) < 0.1, (kind, p, max(rho))
+
+
+def test_gauss_seidel_vcycle_symmetric():
+    """Forward sweeps before and backward sweeps after the coarse correction
+    make the Gauss-Seidel V-cycle symmetric positive definite, as CG needs."""
+    H = mg.Hierarchy(dict(fi.square_mms(cells=4, p=3), smoother="gauss_seidel"))
+    N = H.A.shape[0]
+    V = _dense(H.vcycle, N)
+    assert np.abs(V - V.T).max() < 1e-9 * np.abs(V).max()
+    assert np.linalg.eigvalsh((V + V.T) / 2).min() > 0
