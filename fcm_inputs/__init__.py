@@ -28,7 +28,9 @@ omega, n_pre, n_post        smoother settings (omega None: paper default)
 coarse_cells                h-coarsening stops once every axis has at most
                             this many cells
 overlay_levels              multi-level hp refinement depth K (0: uniform)
-smoother                    "elementwise" | "patchwise" (optional)
+smoother                    "elementwise" | "patchwise" | "jacobi" | "gauss_seidel"
+space, drop_outside         "tensor" | "trunk" elements; remove fully fictitious
+                            cells (oracle only)
 """
 from __future__ import annotations
 
@@ -186,6 +188,37 @@ def perforated_plate(cells=32, p=2, overlay_levels=0, alpha=1e-8, quad_depth=3):
                  name=f"perforated_plate_{cells}^2_p{p}_k{overlay_levels}")
 
 
+def popcorn_centers(r0=0.6):
+    """The twelve bump centres of the popcorn surface (Sec. 4.4) on the
+    sphere of radius r0: (r0/sqrt 5)(2 cos t_k, 2 sin t_k, +-1) with
+    t_k = 2 k pi / 5 (z = +1) and (2k - 1) pi / 5 (z = -1), k = 0..4, and the
+    poles (0, 0, +-r0)."""
+    s = r0 / math.sqrt(5.0)
+    out = []
+    for k in range(5):
+        t = 2.0 * k * math.pi / 5.0
+        out.append((s * 2.0 * math.cos(t), s * 2.0 * math.sin(t), s))
+    for k in range(5):
+        t = (2.0 * k - 1.0) * math.pi / 5.0
+        out.append((s * 2.0 * math.cos(t), s * 2.0 * math.sin(t), -s))
+    out += [(0.0, 0.0, r0), (0.0, 0.0, -r0)]
+    return out
+
+
+def popcorn(cells=97, p=3, alpha=1e-6, quad_depth=3, space="trunk", drop_outside=True):
+    """Popcorn benchmark (Sec. 4.4): the embedding cube (-1, 1)^3, the
+    popcorn level set with r0 = 0.6, A = 3, sigma = 0.2, manufactured
+    u = x^3 + x y^2 + y^3 + z^4 + sin(3 (x^2 + y^2)) (source -Lap u, Dirichlet
+    u on the surface by penalty, beta = 1e4), trunk-space elements, fully
+    fictitious cells removed; 97^3 cells, p = 3 is the paper's coarsest mesh."""
+    return _base(3, (cells,) * 3, p, lo=(-1.0,) * 3, hi=(1.0,) * 3, alpha=alpha, beta=1e4,
+                 geometry=dict(kind="popcorn", r0=0.6, A=3.0, sigma=0.2,
+                               centers=popcorn_centers(0.6)),
+                 source=dict(kind="popcorn"), dirichlet=dict(kind="levelset", g="popcorn"),
+                 quad_depth=quad_depth, space=space, drop_outside=drop_outside,
+                 name=f"popcorn_{cells}^3_p{p}")
+
+
 def random_rotation(rng: SplitMix64) -> list[list[float]]:
     """Rotation matrix of a uniform random unit quaternion (Shoemake 1992)."""
     u1, u2, u3 = rng.uniform(), rng.uniform(), rng.uniform()
@@ -233,4 +266,5 @@ CONFIGS = {
     "square_mms": square_mms,
     "poisson3d_sphere_mlhp": poisson3d_sphere_mlhp,
     "perforated_plate": perforated_plate,
+    "popcorn": popcorn,
 }

@@ -117,6 +117,12 @@ def source_values(prob, pts):
     if s["kind"] == "square_mms":
         a = s["a"]
         return np.cos(a * (pts[:, 0] - 0.5)) * np.sin(a * (pts[:, 1] - 0.5))
+    if s["kind"] == "popcorn":
+        # f = -kappa Lap u for u = x^3 + x y^2 + y^3 + z^4 + sin(3 (x^2 + y^2))
+        x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+        r2 = x * x + y * y
+        lap = 8.0 * x + 6.0 * y + 12.0 * z * z + 12.0 * np.cos(3.0 * r2) - 36.0 * r2 * np.sin(3.0 * r2)
+        return -prob["kappa"] * lap
     raise ValueError(s["kind"])
 
 
@@ -138,6 +144,9 @@ def dirichlet_values(prob, pts):
         a = s["a"]
         return (np.cos(a * (pts[:, 0] - 0.5)) * np.sin(a * (pts[:, 1] - 0.5))
                 / (2.0 * s["kappa"] * a * a))
+    if g == "popcorn":
+        x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+        return x ** 3 + x * y * y + y ** 3 + z ** 4 + np.sin(3.0 * (x * x + y * y))
     raise ValueError(g)
 
 
@@ -149,7 +158,7 @@ def exact_solution(prob, pts):
         for a in range(prob["dim"]):
             u = u * np.sin(math.pi * pts[:, a])
         return u
-    if s == "square_mms":
+    if s in ("square_mms", "popcorn"):
         return dirichlet_values(prob, pts)
     raise ValueError("no manufactured solution")
 

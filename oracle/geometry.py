@@ -13,10 +13,13 @@ Kinds:
   ball       psi = |x - c| - r                         (circle / sphere)
   voids      psi = max_k (r_k - |x - c_k|)             (block minus balls)
   ellipsoid  psi = |diag(1/a) R^T (x - c)| - 1
+  popcorn    psi = |x| - r0 - sum_k A exp(-|x - c_k|^2 / sigma^2)   (Sec. 4.4)
 
 Box classification (the paper leaves the cut test open; this is the
 reading): balls and voids use exact nearest/farthest point distances, the
-ellipsoid a sign test of psi on a 5^d lattice including the corners.
+ellipsoid and the popcorn a sign test of psi on a 5^d lattice including the
+corners (``classify_grid`` evaluates the same test for a whole grid at once,
+with the same arithmetic).
 Floating-point operations are written out in a fixed order so that a second
 implementation performing the same operations gets identical results.
 """
@@ -61,6 +64,15 @@ def levelset(geom: dict, x: np.ndarray) -> np.ndarray:
             t = y / ax[i]
             q = t * t if q is None else q + t * t
         return np.sqrt(q) - 1.0
+    if kind == "popcorn":
+        r0, amp, sig2 = geom["r0"], geom["A"], geom["sigma"] * geom["sigma"]
+        s = x[..., 0] * x[..., 0] + x[..., 1] * x[..., 1] + x[..., 2] * x[..., 2]
+        out = np.sqrt(s) - r0
+        for (cx, cy, cz) in geom["centers"]:
+            d2 = ((x[..., 0] - cx) * (x[..., 0] - cx) + (x[..., 1] - cy) * (x[..., 1] - cy)
+                  + (x[..., 2] - cz) * (x[..., 2] - cz))
+            out = out - amp * np.exp(-d2 / sig2)
+        return out
     raise ValueError(kind)
 
 
@@ -106,7 +118,7 @@ def classify_box(geom: dict, lo, hi) -> int:
             if dmin2 < r2:
                 all_clear = False
         return INSIDE if all_clear else CUT
-    if kind == "ellipsoid":
+    if kind in ("ellipsoid", "popcorn"):
         d = len(lo)
         ts = [k * 0.25 for k in range(5)]
         pts = []
@@ -122,3 +134,36 @@ def classify_box(geom: dict, lo, hi) -> int:
             return OUTSIDE
         return CUT
     raise ValueError(kind)
+
+
+def classify_grid(geom: dict, lo, hi, cells) -> np.ndarray:
+    """Classes of all cells of a 3D grid (linear order, x fastest), for the
+    lattice-tested kinds: the test of ``classify_box`` evaluated for every
+    cell at once, lattice points lo_c + t (hi_c - lo_c) with the cell
+    corners lo_c = lo + c h, hi_c = lo + (c + 1) h, h = (hi - lo) / C."""
+    assert geom["kind"] in ("ellipsoid", "popcorn") and len(cells) == 3
+    ts = [k * 0.25 for k in range(5)]
+    axes = []
+    for a in range(3):
+        h = (hi[a] - lo[a]) / cells[a]
+        c = np.arange(cells[a], dtype=np.float64)
+        x0 = lo[a] + c * h
+        x1 = lo[a] + (c + 1.0) * h
+        axes.append([x0 + t * (x1 - x0) for t in ts])
+    shape = (cells[2], cells[1], cells[0])
+    any_in = np.zeros(shape, dtype=bool)
+    any_out = np.zeros(shape, dtype=bool)
+    for kz in range(5):
+        for ky in range(5):
+            for kx in range(5):
+                X = np.empty(shape + (3,))
+                X[..., 0] = axes[0][kx][None, None, :]
+                X[..., 1] = axes[1][ky][None, :, None]
+                X[..., 2] = axes[2][kz][:, None, None]
+                v = levelset(geom, X)
+                any_in |= v <= 0.0
+                any_out |= v > 0.0
+    cls = np.full(shape, CUT, dtype=np.int8)
+    cls[~any_out] = INSIDE
+    cls[~any_in] = OUTSIDE
+    return cls.ravel()

@@ -83,11 +83,9 @@ class TrunkSpace:
         self.local = trunk_local_mask(d, p)
         self.cell_list = list(all_cells(d, C))
         if prob.get("drop_outside") and classes is not None:
-            self.cell_list = [c for c, k in zip(self.cell_list, classes) if k != OUTSIDE]
-            used = np.zeros(self.Mt, dtype=bool)
-            for c in self.cell_list:
-                used[cell_dofs(d, C, p, c)] = True
-            keep &= used
+            kept = np.asarray(classes) != OUTSIDE
+            self.cell_list = [c for c, k in zip(self.cell_list, kept) if k]
+            keep &= _supported(d, C, p, np.flatnonzero(kept))
         self.tensor_index = np.flatnonzero(keep)        # kept scalar tensor DOFs, in order
         self.M = len(self.tensor_index)
         self.N = self.nf * self.M
@@ -103,6 +101,28 @@ class TrunkSpace:
         g = self.renumber[sc]
         assert (g >= 0).all()
         return pos, np.concatenate([f * self.M + g for f in range(self.nf)])
+
+
+def _supported(dim, C, p, cells) -> np.ndarray:
+    """Scalar tensor DOFs supported on at least one of the given cells
+    (linear cell ids, x fastest): every local mode of every cell, with the
+    1D index of mode j of cell c being c (j = 0), c + 1 (j = 1) or
+    (C + 1) + (j - 2) C + c (bubble of degree j)."""
+    coords, rem = [], np.asarray(cells, dtype=np.int64)
+    for a in range(dim):
+        coords.append(rem % C[a])
+        rem = rem // C[a]
+    used = np.zeros(ndofs(dim, C, p), dtype=bool)
+    for js in local_modes(dim, p):
+        g = np.zeros(len(cells), dtype=np.int64)
+        stride = 1
+        for a in range(dim):
+            c, j = coords[a], js[a]
+            ia = c if j == 0 else (c + 1 if j == 1 else (C[a] + 1) + (j - 2) * C[a] + c)
+            g += ia * stride
+            stride *= m_1d(C[a], p)
+        used[g] = True
+    return used
 
 
 def assemble_trunk(prob):

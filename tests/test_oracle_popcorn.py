@@ -1,0 +1,79 @@
+"""Pins of the popcorn benchmark of Sec. 4.4 in the oracle.
+
+* The whole-grid classification is the per-cell cut test, bit for bit.
+* The twelve bump centres lie on the sphere |x| = r0.
+* The paper's coarsest mesh: 96^3 cells of (-1, 1)^3 with the fully
+  fictitious ones removed keep 250,336 elements and 1.83e6 trunk-space DOFs
+  of degree 3 within 0.5% (tests/golden/popcorn_coarsest_mesh.json; the
+  readings of the garbled centre formula and of the unstated grid and cut
+  test are listed there).
+* The manufactured Poisson problem converges towards
+  u = x^3 + x y^2 + y^3 + z^4 + sin(3 (x^2 + y^2)) under refinement.
+"""
+import json
+import os
+
+import numpy as np
+
+import fcm_inputs as fi
+from oracle.assembly import exact_solution, shape_functions
+from oracle.geometry import OUTSIDE, classify_box, classify_grid, levelset
+from oracle.grid import all_cells, cell_box
+from oracle.multigrid import pcg
+from oracle.trunk import TrunkHierarchy, TrunkSpace
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_classify_grid_is_the_cell_test():
+    prob = dict(fi.popcorn(), cells=(6, 7, 8))
+    got = classify_grid(prob["geometry"], prob["lo"], prob["hi"], prob["cells"])
+    ref = [classify_box(prob["geometry"], *cell_box(prob["lo"], prob["hi"], prob["cells"], c))
+           for c in all_cells(3, prob["cells"])]
+    assert got.tolist() == ref
+    assert len(set(ref)) == 3
+
+
+def test_bump_centres_on_the_sphere():
+    c = np.array(fi.popcorn()["geometry"]["centers"])
+    assert c.shape == (12, 3)
+    assert np.allclose(np.linalg.norm(c, axis=1), 0.6, rtol=0, atol=1e-15)
+    assert np.allclose(c.sum(axis=0), 0.0, atol=1e-14)   # symmetric arrangement
+
+
+def test_paper_coarsest_mesh_counts():
+    with open(os.path.join(GOLDEN, "popcorn_coarsest_mesh.json")) as f:
+        g = json.load(f)
+    prob = fi.popcorn(cells=g["cells"], p=g["p"])
+    cls = classify_grid(prob["geometry"], prob["lo"], prob["hi"], prob["cells"])
+    kept = int((cls != OUTSIDE).sum())
+    space = TrunkSpace(prob, cls)
+    tol = g["tolerance_relative"]
+    assert abs(kept - g["elements"]) <= tol * g["elements"], kept
+    assert abs(space.M - g["dofs"]) <= tol * g["dofs"], space.M
+
+
+def _solve_error(C):
+    prob = fi.popcorn(cells=C, p=2)
+    H = TrunkHierarchy(prob)
+    x, k, _ = pcg(H.A, H.b, H.vcycle, rtol=1e-8, maxit=300)
+    assert np.linalg.norm(H.b - H.A @ x) <= 1e-8 * np.linalg.norm(H.b)
+    rng = np.random.default_rng(0)
+    err = scale = 0.0
+    for c in H.space.cell_list:
+        lo, hi = (np.asarray(v) for v in cell_box(prob["lo"], prob["hi"], prob["cells"], c))
+        pts = lo + rng.random((10, 3)) * (hi - lo)
+        pts = pts[levelset(prob["geometry"], pts) <= 0.0]
+        if not len(pts):
+            continue
+        N, _ = shape_functions(2, lo, hi, pts)
+        pos, gd = H.space.cell_dofs(c)
+        u = exact_solution(prob, pts)
+        err = max(err, np.abs(N[:, pos] @ x[gd] - u).max())
+        scale = max(scale, np.abs(u).max())
+    return err / scale
+
+
+def test_popcorn_poisson_converges_to_the_manufactured_solution():
+    e6, e8 = _solve_error(6), _solve_error(8)
+    assert e6 < 0.06 and e8 < 0.6 * e6, (e6, e8)
