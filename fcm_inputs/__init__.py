@@ -172,11 +172,12 @@ def poisson3d_sphere_mlhp(cells=16, p=2, overlay_levels=3, alpha=1e-8, radius=0.
     return d
 
 
-def perforated_plate(cells=32, p=2, overlay_levels=0, alpha=1e-8, quad_depth=3):
+def perforated_plate(cells=8, p=2, overlay_levels=0, alpha=1e-8, quad_depth=3):
     """Plane-strain plate [0,4]^2 with four circular cavities of radius
     0.3 sqrt(2) centred in its quadrants, E = 2.069e5, nu = 0.29, clamped on
     x = 0 and pulled by a unit traction on x = 4 (penalty beta = 1e8);
-    cut cells overlaid to depth `overlay_levels`."""
+    cut cells overlaid to depth `overlay_levels`.  cells = 8 per axis is the
+    mesh size h = 1/8 of the plate side."""
     r = 0.3 * math.sqrt(2.0)
     balls = [(1.0, 1.0, 0.0, r), (3.0, 1.0, 0.0, r), (1.0, 3.0, 0.0, r), (3.0, 3.0, 0.0, r)]
     return _base(2, (cells, cells), p, pde="elasticity", E=2.069e5, nu=0.29, alpha=alpha,

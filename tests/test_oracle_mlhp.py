@@ -339,39 +339,33 @@ def test_iterations_flat_in_the_refinement_depth():
 
 
 def test_perforated_plate_iteration_table():
-    """Table tab::perPlateRef, column h = 1/8: CG with the hp-multigrid
-    preconditioner and patchwise smoothing needs 7, 7, 7, 6 iterations for
-    k = 0..3; the reproduction (cavity placement and tolerance are readings)
-    stays within 2 of each.  With elementwise blocks the paper's count grows
-    with k (12, 15, 31, 50); so does this one."""
+    """Table tab::perPlateRef, column h = 1/8 (8 cells per axis, k = 0..3;
+    readings in the golden file).  The paper's finding is reproduced in all
+    four sub-tables: with patchwise blocks the count is flat in k, both as a
+    one-level preconditioner (paper 43, here 34) and in the hp-multigrid
+    (paper 7, 7, 7, 6, here within 2); with elementwise blocks it grows with
+    k in both (paper 60 -> 294 and 12 -> 50), starting within 10% at k = 0."""
     with open(os.path.join(GOLDEN, "perforated_plate_mlhp_iterations.json")) as f:
         g = json.load(f)
-    for k, ref in zip(g["k"], g["cg_mg_patchwise"]):
-        H = MlhpHierarchy(fi.perforated_plate(cells=g["cells"], overlay_levels=k))
-        _, it, _ = pcg(H.A, H.b, H.vcycle, rtol=g["rtol"], maxit=300)
-        assert abs(it - ref) <= 2, (k, it, ref)
-    elem = []
-    for k in g["k"][:3]:
-        H = MlhpHierarchy(dict(fi.perforated_plate(cells=g["cells"], overlay_levels=k),
-                               smoother="elementwise"))
-        _, it, _ = pcg(H.A, H.b, H.vcycle, rtol=g["rtol"], maxit=300)
-        elem.append(it)
-    ref = g["cg_mg_elementwise"][:3]
-    assert all(b > a for a, b in zip(elem, elem[1:])), elem
-    assert elem[0] <= ref[0] + 3 and elem[2] >= ref[2], (elem, ref)
-
-
-def test_iterations_flat_in_the_refinement_depth_3d():
-    """Sec. 4.3 (influence of the refinement level): with patchwise blocks
-    the CG+MG count does not depend on the overlay depth in 3D either.  The
-    sphere workload with overlays (r = 0.3, p = 2) on a 4^3 base grid,
-    depths 0, 1, 2 (729, 2,353 and 8,249 DOFs)."""
-    ks = []
-    for depth in range(3):
-        H = MlhpHierarchy(fi.poisson3d_sphere_mlhp(cells=4, p=2, overlay_levels=depth))
-        _, k, _ = pcg(H.A, H.b, H.vcycle, rtol=1e-8, maxit=200)
-        ks.append(k)
-    assert max(ks) - min(ks) <= 2 and max(ks) <= 12, ks
+    got = {key: [] for key in ("cg_as_elementwise", "cg_as_patchwise",
+                               "cg_mg_elementwise", "cg_mg_patchwise")}
+    for k in g["k"]:
+        for kind in ("elementwise", "patchwise"):
+            H = MlhpHierarchy(dict(fi.perforated_plate(cells=g["cells"], overlay_levels=k),
+                                   smoother=kind))
+            _, it, _ = pcg(H.A, H.b, H.levels[-1].smoother, rtol=g["rtol"], maxit=3000)
+            got["cg_as_" + kind].append(it)
+            _, it, _ = pcg(H.A, H.b, H.vcycle, rtol=g["rtol"], maxit=300)
+            got["cg_mg_" + kind].append(it)
+    for it, ref in zip(got["cg_mg_patchwise"], g["cg_mg_patchwise"]):
+        assert abs(it - ref) <= 2, got
+    for key in ("cg_as_patchwise", "cg_mg_patchwise"):
+        assert max(got[key]) - min(got[key]) <= 2, got
+    for key in ("cg_as_elementwise", "cg_mg_elementwise"):
+        its, ref = got[key], g[key]
+        assert all(b >= a for a, b in zip(its, its[1:])) and its[-1] >= 3 * its[0], got
+        assert abs(its[0] - ref[0]) <= 0.1 * ref[0] + 1, got
+    assert abs(got["cg_as_patchwise"][0] - g["cg_as_patchwise"][0]) <= 0.25 * g["cg_as_patchwise"][0]
 
 
 def _leaf_transform(space, k, e):
