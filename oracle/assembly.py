@@ -20,8 +20,8 @@ import math
 import numpy as np
 import scipy.sparse as sp
 
-from .basis import basis_1d, gauss_legendre
-from .geometry import CUT, INSIDE, OUTSIDE, classify_box
+from .basis import basis_1d
+from .geometry import CUT, INSIDE, classify_box
 from .grid import all_cells, cell_box, cell_dofs, local_modes, ndofs
 from .quadrature import cell_rules, face_rule, leaf_rule
 

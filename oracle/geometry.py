@@ -25,8 +25,6 @@ implementation performing the same operations gets identical results.
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 INSIDE, OUTSIDE, CUT = 0, 1, 2

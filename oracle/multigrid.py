@@ -44,7 +44,6 @@ Test infrastructure only (see ``oracle/__init__``).
 from __future__ import annotations
 
 import itertools
-import math
 
 import numpy as np
 import scipy.linalg as sla
@@ -52,7 +51,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .assembly import assemble, nfields
-from .grid import all_cells, cell_dofs, m_1d, ndofs
+from .grid import all_cells, cell_dofs, m_1d
 
 
 THETA = 1.75

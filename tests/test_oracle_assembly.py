@@ -20,7 +20,7 @@ from oracle.assembly import (assemble, element_system, elasticity_C, exact_solut
                              shape_functions)
 from oracle.basis import element_1d_matrices
 from oracle.geometry import INSIDE, OUTSIDE
-from oracle.grid import all_cells, cell_box, cell_dofs, m_1d, ndofs
+from oracle.grid import all_cells, cell_box, cell_dofs, m_1d
 from oracle.quadrature import leaf_rule
 
 

@@ -25,7 +25,7 @@ import fcm_inputs as fi
 from oracle.assembly import shape_functions
 from oracle.geometry import OUTSIDE, levelset
 from oracle.grid import all_cells, cell_box, cell_dofs
-from oracle.multigrid import Level, pcg
+from oracle.multigrid import pcg
 from oracle.quadrature import leaf_rule
 from oracle.trunk import (TrunkHierarchy, TrunkSpace, assemble_trunk, trunk_global_mask,
                           trunk_local_mask)
