@@ -190,7 +190,7 @@ def perforated_plate(cells=8, p=2, overlay_levels=0, alpha=1e-8, quad_depth=3):
 
 
 def popcorn_centers(r0=0.6):
-    """The twelve bump centres of the popcorn surface (Sec. 4.4) on the
+    """The twelve bump centres of the popcorn surface (Sec. 4.3.2) on the
     sphere of radius r0: (r0/sqrt 5)(2 cos t_k, 2 sin t_k, +-1) with
     t_k = 2 k pi / 5 (z = +1) and (2k - 1) pi / 5 (z = -1), k = 0..4, and the
     poles (0, 0, +-r0)."""
@@ -207,7 +207,7 @@ def popcorn_centers(r0=0.6):
 
 
 def popcorn(cells=97, p=3, alpha=1e-6, quad_depth=3, space="trunk", drop_outside=True):
-    """Popcorn benchmark (Sec. 4.4): the embedding cube (-1, 1)^3, the
+    """Popcorn benchmark (Sec. 4.3.2): the embedding cube (-1, 1)^3, the
     popcorn level set with r0 = 0.6, A = 3, sigma = 0.2, manufactured
     u = x^3 + x y^2 + y^3 + z^4 + sin(3 (x^2 + y^2)) (source -Lap u, Dirichlet
     u on the surface by penalty, beta = 1e4), trunk-space elements, fully

@@ -5,7 +5,7 @@ Test infrastructure only (see ``oracle/__init__``).
 FCM embeds the physical domain in a box and marks it by an indicator alpha
 (Sec. 2.1, Eq. weakform): alpha = 1 in Omega_phys, alpha = eps << 1 in
 Omega_fict.  Geometry is given by a level set psi with Omega_phys = {psi <= 0}
-(the popcorn convention of Sec. 4.4, points on the surface count as
+(the popcorn convention of Sec. 4.3.2, points on the surface count as
 physical).
 
 Kinds:
@@ -13,7 +13,7 @@ Kinds:
   ball       psi = |x - c| - r                         (circle / sphere)
   voids      psi = max_k (r_k - |x - c_k|)             (block minus balls)
   ellipsoid  psi = |diag(1/a) R^T (x - c)| - 1
-  popcorn    psi = |x| - r0 - sum_k A exp(-|x - c_k|^2 / sigma^2)   (Sec. 4.4)
+  popcorn    psi = |x| - r0 - sum_k A exp(-|x - c_k|^2 / sigma^2)   (Sec. 4.3.2)
 
 Box classification (the paper leaves the cut test open; this is the
 reading): balls and voids use exact nearest/farthest point distances, the

@@ -3,7 +3,7 @@
 Test infrastructure only (see ``oracle/__init__``).
 
 Volume integrals on cut cells use a space tree (Sec. 2.1 and the rod example
-of Sec. 4.3, "octree ... depth of 3"): a cut (sub)cell is bisected along
+of Sec. 4.3.1, "octree ... depth of 3"): a cut (sub)cell is bisected along
 every axis until it is uncut or the maximum depth is reached.  Each leaf gets
 a (p+1)^d Gauss-Legendre rule.  Uncut leaves carry the constant alpha of
 their class; leaves still cut at the maximum depth evaluate alpha point by
@@ -13,7 +13,7 @@ of ``geometry.classify_box`` are the readings.
 
 Dirichlet data on the immersed boundary are imposed by penalty (Eq. weakform,
 second integral).  The paper extracts the surface with marching cubes
-(Sec. 4.4); the reading here is marching simplices on every leaf that is
+(Sec. 4.3.2); the reading here is marching simplices on every leaf that is
 still cut at the maximum depth: the leaf is split into the d! Kuhn simplices
 that share its main diagonal, psi is interpolated linearly along each edge
 whose end values change sign (psi <= 0 counts as inside), and the zero set of

@@ -16,7 +16,7 @@ its DOFs keep their tensor order and are renumbered consecutively.  Lowering
 p keeps a subset, so the p-multigrid transfers stay binary (Sec. 3.2).
 
 Removal of fully fictitious cells (the paper's DOF counts, Sec. 4.3 and
-4.5, imply it): cells classified outside the physical domain are dropped
+4.3.2, imply it): cells classified outside the physical domain are dropped
 together with the DOFs supported only on them.  The nested Q1 h-levels
 below p = 1 then interpolate onto the kept fine nodes only, and coarse nodes
 that no kept fine node depends on are dropped.

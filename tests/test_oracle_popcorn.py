@@ -1,4 +1,4 @@
-"""Pins of the popcorn benchmark of Sec. 4.4 in the oracle.
+"""Pins of the popcorn benchmark of Sec. 4.3.2 in the oracle.
 
 * The whole-grid classification is the per-cell cut test, bit for bit.
 * The twelve bump centres lie on the sphere |x| = r0.
