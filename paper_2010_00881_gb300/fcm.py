@@ -225,7 +225,16 @@ def restriction_1d(p: int, dk: int, pos: int) -> np.ndarray:
 
 
 def descriptors(prob: dict, build_mixed: bool = True):
-    """C descriptors for a problem dict of ``fcm_inputs``."""
+    """C descriptors for a problem dict of ``fcm_inputs``.  Raises
+    ValueError for problem features the library has no descriptor for
+    (trunk-space elements, removal of fictitious cells, geometry kinds or
+    smoothers it does not know) instead of dropping them."""
+    if prob.get("space", "tensor") != "tensor" or prob.get("drop_outside"):
+        raise ValueError("the library discretises with the full tensor-product space on all cells")
+    if prob["geometry"]["kind"] not in GEOM:
+        raise ValueError(f"geometry kind {prob['geometry']['kind']!r} has no library descriptor")
+    if prob.get("smoother", "elementwise") not in ("elementwise", "patchwise"):
+        raise ValueError(f"smoother {prob['smoother']!r} has no library descriptor")
     d = prob["dim"]
     g = fcm_grid()
     g.dim = d

@@ -44,6 +44,16 @@ def test_invalid_setup(over, status):
     assert len(F.load().fcm_last_error()) > 0
 
 
+@pytest.mark.parametrize("prob", [fi.poisson3d_sphere_mlhp(cells=4),
+                                  dict(fi.poisson2d_circle(cells=4), smoother="patchwise")])
+def test_problem_dicts_beyond_the_gpu_path(prob):
+    """Overlay and patchwise problem dicts reach fcm_setup through the
+    binding, which rejects them before launching anything."""
+    with pytest.raises(F.FcmError) as e:
+        F.Solver(prob)
+    assert e.value.status == F.FCM_E_UNSUPPORTED
+
+
 def test_nan_rhs_rejected():
     s = F.Solver(fi.poisson2d_circle(cells=8))
     b = s.rhs()
