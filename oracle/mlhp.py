@@ -173,12 +173,15 @@ class MlhpMesh:
 
 
 class MlhpSpace:
-    """Active functions of a multi-level hp mesh at degree p."""
+    """Active functions of a multi-level hp mesh at degree p; with
+    trunk=True only the modes whose bubble degrees sum to at most p
+    (trunk-space elements, as ``oracle.trunk`` defines them)."""
 
-    def __init__(self, mesh: MlhpMesh, p: int, nf: int = 1):
+    def __init__(self, mesh: MlhpMesh, p: int, nf: int = 1, trunk: bool = False):
         self.mesh = mesh
         self.p = p
         self.nf = nf
+        self.trunk = trunk
         d = mesh.dim
         self.modes = local_modes(d, p)
         comps = {}
@@ -194,13 +197,18 @@ class MlhpSpace:
         for k, t in keys:
             odd = [a for a in range(d) if t[a] % 2]
             for qs in itertools.product(range(2, p + 1), repeat=len(odd)):
+                if trunk and sum(qs) > p:
+                    continue
                 funcs.append((k, t, _rev(qs)))
         self.funcs = funcs
         self.fid = {f: i for i, f in enumerate(funcs)}
         self.M = len(funcs)
         self.N = nf * self.M
         self.level = np.array([f[0] for f in funcs], dtype=np.int64)
-        self.degree = np.array([max(f[2]) if f[2] else 1 for f in funcs], dtype=np.int64)
+        # polynomial degree of each function's mode: the largest bubble degree,
+        # or for trunk elements their sum (level p_l keeps degree <= p_l)
+        agg = sum if trunk else max
+        self.degree = np.array([agg(f[2]) if f[2] else 1 for f in funcs], dtype=np.int64)
 
     def leaf_functions(self, k, e):
         """Per ancestor j of leaf (k, e): (j, box, active local-mode columns
@@ -330,7 +338,8 @@ def assemble_mlhp(prob, space: MlhpSpace = None):
     """Global CSR matrix and load over the active functions, summed from the
     leaf element systems.  Returns (A, b, space)."""
     if space is None:
-        space = MlhpSpace(mesh_for(prob), prob["p"], nfields(prob))
+        space = MlhpSpace(mesh_for(prob), prob["p"], nfields(prob),
+                          trunk=prob.get("space", "tensor") == "trunk")
     rows, cols, vals = [], [], []
     b = np.zeros(space.N)
     for k, e in space.mesh.leaves():

@@ -33,6 +33,7 @@ from oracle.mlhp import (MlhpHierarchy, MlhpMesh, MlhpSpace, assemble_mlhp,
                          hp_level_sets, mesh_for, schwarz_blocks)
 from oracle.multigrid import pcg
 from oracle.quadrature import leaf_rule
+from oracle.trunk import trunk_local_mask
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -90,6 +91,12 @@ def _leaf_space_check(space):
                     R[:, idx * nl:(idx + 1) * nl] = sign * V
                 rows.append(R)
     R = np.concatenate(rows) if rows else np.zeros((0, T.shape[0]))
+    if space.trunk:
+        # the discontinuous space of trunk-space leaves: every active function
+        # restricted to a leaf must lie in the leaf's trunk modes
+        keep = np.tile(trunk_local_mask(d, p), len(leaves))
+        assert np.abs(T[~keep]).max(initial=0.0) <= 1e-12 * np.abs(T).max()
+        T, R = T[keep], R[:, keep]
     viol = np.abs(R @ T).max() / np.abs(T).max() if len(R) else 0.0
     sT = np.linalg.svd(T, compute_uv=False)
     rankT = int(np.sum(sT > 1e-10 * sT[0]))
@@ -119,6 +126,18 @@ def test_basis_spans_the_c0_leaf_space_2d(p, depth, seed):
     assert viol < 1e-12            # every active function is continuous
     assert rankT == M              # linearly independent
     assert null == M               # and spanning the whole C0 space
+
+
+@pytest.mark.parametrize("dim,p,depth,seed", [(2, 3, 2, 7), (2, 4, 2, 8), (3, 4, 1, 9)])
+def test_trunk_basis_spans_the_c0_trunk_leaf_space(dim, p, depth, seed):
+    """With trunk-space elements the active functions are a basis of the C0
+    space of piecewise trunk polynomials on the leaves."""
+    cells, hi = ((3, 2), (1.5, 1.0)) if dim == 2 else ((2, 2, 1), (1.0, 1.0, 0.5))
+    mesh = MlhpMesh(dim, cells, (0.0,) * dim, hi, depth, _random_rule(seed, 0.45))
+    space = MlhpSpace(mesh, p, trunk=True)
+    assert space.M < MlhpSpace(mesh, p).M
+    viol, rankT, null, M = _leaf_space_check(space)
+    assert viol < 1e-12 and rankT == M == null
 
 
 @pytest.mark.parametrize("p,depth,seed", [(1, 2, 5), (2, 2, 6)])
@@ -176,6 +195,23 @@ def test_without_overlays_equals_uniform_assembly(make):
     D = (A - Au[perm][:, perm]).toarray()
     assert np.abs(D).max() <= 1e-14 * abs(Au).max()
     assert np.abs(b - bu[perm]).max() <= 1e-14 * np.abs(bu).max()
+
+
+@pytest.mark.parametrize("make", [
+    lambda: fi.poisson2d_circle(cells=4, p=4),
+    lambda: fi.poisson3d_sphere(cells=2, p=4, radius=0.3),
+])
+def test_trunk_without_overlays_equals_uniform_trunk_assembly(make):
+    from oracle.trunk import assemble_trunk
+    prob = dict(make(), overlay_levels=0, space="trunk")
+    A, b, space = assemble_mlhp(prob)
+    assert space.trunk
+    At, bt, ts, _ = assemble_trunk(prob)
+    perm = ts.renumber[_uniform_index(space)]
+    assert (perm >= 0).all() and sorted(perm) == list(range(At.shape[0]))
+    D = (A - At[perm][:, perm]).toarray()
+    assert np.abs(D).max() <= 1e-14 * abs(At).max()
+    assert np.abs(b - bt[perm]).max() <= 1e-14 * np.abs(bt).max()
 
 
 def _fine_interpolation(space):
@@ -404,3 +440,13 @@ def test_leaf_matrix_is_the_own_cell_matrix_in_ancestor_coordinates(prob):
         assert np.abs(bL - T.T @ bown).max() <= 1e-11 * max(np.abs(bL).max(), 1e-300)
         cut += cls == CUT
     assert cut > 0
+
+
+def test_trunk_hp_levels_are_lower_degree_trunk_spaces():
+    """With trunk elements the degree-p_l level holds the trunk space of
+    degree p_l (bubble degrees summing to at most p_l) on the same mesh."""
+    mesh = mesh_for(dict(fi.poisson2d_circle(cells=4, p=4), overlay_levels=2))
+    space = MlhpSpace(mesh, 4, trunk=True)
+    sets = hp_level_sets(space)
+    for s, pc in zip(sets[1:4], (3, 2, 1)):
+        assert [space.funcs[i] for i in s] == MlhpSpace(mesh, pc, trunk=True).funcs, pc
