@@ -365,16 +365,21 @@ def pcg(A, b, precond, rtol=1e-8, maxit=500, flexible=False, x0=None):
 
 def mg_solve(A, b, vcycle, rtol=1e-9, maxit=500):
     """Multigrid as a stand-alone solver, x_{i+1} = x_i + V(b - A x_i),
-    with the contraction numbers rho_i = ||r_i|| / ||r_{i-1}|| of Sec. 4."""
+    with the contraction numbers rho_i = ||r_i|| / ||r_{i-1}|| of Sec. 4.
+    A diverging iteration (the residual grown 1e20-fold) stops early; the
+    caller sees it in the returned residual history."""
     nb = np.linalg.norm(b)
     x = np.zeros_like(b)
     r = b.copy()
     norms = [np.linalg.norm(r)]
     k = 0
     while norms[-1] / nb > rtol and k < maxit:
+        if not norms[-1] <= 1e20 * nb:
+            break
         k += 1
-        x = x + vcycle(r)
-        r = b - A @ x
+        with np.errstate(over="ignore", invalid="ignore"):
+            x = x + vcycle(r)
+            r = b - A @ x
         norms.append(np.linalg.norm(r))
     rho = [norms[i] / norms[i - 1] for i in range(1, len(norms))]
     return x, k, rho

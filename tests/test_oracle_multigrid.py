@@ -268,3 +268,26 @@ def test_gauss_seidel_vcycle_symmetric():
     V = _dense(H.vcycle, N)
     assert np.abs(V - V.T).max() < 1e-9 * np.abs(V).max()
     assert np.linalg.eigvalsh((V + V.T) / 2).min() > 0
+
+
+def test_jacobi_and_gauss_seidel_fail_on_cut_cells():
+    """Sec. 4.1.2, Table tab:testcaseB: on an immersed configuration the
+    pointwise smoothers do not cope with the cut cells.  Multigrid as a
+    solver with Jacobi or Gauss-Seidel does not converge (the paper's '*'),
+    and CG+MG with them needs far more iterations than with elementwise AS,
+    which converges in both modes (cut circle, 8 x 8 cells, p = 2)."""
+    prob = fi.poisson2d_circle(cells=8, p=2)
+    counts = {}
+    for kind in ("elementwise", "jacobi", "gauss_seidel"):
+        H = mg.Hierarchy(dict(prob, smoother=kind))
+        _, k, hist = mg.pcg(H.A, H.b, H.vcycle, rtol=1e-9, maxit=200)
+        x, ks, _ = mg.mg_solve(H.A, H.b, H.vcycle, rtol=1e-9, maxit=200)
+        with np.errstate(over="ignore", invalid="ignore"):
+            rel = np.linalg.norm(H.b - H.A @ x) / np.linalg.norm(H.b)
+        counts[kind] = (k, hist[-1], ks, rel)
+    k_as, _, ks_as, rel_as = counts["elementwise"]
+    assert k_as <= 20 and ks_as < 200 and rel_as <= 1e-9, counts
+    for kind in ("jacobi", "gauss_seidel"):
+        k, last, ks, rel = counts[kind]
+        assert not rel <= 1e-6, (kind, counts)            # stand-alone MG fails
+        assert k == 200 and last > 1e-9, (kind, counts)     # CG+MG: > 10x the AS count
