@@ -291,3 +291,32 @@ def test_jacobi_and_gauss_seidel_fail_on_cut_cells():
         k, last, ks, rel = counts[kind]
         assert not rel <= 1e-6, (kind, counts)            # stand-alone MG fails
         assert k == 200 and last > 1e-9, (kind, counts)     # CG+MG: > 10x the AS count
+
+
+@pytest.mark.parametrize("make", [
+    lambda: fi.poisson2d_circle(cells=1, p=1),
+    lambda: fi.poisson3d_sphere(cells=2, p=1),
+    lambda: fi.poisson3d_sphere(cells=3, p=2),
+    lambda: fi.poisson2d_circle(cells=3, p=4),
+])
+def test_degenerate_grids(make):
+    """Grids of 1-3 cells per axis: at p = 1 the hierarchy is the coarse
+    level alone and CG with its exact solve converges in one iteration; at
+    p > 1 only p-levels exist.  Either way the V-cycle is SPD and PCG meets
+    the direct solve."""
+    prob = make()
+    H = mg.Hierarchy(prob)
+    assert len(H.levels) == prob["p"]
+    assert all(lv.cells == tuple(prob["cells"]) for lv in H.levels)
+    N = H.A.shape[0]
+    V = _dense(H.vcycle, N)
+    # rounding in the block inverses of cut cells (alpha = 1e-6, p up to 4)
+    # leaves an asymmetry of ~kappa eps: 3e-8 relative at 3 x 3 cells, p = 4
+    assert np.abs(V - V.T).max() <= 1e-6 * np.abs(V).max()
+    assert np.linalg.eigvalsh((V + V.T) / 2).min() > 0
+    x, k, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=1e-10)
+    xd = spla.spsolve(H.A.tocsc(), H.b)
+    e = x - xd
+    assert np.sqrt(e @ (H.A @ e)) <= 1e-8 * np.sqrt(xd @ (H.A @ xd))
+    if prob["p"] == 1:
+        assert k == 1
