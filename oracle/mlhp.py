@@ -21,7 +21,9 @@ bubble degree per odd axis.  The elements of level k whose closure contains
 the component share its functions, which are C0 across them.  A function of
 an element is a polynomial on that element's box; on every leaf below it it
 is evaluated at the mapped points, so a leaf's element matrix couples the
-functions of all its ancestors (refinement by superposition).
+functions of all its ancestors (refinement by superposition).  With
+trunk-space elements (``MlhpSpace(trunk=True)``, the space of ``oracle.trunk``)
+a component keeps only the bubble-degree combinations that sum to at most p.
 
 Activation.  The paper defers the rule set to Zander et al.; the reading
 here is one that makes the active functions a basis of exactly the C0 space
