@@ -124,6 +124,23 @@ def square_mms(cells=8, p=2, kappa=10.0, beta=1e4, alpha=1e-8):
                  quad_depth=0, name=f"square_mms_{cells}x{cells}_p{p}")
 
 
+def rotated_square(cells=12, p=2, psi_deg=30.0, kappa=10.0, beta=1e4, alpha=1e-8):
+    """Immersed rotating-square Poisson problem (Sec. 4.1.2): the unit square
+    centred at (1/2, 1/2) rotated by psi, in the fixed background box
+    [-1/4, 5/4]^2 that holds every rotation (12 cells per axis: h = 1/8);
+    u = cos(a x') sin(a y') / (2 kappa a^2) in the rotated coordinates,
+    a = 3 pi / 2, source cos(a x') sin(a y'), Dirichlet u on the square's
+    edges by penalty."""
+    a = 1.5 * math.pi
+    ang = math.radians(psi_deg)
+    return _base(2, (cells, cells), p, lo=(-0.25, -0.25), hi=(1.25, 1.25), kappa=kappa,
+                 alpha=alpha, beta=beta,
+                 geometry=dict(kind="rotated_square", center=(0.5, 0.5), half=0.5, angle=ang),
+                 source=dict(kind="square_mms", a=a, kappa=kappa, angle=ang),
+                 dirichlet=dict(kind="levelset", g="square_mms"),
+                 name=f"rotated_square_{cells}x{cells}_p{p}_psi{psi_deg:g}")
+
+
 def draw_voids(n_voids=64, rmin=0.03, rmax=0.08, gap=1.0 / 64, seed=0, max_tries=100000):
     """Void centres and radii for the perforated block: radii U[rmin, rmax],
     centres uniform in the unit cube, rejection keeps a gap between voids and
@@ -268,4 +285,5 @@ CONFIGS = {
     "poisson3d_sphere_mlhp": poisson3d_sphere_mlhp,
     "perforated_plate": perforated_plate,
     "popcorn": popcorn,
+    "rotated_square": rotated_square,
 }

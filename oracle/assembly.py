@@ -21,7 +21,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .basis import basis_1d
-from .geometry import CUT, INSIDE, classify_box
+from .geometry import CUT, INSIDE, classify_box, rotated_coordinates
 from .grid import all_cells, cell_box, cell_dofs, local_modes, ndofs
 from .quadrature import cell_rules, face_rule, leaf_rule
 
@@ -116,6 +116,9 @@ def source_values(prob, pts):
         return prob["kappa"] * d * math.pi ** 2 * u
     if s["kind"] == "square_mms":
         a = s["a"]
+        if s.get("angle", 0.0) != 0.0:
+            xp, yp = rotated_coordinates((0.5, 0.5), s["angle"], pts)
+            return np.cos(a * xp) * np.sin(a * yp)
         return np.cos(a * (pts[:, 0] - 0.5)) * np.sin(a * (pts[:, 1] - 0.5))
     if s["kind"] == "popcorn":
         # f = -kappa Lap u for u = x^3 + x y^2 + y^3 + z^4 + sin(3 (x^2 + y^2))
@@ -142,6 +145,9 @@ def dirichlet_values(prob, pts):
     if g == "square_mms":
         s = prob["source"]
         a = s["a"]
+        if s.get("angle", 0.0) != 0.0:
+            xp, yp = rotated_coordinates((0.5, 0.5), s["angle"], pts)
+            return np.cos(a * xp) * np.sin(a * yp) / (2.0 * s["kappa"] * a * a)
         return (np.cos(a * (pts[:, 0] - 0.5)) * np.sin(a * (pts[:, 1] - 0.5))
                 / (2.0 * s["kappa"] * a * a))
     if g == "popcorn":

@@ -14,6 +14,8 @@ Kinds:
   voids      psi = max_k (r_k - |x - c_k|)             (block minus balls)
   ellipsoid  psi = |diag(1/a) R^T (x - c)| - 1
   popcorn    psi = |x| - r0 - sum_k A exp(-|x - c_k|^2 / sigma^2)   (Sec. 4.3.2)
+  rotated_square  psi = max(|x'|, |y'|) - a, (x', y') = R(-psi_angle)(x - c)
+                  (the rotated square of Sec. 4.1.2)
 
 Box classification (the paper leaves the cut test open; this is the
 reading): balls and voids use exact nearest/farthest point distances, the
@@ -62,6 +64,9 @@ def levelset(geom: dict, x: np.ndarray) -> np.ndarray:
             t = y / ax[i]
             q = t * t if q is None else q + t * t
         return np.sqrt(q) - 1.0
+    if kind == "rotated_square":
+        xp, yp = rotated_coordinates(geom["center"], geom["angle"], x)
+        return np.maximum(np.abs(xp), np.abs(yp)) - geom["half"]
     if kind == "popcorn":
         r0, amp, sig2 = geom["r0"], geom["A"], geom["sigma"] * geom["sigma"]
         s = x[..., 0] * x[..., 0] + x[..., 1] * x[..., 1] + x[..., 2] * x[..., 2]
@@ -72,6 +77,15 @@ def levelset(geom: dict, x: np.ndarray) -> np.ndarray:
             out = out - amp * np.exp(-d2 / sig2)
         return out
     raise ValueError(kind)
+
+
+def rotated_coordinates(center, angle, x):
+    """Coordinates of 2D points x in the frame centred at `center` and
+    rotated by `angle` (radians): x' = cos dx + sin dy, y' = -sin dx + cos dy."""
+    c, s = np.cos(angle), np.sin(angle)
+    dx = x[..., 0] - center[0]
+    dy = x[..., 1] - center[1]
+    return c * dx + s * dy, -s * dx + c * dy
 
 
 def _ball_dist2(lo, hi, c):
@@ -116,7 +130,7 @@ def classify_box(geom: dict, lo, hi) -> int:
             if dmin2 < r2:
                 all_clear = False
         return INSIDE if all_clear else CUT
-    if kind in ("ellipsoid", "popcorn"):
+    if kind in ("ellipsoid", "popcorn", "rotated_square"):
         d = len(lo)
         ts = [k * 0.25 for k in range(5)]
         pts = []

@@ -320,3 +320,32 @@ def test_degenerate_grids(make):
     assert np.sqrt(e @ (H.A @ e)) <= 1e-8 * np.sqrt(xd @ (H.A @ xd))
     if prob["p"] == 1:
         assert k == 1
+
+
+def test_rotated_square_iteration_table():
+    """Table tab:testcaseB (psi = 30 degrees, immersed), CG with multigrid
+    and elementwise AS (5,5), tolerance 1e-9: within 2 of the paper for
+    p = 2..5 at h = 1/8, 1/16, 1/32 (readings of the setup in
+    tests/golden/rotated_square_psi30.json)."""
+    g = json.load(open(os.path.join(GOLDEN, "rotated_square_psi30.json")))
+    for j, C in enumerate(g["cells"][:3]):
+        for p in (2, 3, 4, 5):
+            H = mg.Hierarchy(fi.rotated_square(cells=C, p=p))
+            _, k, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=g["rtol"], maxit=300)
+            assert abs(k - g["cg_mg_elementwise"][str(p)][j]) <= 2, (C, p, k)
+
+
+def test_rotated_square_at_zero_angle_is_the_mesh_fitting_square():
+    """At psi = 0 the rotated manufactured data reduce to square_mms: the
+    source and the Dirichlet data agree at arbitrary points."""
+    from oracle.assembly import dirichlet_values, source_values
+    pts = np.random.default_rng(4).random((50, 2))
+    r = fi.rotated_square(psi_deg=0.0)
+    s = fi.square_mms()
+    assert np.array_equal(source_values(r, pts), source_values(s, pts))
+    r30 = fi.rotated_square(psi_deg=30.0)
+    # a rotation by 90 degrees about the centre maps the 30-degree data to 120
+    c = np.array([0.5, 0.5])
+    q = c + (pts - c) @ np.array([[0.0, 1.0], [-1.0, 0.0]])
+    r120 = fi.rotated_square(psi_deg=120.0)
+    assert np.allclose(dirichlet_values(r120, q), dirichlet_values(r30, pts), atol=1e-15)
