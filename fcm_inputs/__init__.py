@@ -237,6 +237,25 @@ def popcorn(cells=97, p=3, alpha=1e-6, quad_depth=3, space="trunk", drop_outside
                  name=f"popcorn_{cells}^3_p{p}")
 
 
+def cube_cavities(cells=32, p=2, overlay_levels=0, alpha=1e-8, quad_depth=3):
+    """Cube with spherical cavities (Sec. 4.3): the perforated plate in 3D, a
+    cube of side 4 with eight cavities of radius 0.3 sqrt(2) centred in its
+    octants, E = 2.069e5, nu = 0.29, alpha = 1e-8, beta = 1e10, clamped on
+    z = 0 and loaded by the pressure 100 on z = 4; trunk-space elements,
+    fully fictitious cells removed; h = 4 / cells (32 cells: h = 1/32 of
+    the side)."""
+    r = 0.3 * math.sqrt(2.0)
+    balls = [(x, y, z, r) for z in (1.0, 3.0) for y in (1.0, 3.0) for x in (1.0, 3.0)]
+    return _base(3, (cells,) * 3, p, pde="elasticity", E=2.069e5, nu=0.29, alpha=alpha,
+                 beta=1e10, lo=(0.0,) * 3, hi=(4.0,) * 3,
+                 geometry=dict(kind="voids", balls=balls), source=dict(kind="const", f0=0.0),
+                 dirichlet=dict(kind="faces", g="zero", faces=[4]),
+                 traction=dict(face=5, t=(0.0, 0.0, -100.0)), quad_depth=quad_depth,
+                 overlay_levels=overlay_levels, space="trunk", drop_outside=True,
+                 smoother="elementwise" if overlay_levels == 0 else "patchwise",
+                 name=f"cube_cavities_{cells}^3_p{p}_k{overlay_levels}")
+
+
 def random_rotation(rng: SplitMix64) -> list[list[float]]:
     """Rotation matrix of a uniform random unit quaternion (Shoemake 1992)."""
     u1, u2, u3 = rng.uniform(), rng.uniform(), rng.uniform()
@@ -286,4 +305,5 @@ CONFIGS = {
     "perforated_plate": perforated_plate,
     "popcorn": popcorn,
     "rotated_square": rotated_square,
+    "cube_cavities": cube_cavities,
 }

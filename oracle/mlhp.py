@@ -71,7 +71,7 @@ import scipy.sparse as sp
 
 from .assembly import (boundary_faces, dirichlet_values, mass_terms, nfields,
                        shape_functions, volume_terms)
-from .geometry import CUT, INSIDE, classify_box
+from .geometry import CUT, INSIDE, OUTSIDE, classify_box
 from .grid import all_cells, local_modes
 from .multigrid import Hierarchy, Level, pcg
 from .quadrature import cell_rules, face_rule, leaf_rule
@@ -297,6 +297,20 @@ def mesh_for(prob) -> MlhpMesh:
 
 def _leaf_faces(prob, mesh, k, e):
     return boundary_faces(prob, e, tuple(mesh.lattice(k, a) for a in range(mesh.dim)))
+
+
+def kept_functions(space: MlhpSpace, geom) -> np.ndarray:
+    """Removal of fully fictitious cells on an overlay mesh: a function is
+    kept iff one of the leaves it is supported on is not outside the
+    physical domain (boolean mask over the scalar functions)."""
+    mesh = space.mesh
+    used = np.zeros(space.M, dtype=bool)
+    for k, e in mesh.leaves():
+        if classify_box(geom, *mesh.box(k, e)) == OUTSIDE:
+            continue
+        for _, _, _, ids in space.leaf_functions(k, e):
+            used[ids] = True
+    return used
 
 
 def leaf_system(prob, space: MlhpSpace, k, e):
