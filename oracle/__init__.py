@@ -11,13 +11,17 @@ approaches for the finite cell method on uniform and multi-level hp-refined
 grids", arXiv 2010.00881):
 
 * ``basis``       integrated Legendre basis (Sec. 2.1), Gauss-Legendre rules
-* ``geometry``    level sets, cell classification
+* ``geometry``    level sets (balls, voids, ellipsoids, the popcorn of
+                  Sec. 4.3.2, the rotated square of Sec. 4.1.2), cell
+                  classification, whole-grid classification
 * ``quadrature``  space-tree cut-cell integration, surface rules
 * ``assembly``    element matrices and the global system of Eq. (weakform)
 * ``multigrid``   level hierarchy (Eq. restrictionoperation,
                   Eq. hierarchicalMatrices), additive Schwarz smoother
                   (Eq. AdditiveSchwarz; elementwise or patchwise blocks,
-                  Sec. 3.3.1), V-cycle (Algorithm 1), PCG (Sec. 4)
+                  Sec. 3.3.1; Jacobi and Gauss-Seidel for comparison,
+                  Sec. 4.1), V-cycle (Algorithm 1), PCG (Sec. 4), multigrid
+                  as a stand-alone solver
 * ``mlhp``        multi-level hp overlays (Sec. 2.2): overlay mesh, active
                   basis, leaf assembly, hp-multigrid levels (Sec. 3.2,
                   Fig. hpmultigrid) with patchwise blocks over base cells
