@@ -212,6 +212,18 @@ class MlhpSpace:
         agg = sum if trunk else max
         self.degree = np.array([agg(f[2]) if f[2] else 1 for f in funcs], dtype=np.int64)
 
+    def restrict(self, keep):
+        """Keep only the functions where `keep` (a mask over the present
+        ones) is true, renumbered in their order (removal of the functions
+        that only fully fictitious leaves support)."""
+        self.funcs = [f for f, k in zip(self.funcs, keep) if k]
+        self.fid = {f: i for i, f in enumerate(self.funcs)}
+        self.M = len(self.funcs)
+        self.N = self.nf * self.M
+        self.level = self.level[keep]
+        self.degree = self.degree[keep]
+        self._touch = None
+
     def leaf_functions(self, k, e):
         """Per ancestor j of leaf (k, e): (j, box, active local-mode columns
         of its (p+1)^d modes, their scalar function ids)."""
@@ -299,18 +311,29 @@ def _leaf_faces(prob, mesh, k, e):
     return boundary_faces(prob, e, tuple(mesh.lattice(k, a) for a in range(mesh.dim)))
 
 
+def outside_base_cells(mesh: MlhpMesh, geom) -> set:
+    """Base cells lying wholly outside the physical domain."""
+    return {e for e in mesh.E[0] if classify_box(geom, *mesh.box(0, e)) == OUTSIDE}
+
+
 def kept_functions(space: MlhpSpace, geom) -> np.ndarray:
-    """Removal of fully fictitious cells on an overlay mesh: a function is
-    kept iff one of the leaves it is supported on is not outside the
-    physical domain (boolean mask over the scalar functions)."""
+    """Removal of fully fictitious cells on an overlay mesh, at the
+    granularity of base cells: a function is kept iff it touches a base
+    cell that is not wholly outside (boolean mask over the scalar
+    functions).  Removing single overlay leaves instead would leave
+    functions that are linearly dependent on the remaining leaves (a
+    singular system); overlay leaves inside kept base cells stay, weighted
+    by alpha."""
     mesh = space.mesh
-    used = np.zeros(space.M, dtype=bool)
-    for k, e in mesh.leaves():
-        if classify_box(geom, *mesh.box(k, e)) == OUTSIDE:
-            continue
-        for _, _, _, ids in space.leaf_functions(k, e):
-            used[ids] = True
-    return used
+    C = mesh.cells
+    out = set()
+    for e in outside_base_cells(mesh, geom):
+        lin, stride = 0, 1
+        for a in range(mesh.dim):
+            lin += e[a] * stride
+            stride *= C[a]
+        out.add(lin)
+    return np.array([any(c not in out for c in cs) for cs in space.touched_base_cells()])
 
 
 def leaf_system(prob, space: MlhpSpace, k, e):
@@ -353,12 +376,18 @@ def leaf_system(prob, space: MlhpSpace, k, e):
 def assemble_mlhp(prob, space: MlhpSpace = None):
     """Global CSR matrix and load over the active functions, summed from the
     leaf element systems.  Returns (A, b, space)."""
+    drop = bool(prob.get("drop_outside"))
     if space is None:
         space = MlhpSpace(mesh_for(prob), prob["p"], nfields(prob),
                           trunk=prob.get("space", "tensor") == "trunk")
+        if drop:
+            space.restrict(kept_functions(space, prob["geometry"]))
     rows, cols, vals = [], [], []
     b = np.zeros(space.N)
+    removed = outside_base_cells(space.mesh, prob["geometry"]) if drop else set()
     for k, e in space.mesh.leaves():
+        if k == 0 and e in removed:
+            continue
         ids, K, bl, _ = leaf_system(prob, space, k, e)
         dofs = space.dofs(ids)
         rows.append(np.repeat(dofs, len(dofs)))
@@ -453,7 +482,20 @@ class MlhpHierarchy(Hierarchy):
             lv.blocks = schwarz_blocks(space, s, self.smoother_kind)
             levels.append(lv)
             fine_sel = s
-        self._complete(levels)
+        if prob.get("drop_outside"):
+            # the last set holds the kept base-grid hats: continue on those nodes
+            C = space.mesh.cells
+            nodes = []
+            for f in fine_sel:
+                _, t, _ = space.funcs[f]
+                g, stride = 0, 1
+                for a in range(d):
+                    g += (t[a] // 2) * stride
+                    stride *= C[a] + 1
+                nodes.append(g)
+            self._complete_on_nodes(levels, np.array(nodes, dtype=np.int64))
+        else:
+            self._complete(levels)
 
 
 def mlhp_solve(prob, rtol=1e-8, maxit=500):

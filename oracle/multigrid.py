@@ -285,6 +285,68 @@ class Hierarchy:
                 lv.build_pointwise(self.smoother_kind)
                 lv.omega = self.omega
 
+    def _complete_on_nodes(self, levels, nodes):
+        """As _complete, for a last level that holds only the base-grid
+        nodes `nodes` (grid node ids, x fastest; fully fictitious cells
+        removed): Q1 h-levels by Galerkin P^T A P with P = multilinear
+        interpolation onto the held fine nodes, coarse nodes that no held
+        fine node depends on dropped; then smoothers and coarse Cholesky."""
+        d, nf = levels[-1].dim, levels[-1].nf
+        cells = levels[-1].cells
+        while max(levels[-1].cells) > self.prob["coarse_cells"]:
+            fine = levels[-1]
+            P = q1_prolongation(d, cells, 1)[nodes]
+            used = np.flatnonzero(np.asarray(abs(P).sum(axis=0)).ravel() > 0)
+            P = P[:, used]
+            if nf > 1:
+                P = sp.kron(sp.identity(nf, format="csr"), P, format="csr")
+            fine.to_coarse = ("h", P.tocsr())
+            cells = tuple((c + 1) // 2 for c in cells)
+            lv = Level((P.T @ fine.A @ P).tocsr(), cells, 1, nf, d)
+            lv.blocks = self._q1_blocks(cells, used, nf)
+            levels.append(lv)
+            nodes = used
+        levels.reverse()
+        self.levels = levels
+        self._setup_smoothers()
+        levels[0].chol = sla.cho_factor(levels[0].A.toarray(), lower=True)
+
+    def _q1_blocks(self, cells, nodes, nf):
+        """Blocks of a Q1 level holding grid nodes `nodes`: the held nodes
+        of each cell (elementwise) or of the cells around each node."""
+        d = len(cells)
+        pos = {int(n): i for i, n in enumerate(nodes)}
+        M = len(nodes)
+
+        def cell_nodes(c):
+            out = []
+            for off in itertools.product((0, 1), repeat=d):
+                g, stride = 0, 1
+                for a in range(d):
+                    g += (c[a] + off[a]) * stride
+                    stride *= cells[a] + 1
+                if g in pos:
+                    out.append(pos[g])
+            return out
+
+        def fields(ids):
+            ids = np.unique(np.array(ids, dtype=np.int64))
+            return np.concatenate([f * M + ids for f in range(nf)])
+
+        blocks = []
+        if self.smoother_kind == "elementwise":
+            for c in all_cells(d, cells):
+                ids = cell_nodes(c)
+                if ids:
+                    blocks.append(fields(ids))
+            return blocks
+        for v in itertools.product(*[range(cells[a] + 1) for a in reversed(range(d))]):
+            v = tuple(reversed(v))
+            ids = [i for c in cells_around(v, cells) for i in cell_nodes(c)]
+            if ids:
+                blocks.append(fields(ids))
+        return blocks
+
     @property
     def A(self):
         return self.levels[-1].A
@@ -390,3 +452,14 @@ def solve(prob, rtol=1e-8, maxit=500, flexible=False):
     H = Hierarchy(prob)
     x, k, hist = pcg(H.A, H.b, H.vcycle, rtol=rtol, maxit=maxit, flexible=flexible)
     return H, x, k, hist
+
+
+def cells_around(v, C):
+    """The (up to 2^d) cells of a grid with C cells per axis around node v."""
+    d = len(C)
+    out = []
+    for off in itertools.product((0, 1), repeat=d):
+        c = tuple(v[a] - off[a] for a in range(d))
+        if all(0 <= c[a] < C[a] for a in range(d)):
+            out.append(c)
+    return out

@@ -32,7 +32,7 @@ import scipy.sparse as sp
 from .assembly import element_system, nfields
 from .geometry import OUTSIDE
 from .grid import all_cells, cell_dofs, local_modes, m_1d, ndofs
-from .multigrid import Hierarchy, Level, q1_prolongation
+from .multigrid import Hierarchy, Level, cells_around
 
 
 def mode_degrees_1d(C: int, p: int) -> np.ndarray:
@@ -185,7 +185,7 @@ class TrunkHierarchy(Hierarchy):
         for lv, ts in zip(levels, level_t):
             lv.blocks = self._p_blocks(ts)
         nodes = self._q1_nodes(level_t[-1])
-        self._complete_kept(levels, nodes)
+        self._complete_on_nodes(levels, nodes)
 
     def _q1_nodes(self, kept_t):
         """Grid node ids (x fastest) of the p = 1 DOFs (vertices)."""
@@ -226,78 +226,7 @@ class TrunkHierarchy(Hierarchy):
         blocks = []
         for v in itertools.product(*[range(C[a] + 1) for a in reversed(range(d))]):
             v = tuple(reversed(v))
-            ids = [dofs_of(c) for c in _cells_around(v, C) if c in kept_cells]
+            ids = [dofs_of(c) for c in cells_around(v, C) if c in kept_cells]
             if ids:
                 blocks.append(fields(np.concatenate(ids)))
         return blocks
-
-    def _complete_kept(self, levels, nodes):
-        """Q1 h-levels below p = 1 (Galerkin P^T A P with P = multilinear
-        interpolation onto the kept fine nodes; coarse nodes no kept fine
-        node depends on are dropped), smoothers, coarse Cholesky."""
-        d, nf = self.space.dim, self.space.nf
-        cells = self.space.cells
-        while max(levels[-1].cells) > self.prob["coarse_cells"]:
-            fine = levels[-1]
-            P = q1_prolongation(d, cells, 1)[nodes]
-            used = np.flatnonzero(np.asarray(abs(P).sum(axis=0)).ravel() > 0)
-            P = P[:, used]
-            if nf > 1:
-                P = sp.kron(sp.identity(nf, format="csr"), P, format="csr")
-            fine.to_coarse = ("h", P.tocsr())
-            cells = tuple((c + 1) // 2 for c in cells)
-            lv = Level((P.T @ fine.A @ P).tocsr(), cells, 1, nf, d)
-            lv.blocks = self._q1_blocks(cells, used)
-            levels.append(lv)
-            nodes = used
-        levels.reverse()
-        self.levels = levels
-        self._setup_smoothers()
-        levels[0].chol = sla.cho_factor(levels[0].A.toarray(), lower=True)
-
-    def _q1_blocks(self, cells, nodes):
-        """Blocks of a Q1 level holding grid nodes `nodes`: the held nodes
-        of each cell (elementwise) or of the cells around each node."""
-        d, nf = len(cells), self.space.nf
-        pos = {int(n): i for i, n in enumerate(nodes)}
-        M = len(nodes)
-
-        def cell_nodes(c):
-            out = []
-            for off in itertools.product((0, 1), repeat=d):
-                g, stride = 0, 1
-                for a in range(d):
-                    g += (c[a] + off[a]) * stride
-                    stride *= cells[a] + 1
-                if g in pos:
-                    out.append(pos[g])
-            return out
-
-        def fields(ids):
-            ids = np.unique(np.array(ids, dtype=np.int64))
-            return np.concatenate([f * M + ids for f in range(nf)])
-
-        blocks = []
-        if self.smoother_kind == "elementwise":
-            for c in all_cells(d, cells):
-                ids = cell_nodes(c)
-                if ids:
-                    blocks.append(fields(ids))
-            return blocks
-        for v in itertools.product(*[range(cells[a] + 1) for a in reversed(range(d))]):
-            v = tuple(reversed(v))
-            ids = [i for c in _cells_around(v, cells) for i in cell_nodes(c)]
-            if ids:
-                blocks.append(fields(ids))
-        return blocks
-
-
-def _cells_around(v, C):
-    """The (up to 2^d) cells of a grid with C cells per axis around node v."""
-    d = len(C)
-    out = []
-    for off in itertools.product((0, 1), repeat=d):
-        c = tuple(v[a] - off[a] for a in range(d))
-        if all(0 <= c[a] < C[a] for a in range(d)):
-            out.append(c)
-    return out

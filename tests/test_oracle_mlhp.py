@@ -450,3 +450,59 @@ def test_trunk_hp_levels_are_lower_degree_trunk_spaces():
     sets = hp_level_sets(space)
     for s, pc in zip(sets[1:4], (3, 2, 1)):
         assert [space.funcs[i] for i in s] == MlhpSpace(mesh, pc, trunk=True).funcs, pc
+
+
+def test_removing_fictitious_base_cells_on_overlay_meshes():
+    """Removal of fully fictitious cells on overlay meshes works on base
+    cells: the kept system is SPD, the hp-multigrid PCG meets its direct
+    solve in as many iterations as without removal, and the field in the
+    physical domain barely moves (16 x 16 plate, depth 2, cavities holding
+    whole base cells).  Removing single overlay leaves instead leaves a
+    singular system."""
+    from oracle.geometry import levelset
+    from oracle.mlhp import kept_functions, outside_base_cells
+    base = fi.perforated_plate(cells=16, overlay_levels=2)
+    mesh = mesh_for(base)
+    assert outside_base_cells(mesh, base["geometry"])
+    H = MlhpHierarchy(dict(base, drop_outside=True))
+    Hf = MlhpHierarchy(base)
+    assert H.A.shape[0] < Hf.A.shape[0]
+    assert np.linalg.eigvalsh(H.A.toarray()).min() > 0.0
+    x, k, _ = pcg(H.A, H.b, H.vcycle, rtol=1e-9, maxit=300)
+    xf, kf, _ = pcg(Hf.A, Hf.b, Hf.vcycle, rtol=1e-9, maxit=300)
+    xd = spla.spsolve(H.A.tocsc(), H.b)
+    e = x - xd
+    assert np.sqrt(e @ (H.A @ e)) <= 1e-8 * np.sqrt(xd @ (H.A @ xd))
+    assert abs(k - kf) <= 1
+    # the displacement at physical points barely changes
+    rng = np.random.default_rng(5)
+    pts = rng.random((400, 2)) * 4.0
+    pts = pts[levelset(base["geometry"], pts) <= 0.0][:100]
+    ux = H.space.evaluate(xd[:H.space.M], pts)
+    uf = Hf.space.evaluate(spla.spsolve(Hf.A.tocsc(), Hf.b)[:Hf.space.M], pts)
+    assert np.abs(ux - uf).max() <= 1e-5 * np.abs(uf).max()
+    # leaf removal: keep the functions of the leaves that are not outside,
+    # assemble those leaves only -> the matrix has a null space
+    import scipy.sparse as sps
+    from oracle.geometry import OUTSIDE, classify_box
+    from oracle.mlhp import leaf_system
+    space = MlhpSpace(mesh, 2, nf=2)
+    kept_leaves = [(kk, ee) for kk, ee in mesh.leaves()
+                   if classify_box(base["geometry"], *mesh.box(kk, ee)) != OUTSIDE]
+    keep = np.zeros(space.M, dtype=bool)
+    for kk, ee in kept_leaves:
+        for _, _, _, ids in space.leaf_functions(kk, ee):
+            keep[ids] = True
+    assert keep.sum() < kept_functions(space, base["geometry"]).sum()
+    space.restrict(keep)
+    rows, cols, vals = [], [], []
+    for kk, ee in kept_leaves:
+        ids, K, _, _ = leaf_system(base, space, kk, ee)
+        dofs = space.dofs(ids)
+        rows.append(np.repeat(dofs, len(dofs)))
+        cols.append(np.tile(dofs, len(dofs)))
+        vals.append(K.ravel())
+    AL = sps.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                        shape=(space.N, space.N)).toarray()
+    ev = np.linalg.eigvalsh(AL)
+    assert ev[0] <= 1e-12 * ev[-1]
