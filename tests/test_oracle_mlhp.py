@@ -506,3 +506,16 @@ def test_removing_fictitious_base_cells_on_overlay_meshes():
                         shape=(space.N, space.N)).toarray()
     ev = np.linalg.eigvalsh(AL)
     assert ev[0] <= 1e-12 * ev[-1]
+
+
+def test_iterations_flat_in_the_refinement_depth_3d():
+    """Sec. 4.3 (influence of the refinement level): with patchwise blocks
+    the CG+MG count does not depend on the overlay depth in 3D either.  The
+    sphere workload with overlays (r = 0.3, p = 2) on a 3^3 base grid,
+    depths 0, 1, 2 (343, 2,099 and 4,527 DOFs; 6, 6, 7 iterations)."""
+    ks = []
+    for depth in range(3):
+        H = MlhpHierarchy(fi.poisson3d_sphere_mlhp(cells=3, p=2, overlay_levels=depth))
+        _, k, _ = pcg(H.A, H.b, H.vcycle, rtol=1e-8, maxit=200)
+        ks.append(k)
+    assert max(ks) - min(ks) <= 2 and max(ks) <= 12, ks
