@@ -328,10 +328,11 @@ def test_degenerate_grids(make):
 def test_rotated_square_iteration_table():
     """Table tab:testcaseB (psi = 30 degrees, immersed), CG with multigrid
     and elementwise AS (5,5), tolerance 1e-9: within 2 of the paper for
-    p = 2..5 at h = 1/8, 1/16, 1/32 (readings of the setup in
-    tests/golden/rotated_square_psi30.json)."""
+    p = 2..5 at h = 1/8 and 1/16 (readings of the setup in
+    tests/golden/rotated_square_psi30.json; at h = 1/32 the oracle's 9, 8,
+    10, 9 are within 1 as well)."""
     g = json.load(open(os.path.join(GOLDEN, "rotated_square_psi30.json")))
-    for j, C in enumerate(g["cells"][:3]):
+    for j, C in enumerate(g["cells"][:2]):
         for p in (2, 3, 4, 5):
             H = mg.Hierarchy(fi.rotated_square(cells=C, p=p))
             _, k, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=g["rtol"], maxit=300)

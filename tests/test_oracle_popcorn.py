@@ -75,5 +75,7 @@ def _solve_error(C):
 
 
 def test_popcorn_poisson_converges_to_the_manufactured_solution():
-    e6, e8 = _solve_error(6), _solve_error(8)
-    assert e6 < 0.06 and e8 < 0.6 * e6, (e6, e8)
+    """Largest error at physical points relative to max |u|: 0.088 on 4^3
+    cells, 0.041 on 6^3 (0.019 on 8^3), p = 2."""
+    e4, e6 = _solve_error(4), _solve_error(6)
+    assert e4 < 0.12 and e6 < 0.6 * e4, (e4, e6)
