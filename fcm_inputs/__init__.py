@@ -178,6 +178,17 @@ def elasticity3d_voids(cells=64, p=4, alpha=1e-6, n_voids=64, seed=0, quad_depth
                  name=f"elasticity3d_voids_{cells}^3_p{p}")
 
 
+def elasticity_mms(dim=3, cells=4, p=2, E=1.0, nu=0.3, beta=1e9, v=(1.0, -2.0, 3.0)):
+    """Body-fitted linear elasticity on the unit box (no immersed boundary)
+    with the manufactured displacement u = prod_a sin(pi x_a) v: the body force
+    that makes it exact and homogeneous Dirichlet data on every face by
+    penalty (plane strain in 2D)."""
+    return _base(dim, (cells,) * dim, p, pde="elasticity", E=E, nu=nu, alpha=1.0, beta=beta,
+                 geometry=dict(kind="none"), source=dict(kind="elastic_sin3", v=tuple(v)),
+                 dirichlet=dict(kind="faces", g="zero", faces=list(range(2 * dim))),
+                 traction=None, quad_depth=0, name=f"elasticity_mms_{dim}d_{cells}_p{p}")
+
+
 def poisson3d_sphere_mlhp(cells=16, p=2, overlay_levels=3, alpha=1e-8, radius=0.3,
                           quad_depth=3):
     """The sphere problem of poisson3d_sphere (manufactured sin solution,

@@ -340,13 +340,15 @@ void fcm_batch_destroy(fcm_batch* b);
  * K_dev: caller-owned device array of prod(cells) symmetric cell matrices,
  * (p+1)^d x (p+1)^d each, row-major, cells in linear order (x fastest), local
  * DOF order j_x + (p+1) j_y + (p+1)^2 j_z.  x_dev, y_dev: ndofs doubles.
- * stream: cudaStream_t (NULL: legacy default stream); returns after the
- * stream has finished the work.  Scratch: a 4 MiB array compiled into the
+ * stream: cudaStream_t (NULL: legacy default stream); the call synchronizes
+ * the stream before it returns.  Scratch: a 4 MiB array compiled into the
  * library (per GPU, held until exit), so prod(cells) (p+1)^d may be at most
  * about 520,000; larger requests return FCM_E_INVALID.  The first call on a
- * device looks up the array's device address and should precede any stream
- * capture; calls that overlap on the GPU race on the shared array.  Calls
- * no allocating routine. */
+ * device looks up the array's device address (cached per device, so not valid
+ * across cudaDeviceReset) and should come before any stream capture; calls
+ * that overlap on the GPU race on the shared array.  FCM_E_TIMEOUT if a
+ * bounded device wait on a bulk copy expired (y then holds stale products).
+ * Calls no allocating routine. */
 fcm_status fcm_cell_apply_noalloc(int dim, const int* cells, int p, const double* K_dev,
                                   const double* x_dev, double* y_dev, void* stream);
 

@@ -106,6 +106,8 @@ def source_values(prob, pts):
     s = prob["source"]
     d = prob["dim"]
     if prob["pde"] == "elasticity":
+        if s["kind"] == "elastic_sin3":
+            return _elastic_sin3_force(prob, pts)
         return np.zeros((len(pts), d)) + s.get("f0", 0.0)
     if s["kind"] == "const":
         return np.full(len(pts), float(s["f0"]))
@@ -127,6 +129,39 @@ def source_values(prob, pts):
         lap = 8.0 * x + 6.0 * y + 12.0 * z * z + 12.0 * np.cos(3.0 * r2) - 36.0 * r2 * np.sin(3.0 * r2)
         return -prob["kappa"] * lap
     raise ValueError(s["kind"])
+
+
+def _lame(E, nu):
+    """Lame parameters (lambda, mu) of an isotropic material."""
+    return E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), E / (2.0 * (1.0 + nu))
+
+
+def _elastic_sin3_force(prob, pts):
+    """Body force of the manufactured displacement u = phi(x) v with
+    phi = prod_a sin(pi x_a) and a constant vector v (plane strain in 2D):
+    Navier's equation -div sigma = f with sigma = lambda (div u) I + 2 mu eps
+    gives f = -(mu Lap u + (lambda + mu) grad div u)
+           = mu d pi^2 phi v - (lambda + mu) H(phi) v,
+    H the Hessian of phi: H_aa = -pi^2 phi,
+    H_ab = pi^2 cos(pi x_a) cos(pi x_b) prod_{c != a, b} sin(pi x_c)."""
+    d = prob["dim"]
+    v = np.asarray(prob["source"]["v"][:d], dtype=float)
+    lam, mu = _lame(prob["E"], prob["nu"])
+    sn = np.sin(math.pi * pts)
+    cs = np.cos(math.pi * pts)
+    phi = np.prod(sn, axis=1)
+    H = np.empty((len(pts), d, d))
+    for a in range(d):
+        for b in range(d):
+            if a == b:
+                H[:, a, a] = -math.pi ** 2 * phi
+            else:
+                t = math.pi ** 2 * cs[:, a] * cs[:, b]
+                for c in range(d):
+                    if c != a and c != b:
+                        t = t * sn[:, c]
+                H[:, a, b] = t
+    return mu * d * math.pi ** 2 * phi[:, None] * v[None, :] - (lam + mu) * (H @ v)
 
 
 def dirichlet_values(prob, pts):
@@ -159,6 +194,9 @@ def dirichlet_values(prob, pts):
 def exact_solution(prob, pts):
     """Manufactured solution, where the problem has one."""
     s = prob["source"]["kind"]
+    if s == "elastic_sin3":
+        v = np.asarray(prob["source"]["v"][:prob["dim"]], dtype=float)
+        return np.prod(np.sin(math.pi * pts), axis=1)[:, None] * v[None, :]
     if s == "sin3":
         u = np.ones(len(pts))
         for a in range(prob["dim"]):

@@ -16,10 +16,13 @@
 // code cannot use the array's name as a device address, so the first call
 // on each device looks the address up with cudaGetSymbolAddress while that
 // device is current and caches it; make that first call before any stream
-// capture.  All calls on a device share the array: calls whose kernels
-// overlap on the GPU (for example on two streams) race on it.  Each call
-// writes every scratch entry it reads before reading it, so nothing needs to
-// start at zero.
+// capture.  The cached address belongs to the device's current context: after
+// the host application calls cudaDeviceReset the module is loaded again and
+// the cache is stale, so this entry point must not be used across a device
+// reset.  Every call synchronizes its stream before it returns.  All calls on
+// a device share the array: calls whose kernels overlap on the GPU (for
+// example on two streams) race on it.  Each call writes every scratch entry
+// it reads before reading it, so nothing needs to start at zero.
 #include <mutex>
 
 #include "fcm_internal.h"
@@ -114,9 +117,17 @@ extern "C" fcm_status fcm_cell_apply_noalloc(int dim, const int* cells, int p, c
   fcm::launch_gather<double>(g, fcm::GATHER_SET, Y, nullptr, y_dev, 1.0, s);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  // The streaming kernel (stored matrices with more than 16 rows) bounds its
+  // waits on bulk copies; an expired wait leaves stale products in y.
+  int timed_out = 0;
+  if (e == cudaSuccess) e = fcm::read_and_clear_timeout(&timed_out, s);
   if (e != cudaSuccess) {
     fcm::set_last_error(cudaGetErrorString(e));
     return FCM_E_CUDA;
+  }
+  if (timed_out) {
+    fcm::set_last_error("fcm_cell_apply_noalloc: a bounded device wait on a bulk copy expired");
+    return FCM_E_TIMEOUT;
   }
   return FCM_OK;
 }

@@ -199,3 +199,192 @@ def test_immersed_solution_approaches_exact():
             e += float(np.sum(w[keep] * (uh - exact_solution(prob, pts[keep])) ** 2))
         errs.append(math.sqrt(e))
     assert errs[1] < errs[0] / 4, errs
+
+
+# --------------------------------------------------------------------------
+# Linear elasticity (Eq. weakform with the Voigt strain operator B and the
+# isotropic C).  Each pin below fails under a plausible slip in the integrand:
+# a tensor instead of an engineering shear strain in B (shear energy x 1/4),
+# 2 mu on the shear diagonal of C (x 2), a wrong lambda (dilatation energy),
+# a traction term left off the load or put on the wrong face.
+
+def _lame_closed_form(E, nu):
+    return E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), E / (2.0 * (1.0 + nu))
+
+
+def _interpolate_linear(dim, p, x0, x1, Gm):
+    """Coefficients of u(x) = Gm x in the hierarchical basis of one cell:
+    the corner values on the nodal modes, zero on the bubbles (exact, since u
+    is multilinear), fields stacked."""
+    from oracle.grid import local_modes
+    modes = local_modes(dim, p)
+    n = len(modes)
+    v = np.zeros(dim * n)
+    for l, js in enumerate(modes):
+        if max(js) > 1:
+            continue
+        x = np.array([x1[a] if js[a] == 1 else x0[a] for a in range(dim)])
+        u = Gm @ x
+        for k in range(dim):
+            v[k * n + l] = u[k]
+    return v
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 3), (3, 1), (3, 2)])
+def test_elasticity_strain_energy_closed_form(dim, p):
+    """1/2 u^T K u of a homogeneous strain u = G x on one uncut cell equals
+    the closed-form energy V (lambda/2 (tr eps)^2 + mu eps:eps), eps = sym G
+    (plane strain in 2D), for random G and for pure shear, uniaxial strain and
+    dilatation separately."""
+    E, nu = 3.0, 0.27
+    prob = fi.elasticity_mms(dim=dim, cells=3, p=p, E=E, nu=nu)
+    prob["dirichlet"] = dict(kind="none")
+    prob["hi"] = tuple(0.8 + 0.15 * a for a in range(dim))   # non-cubic cells
+    cell = (1,) * dim
+    K, _, cls = element_system(prob, cell)
+    assert cls == INSIDE
+    x0, x1 = cell_box(prob["lo"], prob["hi"], prob["cells"], cell)
+    vol = float(np.prod(np.asarray(x1) - np.asarray(x0)))
+    lam, mu = _lame_closed_form(E, nu)
+    rng = np.random.default_rng(7)
+    fields = [rng.uniform(-1, 1, (dim, dim)) for _ in range(3)]
+    shear = np.zeros((dim, dim))
+    shear[0, 1] = 0.7                                  # u_x = 0.7 y: pure shear
+    uni = np.zeros((dim, dim))
+    uni[0, 0] = 0.4
+    fields += [shear, shear.T, uni, 0.3 * np.eye(dim)]
+    if dim == 3:
+        for a, b in ((1, 2), (2, 0)):
+            g = np.zeros((3, 3))
+            g[a, b] = -0.5
+            fields.append(g)
+    for Gm in fields:
+        u = _interpolate_linear(dim, p, x0, x1, Gm)
+        eps = 0.5 * (Gm + Gm.T)
+        expect = vol * (0.5 * lam * np.trace(eps) ** 2 + mu * np.sum(eps * eps))
+        got = 0.5 * u @ K @ u
+        assert abs(got - expect) <= 1e-12 * max(1.0, abs(expect)), (Gm, got, expect)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 2), (3, 1), (3, 2)])
+def test_elasticity_displacement_patch_test(dim, p):
+    """Patch test: on a 3^d body-fitted block without body force, the
+    coefficients of a linear field u = G x prescribed on every mode that is
+    nonzero on the boundary (corner values on nodes, 0 on bubbles) give, by
+    the interior equations, exactly that field (interior nodes = G x, every
+    interior bubble 0)."""
+    prob = fi.elasticity_mms(dim=dim, cells=3, p=p)
+    prob["source"] = dict(kind="const", f0=0.0)
+    prob["dirichlet"] = dict(kind="none")
+    prob["hi"] = (1.0, 1.3, 0.9)[:dim]
+    A, b, _ = assemble(prob)
+    assert np.abs(b).max() == 0.0
+    Gm = np.random.default_rng(3).uniform(-1, 1, (dim, dim))
+    C = prob["cells"]
+    m = [m_1d(C[a], p) for a in range(dim)]
+    M = int(np.prod(m))
+    idx = np.indices(m[::-1]).reshape(dim, -1)[::-1]   # per-axis 1D index, x fastest
+    nodal = np.all([idx[a] <= C[a] for a in range(dim)], axis=0)
+    # a mode is nonzero on the box boundary iff along some axis it is an end node
+    boundary = np.any([(idx[a] == 0) | (idx[a] == C[a]) for a in range(dim)], axis=0)
+    h = [(prob["hi"][a] - prob["lo"][a]) / C[a] for a in range(dim)]
+    X = np.array([prob["lo"][a] + h[a] * idx[a] for a in range(dim)])   # node coordinates
+    exact = np.zeros(dim * M)
+    for k in range(dim):
+        exact[k * M:(k + 1) * M] = np.where(nodal, (Gm[k] @ X), 0.0)
+    fixed = np.tile(boundary, dim)
+    free = ~fixed
+    Ad = A.toarray()
+    u = exact.copy()
+    u[free] = np.linalg.solve(Ad[np.ix_(free, free)], -Ad[np.ix_(free, fixed)] @ exact[fixed])
+    assert np.abs(u - exact).max() <= 1e-10 * np.abs(exact).max()
+
+
+def test_elasticity_traction_resultant():
+    """The traction load on a box face is int t N dGamma: tested against a
+    constant field (resultant t x face area) and a linear one (first moment)
+    per component, on a box with unequal sides; a load on the wrong face or a
+    dropped term fails one of them."""
+    prob = fi.elasticity_mms(dim=3, cells=2, p=2)
+    prob["source"] = dict(kind="const", f0=0.0)
+    prob["dirichlet"] = dict(kind="none")
+    prob["hi"] = (1.0, 2.0, 3.0)
+    t = np.array([0.7, -1.3, 2.1])
+    prob["traction"] = dict(face=1, t=tuple(t))        # the face x = 1, area 2 x 3
+    _, b, _ = assemble(prob)
+    C, p = prob["cells"], prob["p"]
+    m = [m_1d(C[a], p) for a in range(3)]
+    M = int(np.prod(m))
+    idx = np.indices(m[::-1]).reshape(3, -1)[::-1]
+    nodal = np.all([idx[a] <= C[a] for a in range(3)], axis=0)
+    X = np.array([prob["lo"][a] + (prob["hi"][a] - prob["lo"][a]) / C[a] * idx[a]
+                  for a in range(3)])
+    for k in range(3):
+        bk = b[k * M:(k + 1) * M]
+        assert abs(bk[nodal].sum() - t[k] * 6.0) <= 1e-12 * 6.0
+        # u = y e_k: int_0^2 int_0^3 y dz dy = 6; u = z e_k: 9; u = x e_k: 6 (x = 1)
+        assert abs(bk[nodal] @ X[1][nodal] - t[k] * 6.0) <= 1e-12 * 9.0
+        assert abs(bk[nodal] @ X[2][nodal] - t[k] * 9.0) <= 1e-12 * 9.0
+        assert abs(bk[nodal] @ X[0][nodal] - t[k] * 6.0) <= 1e-12 * 9.0
+
+
+def test_elasticity_manufactured_force_is_navier():
+    """The oracle's manufactured body force equals -div sigma(u) computed by
+    central differences of u with sigma = lambda (div u) I + mu (grad u +
+    grad u^T) (no Voigt notation involved)."""
+    from oracle.assembly import exact_solution, source_values
+    for dim in (2, 3):
+        prob = fi.elasticity_mms(dim=dim, E=2.0, nu=0.31)
+        lam, mu = _lame_closed_form(2.0, 0.31)
+        pts = np.random.default_rng(5).uniform(0.1, 0.9, (6, dim))
+        hh = 1e-4
+
+        def sigma(x):
+            J = np.empty((dim, dim))              # J[i, j] = d u_i / d x_j
+            for j in range(dim):
+                e = np.zeros(dim)
+                e[j] = hh
+                J[:, j] = (exact_solution(prob, (x + e)[None])[0]
+                           - exact_solution(prob, (x - e)[None])[0]) / (2 * hh)
+            return lam * np.trace(J) * np.eye(dim) + mu * (J + J.T)
+
+        for x in pts:
+            div = np.zeros(dim)
+            for j in range(dim):
+                e = np.zeros(dim)
+                e[j] = hh
+                div += (sigma(x + e)[:, j] - sigma(x - e)[:, j]) / (2 * hh)
+            f = source_values(prob, x[None])[0]
+            assert np.allclose(f, -div, rtol=0, atol=2e-5 * np.abs(f).max()), (dim, f, -div)
+
+
+def _l2_error_vec(prob, x):
+    d = prob["dim"]
+    M = int(np.prod([m_1d(prob["cells"][a], prob["p"]) for a in range(d)]))
+    err = 0.0
+    for cell in all_cells(d, prob["cells"]):
+        x0, x1 = cell_box(prob["lo"], prob["hi"], prob["cells"], cell)
+        pts, w = leaf_rule(x0, x1, prob["p"] + 3)
+        N, _ = shape_functions(prob["p"], x0, x1, pts)
+        dofs = cell_dofs(d, prob["cells"], prob["p"], cell)
+        ex = exact_solution(prob, pts)
+        for k in range(d):
+            uh = N @ x[k * M + dofs]
+            err += float(np.sum(w * (uh - ex[:, k]) ** 2))
+    return math.sqrt(err)
+
+
+@pytest.mark.parametrize("dim,p,cells", [(3, 1, (2, 4, 8)), (3, 2, (2, 4, 6)), (2, 2, (4, 8, 16))])
+def test_elasticity_manufactured_h_convergence(dim, p, cells):
+    """Body-fitted elasticity with the manufactured displacement
+    prod sin(pi x_a) (1, -2, 3): the L2 error falls like h^(p+1).  A wrong
+    shear scaling solves another operator, and the error stalls."""
+    errs, hs = [], []
+    for C in cells:
+        prob = fi.elasticity_mms(dim=dim, cells=C, p=p, beta=1e10)
+        A, b, _ = assemble(prob)
+        x = spla.spsolve(A.tocsc(), b)
+        errs.append(_l2_error_vec(prob, x))
+        hs.append(1.0 / C)
+    rate = math.log(errs[-2] / errs[-1]) / math.log(hs[-2] / hs[-1])
+    assert rate > p + 1 - 0.35, (errs, rate)

@@ -32,19 +32,33 @@ def _noalloc(dim, cells, p, K, x, y):
                                       C.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def test_noalloc_apply_matches_fcm_apply_twice():
-    prob = fi.poisson2d_circle()   # 16 x 16 cells, p = 2, cut cells included
+# Each case reaches one kernel of the cell apply: 2D p = 2 (9 DOFs per cell,
+# unpadded rows: the scalar per-cell kernel), 2D p = 3 and 3D p = 1 (16 and 8
+# DOFs: one lane group per cell), 3D p = 3 (64 DOFs, 16-byte rows: the bulk-copy
+# streaming kernel).
+CASES = {
+    "circle16_p2": lambda: fi.poisson2d_circle(),
+    "circle8_p3": lambda: fi.poisson2d_circle(cells=8, p=3),
+    "sphere4_p1": lambda: fi.poisson3d_sphere(cells=4, p=1),
+    "sphere4_p3": lambda: fi.poisson3d_sphere(cells=4, p=3),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_noalloc_apply_matches_fcm_apply_twice(case):
+    prob = CASES[case]()
     s = F.Solver(prob, build_mixed=False)
-    K = np.stack([element_system(prob, c)[0] for c in all_cells(2, prob["cells"])])
+    K = np.stack([element_system(prob, c)[0]
+                  for c in all_cells(prob["dim"], prob["cells"])])
     Kd = torch.from_numpy(np.ascontiguousarray(K)).cuda()
     for seed in (1, 2):
         x = torch.from_numpy(fi.random_vector(s.ndofs, seed=seed)).cuda()
         y = torch.full((s.ndofs,), float("nan"), dtype=torch.float64, device="cuda")
-        st = _noalloc(2, prob["cells"], prob["p"], Kd, x, y)
+        st = _noalloc(prob["dim"], prob["cells"], prob["p"], Kd, x, y)
         assert st == F.FCM_OK, F.load().fcm_last_error()
         ref = s.apply(x)
         rel = (torch.linalg.norm(y - ref) / torch.linalg.norm(ref)).item()
-        assert rel <= 1e-12, (seed, rel)
+        assert rel <= 1e-12, (case, seed, rel)
     s.close()
 
 
