@@ -215,20 +215,46 @@ def run_reference(args, rank):
     print(json.dumps(out))
 
 
-def cpu_baseline(seconds_cap=30.0):
-    """Oracle timed on one bounded sample (rank 0, N = 1)."""
-    from oracle import multigrid as mg
-    prob = oracle_sample()
-    t0 = time.perf_counter()
-    H = mg.Hierarchy(prob)
-    setup_s = time.perf_counter() - t0
-    t = time.perf_counter()
-    _, k, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=RTOL, maxit=MAXIT)
-    dt = time.perf_counter() - t
-    N = H.A.shape[0]
-    return {"value": N / dt, "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+_ORACLE_LEG = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+import fcm_inputs as fi
+from oracle import multigrid as mg
+prob = fi.poisson3d_sphere(cells=8, p=3)
+t0 = time.perf_counter()
+H = mg.Hierarchy(prob)
+setup_s = time.perf_counter() - t0
+t = time.perf_counter()
+_, k, _ = mg.pcg(H.A, H.b, H.vcycle, rtol={rtol!r}, maxit={maxit!r})
+dt = time.perf_counter() - t
+print(json.dumps({{"N": H.A.shape[0], "k": k, "dt": dt, "setup_s": setup_s}}))
+"""
+
+
+def cpu_baseline():
+    """The oracle as it stands on one bounded sample (rank 0, N = 1), run in
+    child processes with numpy/scipy's thread pools at one thread and at all
+    of the host's cores.  The sample: one solve of the same workload family
+    at 8^3 cells, p = 3 (about 10-15 s of CPU work each, setup included)."""
+    ncores = os.cpu_count() or 1
+    legs = {}
+    for threads in (1, ncores):
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(threads)
+        r = subprocess.run([sys.executable, "-c",
+                            _ORACLE_LEG.format(root=ROOT, rtol=RTOL, maxit=MAXIT)],
+                           env=env, capture_output=True, text=True, timeout=600)
+        legs[threads] = json.loads(r.stdout.strip().splitlines()[-1])
+    one, allc = legs[1], legs[ncores]
+    return {"value": one["N"] / one["dt"], "unit": "DOFs/s", "cores": 1, "kind": "oracle",
+            "nproc": ncores,
+            "all_cores": {"value": allc["N"] / allc["dt"], "cores": ncores,
+                          "solve_s": allc["dt"], "setup_s": allc["setup_s"]},
             "sample": (f"one oracle solve of the same workload family at 8^3 cells, p = 3 "
-                       f"({N} DOFs, {k} iterations, {dt:.1f} s; setup {setup_s:.1f} s excluded)")}
+                       f"({one['N']} DOFs, {one['k']} iterations, {one['dt']:.2f} s on 1 "
+                       f"thread, {allc['dt']:.2f} s with {ncores} BLAS/OpenMP threads; setup "
+                       f"{one['setup_s']:.1f} s excluded)")}
 
 
 def run_batch(args, rank, world, local):
@@ -307,6 +333,7 @@ def main():
     import torch.distributed as dist
     from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, Solver
     from paper_2010_00881_gb300 import build as fbuild
+    from paper_2010_00881_gb300 import fcm as F
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -396,12 +423,24 @@ def main():
     peaks, peak_src = load_peaks()
     L = s.num_levels() - 1
     prof = {}
+    top = s.level_info(L)
+    n_loc = top["nloc"]
+    ncells = 1
+    for c in top["cells"][: prob["dim"]]:
+        ncells *= c
+    shared_cells = {5: ncells - top["n_own_cells"], 6: ncells - top["n_own_blocks"]}
     for which, name in ((0, "operator"), (1, "smoother"), (2, "gather"),
-                        (3, "operator_stored"), (4, "smoother_stored")):
+                        (3, "operator_stored"), (4, "smoother_stored"),
+                        (5, "operator_tiles"), (6, "smoother_tiles")):
         for prec, pn in ((FCM_MIXED, "mixed"), (FCM_FP64, "fp64")):
             t_ms = s.profile_op(L, which, prec=prec, reps=20)
             byt = s.op_bytes(L, which, prec=prec)
             prof[f"{name}_{pn}"] = {"ms": t_ms, "bytes": byt, "GBps": byt / (t_ms * 1e-3) / 1e9}
+            if which >= 5:   # shared-matrix GEMM: 2 n^2 flops per cell
+                fl = 2.0 * n_loc * n_loc * shared_cells[which]
+                prof[f"{name}_{pn}"]["TFLOPs"] = fl / (t_ms * 1e-3) / 1e12
+    fma = {"fp64_fma_tflops": F.measure_fma_peak(FCM_FP64),
+           "fp32_fma_tflops": F.measure_fma_peak(FCM_MIXED)}
     dom = prof["smoother_stored_mixed"]
     achieved = dom["GBps"]
     peak = peaks.get("hbm_gbs", 6800.0)
@@ -423,10 +462,11 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": wl_name, "ndofs": N, "rtol": RTOL,
-                       "precision": "mixed: FP32 V-cycle with FP64-accurate (df32) cut-cell "
-                                    "matrices and ill-conditioned block inverses, flexible CG "
-                                    "in FP64 with an FP64-accurate df32 operator; fp64: plain "
-                                    "FP64 throughout",
+                       "precision": "mixed: FP32 V-cycle (shared-matrix products on the "
+                                    "tensor cores in 3xTF32) with FP64-accurate (df32) cut-cell "
+                                    "matrices and ill-conditioned block inverses, inside "
+                                    "flexible CG in FP64 (FP64 operator); fp64: plain FP64 "
+                                    "throughout",
                        "l2": "256 MB buffer written between timed solves",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "iterations": inf_mixed[-1]["iters"],
@@ -442,10 +482,13 @@ def main():
             "gpu_launches": int(sum(i["kernel_launches"] for i in inf_mixed)),
             "roofline": roof,
             "kernels": prof,
+            "peaks_measured": fma,
             "levels": [{"cells": lv["cells"][0], "p": lv["p"], "h": lv["is_h_level"],
                         "ndofs": lv["ndofs"], "own_cells": lv["n_own_cells"],
                         "own_blocks": lv["n_own_blocks"], "fp64_blocks": lv["n_fp64_blocks"],
-                        "omega": round(lv["omega"], 5)} for lv in levels],
+                        "omega": round(lv["omega"], 5),
+                        "max_block_cond": float("%.3g" % lv["max_block_cond"]),
+                        "fp64_in_mixed": lv["fp64_in_mixed"]} for lv in levels],
             "clocks": clk,
         }
         if world == 1 and not args.no_cpu_baseline and args.workload == "sphere":

@@ -55,20 +55,15 @@ typedef enum {
 /* Arithmetic of the preconditioner (the outer CG is always FP64). */
 typedef enum {
   FCM_FP64 = 0,  /* everything in FP64 */
-  FCM_MIXED = 1, /* FP32 V-cycle with FP64-accurate islands inside FP64 flexible CG */
-  /* fcm_apply only: the operator the FCM_MIXED solve uses for its FP64
-   * residuals and search directions (FP64 vectors; cut-cell and shared
-   * matrices as df32 pairs, products compensated in FP32 arithmetic, within
-   * about n 2^-48 of sum |K_ij x_j| per row).  Finest levels with at most 16
-   * DOFs per cell use the FP64 data. */
-  FCM_MIXED_OUTER = 2
+  FCM_MIXED = 1  /* FP32 V-cycle with FP64-accurate islands inside FP64 flexible CG */
 } fcm_precision;
 
-enum { FCM_GEOM_NONE = 0, FCM_GEOM_BALL = 1, FCM_GEOM_VOIDS = 2, FCM_GEOM_ELLIPSOID = 3 };
+enum { FCM_GEOM_NONE = 0, FCM_GEOM_BALL = 1, FCM_GEOM_VOIDS = 2, FCM_GEOM_ELLIPSOID = 3,
+       FCM_GEOM_POPCORN = 4 };
 enum { FCM_PDE_POISSON = 0, FCM_PDE_ELASTICITY = 1 };
-enum { FCM_SRC_CONST = 0, FCM_SRC_SIN3 = 1, FCM_SRC_SQUARE_MMS = 2 };
+enum { FCM_SRC_CONST = 0, FCM_SRC_SIN3 = 1, FCM_SRC_SQUARE_MMS = 2, FCM_SRC_POPCORN = 3 };
 enum { FCM_DIR_NONE = 0, FCM_DIR_LEVELSET = 1, FCM_DIR_FACES = 2 };
-enum { FCM_G_ZERO = 0, FCM_G_SIN3 = 1, FCM_G_SQUARE_MMS = 2 };
+enum { FCM_G_ZERO = 0, FCM_G_SIN3 = 1, FCM_G_SQUARE_MMS = 2, FCM_G_POPCORN = 3 };
 enum { FCM_SMOOTHER_ELEMENTWISE = 0, FCM_SMOOTHER_PATCHWISE = 1 };
 
 /* Grid: dim in {2,3}; cells per axis (>= 1); box [lo, hi]; degree p in
@@ -88,8 +83,11 @@ typedef struct {
  *   BALL       cx cy [cz] r                          psi = |x-c| - r
  *   VOIDS      n_params/4 balls (cx cy cz r)          psi = max_k (r_k - |x-c_k|)
  *   ELLIPSOID  cx cy cz a0 a1 a2 R00 R01 ... R22      psi = |diag(1/a) R^T (x-c)| - 1
+ *   POPCORN    r0 A sigma, then bump centres (cx cy cz)...  (3D, Sec. 4.3.2)
+ *              psi = |x| - r0 - sum_k A exp(-|x - c_k|^2 / sigma^2)
  * Cell and sub-cell classification: exact nearest/farthest distances for
- * balls and voids, a 5^d lattice sign test for the ellipsoid. */
+ * balls and voids, a 5^d lattice sign test for the ellipsoid and the
+ * popcorn. */
 typedef struct {
   int kind;
   int n_params;
@@ -99,7 +97,9 @@ typedef struct {
 /* Physics of Eq. (weakform).  Poisson: kappa scales the stiffness.
  * Elasticity: isotropic E, nu (3D).  alpha: fictitious factor; beta:
  * penalty.  source: CONST (f = f0), SIN3 (f = kappa d pi^2 prod sin(pi x_a)),
- * SQUARE_MMS (f = cos(a x') sin(a y'), x' = x - 1/2, y' = y - 1/2, a = src_a).
+ * SQUARE_MMS (f = cos(a x') sin(a y'), x' = x - 1/2, y' = y - 1/2, a = src_a),
+ * POPCORN (f = -kappa Lap u for the manufactured u = x^3 + x y^2 + y^3 + z^4
+ * + sin(3 (x^2 + y^2)) of Sec. 4.3.2; g POPCORN is that u).
  * dirichlet: LEVELSET (penalty on {psi = 0}) or FACES (bit 2a+s of
  * dirichlet_faces: face of axis a, lower s = 0 / upper s = 1); g selects
  * g_D.  traction_face (-1: none) carries the constant traction vector.
@@ -155,6 +155,11 @@ typedef struct {
   int n_fp64_blocks;         /* of those, kept in FP64 by FCM_MIXED */
   double omega;              /* relaxation used on this level (0 on level 0) */
   double lambda_est;         /* estimate of lambda_max(M^{-1} A) */
+  double max_block_cond;     /* largest infinity-norm condition number of the stored
+                                AS blocks, diagonally scaled (0: none stored) */
+  int fp64_in_mixed;         /* 1: the FCM_MIXED V-cycle runs this level in FP64 (the
+                                finest level when its blocks reach 1e12, or a
+                                single-level hierarchy) */
 } fcm_level_info;
 
 typedef struct fcm_handle fcm_handle;
@@ -259,8 +264,8 @@ fcm_status fcm_mlhp_restriction_1d(int p, int dk, int pos, double* S);
 fcm_status fcm_rhs(const fcm_handle* h, double* b_dev);
 
 /* y = A x on the finest level (prec FCM_FP64: FP64 matrices; FCM_MIXED: the
- * FP32 copies the V-cycle uses, computed in FP32 and widened;
- * FCM_MIXED_OUTER: the FP64-accurate operator of the mixed solve's CG). */
+ * FP32 copies the V-cycle uses, computed in FP32 (shared matrices on the
+ * tensor cores, 3xTF32) and widened). */
 fcm_status fcm_apply(fcm_handle* h, const double* x_dev, double* y_dev, int prec);
 
 /* z = V(r): one V-cycle with zero initial guess (Algorithm 1). */
@@ -282,8 +287,9 @@ fcm_status fcm_cell_classes(const fcm_handle* h, signed char* cls_host);
 /* V-cycle-preconditioned CG from x = 0 (Sec. 4): stops when the recursive
  * relative residual falls below rtol and the recomputed true residual
  * confirms it.  b_dev NULL uses the assembled load.  prec FCM_MIXED runs
- * the FP32 V-cycle inside flexible (Polak-Ribiere) CG whose operator (search
- * directions, true residual) is the FCM_MIXED_OUTER one.  Returns
+ * the FP32 V-cycle inside flexible (Polak-Ribiere) CG; the CG itself (its
+ * operator for search directions and true residual, dot products and
+ * updates) is FP64 in both modes.  Returns
  * FCM_E_NOT_CONVERGED after maxit iterations (x_dev holds the last
  * iterate), FCM_E_BREAKDOWN on p^T A p <= 0 or a non-finite scalar. */
 fcm_status fcm_pcg_solve(fcm_handle* h, const double* b_dev, double* x_dev, double rtol,
@@ -299,11 +305,20 @@ fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_hos
  * which 0: operator cell kernel (y_c = K_c x_c over all cells), 1: smoother
  * cell kernel (A_i^{-1} over all blocks), 2: the DOF gather that follows
  * them, 3 / 4: the stored-matrix (cut-cell / irregular-block) kernel of the
- * operator / smoother alone, without the shared-matrix tiles.  prec selects
+ * operator / smoother alone, without the shared-matrix tiles, 5 / 6: the
+ * shared-matrix tiles of the operator / smoother alone.  prec selects
  * the FP64 or the FCM_MIXED data.  Inputs are the level's work vectors (their
  * current contents); results are discarded. */
 fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int reps,
                           double* avg_ms);
+
+/* Benchmark hook (no counterpart in the paper): the FMA throughput of the
+ * current device in TFLOP/s (2 flops per FMA), FP64 (prec FCM_FP64) or FP32
+ * (FCM_MIXED), from independent FMA chains on every SM timed with CUDA
+ * events; the peak against which the FMA-bound kernels (plain FP64
+ * shared-matrix products, compensated df32 products) are judged.  Allocates
+ * and frees a small device buffer and a stream; takes about 0.1 s. */
+fcm_status fcm_measure_fma_peak(int prec, double* tflops);
 
 /* Bytes the level kernel `which` (as in fcm_profile_op) must move at least
  * once per launch: stored cell matrices or block inverses, one read of

@@ -3,4 +3,4 @@
 The compute path is the CUDA library libfcm.so (C ABI in include/fcm.h);
 ``fcm`` is its ctypes binding and ``build`` compiles it for sm_103a.
 """
-from .fcm import (FCM_FP64, FCM_MIXED, FCM_MIXED_OUTER, FcmError, Solver, load)  # noqa: F401
+from .fcm import (FCM_FP64, FCM_MIXED, FcmError, Solver, load)  # noqa: F401

@@ -27,6 +27,7 @@ SOURCES = {
     "ops.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
+    "peaks.cu": [],
     "batch.cu": [],
     "mlhp.cu": ["-Xcompiler", "-ffp-contract=off"],
 }

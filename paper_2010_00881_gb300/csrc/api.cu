@@ -63,12 +63,9 @@ struct Level {
   // smoother (AS block inverses)
   OpData<double> M64;
   OpData<float> M32;
-  // finest level, mixed path: the outer operator of the mixed solve (FP64
-  // vectors; cut-cell matrices and shared matrices as df32 pairs)
-  OpData<double> A64df;
-  bool has_outer = false;
   double omega = 0.0, lambda = 0.0;
   int n_own_cells = 0, n_own_blocks = 0, n_fp64_blocks = 0;
+  double max_cond = 0.0;  // largest scaled kappa_inf of the stored AS blocks
   // cell sources for Galerkin / block assembly
   int* d_own_index = nullptr;       // per cell: own matrix index or -1
   double* d_scale_cell = nullptr;   // per cell: scale of K_ref for shared cells
@@ -114,6 +111,8 @@ struct fcm_handle {
   double* d_scalar = nullptr;      // reductions for the host
   double* h_scalar = nullptr;      // pinned
   cudaGraphExec_t g_vc64 = nullptr, g_vc32 = nullptr;
+  // mixed V-cycle: levels >= top64 run in FP64 (the rest in FP32)
+  int top64 = 1 << 30;
   long long vc_nodes64 = 0, vc_nodes32 = 0;  // kernel nodes per V-cycle graph
   long long launches = 0;                    // kernels launched by the current solve
 
@@ -175,16 +174,23 @@ void build_shared(Handle* h, SharedSet<T>& S, const std::vector<int>& mat_of,
                   const std::vector<int>& cells, const std::vector<T>& scale, T* mats,
                   int nmats) {
   // cells must already be grouped by matrix id (ascending)
-  std::vector<int4> tiles;
-  int n = (int)cells.size();
-  int i = 0;
-  while (i < n) {
-    int m = mat_of[i];
-    int j = i;
-    while (j < n && mat_of[j] == m && j - i < 64) ++j;  // tiles of <= 64 cells
-    tiles.push_back(make_int4(m, i, j - i, 0));
-    i = j;
-  }
+  auto cut = [&](int size) {
+    std::vector<int4> tiles;
+    int n = (int)cells.size();
+    int i = 0;
+    while (i < n) {
+      int m = mat_of[i];
+      int j = i;
+      while (j < n && mat_of[j] == m && j - i < size) ++j;
+      tiles.push_back(make_int4(m, i, j - i, 0));
+      i = j;
+    }
+    return tiles;
+  };
+  const int n = (int)cells.size();
+  std::vector<int4> tiles = cut(64), tiles_mma = cut(128);
+  S.tl.ntiles_mma = (int)tiles_mma.size();
+  S.tl.tiles_mma = tiles_mma.empty() ? nullptr : h->upload(tiles_mma);
   S.tl.ntiles = (int)tiles.size();
   S.tl.ncells = n;
   S.tl.tiles = tiles.empty() ? nullptr : h->upload(tiles);
@@ -192,6 +198,14 @@ void build_shared(Handle* h, SharedSet<T>& S, const std::vector<int>& mat_of,
   S.scale = scale.empty() ? nullptr : h->upload(scale);
   S.mats = mats;
   S.nmats = nmats;
+}
+
+// Tensor-core operands (TF32 parts in the MMA layout) of an FP32 shared set.
+void prepare_mma(Handle* h, SharedSet<float>& S, int n) {
+  if (!S.mats || S.nmats == 0 || n > 128) return;
+  S.mma_b = h->alloc<float>((size_t)S.nmats * 2 * mma_np(n) * mma_kd(n));
+  launch_mma_operands(n, S.nmats, S.mats, S.mma_b, h->s);
+  CKL();
 }
 
 int next_pow_nodes(int dim, int depth) {
@@ -237,21 +251,6 @@ void apply_A64(Handle* h, Level& L, const double* x, double* y, int mode, const 
   CKL();
 }
 
-// The FP64 residual operator of a solve: the FP64 data, or for FCM_MIXED the
-// df32 outer operator when the finest level has one (FP64-accurate, products
-// in FP32 arithmetic).
-void apply_outer(Handle* h, Level& L, const double* x, double* y, int mode, const double* b,
-                 int prec) {
-  if (prec != FCM_MIXED || !L.has_outer) {
-    apply_A64(h, L, x, y, mode, b);
-    return;
-  }
-  h->launches += 2;
-  launch_cell_op<double>(L.g, L.A64df, x, L.Y, h->s, &h->side);
-  launch_gather<double>(L.g, mode, L.Y, b, y, 1.0, h->s);
-  CKL();
-}
-
 void apply_M64(Handle* h, Level& L, const double* r, double* y) {
   launch_cell_op<double>(L.g, L.M64, r, L.Y, h->s, &h->side);
   launch_gather<double>(L.g, GATHER_SET, L.Y, nullptr, y, 1.0, h->s);
@@ -281,8 +280,12 @@ struct VC<float> {
   static const OpData<float>& M(Level& L) { return L.M32; }
 };
 
+// Levels l >= top64 are recorded in FP64 and the levels below in FP32: at
+// the boundary the FP64 residual is restricted in FP64 and rounded to FP32
+// on the coarser level, whose FP32 correction is widened before the FP64
+// prolongation.
 template <typename TV>
-void record_vcycle(Handle* h, int l) {
+void record_vcycle(Handle* h, int l, int top64) {
   using V = VC<TV>;
   Level& L = h->levels[l];
   cudaStream_t s = h->s;
@@ -290,6 +293,7 @@ void record_vcycle(Handle* h, int l) {
     launch_coarse_solve<TV>((int)L.g.N, L.Linv, V::b(L), V::x(L), s);
     return;
   }
+  const bool to32 = std::is_same<TV, double>::value && l - 1 < top64;
   Level& Lc = h->levels[l - 1];
   const double w = L.omega;
   TV *x = V::x(L), *b = V::b(L), *r = V::r(L), *Y = V::Y(L);
@@ -315,7 +319,13 @@ void record_vcycle(Handle* h, int l) {
     launch_h_restrict<TV>(Lc.g, L.g, rr, V::b(Lc), s);
   else
     launch_p_restrict<TV>(Lc.g, L.g, rr, V::b(Lc), s);
-  record_vcycle<TV>(h, l - 1);
+  if (to32) {
+    launch_copy_d2f(Lc.b, Lc.b32, Lc.g.N, s);
+    record_vcycle<float>(h, l - 1, top64);
+    launch_copy_f2d(Lc.x32, Lc.x, Lc.g.N, s);
+  } else {
+    record_vcycle<TV>(h, l - 1, top64);
+  }
   if (Lc.is_h)
     launch_h_prolong_add<TV>(Lc.g, L.g, V::x(Lc), x, s);
   else
@@ -330,11 +340,15 @@ void record_vcycle(Handle* h, int l) {
 }
 
 template <typename TV>
-cudaGraphExec_t capture_vcycle(Handle* h, long long* nodes) {
+cudaGraphExec_t capture_vcycle(Handle* h, long long* nodes, int top64) {
   cudaGraph_t g;
+  const int top = (int)h->levels.size() - 1;
   CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
   try {
-    record_vcycle<TV>(h, (int)h->levels.size() - 1);
+    if (top >= top64)
+      record_vcycle<double>(h, top, top64);
+    else
+      record_vcycle<TV>(h, top, top64);
   } catch (...) {
     cudaStreamEndCapture(h->s, &g);
     throw;
@@ -402,11 +416,17 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
       throw Error(FCM_E_UNSUPPORTED, "problem too large: DOFs and cells x local DOFs must be < 2^31");
   }
   P.geom_kind = geom->kind;
-  if (geom->kind < FCM_GEOM_NONE || geom->kind > FCM_GEOM_ELLIPSOID)
+  if (geom->kind < FCM_GEOM_NONE || geom->kind > FCM_GEOM_POPCORN)
     throw Error(FCM_E_INVALID, "unknown geometry kind");
   int need = geom->kind == FCM_GEOM_BALL ? P.dim + 1
              : geom->kind == FCM_GEOM_ELLIPSOID ? 15
+             : geom->kind == FCM_GEOM_POPCORN ? 3
              : geom->kind == FCM_GEOM_VOIDS ? 4 : 0;
+  if (geom->kind == FCM_GEOM_POPCORN && (P.dim != 3 || (geom->n_params - 3) % 3))
+    throw Error(FCM_E_INVALID, "popcorn needs 3D and r0, A, sigma plus 3 values per centre");
+  if (geom->kind == FCM_GEOM_POPCORN && geom->n_params >= 3 && geom->params &&
+      !(geom->params[2] > 0.0))
+    throw Error(FCM_E_INVALID, "popcorn sigma must be > 0");
   if (geom->kind == FCM_GEOM_VOIDS && (geom->n_params < 4 || geom->n_params % 4 || P.dim != 3))
     throw Error(FCM_E_INVALID, "voids need 3D and 4 parameters per ball");
   if (geom->kind == FCM_GEOM_ELLIPSOID && P.dim != 3)
@@ -520,6 +540,7 @@ void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, doub
     L.A32.sh.scale = sc32.empty() ? nullptr : h->upload(sc32);
     L.A32.sh.mats = K32;
     L.A32.sh.nmats = L.A64.sh.nmats;
+    prepare_mma(h, L.A32.sh, n);
   }
 }
 
@@ -530,6 +551,14 @@ void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, doub
 // linear dependence that cut cells create).  Calibrated on p = 2..4 cut
 // grids: FP32 blocks up to 1e6 kept the iteration count; 1e5 leaves margin.
 constexpr double kDfCond = 1e5;
+// Finest-level blocks at least this ill-conditioned make the mixed V-cycle
+// keep that level in FP64.  Calibrated by emulating the FP32 roundings of the
+// mixed V-cycle on the oracle's hierarchy: on 3D spheres with alpha = 1e-8 the
+// FP32 input residual and iterate of the finest level cost 2-5 CG iterations
+// at p = 4 (largest kappa_inf 1.5e12 and 4.9e12) and none at p = 3 (3.7e10,
+// 4.3e10); every other rounding (coarser levels, smoother outputs, restricted
+// residuals) costs none.
+constexpr double kFineFp64Cond = 1e12;
 
 void build_smoother(Handle* h, Level& L) {
   const LevelGeom& g = L.g;
@@ -600,6 +629,7 @@ void build_smoother(Handle* h, Level& L) {
     piv.resize(2 * (size_t)nown);
     CK(cudaMemcpyAsync(piv.data(), d_piv, piv.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
+    for (int i = 0; i < nown; ++i) L.max_cond = std::max(L.max_cond, piv[2 * i + 1]);
     L.M64.own.n = nown;
     L.M64.own.cells = d_cells;
     double* m = h->alloc<double>((size_t)nown * n * padded_ld(n));
@@ -675,6 +705,7 @@ void build_smoother(Handle* h, Level& L) {
     L.M32.sh.scale = sc32.empty() ? nullptr : h->upload(sc32);
     L.M32.sh.mats = sinv ? to_f32(h, sinv, sigs.size() * (size_t)n * n) : nullptr;
     L.M32.sh.nmats = (int)sigs.size();
+    prepare_mma(h, L.M32.sh, n);
   }
 }
 
@@ -859,34 +890,26 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   }
   CK(cudaStreamSynchronize(h->s));
   check_timeout(h);
-  // outer operator of the mixed solve on the finest level: df32 copies of the
-  // shared matrices; the df32 cut-cell matrices of the mixed operator
-  {
-    Level& T = h->levels.back();
-    const int n = T.g.nloc;
-    if (h->mixed && n > 16 && T.A32.own.n == 0) {
-      T.A64df.ld = T.A64.ld;
-      T.A64df.own_x = T.A32.own_x;
-      T.A64df.sh = T.A64.sh;
-      if (T.A64.sh.nmats && T.A64.sh.mats) {
-        float2* m = h->alloc<float2>((size_t)T.A64.sh.nmats * n * n);
-        launch_repack(T.A64.sh.nmats, n, n, T.A64.sh.mats, nullptr, 2, m, h->s);
-        CKL();
-        T.A64df.sh_df = m;
-      }
-      T.has_outer = true;
-    }
-  }
   g_stage = "graph capture";
-  h->g_vc64 = capture_vcycle<double>(h, &h->vc_nodes64);
-  if (h->mixed) h->g_vc32 = capture_vcycle<float>(h, &h->vc_nodes32);
+  h->g_vc64 = capture_vcycle<double>(h, &h->vc_nodes64, 0);
+  if (h->mixed) {
+    // The mixed V-cycle runs the finest level in FP64 when FP32 vectors
+    // there would cost CG iterations: a single-level hierarchy (the V-cycle
+    // is the FP64 coarse solve alone), or stored AS blocks of the finest
+    // level with scaled kappa_inf >= kFineFp64Cond, for which rounding the
+    // V-cycle's input residual and its iterate to FP32 (relative 2^-24)
+    // perturbs the block solutions along their near-null directions.
+    const int top = (int)h->levels.size() - 1;
+    if (top == 0 || h->levels[top].max_cond >= kFineFp64Cond) h->top64 = top;
+    h->g_vc32 = capture_vcycle<float>(h, &h->vc_nodes32, h->top64);
+  }
   CK(cudaStreamSynchronize(h->s));
 }
 
 // z = V(r) on the finest level in the requested precision (r, z FP64).
 void run_vcycle(Handle* h, const double* r, double* z, int prec) {
   Level& T = h->levels.back();
-  if (prec == FCM_MIXED) {
+  if (prec == FCM_MIXED && h->top64 > (int)h->levels.size() - 1) {
     if (!h->mixed) throw Error(FCM_E_INVALID, "mixed precision data not built (build_mixed = 0)");
     launch_copy_d2f(r, T.b32, T.g.N, h->s);
     CKL();
@@ -894,6 +917,12 @@ void run_vcycle(Handle* h, const double* r, double* z, int prec) {
     launch_copy_f2d(T.x32, z, T.g.N, h->s);
     CKL();
     h->launches += 2 + h->vc_nodes32;
+  } else if (prec == FCM_MIXED) {  // finest level in FP64
+    if (!h->mixed) throw Error(FCM_E_INVALID, "mixed precision data not built (build_mixed = 0)");
+    if (r != T.b) CK(cudaMemcpyAsync(T.b, r, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaGraphLaunch(h->g_vc32, h->s));
+    h->launches += h->vc_nodes32;
+    if (z != T.x) CK(cudaMemcpyAsync(z, T.x, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   } else {
     if (r != T.b) CK(cudaMemcpyAsync(T.b, r, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     CK(cudaGraphLaunch(h->g_vc64, h->s));
@@ -942,7 +971,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   fcm_status st = FCM_E_NOT_CONVERGED;
   while (k < maxit) {
     ++k;
-    apply_outer(h, T, p, q, GATHER_SET, nullptr, prec);
+    apply_A64(h, T, p, q, GATHER_SET, nullptr);
     launch_dot_partials(p, q, N, h->part, h->s);
     launch_cg_update_xr(x, r, p, q, N, h->part, h->sc, h->part + kDotBlocks, h->s);
     launch_reduce(h->part + kDotBlocks, kDotBlocks, h->d_scalar, h->s);
@@ -958,7 +987,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
     rel = std::sqrt(rr) / nb;
     if (rel <= rtol) {
       // confirm with the true residual b - A x
-      apply_outer(h, T, x, h->cz_old, GATHER_RESID, b, prec);
+      apply_A64(h, T, x, h->cz_old, GATHER_RESID, b);
       double rt = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / nb;
       if (rt <= rtol) {
         st = FCM_OK;
@@ -984,7 +1013,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   check_timeout(h);
   if (sc.flag && st != FCM_OK) st = FCM_E_BREAKDOWN;
   if (st != FCM_OK) {
-    apply_outer(h, T, x, h->cz_old, GATHER_RESID, b, prec);
+    apply_A64(h, T, x, h->cz_old, GATHER_RESID, b);
     inf.relres_true = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / nb;
   }
   inf.iters = k;
@@ -1033,6 +1062,7 @@ fcm_status fcm_setup(const fcm_grid* grid, const fcm_geometry* geom, const fcm_p
   return guarded([&]() {
     double t0 = now_ms();
     std::unique_ptr<fcm_handle> h(new fcm_handle());
+    CK(prepare_kernels());
     h->user = static_cast<cudaStream_t>(stream);
     CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
@@ -1125,7 +1155,7 @@ fcm_status fcm_rhs(const fcm_handle* hc, double* b_dev) {
 }
 
 fcm_status fcm_apply(fcm_handle* h, const double* x, double* y, int prec) {
-  if (!h || !x || !y || (prec != FCM_FP64 && prec != FCM_MIXED && prec != FCM_MIXED_OUTER)) {
+  if (!h || !x || !y || (prec != FCM_FP64 && prec != FCM_MIXED)) {
     g_last_error = "invalid argument";
     return FCM_E_INVALID;
   }
@@ -1134,9 +1164,6 @@ fcm_status fcm_apply(fcm_handle* h, const double* x, double* y, int prec) {
     Level& T = h->levels.back();
     if (prec == FCM_FP64) {
       apply_A64(h, T, x, y, GATHER_SET, nullptr);
-    } else if (prec == FCM_MIXED_OUTER) {
-      if (!h->mixed) throw Error(FCM_E_INVALID, "mixed precision data not built");
-      apply_outer(h, T, x, y, GATHER_SET, nullptr, FCM_MIXED);
     } else {
       if (!h->mixed) throw Error(FCM_E_INVALID, "mixed precision data not built");
       launch_copy_d2f(x, T.x32, T.g.N, h->s);
@@ -1189,6 +1216,8 @@ fcm_status fcm_level_info_get(const fcm_handle* h, int level, fcm_level_info* in
   info->n_own_cells = L.n_own_cells;
   info->n_own_blocks = L.n_own_blocks;
   info->n_fp64_blocks = L.n_fp64_blocks;
+  info->max_block_cond = L.max_cond;
+  info->fp64_in_mixed = h->mixed && level >= h->top64 ? 1 : 0;
   info->omega = L.omega;
   info->lambda_est = L.lambda;
   return FCM_OK;
@@ -1280,7 +1309,7 @@ fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_hos
 
 fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int reps,
                           double* avg_ms) {
-  if (!h || !avg_ms || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 4 ||
+  if (!h || !avg_ms || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 6 ||
       reps < 1 || (prec != FCM_FP64 && prec != FCM_MIXED) || (prec == FCM_MIXED && !h->mixed)) {
     g_last_error = "invalid argument";
     return FCM_E_INVALID;
@@ -1291,9 +1320,16 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    // which 3, 4: the stored-matrix kernel alone (shared tiles dropped)
+    // which 3, 4: the stored-matrix kernel alone (shared tiles dropped);
+    // which 5, 6: the shared-matrix tiles alone (stored sets dropped)
     auto stored = [](auto op) {
       op.sh.tl.ntiles = 0;
+      op.sh.tl.ntiles_mma = 0;
+      return op;
+    };
+    auto tiles = [](auto op) {
+      op.own.n = 0;
+      op.own_x.n = 0;
       return op;
     };
     auto once = [&]() {
@@ -1302,13 +1338,17 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
         else if (which == 1) launch_cell_op<double>(L.g, L.M64, L.r, L.Y, h->s);
         else if (which == 2) launch_gather<double>(L.g, GATHER_RESID, L.Y, L.b, L.r, 1.0, h->s);
         else if (which == 3) launch_cell_op<double>(L.g, stored(L.A64), L.x, L.Y, h->s);
-        else launch_cell_op<double>(L.g, stored(L.M64), L.r, L.Y, h->s);
+        else if (which == 4) launch_cell_op<double>(L.g, stored(L.M64), L.r, L.Y, h->s);
+        else if (which == 5) launch_cell_op<double>(L.g, tiles(L.A64), L.x, L.Y, h->s);
+        else launch_cell_op<double>(L.g, tiles(L.M64), L.r, L.Y, h->s);
       } else {
         if (which == 0) launch_cell_op<float>(L.g, L.A32, L.x32, L.Y32, h->s);
         else if (which == 1) launch_cell_op<float>(L.g, L.M32, L.r32, L.Y32, h->s);
         else if (which == 2) launch_gather<float>(L.g, GATHER_RESID, L.Y32, L.b32, L.r32, 1.0, h->s);
         else if (which == 3) launch_cell_op<float>(L.g, stored(L.A32), L.x32, L.Y32, h->s);
-        else launch_cell_op<float>(L.g, stored(L.M32), L.r32, L.Y32, h->s);
+        else if (which == 4) launch_cell_op<float>(L.g, stored(L.M32), L.r32, L.Y32, h->s);
+        else if (which == 5) launch_cell_op<float>(L.g, tiles(L.A32), L.x32, L.Y32, h->s);
+        else launch_cell_op<float>(L.g, tiles(L.M32), L.r32, L.Y32, h->s);
       }
     };
     once();
@@ -1328,7 +1368,7 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
 }
 
 fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, long long* bytes) {
-  if (!h || !bytes || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 4 ||
+  if (!h || !bytes || level < 1 || level >= (int)h->levels.size() || which < 0 || which > 6 ||
       (prec != FCM_FP64 && prec != FCM_MIXED)) {
     g_last_error = "invalid argument";
     return FCM_E_INVALID;
@@ -1339,6 +1379,10 @@ fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, lon
   long long b = 0;
   if (which == 2) {
     b = nc * n * sv + 2 * L.g.N * sv + L.g.N * sv;  // Y, b, r(out)
+  } else if (which >= 5) {
+    // shared tiles: the matrices once, every tile cell's coefficients and results
+    const SharedSet<double>& s64 = which == 5 ? L.A64.sh : L.M64.sh;
+    b = (long long)s64.nmats * n * n * sv + 2 * (long long)s64.tl.ncells * n * sv;
   } else if (which >= 3) {
     const OpData<double>& d64 = which == 3 ? L.A64 : L.M64;
     const OpData<float>& d32 = which == 3 ? L.A32 : L.M32;

@@ -121,9 +121,11 @@ struct CellSet {
 
 struct TileList {
   int ntiles = 0;
-  int4* tiles = nullptr;     // {matrix id, start, count, 0} (device)
+  int4* tiles = nullptr;     // {matrix id, start, count, 0} (device), <= 64 cells each
   int* cells = nullptr;      // cells grouped by matrix (device)
   int ncells = 0;
+  int ntiles_mma = 0;        // the same cells in tiles of <= 128 (tensor-core kernel)
+  int4* tiles_mma = nullptr;
 };
 
 template <typename T>
@@ -132,16 +134,27 @@ struct SharedSet {
   T* scale = nullptr;        // per entry of tl.cells
   T* mats = nullptr;         // [nmats][nloc][nloc] (canonical, unpadded)
   int nmats = 0;
+  // FP32 only: the matrices as tensor-core operands, [nmats][hi, lo][NP x KD]
+  // in the K-major core-matrix layout (see launch_mma_operands)
+  float* mma_b = nullptr;
 };
+
+// Tensor-core operand sizes of an n x n shared matrix: reduction length KD
+// (n rounded up to a multiple of 8) and N extent NP (n rounded up to a
+// multiple of 16, at least 16).
+inline int mma_kd(int n) { return (n + 7) & ~7; }
+inline int mma_np(int n) { return n <= 16 ? 16 : (n + 15) & ~15; }
+// Split nmats FP32 n x n matrices into TF32 parts (hi = tf32(v), lo = v - hi)
+// in the operand layout of the tensor-core kernel: out holds nmats x 2 x
+// mma_np(n) x mma_kd(n) floats, zero-padded.
+void launch_mma_operands(int n, int nmats, const float* mats, float* out, cudaStream_t s);
 
 template <typename TV>
 struct OpData {
   int ld = 0;                // padded row length of stored matrices
   CellSet own;               // stored matrices in precision TV
-  CellSet own_x;             // df32 matrices (FP32 vectors: islands of the mixed V-cycle;
-                             // FP64 vectors: the mixed solve's outer operator)
+  CellSet own_x;             // FP32 vectors only: df32 matrices (islands of the mixed V-cycle)
   SharedSet<TV> sh;
-  const float2* sh_df = nullptr;  // FP64 vectors only: df32 copy of sh.mats (outer operator)
 };
 
 // Padded row length of stored cell matrices.
@@ -257,6 +270,10 @@ void launch_chol_inverse(int nblk, int n, double* A, double* pivots, int* info,
 void launch_chol_factor(int n, double* A, int* info, cudaStream_t s);
 void launch_dense_assemble(const LevelGeom& g, const double* own_mats, double* A,
                            cudaStream_t s);
+
+// Kernel attributes (shared-memory limits) that must not be set while a
+// stream is being captured; call before the first launch on a device.
+cudaError_t prepare_kernels();
 
 std::string cuda_msg(cudaError_t e);
 

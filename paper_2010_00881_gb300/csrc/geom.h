@@ -44,6 +44,20 @@ FCM_HD inline double levelset(const Geo& G, const double* x) {
     }
     return out;
   }
+  if (G.kind == FCM_GEOM_POPCORN) {
+    // r0 A sigma, then the bump centres
+    const double r0 = G.prm[0], amp = G.prm[1], sig2 = G.prm[2] * G.prm[2];
+    double s = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    double out = sqrt(s) - r0;
+    const int nc = (G.n - 3) / 3;
+    for (int k = 0; k < nc; ++k) {
+      const double* c = G.prm + 3 + 3 * k;
+      double d2 = (x[0] - c[0]) * (x[0] - c[0]) + (x[1] - c[1]) * (x[1] - c[1]) +
+                  (x[2] - c[2]) * (x[2] - c[2]);
+      out = out - amp * exp(-d2 / sig2);
+    }
+    return out;
+  }
   // ellipsoid: c(3) a(3) R(3x3 row-major)
   const double* c = G.prm;
   const double* ax = G.prm + 3;

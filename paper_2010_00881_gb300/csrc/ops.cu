@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "fcm_internal.h"
+#include "tc.cuh"
 
 namespace fcm {
 
@@ -161,28 +162,6 @@ __device__ __forceinline__ void fma_row(Acc<float2>& a, int slot, const float2* 
   float4 v = *reinterpret_cast<const float4*>(row);  // (hi0, lo0, hi1, lo1)
   df_term(a.s[slot * 2 + 0], a.c[slot * 2 + 0], v.x, v.y, xs);
   df_term(a.s[slot * 2 + 1], a.c[slot * 2 + 1], v.z, v.w, xs);
-}
-// df32 entry times an FP64 coefficient given as its own (hi, lo) float split:
-// TwoProduct of the high parts, TwoSum into s, the cross terms
-// hi_K lo_x + lo_K hi_x and every rounding error into c (lo_K lo_x, below
-// 2^-48 of the product, is dropped).
-__device__ __forceinline__ void df_mac(float& s, float& c, float2 k, float2 x) {
-  const float p = k.x * x.x;
-  const float e = fmaf(k.x, x.x, -p);
-  const float t = s + p;
-  const float bb = t - s;
-  const float err = (s - (t - bb)) + (p - bb);
-  s = t;
-  c += err + e + fmaf(k.x, x.y, k.y * x.x);
-}
-__device__ __forceinline__ float2 split_df(double v) {
-  const float h = (float)v;
-  return make_float2(h, (float)(v - (double)h));
-}
-__device__ __forceinline__ void fma_row(Acc<float2>& a, int slot, const float2* row, float2 xs) {
-  float4 v = *reinterpret_cast<const float4*>(row);  // (hi0, lo0, hi1, lo1)
-  df_mac(a.s[slot * 2 + 0], a.c[slot * 2 + 0], make_float2(v.x, v.y), xs);
-  df_mac(a.s[slot * 2 + 1], a.c[slot * 2 + 1], make_float2(v.z, v.w), xs);
 }
 __device__ __forceinline__ double acc_value(const Acc<float>& a, int k) { return a.v[k]; }
 __device__ __forceinline__ double acc_value(const Acc<double>& a, int k) { return a.v[k]; }
@@ -396,6 +375,8 @@ struct CellOpArgs {
   const TV* sh_scale;
   const TV* sh_mats;
   int nb_own, nb_own_x;
+  int ntiles_mma;            // tiles of <= 128 cells (tensor-core kernel, FP32)
+  const int4* tiles_mma;
 };
 
 // ---------------------------------------------------------------------------
@@ -641,18 +622,7 @@ __device__ bool consume_item(const LevelGeom& g, int ld, const StreamSet<TM>& S,
   const uint32_t arrivals = 2 / S.G;
   const int c0 = iu * S.k;
   const int cnt = min(S.k, S.n - c0);
-  // df32 matrices against FP64 coefficients: split each gathered value once
-  // into (hi, lo) floats, in place
-  constexpr bool kSplit = std::is_same<TV, double>::value && std::is_same<TM, float2>::value;
-  using XV = typename std::conditional<kSplit, float2, TV>::type;
-  if constexpr (kSplit) {
-    double* xd = const_cast<double*>(reinterpret_cast<const double*>(xs));
-    for (int e = lane; e < cnt * n; e += 32) {
-      const float2 v = split_df(xd[e]);
-      reinterpret_cast<float2*>(xd)[e] = v;
-    }
-    __syncwarp();
-  }
+  using XV = TV;
   const XV* xv = reinterpret_cast<const XV*>(xs);
   Acc<TM> acc;
   if (S.cpc == 1) {
@@ -1129,117 +1099,223 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
   }
 }
 
-// Shared matrices for the FP64 residuals of the mixed solve: K as df32
-// pairs in shared memory, the gathered FP64 coefficients split once into
-// (hi, lo) floats in place, products and sums by df_mac (value s + c, about
-// n 2^-48 of sum |K||x|).  Tile layout and thread mapping as tile_kernel.
-template <int RB>
-__global__ void __launch_bounds__(kOpThreads) tile_df_kernel(CellOpArgs<double> A,
-                                                             const float2* __restrict__ sh_df) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// Shared matrices on the tensor cores (FP32 vectors).  For a tile of up to
+// 128 cells that share one matrix K (n x n, symmetric), the products are
+// D = X K with X the tile's gathered coefficients, one row per cell: one
+// M = 128, N = NP (n padded to a multiple of 16) GEMM with reduction length
+// KD (n padded to a multiple of 8).  Both operands are split into TF32
+// parts, v = hi + lo with hi = tf32(v) and lo = v - hi (exact in FP32), and
+// D = Xh Kh + Xh Kl + Xl Kh accumulates in FP32 in tensor memory (3xTF32,
+// about FP32 accuracy; the dropped Xl Kl term is below 2^-22 |X||K|).  K's
+// parts, split once at setup into the operand layout, arrive by one bulk
+// copy and stay in shared memory while consecutive tiles use the same
+// matrix; X is gathered through the per-cell DOF table in chunks of KC
+// values of K (KC < KD when the block must fit beside a stored-matrix
+// streaming block on the SM).  Thread 0 issues the MMAs and commits them to
+// an mbarrier; every wait is bounded (on expiry the timeout flag is set and
+// the block stops after a second bounded wait for what is in flight).
+// Epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (one cell
+// per lane) and writes s_c D[c][j] to Y[j][cell], consecutive cells to
+// consecutive addresses.
+constexpr int kMmaCells = 128;
+constexpr int kMmaRegVals = 64;  // gathered values per thread (128 cells x KD <= 128)
+constexpr uint32_t kMmaWaitLimit = 1u << 24;
+
+__global__ void __maxnreg__(112) tc_tile_kernel(CellOpArgs<float> A,
+                                                             const float* __restrict__ mma_b,
+                                                             int KD, int NP, int KC,
+                                                             uint32_t ncols) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ int tab[128];
-  __shared__ int ccell[2][kTileCells];  // cell (-1: empty slot), cell_base
-  __shared__ double cscale[kTileCells];
-  constexpr int npad = 16 * RB;
+  __shared__ int ccell[kMmaCells];
+  __shared__ int cbase[kMmaCells];
+  __shared__ float cscale[kMmaCells];
+  __shared__ __align__(8) uint64_t mbar;   // MMA completion
+  __shared__ __align__(8) uint64_t bbar;   // B operand arrival
+  __shared__ uint32_t tslot;
   const LevelGeom& g = A.g;
   const int n = g.nloc;
-  float2* Ks = reinterpret_cast<float2*>(smem_raw);        // [n][npad]
-  double* Xd = reinterpret_cast<double*>(Ks + n * npad);    // [n][64], then split in place
-  float2* Xf = reinterpret_cast<float2*>(Xd);
+  const uint32_t bbytes = (uint32_t)NP * KD * 4;
+  char* Bh = reinterpret_cast<char*>(smem_raw);
+  char* Bl = Bh + bbytes;
+  char* Ah = Bl + bbytes;
+  char* Al = Ah + (size_t)kMmaCells * KC * 4;
   build_local_table(g, tab);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&bbar, 1);
+  }
+  if (threadIdx.x < 32) tc::tmem_alloc(&tslot, ncols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const uint32_t idesc = tc::make_idesc_tf32(kMmaCells, NP);
+  const uint32_t sboA = (uint32_t)(KC / 4) * 128u, sboB = (uint32_t)(KD / 4) * 128u;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ncells = g.ncells;
-  const int cg = threadIdx.x & 15, rg = threadIdx.x >> 4, i0 = rg * RB;
   int cur_mat = -1;
-  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
-    const int4 tile = A.tiles[t];
-    __syncthreads();  // the previous tile's stores are done with Xd and ccell
-    if (threadIdx.x < kTileCells) {
-      const int c = threadIdx.x;
-      const int cell = c < tile.z ? A.sh_cells[tile.y + c] : 0;
-      ccell[0][c] = c < tile.z ? cell : -1;
-      ccell[1][c] = cell_base_of(g, cell);
-      cscale[c] = c < tile.z ? A.sh_scale[tile.y + c] : 0.0;
-    }
+  uint32_t phase = 0, bphase = 0;
+  bool b_pending = false, failed = false;
+  for (int t = blockIdx.x; t < A.ntiles_mma && !failed; t += gridDim.x) {
+    const int4 tile = A.tiles_mma[t];
     if (tile.x != cur_mat) {
-      const float2* K = sh_df + (size_t)tile.x * n * n;
-      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int k = e / n, j = e - k * n;
-        cp_async_8(Ks + k * npad + j, K + e, 8);
+      // the MMAs of the previous tile have completed (waited below)
+      if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                         tc::smem_u32(&bbar)),
+                     "r"(2u * bbytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(tc::smem_u32(Bh)),
+            "l"(mma_b + (size_t)tile.x * 2 * NP * KD), "r"(2u * bbytes),
+            "r"(tc::smem_u32(&bbar))
+            : "memory");
       }
+      b_pending = true;
       cur_mat = tile.x;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
-      const int k = e >> 6, c = e & (kTileCells - 1);
-      const bool live = ccell[0][c] >= 0;
-      const double* src = live ? A.x + (ccell[1][c] + tab[k]) : A.x;
-      cp_async_8(Xd + e, src, live ? 8 : 0);
+    if (threadIdx.x < kMmaCells) {
+      const int c = threadIdx.x;
+      const bool live = c < tile.z;
+      const int cell = live ? A.sh_cells[tile.y + c] : 0;
+      int cx, cy, cz;
+      cell_coords(g, cell, cx, cy, cz);
+      ccell[c] = live ? cell : -1;
+      cbase[c] = cell_base(g, cx, cy, cz);
+      cscale[c] = live ? A.sh_scale[tile.y + c] : 0.f;
     }
-    cp_async_commit();
-    cp_async_wait<0>();
     __syncthreads();
-    for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) Xf[e] = split_df(Xd[e]);
-    __syncthreads();
-    float sa[RB][4], ca[RB][4];
+    // thread (c, half) gathers cell c's k groups half, half + 2, ..., all of
+    // the tile's values at once (at most 64 per thread for KD <= 128), so the
+    // whole tile costs one round of global loads; the chunks are then split
+    // and stored from registers
+    const int c_me = threadIdx.x & (kMmaCells - 1);
+    const int half = threadIdx.x >> 7;
+    float v[kMmaRegVals];
+    {
+      const bool live = ccell[c_me] >= 0;
+      const float* xb = A.x + cbase[c_me];
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
+      for (int i = 0; i < kMmaRegVals / 4; ++i) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) sa[r][c] = ca[r][c] = 0.f;
-    if (i0 < n) {
-#pragma unroll 2
-      for (int k = 0; k < n; ++k) {
-        const float4* xr = reinterpret_cast<const float4*>(Xf + k * kTileCells + 4 * cg);
-        const float4 x01 = xr[0], x23 = xr[1];
-        const float2 xv[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w),
-                              make_float2(x23.x, x23.y), make_float2(x23.z, x23.w)};
-        const float2* kr = Ks + k * npad + i0;
-#pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          const float2 kv = kr[r];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) df_mac(sa[r][c], ca[r][c], kv, xv[c]);
+        for (int q = 0; q < 4; ++q) {
+          const int k = 4 * (half + 2 * i) + q;
+          v[4 * i + q] = (live && k < n) ? __ldg(xb + tab[k]) : 0.f;
         }
       }
     }
-    __syncthreads();  // every thread is done reading Xf
+    for (int k0 = 0; k0 < KD; k0 += KC) {
+      const int kc = KD - k0 < KC ? KD - k0 : KC;
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      const int i = i0 + r;
-      if (i < n) {
+      for (int i = 0; i < kMmaRegVals / 4; ++i) {
+        const int kg = half + 2 * i;   // k group within the tile
+        if (4 * kg >= k0 && 4 * kg < k0 + kc) {
+          float4 hv, lv;
+          hv.x = tc::to_tf32(v[4 * i + 0]); lv.x = v[4 * i + 0] - hv.x;
+          hv.y = tc::to_tf32(v[4 * i + 1]); lv.y = v[4 * i + 1] - hv.y;
+          hv.z = tc::to_tf32(v[4 * i + 2]); lv.z = v[4 * i + 2] - hv.z;
+          hv.w = tc::to_tf32(v[4 * i + 3]); lv.w = v[4 * i + 3] - hv.w;
+          const uint32_t off = tc::kmajor_offset(c_me, 4 * kg - k0, KC);
+          *reinterpret_cast<float4*>(Ah + off) = hv;
+          *reinterpret_cast<float4*>(Al + off) = lv;
+        }
+      }
+      tc::fence_proxy_async();
+      __syncthreads();
+      bool ok = true;
+      if (threadIdx.x == 0) {
+        if (b_pending) {
+          ok = tc::mbar_wait(&bbar, bphase, kMmaWaitLimit);
+          if (ok) {
+            bphase ^= 1u;
+            b_pending = false;
+          }
+        }
+        if (ok) {
+          tc::fence_after_sync();
+          const uint32_t ah0 = tc::smem_u32(Ah), al0 = tc::smem_u32(Al);
+          const uint32_t bh0 = tc::smem_u32(Bh) + (uint32_t)(k0 / 8) * 256u;
+          const uint32_t bl0 = tc::smem_u32(Bl) + (uint32_t)(k0 / 8) * 256u;
+          for (int s = 0; s < kc / 8; ++s) {
+            const uint64_t ah = tc::make_sdesc(ah0 + 256u * s, 128u, sboA);
+            const uint64_t al = tc::make_sdesc(al0 + 256u * s, 128u, sboA);
+            const uint64_t bh = tc::make_sdesc(bh0 + 256u * s, 128u, sboB);
+            const uint64_t bl = tc::make_sdesc(bl0 + 256u * s, 128u, sboB);
+            tc::mma_tf32(tmem, ah, bh, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
+            tc::mma_tf32(tmem, ah, bl, idesc, 1u);
+            tc::mma_tf32(tmem, al, bh, idesc, 1u);
+          }
+          tc::commit(&mbar);
+        }
+      }
+      // the chunk's MMAs must finish before its operands are overwritten
+      if (__syncthreads_or(!ok)) {
+        // B never arrived: no MMA was issued; let the copy land (bounded)
+        if (threadIdx.x == 0) {
+          atomicExch(&g_stream_timeout, 1);
+          tc::mbar_wait(&bbar, bphase, kMmaWaitLimit);
+        }
+        failed = true;
+        break;
+      }
+      ok = tc::mbar_wait(&mbar, phase, kMmaWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicExch(&g_stream_timeout, 1);
+        tc::mbar_wait(&mbar, phase, kMmaWaitLimit);
+        failed = true;
+        break;
+      }
+      phase ^= 1u;
+    }
+    if (failed) break;
+    tc::fence_after_sync();
+    {
+      const int lg = warp & 3;
+      const int c = 32 * lg + lane;
+      const int cell = ccell[c];
+      const float sc = cscale[c];
+      for (int ch = warp >> 2; 16 * ch < n; ch += kOpThreads / 128) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 16u * ch, v);
+        if (cell >= 0) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          Xd[i * kTileCells + 4 * cg + c] = (double)sa[r][c] + (double)ca[r][c];
+          for (int i = 0; i < 16; ++i) {
+            const int j = 16 * ch + i;
+            if (j < n) A.Y[(size_t)j * ncells + cell] = sc * v[i];
+          }
+        }
       }
     }
+    tc::fence_before_sync();
     __syncthreads();
-    for (int e = threadIdx.x; e < n * kTileCells; e += blockDim.x) {
-      const int i = e >> 6, c = e & (kTileCells - 1);
-      const int cell = ccell[0][c];
-      if (cell >= 0) A.Y[(size_t)i * ncells + cell] = cscale[c] * Xd[e];
-    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_free(tmem, ncols);
+}
+
+// Operand layout of launch_mma_operands: thread e of matrix m handles one
+// (j, k) entry, reading K[k][j] (K symmetric; rows contiguous across threads).
+__global__ void mma_operands_kernel(int n, int KD, int NP, int nmats, const float* mats,
+                                    float* out) {
+  const long long per = (long long)NP * KD;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < per * nmats;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(e / per);
+    const int r = (int)(e - (long long)m * per);
+    const int k = r / NP, j = r - k * NP;
+    const float v = (j < n && k < n) ? mats[(size_t)m * n * n + (size_t)k * n + j] : 0.f;
+    const float hi = tc::to_tf32(v);
+    const uint32_t off = tc::kmajor_offset(j, k, KD) / 4;
+    out[(size_t)m * 2 * per + off] = hi;
+    out[(size_t)m * 2 * per + per + off] = v - hi;
   }
 }
 
-template <int RB>
-void launch_tile_df(const CellOpArgs<double>& A, const float2* sh_df, cudaStream_t s,
-                    bool one_per_sm) {
-  const int n = A.g.nloc;
-  constexpr int npad = 16 * RB;
-  const size_t smem = ((size_t)n * npad + (size_t)n * kTileCells) * 8;
-  static const bool attr = [] {
-    const size_t mx = ((size_t)npad * npad + (size_t)npad * kTileCells) * 8;
-    cudaFuncSetAttribute(tile_df_kernel<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-    cudaFuncSetAttribute(tile_df_kernel<RB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    return true;
-  }();
-  (void)attr;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int grid = one_per_sm ? sms : A.ntiles;
-  if (grid > A.ntiles) grid = A.ntiles;
-  tile_df_kernel<RB><<<grid, kOpThreads, smem, s>>>(A, sh_df);
-}
+
 
 // ---------------------------------------------------------------------------
 // DOF-centric gather of per-cell contributions (Y local-index-major).
@@ -1753,6 +1829,64 @@ void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t
   tile_kernel<TV, RB, NB><<<grid, kOpThreads, smem, s>>>(A);
 }
 
+// Tensor-core tiles (FP32 vectors, n <= 128): K padded to KD (multiple of
+// 8) and N to NP (multiple of 16); the gathered coefficients come in chunks
+// of KC values, as many as `budget` bytes of shared memory hold beside K's
+// two parts (KC = 0: they do not fit).
+int mma_chunk(int n, size_t budget) {
+  const size_t bsz = (size_t)2 * mma_np(n) * mma_kd(n) * 4;
+  if (bsz >= budget) return 0;
+  int KC = (int)((budget - bsz) / (2 * kMmaCells * 4)) & ~7;
+  return KC > mma_kd(n) ? mma_kd(n) : KC;
+}
+
+// Persistent blocks walk the 128-cell tile list; as many per SM as shared
+// memory admits (one when they run beside stored-matrix streaming blocks),
+// at most four (registers), and never more than the SM's 512 tensor-memory
+// columns hold (ncols each).  The kernel's attributes are set by
+// prepare_kernels(), outside any stream capture.
+void launch_tc_tile(const CellOpArgs<float>& A, const float* mma_b, int KC, bool one_per_sm,
+                    cudaStream_t s) {
+  const int n = A.g.nloc;
+  const int KD = mma_kd(n), NP = mma_np(n);
+  uint32_t ncols = 32;
+  while ((int)ncols < NP) ncols <<= 1;
+  const size_t smem = (size_t)2 * NP * KD * 4 + (size_t)2 * kMmaCells * KC * 4;
+  int dev = 0, sms = 148, smem_sm = 228 * 1024;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int per_sm = (int)((size_t)smem_sm / (smem + 3 * 1024));
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm > (int)(512 / ncols)) per_sm = (int)(512 / ncols);
+  if (per_sm < 1 || one_per_sm) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > A.ntiles_mma) grid = A.ntiles_mma;
+  tc_tile_kernel<<<grid, kOpThreads, smem, s>>>(A, mma_b, KD, NP, KC, ncols);
+}
+
+void launch_mma_operands(int n, int nmats, const float* mats, float* out, cudaStream_t s) {
+  if (nmats == 0) return;
+  const long long tot = (long long)nmats * mma_np(n) * mma_kd(n);
+  mma_operands_kernel<<<grid_for(tot), 256, 0, s>>>(n, mma_kd(n), mma_np(n), nmats, mats, out);
+}
+
+cudaError_t prepare_kernels() {
+  // dynamic shared memory up to the opt-in limit minus the static part
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tc_tile_kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_tile_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
 // Items of a stored-matrix set: k whole cells per ring chunk when a cell
 // fits (at most kItemVals coefficients per item), else one cell in cpc
 // chunks of rc rows (as many rows as fit; the last chunk holds the rest).
@@ -1839,6 +1973,8 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   A.sh_cells = op.sh.tl.cells;
   A.sh_scale = op.sh.scale;
   A.sh_mats = op.sh.mats;
+  A.ntiles_mma = op.sh.tl.ntiles_mma;
+  A.tiles_mma = op.sh.tl.tiles_mma;
   auto nb = [](int n) {
     int b = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
     return b > kOwnBlocksCap ? kOwnBlocksCap : b;
@@ -1857,19 +1993,33 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   const bool al = (ld & 3) == 0 && al16(op.own.mats) && al16(op.own_x.mats);
   const bool small = (n == 4 || n == 8 || n == 9 || n == 16) && ld == padded_ld(n) && al;
-  bool fork = side && side->s2 && A.ntiles && (A.nb_own || A.nb_own_x);
+  // FP32 vectors: the shared-matrix products run on the tensor cores
+  // (tc_tile_kernel), with the operand chunk KC sized so that one block fits
+  // beside a streaming block when they run side by side.
+  const bool mma = std::is_same<TV, float>::value && A.ntiles_mma > 0 && n <= 128 &&
+                   op.sh.mma_b != nullptr;
+  int KC = mma ? mma_chunk(n, 200 * 1024) : 0;
+  bool fork = side && side->s2 && (mma ? A.ntiles_mma : A.ntiles) && (A.nb_own || A.nb_own_x);
   if (fork && !small) {
     const size_t stream_smem =
         (size_t)Ring<TV>::stages * kRingChunk +
         (size_t)kConsumers * (2 * kItemVals * sizeof(TV) + 128 * sizeof(double));
-    const int npad = tile_npad(n);
-    const size_t tile_smem =
-        ((size_t)n * npad + (sizeof(TV) == 4 ? 2 : 1) * (size_t)n * kTileCells) * sizeof(TV);
     int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    // + static shared memory of both kernels and the per-block reservation
-    fork = stream_smem + tile_smem + 12 * 1024 <= (size_t)per_sm;
+    // 12 KB: static shared memory of both kernels and the per-block reservation
+    const size_t left = (size_t)per_sm > stream_smem + 12 * 1024
+                            ? (size_t)per_sm - stream_smem - 12 * 1024 : 0;
+    if (mma) {
+      const int kc = mma_chunk(n, left);
+      fork = kc >= 8;
+      if (fork) KC = kc;
+    } else {
+      const int npad = tile_npad(n);
+      const size_t tile_smem =
+          ((size_t)n * npad + (sizeof(TV) == 4 ? 2 : 1) * (size_t)n * kTileCells) * sizeof(TV);
+      fork = tile_smem <= left;
+    }
   }
   if (fork) cudaEventRecord(side->fork, s);
   if (A.nb_own || A.nb_own_x) {
@@ -1884,11 +2034,6 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
       if constexpr (std::is_same<TV, float>::value) {
         StreamArgs<float, float, float2> S{
             g, ld, make_stream_set<float>(op.own.n, op.own.cells, op.own.mats, n, ld),
-            make_stream_set<float2>(op.own_x.n, op.own_x.cells, op.own_x.mats, n, ld), x, Y};
-        launch_stream(S, s);
-      } else if (op.own_x.n) {  // df32 matrices against FP64 vectors (outer operator)
-        StreamArgs<double, double, float2> S{
-            g, ld, make_stream_set<double>(op.own.n, op.own.cells, op.own.mats, n, ld),
             make_stream_set<float2>(op.own_x.n, op.own_x.cells, op.own_x.mats, n, ld), x, Y};
         launch_stream(S, s);
       } else {
@@ -1907,7 +2052,19 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
       }
     }
   }
-  if (A.ntiles) {
+  if (mma) {
+    cudaStream_t st = s;
+    if (fork) {
+      cudaStreamWaitEvent(side->s2, side->fork, 0);
+      st = side->s2;
+    }
+    if constexpr (std::is_same<TV, float>::value)
+      launch_tc_tile(A, op.sh.mma_b, KC, fork && !small, st);
+    if (fork) {
+      cudaEventRecord(side->join, side->s2);
+      cudaStreamWaitEvent(s, side->join, 0);
+    }
+  } else if (A.ntiles) {
     cudaStream_t st = s;
     if (fork) {
       cudaStreamWaitEvent(side->s2, side->fork, 0);
@@ -1918,25 +2075,11 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
     // one block per SM only beside stream blocks; the small-cell kernels
     // leave the SMs' shared memory free
     const bool one = fork && !small;
-    bool done = false;
-    if constexpr (std::is_same<TV, double>::value) {
-      if (op.sh_df) {  // outer operator: df32 shared matrices
-        switch (npad / 16) {
-          case 1: launch_tile_df<1>(A, op.sh_df, st, one); break;
-          case 2: launch_tile_df<2>(A, op.sh_df, st, one); break;
-          case 4: launch_tile_df<4>(A, op.sh_df, st, one); break;
-          default: launch_tile_df<8>(A, op.sh_df, st, one); break;
-        }
-        done = true;
-      }
-    }
-    if (!done) {
-      switch (npad / 16) {
-        case 1: launch_tile<TV, 1>(A, sm_tile, st, one); break;
-        case 2: launch_tile<TV, 2>(A, sm_tile, st, one); break;
-        case 4: launch_tile<TV, 4>(A, sm_tile, st, one); break;
-        default: launch_tile<TV, 8>(A, sm_tile, st, one); break;
-      }
+    switch (npad / 16) {
+      case 1: launch_tile<TV, 1>(A, sm_tile, st, one); break;
+      case 2: launch_tile<TV, 2>(A, sm_tile, st, one); break;
+      case 4: launch_tile<TV, 4>(A, sm_tile, st, one); break;
+      default: launch_tile<TV, 8>(A, sm_tile, st, one); break;
     }
     if (fork) {
       cudaEventRecord(side->join, side->s2);

@@ -122,6 +122,13 @@ __device__ double source_f(const Problem& P, const double* x) {
     for (int a = 0; a < P.dim; ++a) u = u * sin(M_PI * x[a]);
     return P.kappa * P.dim * (M_PI * M_PI) * u;
   }
+  if (P.source == FCM_SRC_POPCORN) {
+    // -kappa Lap u, u = x^3 + x y^2 + y^3 + z^4 + sin(3 (x^2 + y^2))
+    const double r2 = x[0] * x[0] + x[1] * x[1];
+    const double lap = 8.0 * x[0] + 6.0 * x[1] + 12.0 * x[2] * x[2] + 12.0 * cos(3.0 * r2) -
+                       36.0 * r2 * sin(3.0 * r2);
+    return -P.kappa * lap;
+  }
   double a = P.src_a;
   return cos(a * (x[0] - 0.5)) * sin(a * (x[1] - 0.5));
 }
@@ -132,6 +139,10 @@ __device__ double dirichlet_g(const Problem& P, const double* x) {
     double u = 1.0;
     for (int a = 0; a < P.dim; ++a) u = u * sin(M_PI * x[a]);
     return u;
+  }
+  if (P.g == FCM_G_POPCORN) {
+    const double X = x[0], Y = x[1], Z = x[2];
+    return X * X * X + X * Y * Y + Y * Y * Y + Z * Z * Z * Z + sin(3.0 * (X * X + Y * Y));
   }
   double a = P.src_a;
   return cos(a * (x[0] - 0.5)) * sin(a * (x[1] - 0.5)) / (2.0 * P.kappa * a * a);

@@ -17,12 +17,12 @@ LIB_PATH = os.path.join(_HERE, "libfcm.so")
 
 FCM_OK, FCM_E_INVALID, FCM_E_OOM, FCM_E_CUDA, FCM_E_UNSUPPORTED = 0, 1, 2, 3, 4
 FCM_E_NOT_CONVERGED, FCM_E_BREAKDOWN, FCM_E_TIMEOUT = 5, 6, 7
-FCM_FP64, FCM_MIXED, FCM_MIXED_OUTER = 0, 1, 2
-GEOM = {"none": 0, "ball": 1, "voids": 2, "ellipsoid": 3}
+FCM_FP64, FCM_MIXED = 0, 1
+GEOM = {"none": 0, "ball": 1, "voids": 2, "ellipsoid": 3, "popcorn": 4}
 PDE = {"poisson": 0, "elasticity": 1}
-SRC = {"const": 0, "sin3": 1, "square_mms": 2}
+SRC = {"const": 0, "sin3": 1, "square_mms": 2, "popcorn": 3}
 DIR = {"none": 0, "levelset": 1, "faces": 2}
-GVAL = {"zero": 0, "sin3": 1, "square_mms": 2}
+GVAL = {"zero": 0, "sin3": 1, "square_mms": 2, "popcorn": 3}
 OP_APPLY, OP_SMOOTHER, OP_RESTRICT, OP_PROLONG, OP_COARSE = 0, 1, 2, 3, 4
 
 EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_num_levels",
@@ -32,7 +32,8 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
            "fcm_batch_destroy", "fcm_destroy", "fcm_last_error", "fcm_dof_layout",
            "fcm_cell_dofs", "fcm_mlhp_create", "fcm_mlhp_destroy", "fcm_mlhp_sizes",
            "fcm_mlhp_functions", "fcm_mlhp_leaves", "fcm_mlhp_patches",
-           "fcm_mlhp_leaf_classes", "fcm_mlhp_levels", "fcm_mlhp_restriction_1d"]
+           "fcm_mlhp_leaf_classes", "fcm_mlhp_levels", "fcm_mlhp_restriction_1d",
+           "fcm_measure_fma_peak"]
 
 
 class fcm_grid(C.Structure):
@@ -72,7 +73,8 @@ class fcm_level_info(C.Structure):
     _fields_ = [("cells", C.c_int * 3), ("p", C.c_int), ("is_h_level", C.c_int),
                 ("ndofs", C.c_longlong), ("nloc", C.c_int), ("n_own_cells", C.c_int),
                 ("n_own_blocks", C.c_int), ("n_fp64_blocks", C.c_int), ("omega", C.c_double),
-                ("lambda_est", C.c_double)]
+                ("lambda_est", C.c_double), ("max_block_cond", C.c_double),
+                ("fp64_in_mixed", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,6 +109,7 @@ def load():
     lib.fcm_profile_op.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
     lib.fcm_op_bytes.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
     lib.fcm_cell_apply_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int, P, P, P, P]
+    lib.fcm_measure_fma_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
     lib.fcm_setup_batch.argtypes = [C.c_int, C.POINTER(fcm_grid), C.POINTER(fcm_geometry),
                                     C.POINTER(fcm_physics), C.POINTER(fcm_solver_opts), C.c_int, P,
                                     C.POINTER(P)]
@@ -216,6 +219,13 @@ class Overlay:
         self.n_leaves = L
 
 
+def measure_fma_peak(prec: int) -> float:
+    """FMA throughput of the current GPU in TFLOP/s (FCM_FP64 or FCM_MIXED = FP32)."""
+    t = C.c_double()
+    _check(load().fcm_measure_fma_peak(prec, C.byref(t)))
+    return t.value
+
+
 def restriction_1d(p: int, dk: int, pos: int) -> np.ndarray:
     """S[i, j]: coefficient of sub-interval mode i in ancestor mode j, for
     sub-interval pos of 2^dk (fcm_mlhp_restriction_1d)."""
@@ -252,6 +262,8 @@ def descriptors(prob: dict, build_mixed: bool = True):
         params = [v for ball in geo["balls"] for v in ball]
     elif kind == "ellipsoid":
         params = list(geo["center"]) + list(geo["axes"]) + [v for row in geo["rot"] for v in row]
+    elif kind == "popcorn":
+        params = [geo["r0"], geo["A"], geo["sigma"]] + [v for c in geo["centers"] for v in c]
     else:
         params = []
     arr = (C.c_double * max(1, len(params)))(*params)

@@ -7,13 +7,12 @@ Sec. 2; space-tree quadrature of cut cells, Sec. 2.2).  Samples cover
 interior bubble DOFs (one cell) of cut, inside and outside cells, and
 vertex DOFs of cut cells (up to 2^d cells, stored and shared matrices
 mixed).  Bars, per sampled row, relative to s_I = sum_c |K_c[l, :]| |x|:
-FP64 1e-11 (two quadrature summation orders), mixed 1e-5 (FP32 shared
-matrices), the mixed solve's outer operator 1e-11 (df32 matrices, n 2^-48).
+FP64 1e-11 (two quadrature summation orders), mixed 1e-5 (FP32 data, shared
+matrices on the tensor cores in 3xTF32).
 
 The solves are checked by properties that hold at any size: the true
 relative residual (FP64 operator, itself checked above) below the
-tolerance, and the mixed V-cycle costing at most a few iterations more
-than the FP64 one.
+tolerance, and the mixed solve taking the FP64 solve's iteration count +-1.
 """
 import numpy as np
 import pytest
@@ -29,7 +28,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 from oracle.assembly import element_system, nfields  # noqa: E402
 from oracle.geometry import CUT, INSIDE, OUTSIDE  # noqa: E402
 from oracle.grid import cell_dofs  # noqa: E402
-from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, FCM_MIXED_OUTER, Solver  # noqa: E402
+from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED, Solver  # noqa: E402
 
 WORKLOADS = {
     # the throughput workload: 32^3 cells, p = 3, sphere, 912,673 DOFs
@@ -97,7 +96,6 @@ def test_sampled_operator_rows(big):
     xt = torch.from_numpy(x).cuda()
     y64 = s.apply(xt).cpu().numpy()
     y32 = s.apply(xt, prec=FCM_MIXED).cpu().numpy()
-    yo = s.apply(xt, prec=FCM_MIXED_OUTER).cpu().numpy()
     cache = {}
     for I, holders in _samples(prob, cls, rng):
         ref = 0.0
@@ -111,7 +109,6 @@ def test_sampled_operator_rows(big):
             scale += np.abs(K[l]) @ np.abs(xd)
         assert abs(y64[I] - ref) <= 1e-11 * scale, (name, I, y64[I], ref, scale)
         assert abs(y32[I] - ref) <= 1e-5 * scale, (name, I, y32[I], ref, scale)
-        assert abs(yo[I] - ref) <= 1e-11 * scale, (name, I, yo[I], ref, scale)
 
 
 def test_solves(big):
@@ -119,4 +116,4 @@ def test_solves(big):
     _, i64 = s.pcg(rtol=1e-8, prec=FCM_FP64)
     _, i32 = s.pcg(rtol=1e-8, prec=FCM_MIXED)
     assert i64["relres_true"] <= 1e-8 and i32["relres_true"] <= 1e-8
-    assert i32["iters"] <= i64["iters"] + 5, (i32["iters"], i64["iters"])
+    assert abs(i32["iters"] - i64["iters"]) <= 1, (i32["iters"], i64["iters"])
