@@ -313,12 +313,14 @@ def main():
     ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sphere",
-                    choices=["sphere", "batch256", "elasticity64", "circle16"],
+                    choices=["sphere", "batch256", "elasticity64", "circle16", "popcorn"],
                     help="sphere: 32^3 p=3 sphere (default); batch256: independent instances; "
                          "elasticity64: 64^3 block with 64 voids, p = 2; circle16: 2D circle, "
                          "16^2 cells, p = 2")
     ap.add_argument("--batch-n", type=int, default=256,
                     help="instances of the batch workload (the first n of the seeded 256)")
+    ap.add_argument("--cells", type=int, default=0,
+                    help="cells per axis of the popcorn workload (default 96)")
     ap.add_argument("--profile-run", action="store_true",
                     help="setup, W warm-up and K timed mixed solves only (for profilers)")
     args = ap.parse_args()
@@ -349,6 +351,9 @@ def main():
         prob, wl_name = workload(), WORKLOAD
     elif args.workload == "circle16":
         prob, wl_name = fi.poisson2d_circle(), "poisson2d_circle_16^2_p2"
+    elif args.workload == "popcorn":
+        prob = fi.popcorn(cells=args.cells or 96, p=3, space="tensor", drop_outside=False)
+        wl_name = f"popcorn_{args.cells or 96}^3_p3_tensor"
     else:
         prob, wl_name = fi.elasticity3d_voids(cells=64, p=2), "elasticity3d_voids_64^3_p2"
     s = Solver(prob, build_mixed=True)

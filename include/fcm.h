@@ -64,7 +64,7 @@ enum { FCM_PDE_POISSON = 0, FCM_PDE_ELASTICITY = 1 };
 enum { FCM_SRC_CONST = 0, FCM_SRC_SIN3 = 1, FCM_SRC_SQUARE_MMS = 2, FCM_SRC_POPCORN = 3 };
 enum { FCM_DIR_NONE = 0, FCM_DIR_LEVELSET = 1, FCM_DIR_FACES = 2 };
 enum { FCM_G_ZERO = 0, FCM_G_SIN3 = 1, FCM_G_SQUARE_MMS = 2, FCM_G_POPCORN = 3 };
-enum { FCM_SMOOTHER_ELEMENTWISE = 0, FCM_SMOOTHER_PATCHWISE = 1 };
+enum { FCM_SMOOTHER_ELEMENTWISE = 0, FCM_SMOOTHER_PATCHWISE = 1, FCM_SMOOTHER_JACOBI = 2 };
 
 /* Grid: dim in {2,3}; cells per axis (>= 1); box [lo, hi]; degree p in
  * [1, 8].  overlay_levels > 0 (multi-level hp) is FCM_E_UNSUPPORTED in
@@ -119,7 +119,10 @@ typedef struct {
   int quad_depth;
 } fcm_physics;
 
-/* Solver options.  omega <= 0 selects the paper's values (Sec. 3.3.2),
+/* Solver options.  smoother: ELEMENTWISE additive Schwarz (Sec. 3.3.1), or
+ * JACOBI, the pointwise comparison smoother of Sec. 4.1 (x += omega D^{-1} r,
+ * D = diag(A_l); omega <= 0 selects 2/3); PATCHWISE is FCM_E_UNSUPPORTED.
+ * For ELEMENTWISE omega <= 0 selects the paper's values (Sec. 3.3.2),
  * clamped per level to 1.75 / lambda_max(M^{-1} A) where that value would
  * break the stability condition rho(I - omega M^{-1} A) < 1.  n_pre, n_post:
  * smoothing steps (paper: 5, 5).  coarse_cells: h-coarsening stops once
@@ -294,6 +297,20 @@ fcm_status fcm_cell_classes(const fcm_handle* h, signed char* cls_host);
  * iterate), FCM_E_BREAKDOWN on p^T A p <= 0 or a non-finite scalar. */
 fcm_status fcm_pcg_solve(fcm_handle* h, const double* b_dev, double* x_dev, double rtol,
                          int maxit, int prec, fcm_info* info);
+
+/* The paper's solvers (Sec. 4): method FCM_METHOD_CG_MG is fcm_pcg_solve;
+ * FCM_METHOD_MG is multigrid as a stand-alone solver, x_{k+1} = x_k +
+ * V(b - A x_k) from x_0 = 0 until ||b - A x|| / ||b|| <= rtol, with the
+ * contraction numbers rho_k = ||r_k|| / ||r_{k-1}|| (Eq. contraction) written
+ * to rho_host[k - 1] when rho_host (host, maxit doubles) is not NULL;
+ * FCM_E_NOT_CONVERGED after maxit iterations or once the residual exceeds
+ * 1e20 ||b|| (diverged); FCM_METHOD_CG_AS is CG preconditioned by the
+ * finest level's smoother alone, M^{-1} (the one-level additive Schwarz
+ * CG the paper compares with; FP64 only, needs at least two levels).
+ * Other arguments as in fcm_pcg_solve. */
+enum { FCM_METHOD_CG_MG = 0, FCM_METHOD_MG = 1, FCM_METHOD_CG_AS = 2 };
+fcm_status fcm_solve(fcm_handle* h, int method, const double* b_dev, double* x_dev, double rtol,
+                     int maxit, int prec, fcm_info* info, double* rho_host);
 
 /* Same solve through host buffers: b_host (NULL: assembled load) is copied
  * to the device and x is copied back into x_host (ndofs doubles each). */

@@ -66,6 +66,9 @@ struct Level {
   double omega = 0.0, lambda = 0.0;
   int n_own_cells = 0, n_own_blocks = 0, n_fp64_blocks = 0;
   double max_cond = 0.0;  // largest scaled kappa_inf of the stored AS blocks
+  // Jacobi smoother (comparison smoother of Sec. 4.1): inverse diagonal
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
   // cell sources for Galerkin / block assembly
   int* d_own_index = nullptr;       // per cell: own matrix index or -1
   double* d_scale_cell = nullptr;   // per cell: scale of K_ref for shared cells
@@ -99,6 +102,7 @@ struct fcm_handle {
   std::vector<void*> allocs;
   std::vector<fcm::Level> levels;  // 0 = coarsest
   int n_pre = 5, n_post = 5;
+  int smoother = FCM_SMOOTHER_ELEMENTWISE;
   bool mixed = false;
   double setup_ms = 0.0;
   std::vector<signed char> cls;
@@ -252,6 +256,11 @@ void apply_A64(Handle* h, Level& L, const double* x, double* y, int mode, const 
 }
 
 void apply_M64(Handle* h, Level& L, const double* r, double* y) {
+  if (h->smoother == FCM_SMOOTHER_JACOBI) {
+    launch_jacobi<double>(L.g.N, L.dinv64, r, y, 1.0, true, h->s);
+    CKL();
+    return;
+  }
   launch_cell_op<double>(L.g, L.M64, r, L.Y, h->s, &h->side);
   launch_gather<double>(L.g, GATHER_SET, L.Y, nullptr, y, 1.0, h->s);
   CKL();
@@ -269,6 +278,7 @@ struct VC<double> {
   static double* Y(Level& L) { return L.Y; }
   static const OpData<double>& A(Level& L) { return L.A64; }
   static const OpData<double>& M(Level& L) { return L.M64; }
+  static const double* dinv(Level& L) { return L.dinv64; }
 };
 template <>
 struct VC<float> {
@@ -278,6 +288,7 @@ struct VC<float> {
   static float* Y(Level& L) { return L.Y32; }
   static const OpData<float>& A(Level& L) { return L.A32; }
   static const OpData<float>& M(Level& L) { return L.M32; }
+  static const float* dinv(Level& L) { return L.dinv32; }
 };
 
 // Levels l >= top64 are recorded in FP64 and the levels below in FP32: at
@@ -297,16 +308,26 @@ void record_vcycle(Handle* h, int l, int top64) {
   Level& Lc = h->levels[l - 1];
   const double w = L.omega;
   TV *x = V::x(L), *b = V::b(L), *r = V::r(L), *Y = V::Y(L);
+  const bool jac = h->smoother == FCM_SMOOTHER_JACOBI;
+  const TV* dinv = V::dinv(L);
   if (h->n_pre == 0) CK(cudaMemsetAsync(x, 0, L.g.N * sizeof(TV), s));
   for (int k = 0; k < h->n_pre; ++k) {
     if (k == 0) {
-      launch_cell_op<TV>(L.g, V::M(L), b, Y, s, &h->side);
-      launch_gather<TV>(L.g, GATHER_SCALE, Y, nullptr, x, w, s);
+      if (jac) {
+        launch_jacobi<TV>(L.g.N, dinv, b, x, w, true, s);
+      } else {
+        launch_cell_op<TV>(L.g, V::M(L), b, Y, s, &h->side);
+        launch_gather<TV>(L.g, GATHER_SCALE, Y, nullptr, x, w, s);
+      }
     } else {
       launch_cell_op<TV>(L.g, V::A(L), x, Y, s, &h->side);
       launch_gather<TV>(L.g, GATHER_RESID, Y, b, r, 1.0, s);
-      launch_cell_op<TV>(L.g, V::M(L), r, Y, s, &h->side);
-      launch_gather<TV>(L.g, GATHER_ADD, Y, nullptr, x, w, s);
+      if (jac) {
+        launch_jacobi<TV>(L.g.N, dinv, r, x, w, false, s);
+      } else {
+        launch_cell_op<TV>(L.g, V::M(L), r, Y, s, &h->side);
+        launch_gather<TV>(L.g, GATHER_ADD, Y, nullptr, x, w, s);
+      }
     }
   }
   const TV* rr = b;
@@ -333,8 +354,12 @@ void record_vcycle(Handle* h, int l, int top64) {
   for (int k = 0; k < h->n_post; ++k) {
     launch_cell_op<TV>(L.g, V::A(L), x, Y, s, &h->side);
     launch_gather<TV>(L.g, GATHER_RESID, Y, b, r, 1.0, s);
-    launch_cell_op<TV>(L.g, V::M(L), r, Y, s, &h->side);
-    launch_gather<TV>(L.g, GATHER_ADD, Y, nullptr, x, w, s);
+    if (jac) {
+      launch_jacobi<TV>(L.g.N, dinv, r, x, w, false, s);
+    } else {
+      launch_cell_op<TV>(L.g, V::M(L), r, Y, s, &h->side);
+      launch_gather<TV>(L.g, GATHER_ADD, Y, nullptr, x, w, s);
+    }
   }
   CKL();
 }
@@ -465,8 +490,11 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   if (opts->n_pre < 0 || opts->n_post < 0 || opts->n_pre > 64 || opts->n_post > 64)
     throw Error(FCM_E_INVALID, "smoothing steps must be in [0, 64]");
   if (opts->coarse_cells < 1) throw Error(FCM_E_INVALID, "coarse_cells must be >= 1");
-  if (opts->smoother != FCM_SMOOTHER_ELEMENTWISE)
-    throw Error(FCM_E_UNSUPPORTED, "only elementwise additive Schwarz blocks are implemented");
+  if (opts->smoother == FCM_SMOOTHER_PATCHWISE)
+    throw Error(FCM_E_UNSUPPORTED, "patchwise additive Schwarz blocks are not implemented");
+  if (opts->smoother != FCM_SMOOTHER_ELEMENTWISE && opts->smoother != FCM_SMOOTHER_JACOBI)
+    throw Error(FCM_E_INVALID, "unknown smoother");
+  h->smoother = opts->smoother;
   h->n_pre = opts->n_pre;
   h->n_post = opts->n_post;
   h->mixed = opts->build_mixed != 0;
@@ -709,6 +737,34 @@ void build_smoother(Handle* h, Level& L) {
   }
 }
 
+// Jacobi smoother: dinv = 1 / diag(A_l), the cell matrices' diagonals summed
+// by the DOF gather.  The paper's comparison smoother (Sec. 4.1);
+// its damping is not stated: 2/3 unless opts.omega is given.
+void build_jacobi(Handle* h, Level& L) {
+  const OpData<double>& A = L.A64;
+  int* sh_mat = nullptr;
+  if (A.sh.tl.ncells) {
+    // the operator's shared cells all use the one reference matrix
+    std::vector<int> zeros(A.sh.tl.ncells, 0);
+    sh_mat = h->upload(zeros);
+  }
+  launch_cell_diag(L.g, A, sh_mat, L.Y, h->s);
+  double* diag = h->alloc<double>(L.g.N);
+  launch_gather<double>(L.g, GATHER_SET, L.Y, nullptr, diag, 1.0, h->s);
+  CKL();
+  std::vector<double> d(L.g.N);
+  CK(cudaMemcpyAsync(d.data(), diag, L.g.N * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  std::vector<float> d32(L.g.N);
+  for (size_t i = 0; i < d.size(); ++i) {
+    if (!(d[i] > 0.0)) throw Error(FCM_E_INVALID, "Jacobi smoother: non-positive diagonal");
+    d[i] = 1.0 / d[i];
+    d32[i] = (float)d[i];
+  }
+  L.dinv64 = h->upload(d);
+  if (h->mixed) L.dinv32 = h->upload(d32);
+}
+
 // lambda_max(M^{-1} A) by the power method (A inner product), then omega.
 void estimate_omega(Handle* h, Level& L, double omega_paper) {
   const long long N = L.g.N;
@@ -883,6 +939,12 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     Level& L = h->levels[l];
     finish_level_vectors(h, L);
     if (l == 0) continue;
+    if (h->smoother == FCM_SMOOTHER_JACOBI) {
+      g_stage = "Jacobi diagonal";
+      build_jacobi(h, L);
+      L.omega = opts->omega > 0.0 ? opts->omega : 2.0 / 3.0;
+      continue;
+    }
     g_stage = "smoother blocks";
     build_smoother(h, L);
     g_stage = "omega estimate";
@@ -931,8 +993,19 @@ void run_vcycle(Handle* h, const double* r, double* z, int prec) {
   }
 }
 
+// Preconditioner of the CG: one V-cycle (the paper's CG+MG) or, for
+// FCM_METHOD_CG_AS, the finest level's smoother alone (the one-level
+// additive Schwarz preconditioner the paper compares with, Sec. 4.2-4.3).
+void precondition(Handle* h, const double* r, double* z, int prec, int method) {
+  if (method == FCM_METHOD_CG_AS) {
+    apply_M64(h, h->levels.back(), r, z);
+    return;
+  }
+  run_vcycle(h, r, z, prec);
+}
+
 fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int maxit, int prec,
-                    fcm_info* info) {
+                    fcm_info* info, int method = FCM_METHOD_CG_MG) {
   g_stage = "solve";
   double t0 = now_ms();
   h->launches = 0;
@@ -961,7 +1034,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
     if (info) *info = inf;
     return FCM_OK;
   }
-  run_vcycle(h, r, z, prec);
+  precondition(h, r, z, prec, method);
   launch_dot_partials(r, z, N, h->part, h->s);
   launch_cg_init(r, z, N, h->part, p, h->sc, h->s);
   CKL();
@@ -998,7 +1071,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
     }
     if (flexible)
       CK(cudaMemcpyAsync(h->cz_old, z, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-    run_vcycle(h, r, z, prec);
+    precondition(h, r, z, prec, method);
     if (flexible)
       launch_dot2_partials(r, z, h->cz_old, N, h->part, h->s);
     else
@@ -1023,6 +1096,61 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   if (info) *info = inf;
   if (st == FCM_E_NOT_CONVERGED) g_last_error = "maximum number of iterations reached";
   if (st == FCM_E_BREAKDOWN) g_last_error = "CG breakdown (p^T A p <= 0 or non-finite scalar)";
+  return st;
+}
+
+// Multigrid as a stand-alone solver (Sec. 4, Eq. contraction):
+// x_{k+1} = x_k + V(b - A x_k) from x_0 = 0 until ||b - A x_k|| / ||b|| <=
+// rtol; rho[k - 1] = ||r_k|| / ||r_{k-1}||, the contraction numbers.  A
+// residual grown beyond 1e20 ||b|| stops the iteration (diverged).
+fcm_status mg_impl(Handle* h, const double* b_in, double* x, double rtol, int maxit, int prec,
+                   fcm_info* info, double* rho) {
+  g_stage = "solve";
+  double t0 = now_ms();
+  h->launches = 0;
+  Level& T = h->levels.back();
+  const long long N = T.g.N;
+  const double* b = b_in ? b_in : h->b;
+  if (prec == FCM_MIXED && !h->mixed)
+    throw Error(FCM_E_INVALID, "mixed precision data not built (build_mixed = 0)");
+  if (!(rtol > 0.0) || maxit < 0) throw Error(FCM_E_INVALID, "rtol must be > 0, maxit >= 0");
+  double* r = T.b;
+  double* z = h->ctmp;
+  CK(cudaMemsetAsync(x, 0, N * sizeof(double), h->s));
+  CK(cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  const double nb = std::sqrt(host_dot(h, b, b, N));
+  if (!std::isfinite(nb)) throw Error(FCM_E_INVALID, "right-hand side is not finite");
+  fcm_info inf;
+  std::memset(&inf, 0, sizeof(inf));
+  inf.ndofs = N;
+  inf.setup_ms = h->setup_ms;
+  double nr = nb;
+  int k = 0;
+  fcm_status st = FCM_OK;
+  while (nb > 0.0 && nr / nb > rtol) {
+    if (k >= maxit || !(nr <= 1e20 * nb)) {
+      st = FCM_E_NOT_CONVERGED;
+      break;
+    }
+    ++k;
+    run_vcycle(h, r, z, prec);
+    launch_axpby(1.0, z, 1.0, x, N, h->s);
+    apply_A64(h, T, x, r, GATHER_RESID, b);
+    h->launches += 1;
+    const double nn = std::sqrt(host_dot(h, r, r, N));
+    if (rho) rho[k - 1] = nr > 0.0 ? nn / nr : 0.0;
+    nr = nn;
+  }
+  check_timeout(h);
+  inf.iters = k;
+  inf.relres_recursive = nb > 0.0 ? nr / nb : 0.0;
+  inf.relres_true = inf.relres_recursive;
+  inf.kernel_launches = h->launches;
+  inf.solve_ms = now_ms() - t0;
+  if (info) *info = inf;
+  if (st == FCM_E_NOT_CONVERGED)
+    g_last_error = nr <= 1e20 * nb ? "maximum number of iterations reached"
+                                   : "multigrid iteration diverged";
   return st;
 }
 
@@ -1280,6 +1408,28 @@ fcm_status fcm_pcg_solve(fcm_handle* h, const double* b, double* x, double rtol,
   return guarded([&]() {
     CallScope cs(h);
     fcm_status st = pcg_impl(h, b, x, rtol, maxit, prec, info);
+    cs.finish();
+    return st;
+  });
+}
+
+fcm_status fcm_solve(fcm_handle* h, int method, const double* b, double* x, double rtol,
+                     int maxit, int prec, fcm_info* info, double* rho) {
+  if (!h || !x || (prec != FCM_FP64 && prec != FCM_MIXED) || method < FCM_METHOD_CG_MG ||
+      method > FCM_METHOD_CG_AS) {
+    g_last_error = "invalid argument";
+    return FCM_E_INVALID;
+  }
+  if (method == FCM_METHOD_CG_AS && (prec != FCM_FP64 || h->levels.size() < 2)) {
+    g_last_error = method == FCM_METHOD_CG_AS && prec != FCM_FP64
+                       ? "one-level Schwarz CG is FP64 only"
+                       : "one-level Schwarz CG needs a finest level with a smoother";
+    return prec != FCM_FP64 ? FCM_E_UNSUPPORTED : FCM_E_INVALID;
+  }
+  return guarded([&]() {
+    CallScope cs(h);
+    fcm_status st = method == FCM_METHOD_MG ? mg_impl(h, b, x, rtol, maxit, prec, info, rho)
+                                            : pcg_impl(h, b, x, rtol, maxit, prec, info, method);
     cs.finish();
     return st;
   });

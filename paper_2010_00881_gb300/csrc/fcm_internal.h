@@ -181,6 +181,15 @@ template <typename TV>
 void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y,
                     cudaStream_t s, const SideStream* side = nullptr);
 
+// Y[l][c] = diagonal entry l of cell c's matrix in `op` (FP64 data);
+// sh_mat[j]: matrix id of the j-th shared cell (op.sh.tl.cells order).
+void launch_cell_diag(const LevelGeom& g, const OpData<double>& op, const int* sh_mat,
+                      double* Y, cudaStream_t s);
+// Jacobi step: x = w dinv r (init) or x += w dinv r, N entries.
+template <typename TV>
+void launch_jacobi(long long N, const TV* dinv, const TV* r, TV* x, double w, bool init,
+                   cudaStream_t s);
+
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };
 template <typename TV>

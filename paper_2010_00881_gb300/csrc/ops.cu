@@ -1118,10 +1118,11 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
 // per lane) and writes s_c D[c][j] to Y[j][cell], consecutive cells to
 // consecutive addresses.
 constexpr int kMmaCells = 128;
-constexpr int kMmaRegVals = 64;  // gathered values per thread (128 cells x KD <= 128)
+constexpr int kMmaMinN = 48;  // DOFs per cell from which the tensor-core tiles are used
 constexpr uint32_t kMmaWaitLimit = 1u << 24;
 
-__global__ void __maxnreg__(112) tc_tile_kernel(CellOpArgs<float> A,
+template <int RV>
+__global__ void __launch_bounds__(kMmaCells) tc_tile_kernel(CellOpArgs<float> A,
                                                              const float* __restrict__ mma_b,
                                                              int KD, int NP, int KC,
                                                              uint32_t ncols) {
@@ -1187,37 +1188,34 @@ __global__ void __maxnreg__(112) tc_tile_kernel(CellOpArgs<float> A,
       cscale[c] = live ? A.sh_scale[tile.y + c] : 0.f;
     }
     __syncthreads();
-    // thread (c, half) gathers cell c's k groups half, half + 2, ..., all of
-    // the tile's values at once (at most 64 per thread for KD <= 128), so the
-    // whole tile costs one round of global loads; the chunks are then split
-    // and stored from registers
-    const int c_me = threadIdx.x & (kMmaCells - 1);
-    const int half = threadIdx.x >> 7;
-    float v[kMmaRegVals];
-    {
-      const bool live = ccell[c_me] >= 0;
-      const float* xb = A.x + cbase[c_me];
-#pragma unroll
-      for (int i = 0; i < kMmaRegVals / 4; ++i) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int k = 4 * (half + 2 * i) + q;
-          v[4 * i + q] = (live && k < n) ? __ldg(xb + tab[k]) : 0.f;
-        }
-      }
-    }
+    // thread c gathers cell c's values in passes of RV (all loads of a pass
+    // issued before the first is used: one round of loads per pass), then
+    // feeds the pass's chunks of KC (a divisor of RV) to the tensor cores,
+    // splitting and storing kc / 4 16-byte vectors per chunk
+    const int c_me = threadIdx.x;
+    const bool live = ccell[c_me] >= 0;
+    const float* xb = A.x + cbase[c_me];
+    float v[RV];
     for (int k0 = 0; k0 < KD; k0 += KC) {
       const int kc = KD - k0 < KC ? KD - k0 : KC;
+      const int p0 = k0 - k0 % RV;  // first k of this pass
+      if (k0 == p0) {
 #pragma unroll
-      for (int i = 0; i < kMmaRegVals / 4; ++i) {
-        const int kg = half + 2 * i;   // k group within the tile
-        if (4 * kg >= k0 && 4 * kg < k0 + kc) {
+        for (int i = 0; i < RV; ++i) {
+          const int k = p0 + i;
+          v[i] = (live && k < n) ? __ldg(xb + tab[k]) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RV / 4; ++i) {
+        const int kk = 4 * i - (k0 - p0);  // position within the chunk
+        if (kk >= 0 && kk < kc) {
           float4 hv, lv;
           hv.x = tc::to_tf32(v[4 * i + 0]); lv.x = v[4 * i + 0] - hv.x;
           hv.y = tc::to_tf32(v[4 * i + 1]); lv.y = v[4 * i + 1] - hv.y;
           hv.z = tc::to_tf32(v[4 * i + 2]); lv.z = v[4 * i + 2] - hv.z;
           hv.w = tc::to_tf32(v[4 * i + 3]); lv.w = v[4 * i + 3] - hv.w;
-          const uint32_t off = tc::kmajor_offset(c_me, 4 * kg - k0, KC);
+          const uint32_t off = tc::kmajor_offset(c_me, kk, KC);
           *reinterpret_cast<float4*>(Ah + off) = hv;
           *reinterpret_cast<float4*>(Al + off) = lv;
         }
@@ -1276,7 +1274,7 @@ __global__ void __maxnreg__(112) tc_tile_kernel(CellOpArgs<float> A,
       const int c = 32 * lg + lane;
       const int cell = ccell[c];
       const float sc = cscale[c];
-      for (int ch = warp >> 2; 16 * ch < n; ch += kOpThreads / 128) {
+      for (int ch = 0; 16 * ch < n; ++ch) {
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + 16u * ch, v);
         if (cell >= 0) {
@@ -1833,17 +1831,28 @@ void launch_tile(const CellOpArgs<TV>& A, size_t /*sm_one_buffer*/, cudaStream_t
 // 8) and N to NP (multiple of 16); the gathered coefficients come in chunks
 // of KC values, as many as `budget` bytes of shared memory hold beside K's
 // two parts (KC = 0: they do not fit).
+int mma_rv(int n) {  // values per thread and gather pass: KD up to a power of two, <= 64
+  int rv = 8;
+  while (rv < mma_kd(n) && rv < 64) rv <<= 1;
+  return rv;
+}
 int mma_chunk(int n, size_t budget) {
   const size_t bsz = (size_t)2 * mma_np(n) * mma_kd(n) * 4;
   if (bsz >= budget) return 0;
-  int KC = (int)((budget - bsz) / (2 * kMmaCells * 4)) & ~7;
-  return KC > mma_kd(n) ? mma_kd(n) : KC;
+  const int fit = (int)((budget - bsz) / (2 * kMmaCells * 4));
+  // a power of two (a divisor of the pass length), at most one pass
+  int KC = 8;
+  if (fit < 8) return 0;
+  while (2 * KC <= fit && 2 * KC <= mma_rv(n)) KC <<= 1;
+  return KC;
 }
 
-// Persistent blocks walk the 128-cell tile list; as many per SM as shared
+// Persistent blocks of 128 threads (one warp per SM sub-partition, so that a
+// block fits beside a streaming block's nine warps in every sub-partition's
+// register file) walk the 128-cell tile list; as many per SM as shared
 // memory admits (one when they run beside stored-matrix streaming blocks),
-// at most four (registers), and never more than the SM's 512 tensor-memory
-// columns hold (ncols each).  The kernel's attributes are set by
+// at most eight, and never more than the SM's 512 tensor-memory columns hold
+// (ncols each).  The kernel's attributes are set by
 // prepare_kernels(), outside any stream capture.
 void launch_tc_tile(const CellOpArgs<float>& A, const float* mma_b, int KC, bool one_per_sm,
                     cudaStream_t s) {
@@ -1857,12 +1866,17 @@ void launch_tc_tile(const CellOpArgs<float>& A, const float* mma_b, int KC, bool
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   int per_sm = (int)((size_t)smem_sm / (smem + 3 * 1024));
-  if (per_sm > 4) per_sm = 4;
+  if (per_sm > 8) per_sm = 8;
   if (per_sm > (int)(512 / ncols)) per_sm = (int)(512 / ncols);
   if (per_sm < 1 || one_per_sm) per_sm = 1;
   int grid = sms * per_sm;
   if (grid > A.ntiles_mma) grid = A.ntiles_mma;
-  tc_tile_kernel<<<grid, kOpThreads, smem, s>>>(A, mma_b, KD, NP, KC, ncols);
+  switch (mma_rv(n)) {
+    case 8: tc_tile_kernel<8><<<grid, kMmaCells, smem, s>>>(A, mma_b, KD, NP, KC, ncols); break;
+    case 16: tc_tile_kernel<16><<<grid, kMmaCells, smem, s>>>(A, mma_b, KD, NP, KC, ncols); break;
+    case 32: tc_tile_kernel<32><<<grid, kMmaCells, smem, s>>>(A, mma_b, KD, NP, KC, ncols); break;
+    default: tc_tile_kernel<64><<<grid, kMmaCells, smem, s>>>(A, mma_b, KD, NP, KC, ncols); break;
+  }
 }
 
 void launch_mma_operands(int n, int nmats, const float* mats, float* out, cudaStream_t s) {
@@ -1871,19 +1885,28 @@ void launch_mma_operands(int n, int nmats, const float* mats, float* out, cudaSt
   mma_operands_kernel<<<grid_for(tot), 256, 0, s>>>(n, mma_kd(n), mma_np(n), nmats, mats, out);
 }
 
+template <typename K>
+cudaError_t prepare_one(K kernel, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+
 cudaError_t prepare_kernels() {
   // dynamic shared memory up to the opt-in limit minus the static part
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaFuncAttributes fa;
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tc_tile_kernel);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc_tile_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) e = prepare_one(tc_tile_kernel<8>, optin);
+  if (e == cudaSuccess) e = prepare_one(tc_tile_kernel<16>, optin);
+  if (e == cudaSuccess) e = prepare_one(tc_tile_kernel<32>, optin);
+  if (e == cudaSuccess) e = prepare_one(tc_tile_kernel<64>, optin);
   return e;
 }
 
@@ -1994,10 +2017,13 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   const bool al = (ld & 3) == 0 && al16(op.own.mats) && al16(op.own_x.mats);
   const bool small = (n == 4 || n == 8 || n == 9 || n == 16) && ld == padded_ld(n) && al;
   // FP32 vectors: the shared-matrix products run on the tensor cores
-  // (tc_tile_kernel), with the operand chunk KC sized so that one block fits
-  // beside a streaming block when they run side by side.
-  const bool mma = std::is_same<TV, float>::value && A.ntiles_mma > 0 && n <= 128 &&
-                   op.sh.mma_b != nullptr;
+  // (tc_tile_kernel) from kMmaMinN DOFs per cell up, with the operand chunk
+  // KC sized so that one block fits beside a streaming block when they run
+  // side by side.  Below that the product is a few hundred FMAs per cell and
+  // the CUDA-core tiles finish sooner than the tensor-core kernel's fixed
+  // latency (tensor-memory allocation, MMA commit and wait: about 5 us).
+  const bool mma = std::is_same<TV, float>::value && A.ntiles_mma > 0 && n >= kMmaMinN &&
+                   n <= 128 && op.sh.mma_b != nullptr;
   int KC = mma ? mma_chunk(n, 200 * 1024) : 0;
   bool fork = side && side->s2 && (mma ? A.ntiles_mma : A.ntiles) && (A.nb_own || A.nb_own_x);
   if (fork && !small) {
@@ -2087,6 +2113,59 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
     }
   }
 }
+
+// Diagonal of a level operator, cell by cell: Y[l][c] = (K_c)_{ll}, the
+// stored matrix's entry for stored cells and s_c (K_ref)_{ll} for cells that
+// share a matrix; the DOF gather then sums the diagonals of the cells at a
+// DOF (Jacobi smoother, Sec. 4.1).
+__global__ void cell_diag_kernel(LevelGeom g, int ld, int n_own, const int* own_cells,
+                                 const double* own_mats, int n_sh, const int* sh_cells,
+                                 const int* sh_mat, const double* sh_scale,
+                                 const double* sh_mats, double* Y) {
+  const int n = g.nloc;
+  const long long ncells = g.ncells;
+  const long long tot = (long long)(n_own + n_sh) * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), l = (int)(e - (long long)i * n);
+    if (i < n_own) {
+      Y[(size_t)l * ncells + own_cells[i]] = own_mats[((size_t)i * n + l) * ld + l];
+    } else {
+      const int j = i - n_own;
+      Y[(size_t)l * ncells + sh_cells[j]] =
+          sh_scale[j] * sh_mats[((size_t)sh_mat[j] * n + l) * n + l];
+    }
+  }
+}
+
+// x = w dinv r (init) or x += w dinv r.
+template <typename TV>
+__global__ void jacobi_kernel(long long N, const TV* dinv, const TV* r, TV* x, TV w, int init) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const TV z = w * (dinv[i] * r[i]);
+    x[i] = init ? z : x[i] + z;
+  }
+}
+
+void launch_cell_diag(const LevelGeom& g, const OpData<double>& op, const int* sh_mat,
+                      double* Y, cudaStream_t s) {
+  const long long tot = (long long)(op.own.n + op.sh.tl.ncells) * g.nloc;
+  if (tot == 0) return;
+  cell_diag_kernel<<<grid_for(tot), 256, 0, s>>>(
+      g, op.ld, op.own.n, op.own.cells, static_cast<const double*>(op.own.mats),
+      op.sh.tl.ncells, op.sh.tl.cells, sh_mat, op.sh.scale, op.sh.mats, Y);
+}
+
+template <typename TV>
+void launch_jacobi(long long N, const TV* dinv, const TV* r, TV* x, double w, bool init,
+                   cudaStream_t s) {
+  jacobi_kernel<TV><<<grid_for(N), 256, 0, s>>>(N, dinv, r, x, (TV)w, init ? 1 : 0);
+}
+template void launch_jacobi<double>(long long, const double*, const double*, double*, double,
+                                    bool, cudaStream_t);
+template void launch_jacobi<float>(long long, const float*, const float*, float*, double, bool,
+                                   cudaStream_t);
 
 void launch_repack(int count, int n, int ld, const double* src, const int* sel, int kind,
                    void* dst, cudaStream_t s) {

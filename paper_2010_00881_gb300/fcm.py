@@ -24,6 +24,8 @@ SRC = {"const": 0, "sin3": 1, "square_mms": 2, "popcorn": 3}
 DIR = {"none": 0, "levelset": 1, "faces": 2}
 GVAL = {"zero": 0, "sin3": 1, "square_mms": 2, "popcorn": 3}
 OP_APPLY, OP_SMOOTHER, OP_RESTRICT, OP_PROLONG, OP_COARSE = 0, 1, 2, 3, 4
+SMOOTHER = {"elementwise": 0, "patchwise": 1, "jacobi": 2}
+METHOD_CG_MG, METHOD_MG, METHOD_CG_AS = 0, 1, 2
 
 EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_num_levels",
            "fcm_level_info_get", "fcm_level_op", "fcm_cell_classes", "fcm_pcg_solve",
@@ -33,7 +35,7 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
            "fcm_cell_dofs", "fcm_mlhp_create", "fcm_mlhp_destroy", "fcm_mlhp_sizes",
            "fcm_mlhp_functions", "fcm_mlhp_leaves", "fcm_mlhp_patches",
            "fcm_mlhp_leaf_classes", "fcm_mlhp_levels", "fcm_mlhp_restriction_1d",
-           "fcm_measure_fma_peak"]
+           "fcm_measure_fma_peak", "fcm_solve"]
 
 
 class fcm_grid(C.Structure):
@@ -110,6 +112,8 @@ def load():
     lib.fcm_op_bytes.argtypes = [P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
     lib.fcm_cell_apply_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int), C.c_int, P, P, P, P]
     lib.fcm_measure_fma_peak.argtypes = [C.c_int, C.POINTER(C.c_double)]
+    lib.fcm_solve.argtypes = [P, C.c_int, P, P, C.c_double, C.c_int, C.c_int,
+                              C.POINTER(fcm_info), P]
     lib.fcm_setup_batch.argtypes = [C.c_int, C.POINTER(fcm_grid), C.POINTER(fcm_geometry),
                                     C.POINTER(fcm_physics), C.POINTER(fcm_solver_opts), C.c_int, P,
                                     C.POINTER(P)]
@@ -243,7 +247,7 @@ def descriptors(prob: dict, build_mixed: bool = True):
         raise ValueError("the library discretises with the full tensor-product space on all cells")
     if prob["geometry"]["kind"] not in GEOM:
         raise ValueError(f"geometry kind {prob['geometry']['kind']!r} has no library descriptor")
-    if prob.get("smoother", "elementwise") not in ("elementwise", "patchwise"):
+    if prob.get("smoother", "elementwise") not in SMOOTHER:
         raise ValueError(f"smoother {prob['smoother']!r} has no library descriptor")
     d = prob["dim"]
     g = fcm_grid()
@@ -293,7 +297,7 @@ def descriptors(prob: dict, build_mixed: bool = True):
             ph.traction[a] = tr["t"][a] if a < len(tr["t"]) else 0.0
     ph.quad_depth = prob["quad_depth"]
     op = fcm_solver_opts()
-    op.smoother = {"elementwise": 0, "patchwise": 1}[prob.get("smoother", "elementwise")]
+    op.smoother = SMOOTHER[prob.get("smoother", "elementwise")]
     op.omega = prob["omega"] if prob.get("omega") else 0.0
     op.n_pre = prob["n_pre"]
     op.n_post = prob["n_post"]
@@ -386,6 +390,22 @@ class Solver:
         _check(st, allow=(FCM_E_NOT_CONVERGED, FCM_E_BREAKDOWN) if allow_fail else ())
         d = inf.as_dict()
         d["status"] = st
+        return x, d
+
+    def solve(self, method, b=None, rtol=1e-8, maxit=500, prec=FCM_FP64, x=None,
+              allow_fail=False):
+        """fcm_solve: METHOD_CG_MG, METHOD_MG (stand-alone multigrid; info["rho"]
+        holds the contraction numbers) or METHOD_CG_AS (one-level Schwarz CG)."""
+        x = self._empty() if x is None else x
+        inf = fcm_info()
+        rho = np.zeros(max(1, maxit))
+        st = load().fcm_solve(self.h, method, _ptr(b) if b is not None else None, _ptr(x), rtol,
+                              maxit, prec, C.byref(inf), rho.ctypes.data_as(C.c_void_p))
+        _check(st, allow=(FCM_E_NOT_CONVERGED, FCM_E_BREAKDOWN) if allow_fail else ())
+        d = inf.as_dict()
+        d["status"] = st
+        if method == METHOD_MG:
+            d["rho"] = rho[: d["iters"]].copy()
         return x, d
 
     def profile_op(self, level, which, prec=FCM_FP64, reps=20):

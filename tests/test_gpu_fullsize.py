@@ -35,6 +35,9 @@ WORKLOADS = {
     "sphere32_p3": lambda: fi.poisson3d_sphere(),
     # 64^3 cells, p = 2, block with 64 spherical voids, 6.4M DOFs
     "elastic64_p2": lambda: fi.elasticity3d_voids(p=2),
+    # the popcorn of Sec. 4.3.2 on the paper's coarsest grid, 96^3 cells of
+    # (-1, 1)^3, p = 3, tensor-product space on all cells: 24.1M DOFs
+    "popcorn96_p3": lambda: fi.popcorn(cells=96, p=3, space="tensor", drop_outside=False),
 }
 
 

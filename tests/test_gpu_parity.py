@@ -74,6 +74,8 @@ CASES = {
     "sphere2_p1": lambda: fi.poisson3d_sphere(cells=2, p=1),
     "sphere3_p2": lambda: fi.poisson3d_sphere(cells=3, p=2),
     "circle3_p4": lambda: fi.poisson2d_circle(cells=3, p=4),
+    # the popcorn surface of Sec. 4.3.2 (tensor-product space, all cells kept)
+    "popcorn8_p2": lambda: fi.popcorn(cells=8, p=2, space="tensor", drop_outside=False),
 }
 
 # Energy-norm error of the mixed V-cycle against the oracle's FP64 V-cycle
@@ -83,7 +85,7 @@ MIXED_VCYCLE = {
     "circle16_p2": 3.3e-7, "square8_p4": 1.4e-7, "sphere5_p3": 1.5e-4, "sphere7_p2": 3.8e-6,
     "ellipsoid6_p2": 2.6e-6, "sphere4_p4": 2.1e-3, "elastic4_p2": 3.8e-7,
     "elastic5_p1": 2.1e-7, "circle1_p1": 4.1e-8, "sphere2_p1": 1.9e-7, "sphere3_p2": 3.2e-5,
-    "circle3_p4": 2.3e-4,
+    "circle3_p4": 2.3e-4, "popcorn8_p2": 1.7e-6,
 }
 
 
