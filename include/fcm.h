@@ -319,8 +319,9 @@ fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_hos
 
 /* Benchmark hook: replay one kernel of level `level` `reps` times on the
  * handle's stream and return its mean duration from CUDA events (ms).
- * which 0: operator cell kernel (y_c = K_c x_c over all cells), 1: smoother
- * cell kernel (A_i^{-1} over all blocks), 2: the DOF gather that follows
+ * which 0: operator cell kernels (y_c = K_c x_c over all cells: stored and
+ * shared parts side by side, as in the V-cycle), 1: smoother cell kernels
+ * (A_i^{-1} over all blocks, likewise), 2: the DOF gather that follows
  * them, 3 / 4: the stored-matrix (cut-cell / irregular-block) kernel of the
  * operator / smoother alone, without the shared-matrix tiles, 5 / 6: the
  * shared-matrix tiles of the operator / smoother alone.  prec selects

@@ -193,6 +193,18 @@ void build_shared(Handle* h, SharedSet<T>& S, const std::vector<int>& mat_of,
   };
   const int n = (int)cells.size();
   std::vector<int4> tiles = cut(64), tiles_mma = cut(128);
+  // Tensor-core tiles: those of small matrix groups first.  Small groups are
+  // the box-boundary signatures of the smoother, whose cells lie far apart in
+  // memory (their gathers are the slowest); persistent blocks take tiles
+  // blockIdx, blockIdx + grid, ..., so the slow tiles go to different blocks
+  // in the first round instead of piling up at the end.
+  {
+    std::map<int, int> group;
+    for (const int4& t : tiles_mma) group[t.x] += t.z;
+    std::stable_sort(tiles_mma.begin(), tiles_mma.end(), [&](const int4& a, const int4& b) {
+      return group[a.x] < group[b.x];
+    });
+  }
   S.tl.ntiles_mma = (int)tiles_mma.size();
   S.tl.tiles_mma = tiles_mma.empty() ? nullptr : h->upload(tiles_mma);
   S.tl.ntiles = (int)tiles.size();
@@ -733,6 +745,7 @@ void build_smoother(Handle* h, Level& L) {
     L.M32.sh.scale = sc32.empty() ? nullptr : h->upload(sc32);
     L.M32.sh.mats = sinv ? to_f32(h, sinv, sigs.size() * (size_t)n * n) : nullptr;
     L.M32.sh.nmats = (int)sigs.size();
+    L.M32.sh.mma_only_alone = true;
     prepare_mma(h, L.M32.sh, n);
   }
 }
@@ -1484,16 +1497,16 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
     };
     auto once = [&]() {
       if (prec == FCM_FP64) {
-        if (which == 0) launch_cell_op<double>(L.g, L.A64, L.x, L.Y, h->s);
-        else if (which == 1) launch_cell_op<double>(L.g, L.M64, L.r, L.Y, h->s);
+        if (which == 0) launch_cell_op<double>(L.g, L.A64, L.x, L.Y, h->s, &h->side);
+        else if (which == 1) launch_cell_op<double>(L.g, L.M64, L.r, L.Y, h->s, &h->side);
         else if (which == 2) launch_gather<double>(L.g, GATHER_RESID, L.Y, L.b, L.r, 1.0, h->s);
         else if (which == 3) launch_cell_op<double>(L.g, stored(L.A64), L.x, L.Y, h->s);
         else if (which == 4) launch_cell_op<double>(L.g, stored(L.M64), L.r, L.Y, h->s);
         else if (which == 5) launch_cell_op<double>(L.g, tiles(L.A64), L.x, L.Y, h->s);
         else launch_cell_op<double>(L.g, tiles(L.M64), L.r, L.Y, h->s);
       } else {
-        if (which == 0) launch_cell_op<float>(L.g, L.A32, L.x32, L.Y32, h->s);
-        else if (which == 1) launch_cell_op<float>(L.g, L.M32, L.r32, L.Y32, h->s);
+        if (which == 0) launch_cell_op<float>(L.g, L.A32, L.x32, L.Y32, h->s, &h->side);
+        else if (which == 1) launch_cell_op<float>(L.g, L.M32, L.r32, L.Y32, h->s, &h->side);
         else if (which == 2) launch_gather<float>(L.g, GATHER_RESID, L.Y32, L.b32, L.r32, 1.0, h->s);
         else if (which == 3) launch_cell_op<float>(L.g, stored(L.A32), L.x32, L.Y32, h->s);
         else if (which == 4) launch_cell_op<float>(L.g, stored(L.M32), L.r32, L.Y32, h->s);

@@ -137,6 +137,11 @@ struct SharedSet {
   // FP32 only: the matrices as tensor-core operands, [nmats][hi, lo][NP x KD]
   // in the K-major core-matrix layout (see launch_mma_operands)
   float* mma_b = nullptr;
+  // FP32 only: use the tensor cores only where the CUDA-core tiles cannot
+  // run beside the stored-matrix streaming (set for the smoother's shared
+  // inverses, whose many per-signature operands cost more than they gain
+  // when both kernels fit side by side)
+  bool mma_only_alone = false;
 };
 
 // Tensor-core operand sizes of an n x n shared matrix: reduction length KD

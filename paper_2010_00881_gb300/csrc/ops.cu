@@ -2022,20 +2022,29 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   // side by side.  Below that the product is a few hundred FMAs per cell and
   // the CUDA-core tiles finish sooner than the tensor-core kernel's fixed
   // latency (tensor-memory allocation, MMA commit and wait: about 5 us).
-  const bool mma = std::is_same<TV, float>::value && A.ntiles_mma > 0 && n >= kMmaMinN &&
-                   n <= 128 && op.sh.mma_b != nullptr;
+  bool mma = std::is_same<TV, float>::value && A.ntiles_mma > 0 && n >= kMmaMinN &&
+             n <= 128 && op.sh.mma_b != nullptr;
   int KC = mma ? mma_chunk(n, 200 * 1024) : 0;
-  bool fork = side && side->s2 && (mma ? A.ntiles_mma : A.ntiles) && (A.nb_own || A.nb_own_x);
-  if (fork && !small) {
+  const bool stored = A.nb_own || A.nb_own_x;
+  // shared memory left on an SM beside one streaming block (12 KB: static
+  // shared memory of both kernels and the per-block reservations)
+  size_t left = 0;
+  if (side && side->s2 && stored && !small) {
     const size_t stream_smem =
         (size_t)Ring<TV>::stages * kRingChunk +
         (size_t)kConsumers * (2 * kItemVals * sizeof(TV) + 128 * sizeof(double));
     int dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    // 12 KB: static shared memory of both kernels and the per-block reservation
-    const size_t left = (size_t)per_sm > stream_smem + 12 * 1024
-                            ? (size_t)per_sm - stream_smem - 12 * 1024 : 0;
+    left = (size_t)per_sm > stream_smem + 12 * 1024 ? (size_t)per_sm - stream_smem - 12 * 1024 : 0;
+  }
+  if (mma && op.sh.mma_only_alone && side && side->s2 && stored) {
+    const int npad = tile_npad(n);
+    const size_t cc_smem = ((size_t)n * npad + 2 * (size_t)n * kTileCells) * sizeof(TV);
+    if (small || cc_smem <= left) mma = false;  // CUDA-core tiles run beside the stream
+  }
+  bool fork = side && side->s2 && (mma ? A.ntiles_mma : A.ntiles) && stored;
+  if (fork && !small) {
     if (mma) {
       const int kc = mma_chunk(n, left);
       fork = kc >= 8;
