@@ -163,6 +163,9 @@ typedef struct {
   int fp64_in_mixed;         /* 1: the FCM_MIXED V-cycle runs this level in FP64 (the
                                 finest level when its blocks reach 1e12, or a
                                 single-level hierarchy) */
+  int kron_operator;         /* 1: the FP64 operator applies its shared (uncut Poisson)
+                                cells by sum factorisation of the Kronecker-sum cell
+                                matrix instead of the dense matrix */
 } fcm_level_info;
 
 typedef struct fcm_handle fcm_handle;

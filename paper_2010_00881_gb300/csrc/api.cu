@@ -532,6 +532,108 @@ float* to_f32(Handle* h, const double* src, size_t n) {
   return d;
 }
 
+// 1D element matrices of the integrated Legendre basis of degree p on
+// [-1, 1] (Sec. 2.1): N_0 = (1 - t) / 2, N_1 = (1 + t) / 2,
+// N_j = (P_j - P_{j-2}) / sqrt(4 j - 2), N_j' = sqrt((2 j - 1) / 2) P_{j-1};
+// Kh[i][j] = int N_i' N_j', Mh[i][j] = int N_i N_j by a (p + 2)-point Gauss
+// rule (exact for these degrees; nodes by Newton's method on P_m).
+void legendre_1d_matrices(int p, std::vector<double>& Kh, std::vector<double>& Mh) {
+  const int P = p + 1, m = p + 2;
+  std::vector<double> xs(m), ws(m);
+  auto legendre = [m](double x, double& pm, double& pm1) {
+    double p0 = 1.0, p1 = x;
+    for (int k = 2; k <= m; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    pm = p1;
+    pm1 = p0;
+  };
+  for (int i = 0; i < m; ++i) {
+    double x = std::cos(M_PI * (i + 0.75) / (m + 0.5)), pm, pm1;
+    for (int it = 0; it < 100; ++it) {
+      legendre(x, pm, pm1);
+      const double dx = pm / (m * (x * pm - pm1) / (x * x - 1.0));
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    legendre(x, pm, pm1);
+    const double dp = m * (x * pm - pm1) / (x * x - 1.0);
+    xs[i] = x;
+    ws[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  Kh.assign(P * P, 0.0);
+  Mh.assign(P * P, 0.0);
+  std::vector<double> N(P), dN(P), L(P + 1);
+  for (int q = 0; q < m; ++q) {
+    const double t = xs[q];
+    L[0] = 1.0;
+    L[1] = t;
+    for (int k = 2; k <= P; ++k) L[k] = ((2.0 * k - 1.0) * t * L[k - 1] - (k - 1.0) * L[k - 2]) / k;
+    N[0] = 0.5 * (1.0 - t);
+    N[1] = 0.5 * (1.0 + t);
+    dN[0] = -0.5;
+    dN[1] = 0.5;
+    for (int j = 2; j < P; ++j) {
+      N[j] = (L[j] - L[j - 2]) / std::sqrt(4.0 * j - 2.0);
+      dN[j] = std::sqrt((2.0 * j - 1.0) / 2.0) * L[j - 1];
+    }
+    for (int i = 0; i < P; ++i)
+      for (int j = 0; j < P; ++j) {
+        Kh[i * P + j] += ws[q] * dN[i] * dN[j];
+        Mh[i * P + j] += ws[q] * N[i] * N[j];
+      }
+  }
+}
+
+// When the level's shared operator matrix is the Kronecker sum of the 1D
+// matrices (the uncut Poisson cell; checked entry by entry against the
+// assembled K_ref to 1e-12 relative), store its 1D factors so that the FP64
+// shared tiles are applied by sum factorisation.
+void prepare_kron(Handle* h, Level& L) {
+  const Problem& P = h->P;
+  const int p = L.g.p, dim = L.g.dim, n = L.g.nloc;
+  if (P.pde != FCM_PDE_POISSON || L.is_h || !L.Kref || L.A64.sh.tl.ncells == 0 ||
+      !kron_supported(dim, p))
+    return;
+  std::vector<double> Kh, Mh;
+  legendre_1d_matrices(p, Kh, Mh);
+  const int Q = p + 1;
+  std::vector<double> F((size_t)dim * 2 * Q * Q);
+  for (int a = 0; a < dim; ++a)
+    for (int e = 0; e < Q * Q; ++e) {
+      F[(size_t)(a * 2 + 0) * Q * Q + e] = Kh[e] * (2.0 / P.h[a]);
+      F[(size_t)(a * 2 + 1) * Q * Q + e] = Mh[e] * (P.h[a] / 2.0);
+    }
+  auto fac = [&](int a, int which, int i, int j) {
+    return F[(size_t)(a * 2 + which) * Q * Q + i * Q + j];
+  };
+  std::vector<double> Kr((size_t)n * n);
+  CK(cudaMemcpyAsync(Kr.data(), L.Kref, Kr.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  std::vector<double> Kk((size_t)n * n, 0.0);
+  double kmax = 0.0;
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      const int jr[3] = {r % Q, (r / Q) % Q, r / (Q * Q)}, jc[3] = {c % Q, (c / Q) % Q, c / (Q * Q)};
+      double sum = 0.0;
+      for (int a = 0; a < dim; ++a) {
+        double t = 1.0;
+        for (int b = 0; b < dim; ++b) t *= fac(b, a == b ? 0 : 1, jr[b], jc[b]);
+        sum += t;
+      }
+      Kk[(size_t)r * n + c] = sum;
+      kmax = std::max(kmax, std::fabs(Kr[(size_t)r * n + c]));
+    }
+  const double c0 = Kr[0] / Kk[0];
+  for (size_t e = 0; e < Kk.size(); ++e)
+    if (!(std::fabs(Kr[e] - c0 * Kk[e]) <= 1e-12 * kmax)) return;
+  for (int a = 0; a < dim; ++a)
+    for (int e = 0; e < Q * Q; ++e) F[(size_t)(a * 2 + 0) * Q * Q + e] *= c0;
+  L.A64.sh.kron = h->upload(F);
+}
+
 // Operator data of a level from per-cell own matrices + shared K_ref.
 void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, double* own_mats,
                     double* Kref, const std::vector<int>& sh_cells,
@@ -866,6 +968,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     L.g = gt;
     build_operator(h, L, own_cells, own_cells.empty() ? nullptr : Ktop, KrefTop, sh_cells,
                    sh_scale);
+    prepare_kron(h, L);
     lv.push_back(std::move(L));
   }
   for (int pc = p - 1; pc >= 1; --pc) {
@@ -878,6 +981,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     launch_extract_sub(1, dim, nf, p, pc, KrefTop, Kref, h->s);
     CKL();
     build_operator(h, L, own_cells, Kown, Kref, sh_cells, sh_scale);
+    prepare_kron(h, L);
     lv.push_back(std::move(L));
   }
   while (true) {
@@ -1359,6 +1463,7 @@ fcm_status fcm_level_info_get(const fcm_handle* h, int level, fcm_level_info* in
   info->n_fp64_blocks = L.n_fp64_blocks;
   info->max_block_cond = L.max_cond;
   info->fp64_in_mixed = h->mixed && level >= h->top64 ? 1 : 0;
+  info->kron_operator = L.A64.sh.kron ? 1 : 0;
   info->omega = L.omega;
   info->lambda_est = L.lambda;
   return FCM_OK;

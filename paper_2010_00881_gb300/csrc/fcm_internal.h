@@ -142,7 +142,15 @@ struct SharedSet {
   // inverses, whose many per-signature operands cost more than they gain
   // when both kernels fit side by side)
   bool mma_only_alone = false;
+  // FP64 only, set when the one shared matrix is a Kronecker sum (the uncut
+  // Poisson cell, Sec. 2.1): its 1D factors [axis][K1, M1][P][P] with
+  // P = p + 1, K = sum_a (x)_b (K1 if a == b else M1)_b, axis x fastest
+  const double* kron = nullptr;
 };
+
+// Whether the sum-factorised apply of a Kronecker-sum shared matrix
+// (SharedSet::kron) is built for this dimension and degree.
+bool kron_supported(int dim, int p);
 
 // Tensor-core operand sizes of an n x n shared matrix: reduction length KD
 // (n rounded up to a multiple of 8) and N extent NP (n rounded up to a

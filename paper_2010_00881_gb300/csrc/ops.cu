@@ -1099,6 +1099,132 @@ __global__ void __launch_bounds__(kOpThreads) tile_kernel(CellOpArgs<TV> A) {
   }
 }
 
+// Shared operator matrix of uncut Poisson cells by sum factorisation (FP64).
+// The uncut cell matrix is the Kronecker sum K = sum_a (x)_b F_ab with
+// F_ab = K1_a (1D stiffness) if a == b and M1_b (1D mass) otherwise (Sec.
+// 2.1; tensor-product basis, x fastest).  Applied to a cell's coefficient
+// tensor X (P^D values) as 1D contractions along the axes, reusing partial
+// products: D = 3: U = M_x X, V = K_x X; W = M_y V + K_y U, T = M_y U;
+// Y = M_z W + K_z T (7 P^4 multiply-adds instead of P^6); D = 2: U = M_x X,
+// V = K_x X; Y = M_y V + K_y U.  GB300's FP64 rate is 1/64 of its FP32 rate
+// and this product is bound by it, so fewer FMAs is what counts.  A block
+// takes 64-cell tiles in batches of CT cells staged in shared memory (three
+// buffers of CT x P^D values, rows padded by one to spread banks); each
+// thread contracts whole lines (P values along one axis) from registers.
+template <int P, int D, int CT>
+__global__ void __launch_bounds__(kOpThreads) kron_tile_kernel(CellOpArgs<double> A,
+                                                               const double* __restrict__ kron) {
+  constexpr int NL = D == 3 ? P * P * P : P * P;  // values per cell
+  constexpr int LD = NL + 1;                      // padded row
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int tab[128];
+  __shared__ double F[D][2][P * P];               // [axis][K1, M1]
+  __shared__ int ccell[CT], cbase[CT];
+  __shared__ double cscale[CT];
+  double* B0 = reinterpret_cast<double*>(smem_raw);
+  double* B1 = B0 + CT * LD;
+  double* B2 = B1 + CT * LD;
+  const LevelGeom& g = A.g;
+  build_local_table(g, tab);
+  for (int e = threadIdx.x; e < D * 2 * P * P; e += blockDim.x) (&F[0][0][0])[e] = kron[e];
+  const long long ncells = g.ncells;
+  // contraction of one line: out[i] = sum_j Mat[i][j] in[j]
+  auto line = [&](const double* M, const double* in, double* out) {
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < P; ++j) s = fma(M[i * P + j], in[j], s);
+      out[i] = s;
+    }
+  };
+  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+    const int4 tile = A.tiles[t];
+    for (int c0 = 0; c0 < tile.z; c0 += CT) {
+      const int cnt = min(CT, tile.z - c0);
+      __syncthreads();
+      if (threadIdx.x < CT) {
+        const int c = threadIdx.x;
+        const bool live = c < cnt;
+        const int cell = live ? A.sh_cells[tile.y + c0 + c] : 0;
+        int cx, cy, cz;
+        cell_coords(g, cell, cx, cy, cz);
+        ccell[c] = live ? cell : -1;
+        cbase[c] = cell_base(g, cx, cy, cz);
+        cscale[c] = live ? A.sh_scale[tile.y + c0 + c] : 0.0;
+      }
+      __syncthreads();
+      // gather X (consecutive threads: consecutive cells of one local DOF)
+      for (int e = threadIdx.x; e < NL * CT; e += blockDim.x) {
+        const int l = e / CT, c = e - l * CT;
+        B0[c * LD + l] = ccell[c] >= 0 ? __ldg(A.x + cbase[c] + tab[l]) : 0.0;
+      }
+      __syncthreads();
+      // pass 1, along x (stride 1): U = M_x X -> B1, V = K_x X -> B2
+      for (int e = threadIdx.x; e < CT * (NL / P); e += blockDim.x) {
+        const int c = e / (NL / P), r = e - c * (NL / P);
+        const double* in = B0 + c * LD + r * P;
+        double v[P], o[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) v[j] = in[j];
+        line(F[0][1], v, o);
+#pragma unroll
+        for (int j = 0; j < P; ++j) B1[c * LD + r * P + j] = o[j];
+        line(F[0][0], v, o);
+#pragma unroll
+        for (int j = 0; j < P; ++j) B2[c * LD + r * P + j] = o[j];
+      }
+      __syncthreads();
+      // pass 2, along y (stride P): lines (c, x, z)
+      for (int e = threadIdx.x; e < CT * (NL / P); e += blockDim.x) {
+        const int c = e / (NL / P), r = e - c * (NL / P);
+        const int ix = r % P, iz = r / P;
+        const int base = c * LD + ix + iz * P * P;
+        double u[P], v[P], o1[P], o2[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          u[j] = B1[base + j * P];
+          v[j] = B2[base + j * P];
+        }
+        line(F[1][1], v, o1);   // M_y V
+        line(F[1][0], u, o2);   // K_y U
+#pragma unroll
+        for (int j = 0; j < P; ++j) B0[base + j * P] = o1[j] + o2[j];   // Y (2D) or W (3D)
+        if constexpr (D == 3) {
+          line(F[1][1], u, o1);                                            // T = M_y U
+#pragma unroll
+          for (int j = 0; j < P; ++j) B2[base + j * P] = o1[j];
+        }
+      }
+      __syncthreads();
+      const double* Yb = B0;
+      if constexpr (D == 3) {
+        // pass 3, along z (stride P^2): Y = M_z W + K_z T -> B1
+        for (int e = threadIdx.x; e < CT * P * P; e += blockDim.x) {
+          const int c = e / (P * P), r = e - c * (P * P);
+          const int base = c * LD + r;
+          double w[P], tt[P], o1[P], o2[P];
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            w[j] = B0[base + j * P * P];
+            tt[j] = B2[base + j * P * P];
+          }
+          line(F[2][1], w, o1);
+          line(F[2][0], tt, o2);
+#pragma unroll
+          for (int j = 0; j < P; ++j) B1[base + j * P * P] = o1[j] + o2[j];
+        }
+        __syncthreads();
+        Yb = B1;
+      }
+      for (int e = threadIdx.x; e < NL * CT; e += blockDim.x) {
+        const int l = e / CT, c = e - l * CT;
+        if (ccell[c] >= 0) A.Y[(size_t)l * ncells + ccell[c]] = cscale[c] * Yb[c * LD + l];
+      }
+    }
+  }
+}
+
 // Shared matrices on the tensor cores (FP32 vectors).  For a tile of up to
 // 128 cells that share one matrix K (n x n, symmetric), the products are
 // D = X K with X the tile's gathered coefficients, one row per cell: one
@@ -1879,6 +2005,57 @@ void launch_tc_tile(const CellOpArgs<float>& A, const float* mma_b, int KC, bool
   }
 }
 
+// Sum-factorised shared tiles (FP64, Poisson): P = p + 1, D = dim; batches
+// of 32 cells (16 when a cell has more than 64 DOFs), three shared-memory
+// buffers of about 50 KB together, so a block fits beside a streaming block.
+inline int kron_ct(int nl) { return nl <= 64 ? 32 : 16; }
+inline size_t kron_smem(int nl) { return (size_t)3 * kron_ct(nl) * (nl + 1) * sizeof(double); }
+
+template <int P, int D>
+void launch_kron_p(const CellOpArgs<double>& A, const double* kron, int grid, cudaStream_t s) {
+  constexpr int NL = D == 3 ? P * P * P : P * P;
+  constexpr int CT = NL <= 64 ? 32 : 16;
+  kron_tile_kernel<P, D, CT><<<grid, kOpThreads, kron_smem(NL), s>>>(A, kron);
+}
+
+bool kron_supported(int dim, int p) {
+  return (dim == 3 && p >= 1 && p <= 4) || (dim == 2 && p >= 1 && p <= 8);
+}
+
+void launch_kron_tile(const CellOpArgs<double>& A, const double* kron, bool one_per_sm,
+                      cudaStream_t s) {
+  const int nl = A.g.nloc;
+  int dev = 0, sms = 148, smem_sm = 228 * 1024;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int per_sm = (int)((size_t)smem_sm / (kron_smem(nl) + 4 * 1024));
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm < 1 || one_per_sm) per_sm = 1;
+  int grid = sms * per_sm;
+  if (grid > A.ntiles) grid = A.ntiles;
+  const int P = A.g.p + 1;
+  if (A.g.dim == 3) {
+    switch (P) {
+      case 2: launch_kron_p<2, 3>(A, kron, grid, s); break;
+      case 3: launch_kron_p<3, 3>(A, kron, grid, s); break;
+      case 4: launch_kron_p<4, 3>(A, kron, grid, s); break;
+      default: launch_kron_p<5, 3>(A, kron, grid, s); break;
+    }
+  } else {
+    switch (P) {
+      case 2: launch_kron_p<2, 2>(A, kron, grid, s); break;
+      case 3: launch_kron_p<3, 2>(A, kron, grid, s); break;
+      case 4: launch_kron_p<4, 2>(A, kron, grid, s); break;
+      case 5: launch_kron_p<5, 2>(A, kron, grid, s); break;
+      case 6: launch_kron_p<6, 2>(A, kron, grid, s); break;
+      case 7: launch_kron_p<7, 2>(A, kron, grid, s); break;
+      case 8: launch_kron_p<8, 2>(A, kron, grid, s); break;
+      default: launch_kron_p<9, 2>(A, kron, grid, s); break;
+    }
+  }
+}
+
 void launch_mma_operands(int n, int nmats, const float* mats, float* out, cudaStream_t s) {
   if (nmats == 0) return;
   const long long tot = (long long)nmats * mma_np(n) * mma_kd(n);
@@ -1907,6 +2084,18 @@ cudaError_t prepare_kernels() {
   if (e == cudaSuccess) e = prepare_one(tc_tile_kernel<16>, optin);
   if (e == cudaSuccess) e = prepare_one(tc_tile_kernel<32>, optin);
   if (e == cudaSuccess) e = prepare_one(tc_tile_kernel<64>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<2, 3, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<3, 3, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<4, 3, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<5, 3, 16>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<2, 2, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<3, 2, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<4, 2, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<5, 2, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<6, 2, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<7, 2, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<8, 2, 32>, optin);
+  if (e == cudaSuccess) e = prepare_one(kron_tile_kernel<9, 2, 16>, optin);
   return e;
 }
 
@@ -2049,6 +2238,8 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
       const int kc = mma_chunk(n, left);
       fork = kc >= 8;
       if (fork) KC = kc;
+    } else if (op.sh.kron) {
+      fork = kron_smem(n) <= left;
     } else {
       const int npad = tile_npad(n);
       const size_t tile_smem =
@@ -2110,6 +2301,16 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
     // one block per SM only beside stream blocks; the small-cell kernels
     // leave the SMs' shared memory free
     const bool one = fork && !small;
+    if constexpr (std::is_same<TV, double>::value) {
+      if (op.sh.kron) {
+        launch_kron_tile(A, op.sh.kron, one, st);
+        if (fork) {
+          cudaEventRecord(side->join, side->s2);
+          cudaStreamWaitEvent(s, side->join, 0);
+        }
+        return;
+      }
+    }
     switch (npad / 16) {
       case 1: launch_tile<TV, 1>(A, sm_tile, st, one); break;
       case 2: launch_tile<TV, 2>(A, sm_tile, st, one); break;

@@ -76,7 +76,7 @@ class fcm_level_info(C.Structure):
                 ("ndofs", C.c_longlong), ("nloc", C.c_int), ("n_own_cells", C.c_int),
                 ("n_own_blocks", C.c_int), ("n_fp64_blocks", C.c_int), ("omega", C.c_double),
                 ("lambda_est", C.c_double), ("max_block_cond", C.c_double),
-                ("fp64_in_mixed", C.c_int)]
+                ("fp64_in_mixed", C.c_int), ("kron_operator", C.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

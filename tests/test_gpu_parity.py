@@ -348,6 +348,19 @@ def test_host_buffer_solve_matches_device_solve(case):
     assert np.array_equal(xh, xd.cpu().numpy())
 
 
+def test_kron_operator_where_the_cell_matrix_is_a_kronecker_sum(case):
+    """The FP64 operator applies the shared cells of every Poisson p-level by
+    sum factorisation (its parity is test_apply_fp64 and
+    test_level_operators); elasticity keeps the dense shared matrix."""
+    name, prob, H, s = case
+    for l in range(s.num_levels()):
+        info = s.level_info(l)
+        ncells = int(np.prod(info["cells"][: prob["dim"]]))
+        want = (prob["pde"] == "poisson" and not info["is_h_level"]
+                and info["n_own_cells"] < ncells)
+        assert info["kron_operator"] == (1 if want else 0), (name, l, info)
+
+
 def test_single_level_mixed_runs_fp64(case):
     """A single-level hierarchy (the coarse solve alone) or finest blocks
     with kappa_inf >= 1e12 run the finest level of the mixed V-cycle in FP64;
