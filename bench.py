@@ -479,6 +479,14 @@ def main():
             "fp64": {"value": value64, "unit": "DOFs/s", "ms_per_step": tot64 / args.steps,
                      "iterations": inf_fp64[-1]["iters"],
                      "relres_true": inf_fp64[-1]["relres_true"]},
+            # the whole solve against HBM: algorithmic bytes of every launch
+            # the solve made (fcm_info.bytes_moved_est) over the device time
+            "solve_bandwidth": {
+                "bytes_per_step": inf_mixed[-1]["bytes_moved_est"],
+                "GBps": inf_mixed[-1]["bytes_moved_est"] / (tot / args.steps * 1e-3) / 1e9,
+                "frac": inf_mixed[-1]["bytes_moved_est"] / (tot / args.steps * 1e-3) / 1e9
+                        / peaks.get("hbm_gbs", 6800.0),
+                "fp64_GBps": inf_fp64[-1]["bytes_moved_est"] / (tot64 / args.steps * 1e-3) / 1e9},
             "speedup_mixed_vs_fp64": value / value64,
             "vcycles_per_s": (inf_mixed[-1]["iters"] + 1) * args.steps / (tot / 1e3),
             "setup_ms": inf_mixed[-1]["setup_ms"],

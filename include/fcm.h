@@ -25,6 +25,9 @@
  *    is ix + m_x (iy + m_y iz) with m = C p + 1; vector fields (elasticity)
  *    stack whole scalar fields.  `_dev` pointers are device memory of the
  *    device current at setup, `_host` pointers host memory.
+ *  - With trunk-space elements (fcm_grid.space) the vectors keep this
+ *    layout: inputs' entries on the removed modes are ignored (a solve's
+ *    b_dev is taken as zero there) and every output is zero there.
  *  - The handle owns all device state (matrices, inverses, work vectors,
  *    captured graphs) and frees it in fcm_destroy.  All work is ordered on
  *    the CUDA stream given at setup; calls return after that stream has
@@ -68,7 +71,14 @@ enum { FCM_SMOOTHER_ELEMENTWISE = 0, FCM_SMOOTHER_PATCHWISE = 1, FCM_SMOOTHER_JA
 
 /* Grid: dim in {2,3}; cells per axis (>= 1); box [lo, hi]; degree p in
  * [1, 8].  overlay_levels > 0 (multi-level hp) is FCM_E_UNSUPPORTED in
- * fcm_setup; fcm_mlhp_create builds the overlay topology on the host. */
+ * fcm_setup; fcm_mlhp_create builds the overlay topology on the host.
+ * space: FCM_SPACE_TENSOR (Q_p on every cell) or FCM_SPACE_TRUNK, the
+ * trunk space of Sec. 4.3 (of the tensor modes, those whose bubble degrees
+ * sum to at most p; the p-levels use the trunk spaces of their degrees).
+ * With trunk elements vectors keep the tensor layout: the other modes are
+ * removed from the system (zero rows, columns, loads and corrections) and
+ * stay zero in every result; fcm_level_info.ndofs_active counts the rest. */
+enum { FCM_SPACE_TENSOR = 0, FCM_SPACE_TRUNK = 1 };
 typedef struct {
   int dim;
   int cells[3];
@@ -76,6 +86,7 @@ typedef struct {
   int p;
   int overlay_levels;
   int overlay_p;
+  int space;
 } fcm_grid;
 
 /* Level-set geometry, Omega_phys = {psi <= 0}.  params (host memory, read
@@ -144,6 +155,11 @@ typedef struct {
   double solve_ms;           /* wall time of this solve (host clock) */
   long long ndofs;
   long long kernel_launches; /* device kernels this solve launched (graph nodes included) */
+  long long bytes_moved_est; /* algorithmic bytes of this solve: every launch's stored
+                                matrices once, its input and output vectors once (the
+                                per-kernel byte model of fcm_op_bytes), summed over the
+                                launches made; divided by solve_ms, the solve's
+                                effective bandwidth */
 } fcm_info;
 
 /* Per-level description (test and benchmark introspection). */
@@ -166,6 +182,7 @@ typedef struct {
   int kron_operator;         /* 1: the FP64 operator applies its shared (uncut Poisson)
                                 cells by sum factorisation of the Kronecker-sum cell
                                 matrix instead of the dense matrix */
+  long long ndofs_active;    /* DOFs of the level's space (ndofs unless trunk) */
 } fcm_level_info;
 
 typedef struct fcm_handle fcm_handle;

@@ -119,6 +119,8 @@ struct fcm_handle {
   int top64 = 1 << 30;
   long long vc_nodes64 = 0, vc_nodes32 = 0;  // kernel nodes per V-cycle graph
   long long launches = 0;                    // kernels launched by the current solve
+  long long vc_bytes64 = 0, vc_bytes32 = 0;  // algorithmic bytes per V-cycle graph launch
+  long long bytes = 0;                       // algorithmic bytes of the current solve
 
   template <typename T>
   T* alloc(size_t count) {
@@ -250,7 +252,71 @@ void check_timeout(Handle* h) {
   if (flag) throw Error(FCM_E_TIMEOUT, "a bounded device wait on a bulk copy expired");
 }
 
+// Bytes the level kernel `which` (0 operator, 1 smoother, 2 residual gather,
+// 3 / 4 stored parts of 0 / 1, 5 / 6 shared tiles of 0 / 1) must move at
+// least once per launch.
+long long op_bytes(const Level& L, int which, int prec) {
+  const long long n = L.g.nloc, nc = L.g.ncells;
+  const long long sv = prec == FCM_FP64 ? 8 : 4;
+  if (which == 2) return nc * n * sv + 2 * L.g.N * sv + L.g.N * sv;  // Y, b, r(out)
+  if (which >= 5) {
+    // shared tiles: the matrices once, every tile cell's coefficients and results
+    const SharedSet<double>& s64 = which == 5 ? L.A64.sh : L.M64.sh;
+    return (long long)s64.nmats * n * n * sv + 2 * (long long)s64.tl.ncells * n * sv;
+  }
+  const OpData<double>& d64 = which == 0 || which == 3 ? L.A64 : L.M64;
+  const OpData<float>& d32 = which == 0 || which == 3 ? L.A32 : L.M32;
+  const long long ld = padded_ld((int)n);
+  if (which >= 3) {
+    long long mats, cells;
+    if (prec == FCM_FP64) {
+      mats = (long long)d64.own.n * n * ld * 8;
+      cells = d64.own.n;
+    } else {
+      mats = (long long)d32.own.n * n * ld * 4 + (long long)d32.own_x.n * n * ld * 8;
+      cells = (long long)d32.own.n + d32.own_x.n;
+    }
+    return mats + 2 * cells * n * sv;  // stored matrices, their coefficients and results
+  }
+  long long mats;
+  if (prec == FCM_FP64)
+    mats = (long long)d64.own.n * n * ld * 8 + (long long)d64.sh.nmats * n * n * 8;
+  else
+    mats = (long long)d32.own.n * n * ld * 4 + (long long)d32.own_x.n * n * ld * 8 +
+           (long long)d32.sh.nmats * n * n * 4;
+  return mats + 2 * nc * n * sv;  // gathered coefficients + per-cell results
+}
+
+// Algorithmic bytes of the launches record_vcycle makes for level l and the
+// levels below it (the same sequence of cell operations, gathers, Jacobi
+// steps, transfers, precision copies and the coarse solve).
+long long vcycle_bytes(const Handle* h, int l, int top64, bool fp64) {
+  const Level& L = h->levels[l];
+  const long long sv = fp64 ? 8 : 4, N = L.g.N;
+  const int prec = fp64 ? FCM_FP64 : FCM_MIXED;
+  if (l == 0) return N * N * 8 + 2 * N * sv;  // two triangular factor products
+  const Level& Lc = h->levels[l - 1];
+  const long long Nc = Lc.g.N;
+  const long long cellY = (long long)L.g.ncells * L.g.nloc * sv;
+  const bool jac = h->smoother == FCM_SMOOTHER_JACOBI;
+  const long long resid = op_bytes(L, 0, prec) + cellY + 3 * N * sv;
+  const long long corr = jac ? 4 * N * sv : op_bytes(L, 1, prec) + cellY + 2 * N * sv;
+  const long long first = jac ? 3 * N * sv : op_bytes(L, 1, prec) + cellY + N * sv;
+  long long b = 0;
+  if (h->n_pre == 0) b += N * sv;
+  for (int k = 0; k < h->n_pre; ++k) b += k == 0 ? first : resid + corr;
+  if (h->n_pre > 0) b += resid;
+  b += (N + Nc) * sv;  // restriction
+  const bool to32 = fp64 && l - 1 < top64;
+  if (to32) b += 2 * Nc * (8 + 4) + vcycle_bytes(h, l - 1, top64, false);
+  else b += vcycle_bytes(h, l - 1, top64, fp64);
+  b += (Nc + 2 * N) * sv;  // prolongation
+  b += (long long)h->n_post * (resid + corr);
+  return b;
+}
+
 double host_dot(Handle* h, const double* a, const double* b, long long n) {
+  h->bytes += (a == b ? 1 : 2) * n * 8;
   h->launches += 2;
   launch_dot_partials(a, b, n, h->part, h->s);
   launch_reduce(h->part, kDotBlocks, h->d_scalar, h->s);
@@ -262,12 +328,17 @@ double host_dot(Handle* h, const double* a, const double* b, long long n) {
 
 void apply_A64(Handle* h, Level& L, const double* x, double* y, int mode, const double* b) {
   h->launches += 2;
+  h->bytes += op_bytes(L, 0, FCM_FP64) + (long long)L.g.ncells * L.g.nloc * 8 +
+              (mode == GATHER_RESID ? 3 : 1) * L.g.N * 8;
   launch_cell_op<double>(L.g, L.A64, x, L.Y, h->s, &h->side);
   launch_gather<double>(L.g, mode, L.Y, b, y, 1.0, h->s);
   CKL();
 }
 
 void apply_M64(Handle* h, Level& L, const double* r, double* y) {
+  h->bytes += h->smoother == FCM_SMOOTHER_JACOBI
+                  ? 3 * L.g.N * 8
+                  : op_bytes(L, 1, FCM_FP64) + (long long)L.g.ncells * L.g.nloc * 8 + L.g.N * 8;
   if (h->smoother == FCM_SMOOTHER_JACOBI) {
     launch_jacobi<double>(L.g.N, L.dinv64, r, y, 1.0, true, h->s);
     CKL();
@@ -409,6 +480,63 @@ cudaGraphExec_t capture_vcycle(Handle* h, long long* nodes, int top64) {
 }
 
 // ---------------------------------------------------------------------------
+// Trunk-space levels: the finest level and the p-levels of degree >= 2 of a
+// trunk-space problem (the p = 1 and Q1 levels hold vertex modes only).
+bool trunk_level(const Handle* h, const Level& L) {
+  return h->P.trunk && !L.is_h && L.g.p >= 2;
+}
+
+// Scalar DOFs of a level kept by the trunk space of the level's degree: the
+// bubble degrees of the 1D indices (index i > C of a C-cell axis is a bubble
+// of degree 2 + (i - C - 1) / C) sum to at most p.
+std::vector<unsigned char> trunk_keep(const LevelGeom& g) {
+  std::vector<unsigned char> keep((size_t)g.M);
+  for (long long i = 0; i < g.M; ++i) {
+    long long t = i;
+    int sum = 0;
+    for (int a = 0; a < g.dim; ++a) {
+      const int ia = (int)(t % g.m[a]);
+      t /= g.m[a];
+      if (ia > g.C[a]) sum += 2 + (ia - g.C[a] - 1) / g.C[a];
+    }
+    keep[(size_t)i] = sum <= g.p;
+  }
+  return keep;
+}
+
+long long active_dofs(const Handle* h, const Level& L) {
+  if (!trunk_level(h, L)) return L.g.N;
+  // count by the distribution of bubble-degree sums, axis by axis
+  const int p = L.g.p;
+  std::vector<long long> cnt(p + 1, 0);
+  cnt[0] = 1;
+  for (int a = 0; a < L.g.dim; ++a) {
+    std::vector<long long> nx(p + 1, 0);
+    for (int s = 0; s <= p; ++s) {
+      if (!cnt[s]) continue;
+      nx[s] += cnt[s] * (L.g.C[a] + 1);
+      for (int q = 2; s + q <= p; ++q) nx[s + q] += cnt[s] * L.g.C[a];
+    }
+    cnt.swap(nx);
+  }
+  long long m = 0;
+  for (long long c : cnt) m += c;
+  return m * L.g.nf;
+}
+
+// The right-hand side of a solve: the assembled load, or the caller's vector
+// with the entries of removed trunk modes taken as zero (copied to cb).
+const double* solve_rhs(Handle* h, const double* b_in) {
+  if (!b_in) return h->b;
+  if (!h->P.trunk) return b_in;
+  const LevelGeom& g = h->levels.back().g;
+  if (b_in != h->cb)
+    CK(cudaMemcpyAsync(h->cb, b_in, g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  launch_trunk_mask_vec(g, g.p, h->cb, h->s);
+  CKL();
+  return h->cb;
+}
+
 void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
                    const fcm_physics* phys, const fcm_solver_opts* opts) {
   if (!grid || !geom || !phys || !opts) throw Error(FCM_E_INVALID, "null descriptor");
@@ -416,10 +544,13 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   if (grid->p < 1 || grid->p > kMaxP) throw Error(FCM_E_INVALID, "p must be in [1, 8]");
   if (grid->overlay_levels > 0)
     throw Error(FCM_E_UNSUPPORTED, "multi-level hp overlays are not implemented");
+  if (grid->space != FCM_SPACE_TENSOR && grid->space != FCM_SPACE_TRUNK)
+    throw Error(FCM_E_INVALID, "unknown element space");
   Problem& P = h->P;
   std::memset(&P, 0, sizeof(P));
   P.dim = grid->dim;
   P.p = grid->p;
+  P.trunk = grid->space == FCM_SPACE_TRUNK ? 1 : 0;
   P.pde = phys->pde;
   if (P.pde != FCM_PDE_POISSON && P.pde != FCM_PDE_ELASTICITY)
     throw Error(FCM_E_INVALID, "unknown pde");
@@ -506,6 +637,8 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     throw Error(FCM_E_UNSUPPORTED, "patchwise additive Schwarz blocks are not implemented");
   if (opts->smoother != FCM_SMOOTHER_ELEMENTWISE && opts->smoother != FCM_SMOOTHER_JACOBI)
     throw Error(FCM_E_INVALID, "unknown smoother");
+  if (P.trunk && opts->smoother == FCM_SMOOTHER_JACOBI)
+    throw Error(FCM_E_UNSUPPORTED, "the Jacobi smoother is not built for trunk-space elements");
   h->smoother = opts->smoother;
   h->n_pre = opts->n_pre;
   h->n_post = opts->n_post;
@@ -594,7 +727,7 @@ void legendre_1d_matrices(int p, std::vector<double>& Kh, std::vector<double>& M
 void prepare_kron(Handle* h, Level& L) {
   const Problem& P = h->P;
   const int p = L.g.p, dim = L.g.dim, n = L.g.nloc;
-  if (P.pde != FCM_PDE_POISSON || L.is_h || !L.Kref || L.A64.sh.tl.ncells == 0 ||
+  if (P.pde != FCM_PDE_POISSON || P.trunk || L.is_h || !L.Kref || L.A64.sh.tl.ncells == 0 ||
       !kron_supported(dim, p))
     return;
   std::vector<double> Kh, Mh;
@@ -706,6 +839,10 @@ void build_smoother(Handle* h, Level& L) {
   const LevelGeom& g = L.g;
   const int n = g.nloc;
   const int nc = g.ncells;
+  // trunk-space blocks: the removed modes' rows and columns are zero; a unit
+  // diagonal there keeps the block factorisable, and zeroing them again in
+  // the inverse keeps the smoother's output zero on those modes
+  const bool trunk = trunk_level(h, L);
   std::vector<int> own_blocks;
   std::vector<std::pair<int, int>> shared;  // (sig, cell)
   std::vector<double> shared_s;
@@ -763,10 +900,12 @@ void build_smoother(Handle* h, Level& L) {
     inv = h->alloc<double>((size_t)nown * n * n);
     launch_block_assemble(g, nown, d_cells, src, inv, h->s);
     CKL();
+    if (trunk) launch_trunk_mask_mats(nown, g.dim, g.nf, g.p, g.p, true, inv, h->s);
     double* d_piv = h->alloc<double>(2 * (size_t)nown);
     int* d_info = h->alloc<int>(nown);
     launch_chol_inverse(nown, n, inv, d_piv, d_info, h->s);
     CKL();
+    if (trunk) launch_trunk_mask_mats(nown, g.dim, g.nf, g.p, g.p, false, inv, h->s);
     check_status(h, d_info, nown, "additive Schwarz block");
     piv.resize(2 * (size_t)nown);
     CK(cudaMemcpyAsync(piv.data(), d_piv, piv.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -804,9 +943,11 @@ void build_smoother(Handle* h, Level& L) {
     sinv = h->alloc<double>(sigs.size() * (size_t)n * n);
     launch_block_assemble(g, (int)sigs.size(), d_ref, src, sinv, h->s);
     CKL();
+    if (trunk) launch_trunk_mask_mats((long long)sigs.size(), g.dim, g.nf, g.p, g.p, true, sinv, h->s);
     int* d_info = h->alloc<int>(sigs.size());
     launch_chol_inverse((int)sigs.size(), n, sinv, nullptr, d_info, h->s);
     CKL();
+    if (trunk) launch_trunk_mask_mats((long long)sigs.size(), g.dim, g.nf, g.p, g.p, false, sinv, h->s);
     check_status(h, d_info, (int)sigs.size(), "reference Schwarz block");
   }
   build_shared<double>(h, L.M64.sh, mat_of, cells, scale, sinv, (int)sigs.size());
@@ -886,7 +1027,19 @@ void estimate_omega(Handle* h, Level& L, double omega_paper) {
   double* v = L.x;
   double* Av = L.r;
   double* w = L.b;
-  launch_fill_sin(v, N, h->s);
+  if (trunk_level(h, L)) {
+    // v_k = sin(k + 1) over the level's trunk DOFs numbered consecutively
+    // (the removed modes zero), the start vector of the tensor case
+    std::vector<double> hv((size_t)N, 0.0);
+    std::vector<unsigned char> keep = trunk_keep(L.g);
+    long long k = 0;
+    for (long long i = 0; i < N; ++i)
+      if (keep[(size_t)(i % L.g.M)]) hv[(size_t)i] = std::sin((double)(k++) + 1.0);
+    CK(cudaMemcpyAsync(v, hv.data(), N * sizeof(double), cudaMemcpyHostToDevice, h->s));
+    CK(cudaStreamSynchronize(h->s));
+  } else {
+    launch_fill_sin(v, N, h->s);
+  }
   CKL();
   double lam = 0.0;
   for (int it = 0; it < 40; ++it) {
@@ -950,6 +1103,9 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   int* scratch = h->alloc<int>((scratch_bytes + 3) / 4);
   launch_element_own(P, gauss, ne, d_elist, Ktop, bown, scratch, max_nodes, h->s);
   CKL();
+  // trunk space: remove the non-trunk modes from every cell matrix (and,
+  // below, from the load)
+  if (P.trunk && p >= 2) launch_trunk_mask_mats(ne, dim, nf, p, p, false, Ktop, h->s);
   double* KrefTop = Ktop + (size_t)(ne - 1) * n * n;
   // load vector
   double* Bcells = h->alloc<double>((size_t)ncell * n);
@@ -958,6 +1114,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   launch_scatter_rows((int)own_cells.size(), d_elist, bown, n, ncell, Bcells, h->s);
   h->b = h->alloc<double>(gt.N);
   launch_gather<double>(gt, GATHER_SET, Bcells, nullptr, h->b, 1.0, h->s);
+  if (P.trunk && p >= 2) launch_trunk_mask_vec(gt, p, h->b, h->s);
   CKL();
 
   g_stage = "level hierarchy";
@@ -979,6 +1136,10 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     double* Kref = h->alloc<double>((size_t)nl * nl);
     launch_extract_sub((int)own_cells.size(), dim, nf, p, pc, Ktop, Kown, h->s);
     launch_extract_sub(1, dim, nf, p, pc, KrefTop, Kref, h->s);
+    if (P.trunk && pc >= 2) {
+      launch_trunk_mask_mats((long long)own_cells.size(), dim, nf, pc, pc, false, Kown, h->s);
+      launch_trunk_mask_mats(1, dim, nf, pc, pc, false, Kref, h->s);
+    }
     CKL();
     build_operator(h, L, own_cells, Kown, Kref, sh_cells, sh_scale);
     prepare_kron(h, L);
@@ -1071,6 +1232,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   check_timeout(h);
   g_stage = "graph capture";
   h->g_vc64 = capture_vcycle<double>(h, &h->vc_nodes64, 0);
+  h->vc_bytes64 = vcycle_bytes(h, (int)h->levels.size() - 1, 0, true);
   if (h->mixed) {
     // The mixed V-cycle runs the finest level in FP64 when FP32 vectors
     // there would cost CG iterations: a single-level hierarchy (the V-cycle
@@ -1081,6 +1243,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     const int top = (int)h->levels.size() - 1;
     if (top == 0 || h->levels[top].max_cond >= kFineFp64Cond) h->top64 = top;
     h->g_vc32 = capture_vcycle<float>(h, &h->vc_nodes32, h->top64);
+    h->vc_bytes32 = vcycle_bytes(h, top, h->top64, top >= h->top64);
   }
   CK(cudaStreamSynchronize(h->s));
 }
@@ -1096,16 +1259,19 @@ void run_vcycle(Handle* h, const double* r, double* z, int prec) {
     launch_copy_f2d(T.x32, z, T.g.N, h->s);
     CKL();
     h->launches += 2 + h->vc_nodes32;
+    h->bytes += h->vc_bytes32 + 2 * T.g.N * (8 + 4);
   } else if (prec == FCM_MIXED) {  // finest level in FP64
     if (!h->mixed) throw Error(FCM_E_INVALID, "mixed precision data not built (build_mixed = 0)");
     if (r != T.b) CK(cudaMemcpyAsync(T.b, r, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     CK(cudaGraphLaunch(h->g_vc32, h->s));
     h->launches += h->vc_nodes32;
+    h->bytes += h->vc_bytes32 + 4 * T.g.N * 8;
     if (z != T.x) CK(cudaMemcpyAsync(z, T.x, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   } else {
     if (r != T.b) CK(cudaMemcpyAsync(T.b, r, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
     CK(cudaGraphLaunch(h->g_vc64, h->s));
     h->launches += h->vc_nodes64;
+    h->bytes += h->vc_bytes64 + 4 * T.g.N * 8;
     if (z != T.x) CK(cudaMemcpyAsync(z, T.x, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   }
 }
@@ -1126,9 +1292,10 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   g_stage = "solve";
   double t0 = now_ms();
   h->launches = 0;
+  h->bytes = 0;
   Level& T = h->levels.back();
   const long long N = T.g.N;
-  const double* b = b_in ? b_in : h->b;
+  const double* b = solve_rhs(h, b_in);
   const bool flexible = prec == FCM_MIXED;
   if (prec == FCM_MIXED && !h->mixed)
     throw Error(FCM_E_INVALID, "mixed precision data not built (build_mixed = 0)");
@@ -1139,6 +1306,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   double* q = h->cq;
   CK(cudaMemsetAsync(x, 0, N * sizeof(double), h->s));
   CK(cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  h->bytes += 3 * N * 8;
   double bb = host_dot(h, b, b, N);
   if (!std::isfinite(bb)) throw Error(FCM_E_INVALID, "right-hand side is not finite");
   double nb = std::sqrt(bb);
@@ -1156,6 +1324,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   launch_cg_init(r, z, N, h->part, p, h->sc, h->s);
   CKL();
   h->launches += 2;
+  h->bytes += 5 * N * 8;
   int k = 0;
   double rel = 1.0;
   fcm_status st = FCM_E_NOT_CONVERGED;
@@ -1167,6 +1336,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
     launch_reduce(h->part + kDotBlocks, kDotBlocks, h->d_scalar, h->s);
     CKL();
     h->launches += 3;
+    h->bytes += 8 * N * 8;  // p.q; x, r updated from p, q
     CK(cudaMemcpyAsync(h->h_scalar, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
     double rr = h->h_scalar[0];
@@ -1185,9 +1355,12 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
         break;
       }
       CK(cudaMemcpyAsync(r, h->cz_old, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+      h->bytes += 2 * N * 8;
     }
-    if (flexible)
+    if (flexible) {
       CK(cudaMemcpyAsync(h->cz_old, z, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+      h->bytes += 2 * N * 8;
+    }
     precondition(h, r, z, prec, method);
     if (flexible)
       launch_dot2_partials(r, z, h->cz_old, N, h->part, h->s);
@@ -1196,6 +1369,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
     launch_cg_update_p(p, z, N, h->part, flexible ? 1 : 0, h->sc, h->s);
     CKL();
     h->launches += 3;
+    h->bytes += (flexible ? 6 : 5) * N * 8;  // r.z (and r.z_old); p from z
   }
   CGScalars sc;
   CK(cudaMemcpyAsync(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, h->s));
@@ -1208,6 +1382,7 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   }
   inf.iters = k;
   inf.kernel_launches = h->launches;
+  inf.bytes_moved_est = h->bytes;
   inf.relres_recursive = rel;
   inf.solve_ms = now_ms() - t0;
   if (info) *info = inf;
@@ -1225,9 +1400,10 @@ fcm_status mg_impl(Handle* h, const double* b_in, double* x, double rtol, int ma
   g_stage = "solve";
   double t0 = now_ms();
   h->launches = 0;
+  h->bytes = 0;
   Level& T = h->levels.back();
   const long long N = T.g.N;
-  const double* b = b_in ? b_in : h->b;
+  const double* b = solve_rhs(h, b_in);
   if (prec == FCM_MIXED && !h->mixed)
     throw Error(FCM_E_INVALID, "mixed precision data not built (build_mixed = 0)");
   if (!(rtol > 0.0) || maxit < 0) throw Error(FCM_E_INVALID, "rtol must be > 0, maxit >= 0");
@@ -1235,6 +1411,7 @@ fcm_status mg_impl(Handle* h, const double* b_in, double* x, double rtol, int ma
   double* z = h->ctmp;
   CK(cudaMemsetAsync(x, 0, N * sizeof(double), h->s));
   CK(cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  h->bytes += 3 * N * 8;
   const double nb = std::sqrt(host_dot(h, b, b, N));
   if (!std::isfinite(nb)) throw Error(FCM_E_INVALID, "right-hand side is not finite");
   fcm_info inf;
@@ -1252,6 +1429,7 @@ fcm_status mg_impl(Handle* h, const double* b_in, double* x, double rtol, int ma
     ++k;
     run_vcycle(h, r, z, prec);
     launch_axpby(1.0, z, 1.0, x, N, h->s);
+    h->bytes += 3 * N * 8;
     apply_A64(h, T, x, r, GATHER_RESID, b);
     h->launches += 1;
     const double nn = std::sqrt(host_dot(h, r, r, N));
@@ -1263,6 +1441,7 @@ fcm_status mg_impl(Handle* h, const double* b_in, double* x, double rtol, int ma
   inf.relres_recursive = nb > 0.0 ? nr / nb : 0.0;
   inf.relres_true = inf.relres_recursive;
   inf.kernel_launches = h->launches;
+  inf.bytes_moved_est = h->bytes;
   inf.solve_ms = now_ms() - t0;
   if (info) *info = inf;
   if (st == FCM_E_NOT_CONVERGED)
@@ -1457,6 +1636,7 @@ fcm_status fcm_level_info_get(const fcm_handle* h, int level, fcm_level_info* in
   info->p = L.g.p;
   info->is_h_level = L.is_h ? 1 : 0;
   info->ndofs = L.g.N;
+  info->ndofs_active = active_dofs(h, L);
   info->nloc = L.g.nloc;
   info->n_own_cells = L.n_own_cells;
   info->n_own_blocks = L.n_own_blocks;
@@ -1641,42 +1821,7 @@ fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, lon
     g_last_error = "invalid argument";
     return FCM_E_INVALID;
   }
-  const Level& L = h->levels[level];
-  const long long n = L.g.nloc, nc = L.g.ncells;
-  const long long sv = prec == FCM_FP64 ? 8 : 4;
-  long long b = 0;
-  if (which == 2) {
-    b = nc * n * sv + 2 * L.g.N * sv + L.g.N * sv;  // Y, b, r(out)
-  } else if (which >= 5) {
-    // shared tiles: the matrices once, every tile cell's coefficients and results
-    const SharedSet<double>& s64 = which == 5 ? L.A64.sh : L.M64.sh;
-    b = (long long)s64.nmats * n * n * sv + 2 * (long long)s64.tl.ncells * n * sv;
-  } else if (which >= 3) {
-    const OpData<double>& d64 = which == 3 ? L.A64 : L.M64;
-    const OpData<float>& d32 = which == 3 ? L.A32 : L.M32;
-    const long long ld = padded_ld((int)n);
-    long long mats, cells;
-    if (prec == FCM_FP64) {
-      mats = (long long)d64.own.n * n * ld * 8;
-      cells = d64.own.n;
-    } else {
-      mats = (long long)d32.own.n * n * ld * 4 + (long long)d32.own_x.n * n * ld * 8;
-      cells = (long long)d32.own.n + d32.own_x.n;
-    }
-    b = mats + 2 * cells * n * sv;  // stored matrices, their coefficients and results
-  } else {
-    const OpData<double>& d64 = which == 0 ? L.A64 : L.M64;
-    const OpData<float>& d32 = which == 0 ? L.A32 : L.M32;
-    const long long ld = padded_ld((int)n);
-    long long mats;
-    if (prec == FCM_FP64)
-      mats = (long long)d64.own.n * n * ld * 8 + (long long)d64.sh.nmats * n * n * 8;
-    else
-      mats = (long long)d32.own.n * n * ld * 4 + (long long)d32.own_x.n * n * ld * 8 +
-             (long long)d32.sh.nmats * n * n * 4;
-    b = mats + 2 * nc * n * sv;  // gathered coefficients + per-cell results
-  }
-  *bytes = b;
+  *bytes = op_bytes(h->levels[level], which, prec);
   return FCM_OK;
 }
 

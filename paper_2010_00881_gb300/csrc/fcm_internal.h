@@ -100,6 +100,7 @@ struct Problem {
   int traction_face;
   double traction[3];
   int quad_depth;
+  int trunk;                    // 1: trunk-space elements (non-trunk modes removed)
 };
 
 // Cell classes.
@@ -202,6 +203,14 @@ void launch_cell_diag(const LevelGeom& g, const OpData<double>& op, const int* s
 template <typename TV>
 void launch_jacobi(long long N, const TV* dinv, const TV* r, TV* x, double w, bool init,
                    cudaStream_t s);
+
+// Trunk space of degree q on a level of degree p: zero the rows and columns
+// of the non-trunk local modes of `count` canonical n x n matrices (with a
+// unit diagonal there if unit_diag, so that a block stays invertible), or
+// zero the non-trunk entries of a level vector.
+void launch_trunk_mask_mats(long long count, int dim, int nf, int p, int q, bool unit_diag,
+                            double* mats, cudaStream_t s);
+void launch_trunk_mask_vec(const LevelGeom& g, int q, double* v, cudaStream_t s);
 
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };

@@ -386,6 +386,8 @@ void validate(const fcm_grid* g, const fcm_geometry* geom) {
   if (g->p < 1 || g->p > fcm::kMaxP) throw Invalid{"fcm_mlhp_create: p outside [1, 8]"};
   if (g->overlay_levels < 0 || g->overlay_levels > kMaxOverlay)
     throw Invalid{"fcm_mlhp_create: overlay_levels outside [0, 10]"};
+  if (g->space != FCM_SPACE_TENSOR)
+    throw Invalid{"fcm_mlhp_create: the overlay topology is built for tensor-product elements"};
   if (g->overlay_p != 0 && g->overlay_p != g->p)
     throw Invalid{"fcm_mlhp_create: overlays carry the base degree (overlay_p 0 or p)"};
   for (int a = 0; a < g->dim; ++a) {

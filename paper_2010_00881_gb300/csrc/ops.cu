@@ -2377,6 +2377,66 @@ template void launch_jacobi<double>(long long, const double*, const double*, dou
 template void launch_jacobi<float>(long long, const float*, const float*, float*, double, bool,
                                    cudaStream_t);
 
+// Trunk space (the paper's 3D elements, Sec. 4.3): of the (p+1)^d tensor
+// modes of a cell, the trunk space of degree q keeps those whose bubble
+// degrees (local mode j >= 2 has degree j) sum to at most q.  The library
+// keeps the tensor layout and removes the other modes from the system: their
+// rows and columns of every cell matrix and block inverse are zero and their
+// load entries zero, so iterates and corrections stay zero on them.
+__device__ __forceinline__ bool trunk_masked_local(int l, int dim, int nloc_s, int P, int q) {
+  int s = l % nloc_s, sum = 0;
+  for (int a = 0; a < dim; ++a) {
+    const int j = s % P;
+    s /= P;
+    if (j >= 2) sum += j;
+  }
+  return sum > q;
+}
+
+__global__ void trunk_mask_mats_kernel(long long count, int dim, int nf, int p, int q, int unit,
+                                       double* mats) {
+  const int P = p + 1;
+  int nloc_s = 1;
+  for (int a = 0; a < dim; ++a) nloc_s *= P;
+  const int n = nf * nloc_s;
+  const long long tot = count * n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int rc = (int)(e % ((long long)n * n));
+    const int r = rc / n, c = rc - r * n;
+    const bool mr = trunk_masked_local(r, dim, nloc_s, P, q);
+    const bool mc = trunk_masked_local(c, dim, nloc_s, P, q);
+    if (mr || mc) mats[e] = (unit && r == c) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void trunk_mask_vec_kernel(LevelGeom g, int q, double* v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long t = i % g.M;
+    int sum = 0;
+    for (int a = 0; a < g.dim; ++a) {
+      const int ia = (int)(t % g.m[a]);
+      t /= g.m[a];
+      if (ia > g.C[a]) sum += 2 + (ia - g.C[a] - 1) / g.C[a];
+    }
+    if (sum > q) v[i] = 0.0;
+  }
+}
+
+void launch_trunk_mask_mats(long long count, int dim, int nf, int p, int q, bool unit_diag,
+                            double* mats, cudaStream_t s) {
+  if (count == 0) return;
+  int n = nf;
+  for (int a = 0; a < dim; ++a) n *= p + 1;
+  trunk_mask_mats_kernel<<<grid_for(count * n * n), 256, 0, s>>>(count, dim, nf, p, q,
+                                                                 unit_diag ? 1 : 0, mats);
+}
+
+void launch_trunk_mask_vec(const LevelGeom& g, int q, double* v, cudaStream_t s) {
+  trunk_mask_vec_kernel<<<grid_for(g.N), 256, 0, s>>>(g, q, v);
+}
+
 void launch_repack(int count, int n, int ld, const double* src, const int* sel, int kind,
                    void* dst, cudaStream_t s) {
   if (count == 0) return;

@@ -26,6 +26,7 @@ GVAL = {"zero": 0, "sin3": 1, "square_mms": 2, "popcorn": 3}
 OP_APPLY, OP_SMOOTHER, OP_RESTRICT, OP_PROLONG, OP_COARSE = 0, 1, 2, 3, 4
 SMOOTHER = {"elementwise": 0, "patchwise": 1, "jacobi": 2}
 METHOD_CG_MG, METHOD_MG, METHOD_CG_AS = 0, 1, 2
+SPACE_TENSOR, SPACE_TRUNK = 0, 1
 
 EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_num_levels",
            "fcm_level_info_get", "fcm_level_op", "fcm_cell_classes", "fcm_pcg_solve",
@@ -41,7 +42,7 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
 class fcm_grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("cells", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("p", C.c_int), ("overlay_levels", C.c_int),
-                ("overlay_p", C.c_int)]
+                ("overlay_p", C.c_int), ("space", C.c_int)]
 
 
 class fcm_geometry(C.Structure):
@@ -65,7 +66,7 @@ class fcm_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("relres_recursive", C.c_double),
                 ("relres_true", C.c_double), ("setup_ms", C.c_double),
                 ("solve_ms", C.c_double), ("ndofs", C.c_longlong),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("bytes_moved_est", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,7 +77,8 @@ class fcm_level_info(C.Structure):
                 ("ndofs", C.c_longlong), ("nloc", C.c_int), ("n_own_cells", C.c_int),
                 ("n_own_blocks", C.c_int), ("n_fp64_blocks", C.c_int), ("omega", C.c_double),
                 ("lambda_est", C.c_double), ("max_block_cond", C.c_double),
-                ("fp64_in_mixed", C.c_int), ("kron_operator", C.c_int)]
+                ("fp64_in_mixed", C.c_int), ("kron_operator", C.c_int),
+                ("ndofs_active", C.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -243,8 +245,8 @@ def descriptors(prob: dict, build_mixed: bool = True):
     ValueError for problem features the library has no descriptor for
     (trunk-space elements, removal of fictitious cells, geometry kinds or
     smoothers it does not know) instead of dropping them."""
-    if prob.get("space", "tensor") != "tensor" or prob.get("drop_outside"):
-        raise ValueError("the library discretises with the full tensor-product space on all cells")
+    if prob.get("space", "tensor") not in ("tensor", "trunk") or prob.get("drop_outside"):
+        raise ValueError("the library discretises all cells with tensor-product or trunk elements")
     if prob["geometry"]["kind"] not in GEOM:
         raise ValueError(f"geometry kind {prob['geometry']['kind']!r} has no library descriptor")
     if prob.get("smoother", "elementwise") not in SMOOTHER:
@@ -258,6 +260,7 @@ def descriptors(prob: dict, build_mixed: bool = True):
         g.hi[a] = prob["hi"][a] if a < d else 0.0
     g.p = prob["p"]
     g.overlay_levels = prob.get("overlay_levels", 0)
+    g.space = SPACE_TRUNK if prob.get("space", "tensor") == "trunk" else SPACE_TENSOR
     geo = prob["geometry"]
     kind = geo["kind"]
     if kind == "ball":

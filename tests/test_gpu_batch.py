@@ -48,17 +48,52 @@ def test_batch_equals_individual_solves(batch, prec):
         s.close()
 
 
-def test_batch_instance_matches_oracle():
+def _oracle_batch_problems():
+    out = []
+    for i, p in enumerate((2, 3, 4, 2)):
+        prob = fi.batch_instance(10 + i)
+        c = 5 + (i % 2)
+        prob["cells"] = (c, c, c)
+        prob["p"] = p
+        out.append(prob)
+    return out
+
+
+@pytest.fixture(scope="module")
+def oracle_batch():
+    """Four instances of the batch workload (rotated ellipsoids, p = 2..4,
+    5 or 6 cells per axis) with their oracle hierarchies and solutions."""
     from oracle import multigrid as mg
-    prob = small_batch(2)[1]
-    H = mg.Hierarchy(prob)
-    xo, ko, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=1e-8)
-    b = F.Batch([prob], threads=1)
-    xs, infos = b.pcg(rtol=1e-8, prec=FCM_FP64)
-    assert abs(infos[0]["iters"] - ko) <= 1
-    e = xs[0].cpu().numpy() - xo
-    assert np.sqrt(e @ (H.A @ e)) / np.sqrt(xo @ (H.A @ xo)) <= 1e-7
+    probs = _oracle_batch_problems()
+    Hs = [mg.Hierarchy(prob) for prob in probs]
+    sols = [mg.pcg(H.A, H.b, H.vcycle, rtol=1e-8) for H in Hs]
+    b = F.Batch(probs, threads=2)
+    yield probs, Hs, sols, b
     b.close()
+
+
+@pytest.mark.parametrize("prec", [FCM_FP64, FCM_MIXED])
+def test_batch_matches_oracle(oracle_batch, prec):
+    """Every instance of a batched solve takes the oracle's iteration count
+    +-1 and meets the tolerance in the oracle's own residual b - A x."""
+    import scipy.sparse.linalg as spla
+    probs, Hs, sols, b = oracle_batch
+    xs, infos = b.pcg(rtol=1e-8, prec=prec)
+    for i, (H, (xo, ko, _), x, info) in enumerate(zip(Hs, sols, xs, infos)):
+        x = x.cpu().numpy()
+        assert abs(info["iters"] - ko) <= 1, (i, prec, info["iters"], ko)
+        assert np.linalg.norm(H.b - H.A @ x) / np.linalg.norm(H.b) <= 1.01e-8, i
+        # two Krylov paths to residual 1e-8: ||x - xo||_A is bounded by the
+        # residuals' A^-1 norms (slack 1.5)
+        lu = spla.splu(H.A.tocsc())
+
+        def rnorm_ainv(v):
+            r = H.b - H.A @ v
+            return np.sqrt(abs(r @ lu.solve(r)))
+
+        e = x - xo
+        ea = np.sqrt(max(e @ (H.A @ e), 0.0))
+        assert ea <= 1.5 * (rnorm_ainv(x) + rnorm_ainv(xo)) + 1e-300, (i, prec)
 
 
 def test_batch_reports_failing_instance():
