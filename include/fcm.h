@@ -98,11 +98,18 @@ typedef struct {
  *              psi = |x| - r0 - sum_k A exp(-|x - c_k|^2 / sigma^2)
  * Cell and sub-cell classification: exact nearest/farthest distances for
  * balls and voids, a 5^d lattice sign test for the ellipsoid and the
- * popcorn. */
+ * popcorn.
+ * complement: 0 keeps Omega_phys = {psi <= 0}; 1 makes the other side
+ * physical, Omega_phys = {psi >= 0} (a hole instead of an inclusion): psi
+ * is negated and the box classification swaps inside and outside (cut
+ * stays), so the cut cells and their space trees are the same.  The field
+ * is last and zero keeps the usual side, so zero-initialised descriptors
+ * are unaffected. */
 typedef struct {
   int kind;
   int n_params;
   const double* params;
+  int complement;
 } fcm_geometry;
 
 /* Physics of Eq. (weakform).  Poisson: kappa scales the stiffness.
@@ -195,6 +202,9 @@ fcm_status fcm_setup(const fcm_grid* grid, const fcm_geometry* geom,
                      const fcm_physics* phys, const fcm_solver_opts* opts,
                      void* stream, fcm_handle** out);
 
+/* Number of DOFs of the finest level (the length of every solve vector):
+ * the hierarchical tensor-product layout below, nf prod_a (C_a p + 1)
+ * (Sec. 2.1; with trunk elements the removed modes keep their slots). */
 fcm_status fcm_ndofs(const fcm_handle* h, long long* n);
 
 /* The DOF layout above, for callers that hold vectors in another order
@@ -298,12 +308,16 @@ fcm_status fcm_vcycle(fcm_handle* h, const double* r_dev, double* z_dev, int pre
  * block inverses, no omega); op 2: y = R_l x (to level l-1); op 3: y = R_l^T x
  * (from level l-1); op 4: y = A_0^{-1} x (level 0 only).  Level 0 is the
  * coarsest, fcm_num_levels()-1 the finest.  Vectors have that level's size. */
+/* fcm_num_levels: levels of the hierarchy of Sec. 3.2 (Fig. hpmultigrid):
+ * the p-levels p, p-1, ..., 1 on the finest grid, then the nested Q1
+ * h-levels of the Remark of Sec. 3.2 down to the coarse grid. */
 fcm_status fcm_num_levels(const fcm_handle* h, int* n);
 fcm_status fcm_level_info_get(const fcm_handle* h, int level, fcm_level_info* info);
 fcm_status fcm_level_op(fcm_handle* h, int level, int op, const double* x_dev,
                         double* y_dev);
 
-/* Cell classes of the finest grid (0 inside, 1 outside, 2 cut), linear cell
+/* Cell classes of the finest grid (0 inside, 1 outside, 2 cut: Omega_phys,
+ * Omega_fict and the cells the boundary crosses, Sec. 2.1), linear cell
  * order (x fastest), into a host array of prod(cells) bytes. */
 fcm_status fcm_cell_classes(const fcm_handle* h, signed char* cls_host);
 
@@ -337,8 +351,11 @@ fcm_status fcm_solve(fcm_handle* h, int method, const double* b_dev, double* x_d
 fcm_status fcm_pcg_solve_host(fcm_handle* h, const double* b_host, double* x_host,
                               double rtol, int maxit, int prec, fcm_info* info);
 
-/* Benchmark hook: replay one kernel of level `level` `reps` times on the
- * handle's stream and return its mean duration from CUDA events (ms).
+/* Benchmark hook (no counterpart in the paper, which reports no timings of
+ * its own kernels): replay one kernel of level `level` `reps` times on the
+ * handle's stream and return its mean duration from CUDA events (ms); the
+ * kernels are the level operations of Algorithm 1 (residual and smoothing
+ * steps, Eq. AdditiveSchwarz).
  * which 0: operator cell kernels (y_c = K_c x_c over all cells: stored and
  * shared parts side by side, as in the V-cycle), 1: smoother cell kernels
  * (A_i^{-1} over all blocks, likewise), 2: the DOF gather that follows
@@ -358,9 +375,10 @@ fcm_status fcm_profile_op(fcm_handle* h, int level, int which, int prec, int rep
  * and frees a small device buffer and a stream; takes about 0.1 s. */
 fcm_status fcm_measure_fma_peak(int prec, double* tflops);
 
-/* Bytes the level kernel `which` (as in fcm_profile_op) must move at least
- * once per launch: stored cell matrices or block inverses, one read of
- * every input coefficient per cell and one write of every per-cell result. */
+/* Benchmark hook (no counterpart in the paper): bytes the level kernel
+ * `which` (as in fcm_profile_op) must move at least once per launch:
+ * stored cell matrices or block inverses, one read of every input
+ * coefficient per cell and one write of every per-cell result. */
 fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec,
                         long long* bytes);
 

@@ -17,6 +17,13 @@ Kinds:
   rotated_square  psi = max(|x'|, |y'|) - a, (x', y') = R(-psi_angle)(x - c)
                   (the rotated square of Sec. 4.1.2)
 
+complement (optional, default False): the physical domain is the other
+side, Omega_phys = {psi >= 0} (a hole instead of an inclusion; the paper's
+level sets mark either side, e.g. the voids of Sec. 4.3 are fictitious
+balls).  The reading: psi is negated exactly, and the box classification
+swaps INSIDE and OUTSIDE (CUT stays), so the space-tree quadrature visits
+the same cut cells and leaves with the indicator alpha swapped.
+
 Box classification (the paper leaves the cut test open; this is the
 reading): balls and voids use exact nearest/farthest point distances, the
 ellipsoid and the popcorn a sign test of psi on a 5^d lattice including the
@@ -33,7 +40,23 @@ INSIDE, OUTSIDE, CUT = 0, 1, 2
 
 
 def levelset(geom: dict, x: np.ndarray) -> np.ndarray:
-    """psi at points x of shape (..., d)."""
+    """psi at points x of shape (..., d) (negated for a complement domain)."""
+    v = _levelset_kind(geom, x)
+    return -v if geom.get("complement") else v
+
+
+def _swap(cls):
+    """INSIDE <-> OUTSIDE, CUT kept (a class or an array of classes)."""
+    if np.ndim(cls) == 0:
+        return OUTSIDE if cls == INSIDE else (INSIDE if cls == OUTSIDE else cls)
+    out = cls.copy()
+    out[cls == INSIDE] = OUTSIDE
+    out[cls == OUTSIDE] = INSIDE
+    return out
+
+
+def _levelset_kind(geom: dict, x: np.ndarray) -> np.ndarray:
+    """psi of the geometry kind at points x of shape (..., d)."""
     x = np.asarray(x, dtype=np.float64)
     d = x.shape[-1]
     kind = geom["kind"]
@@ -108,6 +131,12 @@ def _ball_dist2(lo, hi, c):
 
 def classify_box(geom: dict, lo, hi) -> int:
     """INSIDE (all physical), OUTSIDE (all fictitious) or CUT."""
+    c = _classify_box_kind(geom, lo, hi)
+    return _swap(c) if geom.get("complement") else c
+
+
+def _classify_box_kind(geom: dict, lo, hi) -> int:
+    """classify_box for the kind's own domain {psi <= 0}."""
     kind = geom["kind"]
     if kind == "none":
         return INSIDE
@@ -139,7 +168,7 @@ def classify_box(geom: dict, lo, hi) -> int:
                 for kx in range(5):
                     k = (kx, ky, kz)
                     pts.append([lo[a] + ts[k[a]] * (hi[a] - lo[a]) for a in range(d)])
-        psi = levelset(geom, np.array(pts))
+        psi = _levelset_kind(geom, np.array(pts))
         if np.all(psi <= 0.0):
             return INSIDE
         if np.all(psi > 0.0):
@@ -182,6 +211,13 @@ def _classify_grid_voids(geom, lo, hi, cells):
 
 
 def classify_grid(geom: dict, lo, hi, cells) -> np.ndarray:
+    """Classes of all cells of a 3D grid (see _classify_grid_kind), swapped
+    for a complement domain."""
+    c = _classify_grid_kind(geom, lo, hi, cells)
+    return _swap(c) if geom.get("complement") else c
+
+
+def _classify_grid_kind(geom: dict, lo, hi, cells) -> np.ndarray:
     """Classes of all cells of a 3D grid (linear order, x fastest): the test
     of ``classify_box`` evaluated for every cell at once.  Lattice-tested
     kinds use the lattice points lo_c + t (hi_c - lo_c) with the cell corners
@@ -207,7 +243,7 @@ def classify_grid(geom: dict, lo, hi, cells) -> np.ndarray:
                 X[..., 0] = axes[0][kx][None, None, :]
                 X[..., 1] = axes[1][ky][None, :, None]
                 X[..., 2] = axes[2][kz][:, None, None]
-                v = levelset(geom, X)
+                v = _levelset_kind(geom, X)
                 any_in |= v <= 0.0
                 any_out |= v > 0.0
     cls = np.full(shape, CUT, dtype=np.int8)

@@ -81,6 +81,10 @@ struct Level {
   float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr, *Y32 = nullptr;
   // coarsest level: inverse Cholesky factor
   double* Linv = nullptr;
+  // node-centric operator and smoother (levels with one mode per node and
+  // field, see launch_node); ok = false elsewhere
+  NodeSet<double> nA64, nM64;
+  NodeSet<float> nA32, nM32;
   FineCellSource source() const {
     FineCellSource s;
     s.own_index = d_own_index;
@@ -362,6 +366,8 @@ struct VC<double> {
   static const OpData<double>& A(Level& L) { return L.A64; }
   static const OpData<double>& M(Level& L) { return L.M64; }
   static const double* dinv(Level& L) { return L.dinv64; }
+  static const NodeSet<double>& nA(Level& L) { return L.nA64; }
+  static const NodeSet<double>& nM(Level& L) { return L.nM64; }
 };
 template <>
 struct VC<float> {
@@ -372,6 +378,8 @@ struct VC<float> {
   static const OpData<float>& A(Level& L) { return L.A32; }
   static const OpData<float>& M(Level& L) { return L.M32; }
   static const float* dinv(Level& L) { return L.dinv32; }
+  static const NodeSet<float>& nA(Level& L) { return L.nA32; }
+  static const NodeSet<float>& nM(Level& L) { return L.nM32; }
 };
 
 // Levels l >= top64 are recorded in FP64 and the levels below in FP32: at
@@ -393,30 +401,36 @@ void record_vcycle(Handle* h, int l, int top64) {
   TV *x = V::x(L), *b = V::b(L), *r = V::r(L), *Y = V::Y(L);
   const bool jac = h->smoother == FCM_SMOOTHER_JACOBI;
   const TV* dinv = V::dinv(L);
+  // one operator or smoother application with its DOF gather: the
+  // node-centric pass where the level has one (p = 1 and Q1 levels), else
+  // the cell kernels and the gather
+  auto apply = [&](bool smoother, const TV* in, const TV* bb, TV* out, double wt, int mode) {
+    const NodeSet<TV>& nd = smoother ? V::nM(L) : V::nA(L);
+    if (nd.ok) {
+      launch_node<TV>(L.g, nd, in, bb, out, wt, mode, s);
+    } else {
+      launch_cell_op<TV>(L.g, smoother ? V::M(L) : V::A(L), in, Y, s, &h->side);
+      launch_gather<TV>(L.g, mode, Y, bb, out, wt, s);
+    }
+  };
   if (h->n_pre == 0) CK(cudaMemsetAsync(x, 0, L.g.N * sizeof(TV), s));
   for (int k = 0; k < h->n_pre; ++k) {
     if (k == 0) {
-      if (jac) {
+      if (jac)
         launch_jacobi<TV>(L.g.N, dinv, b, x, w, true, s);
-      } else {
-        launch_cell_op<TV>(L.g, V::M(L), b, Y, s, &h->side);
-        launch_gather<TV>(L.g, GATHER_SCALE, Y, nullptr, x, w, s);
-      }
+      else
+        apply(true, b, nullptr, x, w, GATHER_SCALE);
     } else {
-      launch_cell_op<TV>(L.g, V::A(L), x, Y, s, &h->side);
-      launch_gather<TV>(L.g, GATHER_RESID, Y, b, r, 1.0, s);
-      if (jac) {
+      apply(false, x, b, r, 1.0, GATHER_RESID);
+      if (jac)
         launch_jacobi<TV>(L.g.N, dinv, r, x, w, false, s);
-      } else {
-        launch_cell_op<TV>(L.g, V::M(L), r, Y, s, &h->side);
-        launch_gather<TV>(L.g, GATHER_ADD, Y, nullptr, x, w, s);
-      }
+      else
+        apply(true, r, nullptr, x, w, GATHER_ADD);
     }
   }
   const TV* rr = b;
   if (h->n_pre > 0) {
-    launch_cell_op<TV>(L.g, V::A(L), x, Y, s, &h->side);
-    launch_gather<TV>(L.g, GATHER_RESID, Y, b, r, 1.0, s);
+    apply(false, x, b, r, 1.0, GATHER_RESID);
     rr = r;
   }
   if (Lc.is_h)
@@ -435,14 +449,11 @@ void record_vcycle(Handle* h, int l, int top64) {
   else
     launch_p_prolong_add<TV>(Lc.g, L.g, V::x(Lc), x, s);
   for (int k = 0; k < h->n_post; ++k) {
-    launch_cell_op<TV>(L.g, V::A(L), x, Y, s, &h->side);
-    launch_gather<TV>(L.g, GATHER_RESID, Y, b, r, 1.0, s);
-    if (jac) {
+    apply(false, x, b, r, 1.0, GATHER_RESID);
+    if (jac)
       launch_jacobi<TV>(L.g.N, dinv, r, x, w, false, s);
-    } else {
-      launch_cell_op<TV>(L.g, V::M(L), r, Y, s, &h->side);
-      launch_gather<TV>(L.g, GATHER_ADD, Y, nullptr, x, w, s);
-    }
+    else
+      apply(true, r, nullptr, x, w, GATHER_ADD);
   }
   CKL();
 }
@@ -477,6 +488,33 @@ cudaGraphExec_t capture_vcycle(Handle* h, long long* nodes, int top64) {
   CK(cudaGraphInstantiate(&ex, g, 0));
   CK(cudaGraphDestroy(g));
   return ex;
+}
+
+// ---------------------------------------------------------------------------
+// Levels whose operations run node-centric (launch_node): one mode per node
+// and field (p = 1 and the Q1 h-levels), scalar or vector fields.
+bool node_level(const Level& L) {
+  const LevelGeom& g = L.g;
+  const bool shape = (g.dim == 3 && (g.nf == 1 || g.nf == 3)) || (g.dim == 2 && (g.nf == 1 || g.nf == 2));
+  return (L.is_h || g.p == 1) && shape && g.nloc == (g.nf << g.dim);
+}
+
+// Node set from per-cell codes, shared matrix ids and scales (host arrays).
+template <typename TV>
+NodeSet<TV> make_node_set(Handle* h, const std::vector<int>& code, const std::vector<int>& mat,
+                          const std::vector<double>& scale, int ld, const void* m1,
+                          const void* m2, const TV* sh) {
+  NodeSet<TV> S;
+  S.ok = true;
+  S.ld = ld;
+  S.code = h->upload(code);
+  S.mat = h->upload(mat);
+  std::vector<TV> sc(scale.begin(), scale.end());
+  S.scale = h->upload(sc);
+  S.m1 = m1;
+  S.m2 = m2;
+  S.sh = sh;
+  return S;
 }
 
 // ---------------------------------------------------------------------------
@@ -584,6 +622,9 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
       throw Error(FCM_E_UNSUPPORTED, "problem too large: DOFs and cells x local DOFs must be < 2^31");
   }
   P.geom_kind = geom->kind;
+  if (geom->complement != 0 && geom->complement != 1)
+    throw Error(FCM_E_INVALID, "geometry complement must be 0 or 1");
+  P.geom_complement = geom->complement;
   if (geom->kind < FCM_GEOM_NONE || geom->kind > FCM_GEOM_POPCORN)
     throw Error(FCM_E_INVALID, "unknown geometry kind");
   int need = geom->kind == FCM_GEOM_BALL ? P.dim + 1
@@ -727,8 +768,11 @@ void legendre_1d_matrices(int p, std::vector<double>& Kh, std::vector<double>& M
 void prepare_kron(Handle* h, Level& L) {
   const Problem& P = h->P;
   const int p = L.g.p, dim = L.g.dim, n = L.g.nloc;
+  // only where the factorised product needs fewer FMAs than the dense one
+  // (7 P^4 against P^6 in 3D, 4 P^3 against P^4 in 2D, P = p + 1: p >= 2 in
+  // 3D, p >= 4 in 2D)
   if (P.pde != FCM_PDE_POISSON || P.trunk || L.is_h || !L.Kref || L.A64.sh.tl.ncells == 0 ||
-      !kron_supported(dim, p))
+      !kron_supported(dim, p) || (dim == 3 && p < 2) || (dim == 2 && p < 4))
     return;
   std::vector<double> Kh, Mh;
   legendre_1d_matrices(p, Kh, Mh);
@@ -794,6 +838,17 @@ void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, doub
   for (size_t i = 0; i < sh_cells.size(); ++i) L.h_scale_cell[sh_cells[i]] = sh_scale[i];
   L.d_own_index = h->upload(L.h_own_index);
   L.d_scale_cell = h->upload(L.h_scale_cell);
+  const bool node = node_level(L);
+  std::vector<int> code64, code32, nmat0;
+  if (node) {
+    code64 = L.h_own_index;
+    code32.resize(L.g.ncells);
+    for (int c = 0; c < L.g.ncells; ++c)
+      code32[c] = L.h_own_index[c] >= 0 ? -(L.h_own_index[c] + 2) : -1;  // df32 set
+    nmat0.assign(L.g.ncells, 0);
+    L.nA64 = make_node_set<double>(h, code64, nmat0, L.h_scale_cell, ld, L.A64.own.mats, nullptr,
+                                   L.A64.sh.mats);
+  }
   if (h->mixed) {
     // Cell matrices with their own entries (cut cells, penalty faces, all
     // Galerkin h-level cells) keep FP64 accuracy in the FP32 V-cycle (df32
@@ -816,6 +871,9 @@ void build_operator(Handle* h, Level& L, const std::vector<int>& own_cells, doub
     L.A32.sh.mats = K32;
     L.A32.sh.nmats = L.A64.sh.nmats;
     prepare_mma(h, L.A32.sh, n);
+    if (node)
+      L.nA32 = make_node_set<float>(h, code32, nmat0, L.h_scale_cell, ld, L.A32.own.mats,
+                                    L.A32.own_x.mats, L.A32.sh.mats);
   }
 }
 
@@ -951,6 +1009,22 @@ void build_smoother(Handle* h, Level& L) {
     check_status(h, d_info, (int)sigs.size(), "reference Schwarz block");
   }
   build_shared<double>(h, L.M64.sh, mat_of, cells, scale, sinv, (int)sigs.size());
+  // node-centric smoother: per cell its stored block or its shared inverse
+  const bool node = node_level(L);
+  std::vector<int> ncode, nmat;
+  std::vector<double> nscale;
+  if (node) {
+    ncode.assign(nc, -1);
+    nmat.assign(nc, 0);
+    nscale.assign(nc, 0.0);
+    for (int i = 0; i < nown; ++i) ncode[own_blocks[i]] = i;
+    for (size_t k = 0; k < cells.size(); ++k) {
+      nmat[cells[k]] = mat_of[k];
+      nscale[cells[k]] = scale[k];
+    }
+    L.nM64 = make_node_set<double>(h, ncode, nmat, nscale, padded_ld(n), L.M64.own.mats, nullptr,
+                                   L.M64.sh.mats);
+  }
   // mixed precision copies
   if (h->mixed) {
     const int ld = padded_ld(n);
@@ -990,6 +1064,13 @@ void build_smoother(Handle* h, Level& L) {
     L.M32.sh.nmats = (int)sigs.size();
     L.M32.sh.mma_only_alone = true;
     prepare_mma(h, L.M32.sh, n);
+    if (node) {
+      std::vector<int> code32(nc, -1);
+      for (size_t i = 0; i < c32.size(); ++i) code32[c32[i]] = (int)i;
+      for (size_t i = 0; i < cx.size(); ++i) code32[cx[i]] = -((int)i + 2);
+      L.nM32 = make_node_set<float>(h, code32, nmat, nscale, ld, L.M32.own.mats,
+                                    L.M32.own_x.mats, L.M32.sh.mats);
+    }
   }
 }
 

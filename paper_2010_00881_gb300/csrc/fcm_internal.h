@@ -90,6 +90,7 @@ struct Problem {
   int C[3];
   double lo[3], hi[3], h[3];
   int geom_kind;
+  int geom_complement;          // 1: Omega_phys = {psi >= 0}
   int n_gparams;
   double* d_gparams;            // device copy of geometry parameters
   double kappa, E, nu, alpha, beta;
@@ -211,6 +212,29 @@ void launch_jacobi(long long N, const TV* dinv, const TV* r, TV* x, double w, bo
 void launch_trunk_mask_mats(long long count, int dim, int nf, int p, int q, bool unit_diag,
                             double* mats, cudaStream_t s);
 void launch_trunk_mask_vec(const LevelGeom& g, int q, double* v, cudaStream_t s);
+
+// Node-centric operations of the levels with one mode per node and field
+// (p = 1 and the Q1 h-levels: n = nf 2^d): the cell products and the DOF
+// gather in one pass, every DOF summing the rows of its cells' matrices
+// against their coefficients (see node_kernel).  Per cell: code >= 0
+// indexes the first stored set (m1, TV precision), code <= -2 the second
+// (m2: df32 pairs in the mixed path), code -1 a shared matrix mat[c]
+// (canonical n x n in sh) scaled by scale[c].
+template <typename TV>
+struct NodeSet {
+  bool ok = false;
+  int ld = 0;
+  const int* code = nullptr;
+  const int* mat = nullptr;
+  const TV* scale = nullptr;
+  const void* m1 = nullptr;
+  const void* m2 = nullptr;
+  const TV* sh = nullptr;
+};
+// out = mode(sum), the gather modes below; x the cell products' input.
+template <typename TV>
+void launch_node(const LevelGeom& g, const NodeSet<TV>& op, const TV* x, const TV* b, TV* out,
+                 double w, int mode, cudaStream_t s);
 
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };

@@ -21,9 +21,28 @@ namespace fcm {
 struct Geo {
   int kind, dim, n;
   const double* prm;
+  int complement;  // 1: the physical side is {psi >= 0}
 };
 
+FCM_HD inline double levelset_kind(const Geo& G, const double* x);
+FCM_HD inline int classify_box_kind(const Geo& G, const double* lo, const double* hi);
+
+// psi of the physical domain: the kind's psi, negated (exactly) for a
+// complement domain.
 FCM_HD inline double levelset(const Geo& G, const double* x) {
+  const double v = levelset_kind(G, x);
+  return G.complement ? -v : v;
+}
+
+// Box class of the physical domain: a complement domain swaps inside and
+// outside (cut boxes stay cut).
+FCM_HD inline int classify_box(const Geo& G, const double* lo, const double* hi) {
+  const int c = classify_box_kind(G, lo, hi);
+  if (!G.complement) return c;
+  return c == CLS_INSIDE ? CLS_OUTSIDE : (c == CLS_OUTSIDE ? CLS_INSIDE : c);
+}
+
+FCM_HD inline double levelset_kind(const Geo& G, const double* x) {
   if (G.kind == FCM_GEOM_NONE) return -1.0;
   if (G.kind == FCM_GEOM_BALL) {
     const double* c = G.prm;
@@ -90,7 +109,7 @@ FCM_HD inline void ball_dist2(int dim, const double* lo, const double* hi, const
   }
 }
 
-FCM_HD inline int classify_box(const Geo& G, const double* lo, const double* hi) {
+FCM_HD inline int classify_box_kind(const Geo& G, const double* lo, const double* hi) {
   if (G.kind == FCM_GEOM_NONE) return CLS_INSIDE;
   if (G.kind == FCM_GEOM_BALL) {
     double r = G.prm[G.dim];
@@ -121,7 +140,7 @@ FCM_HD inline int classify_box(const Geo& G, const double* lo, const double* hi)
         int k[3] = {kx, ky, kz};
         double x[3];
         for (int a = 0; a < 3; ++a) x[a] = lo[a] + (k[a] * 0.25) * (hi[a] - lo[a]);
-        double v = levelset(G, x);
+        double v = levelset_kind(G, x);
         if (v <= 0.0)
           any_in = true;
         else

@@ -399,6 +399,8 @@ void validate(const fcm_grid* g, const fcm_geometry* geom) {
   }
   if (geom->kind < FCM_GEOM_NONE || geom->kind > FCM_GEOM_ELLIPSOID)
     throw Invalid{"fcm_mlhp_create: unknown geometry kind"};
+  if (geom->complement != 0 && geom->complement != 1)
+    throw Invalid{"fcm_mlhp_create: complement must be 0 or 1"};
   const int need = geom->kind == FCM_GEOM_BALL ? g->dim + 1
                    : geom->kind == FCM_GEOM_ELLIPSOID ? 15
                    : geom->kind == FCM_GEOM_VOIDS ? 4 : 0;
@@ -435,7 +437,7 @@ fcm_status fcm_mlhp_create(const fcm_grid* grid, const fcm_geometry* geom, fcm_m
       m->hi[a] = grid->hi[a];
     }
     if (geom->n_params > 0) m->prm.assign(geom->params, geom->params + geom->n_params);
-    m->geo = fcm::Geo{geom->kind, grid->dim, geom->n_params, m->prm.data()};
+    m->geo = fcm::Geo{geom->kind, grid->dim, geom->n_params, m->prm.data(), geom->complement};
     m->build();
     *out = m.release();
     return FCM_OK;

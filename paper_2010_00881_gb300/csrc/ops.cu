@@ -625,7 +625,40 @@ __device__ bool consume_item(const LevelGeom& g, int ld, const StreamSet<TM>& S,
   using XV = TV;
   const XV* xv = reinterpret_cast<const XV*>(xs);
   Acc<TM> acc;
-  if (S.cpc == 1) {
+  if (S.cpc == 1 && S.k > 1) {
+    // small cells, several per chunk: lane (c, cv) multiplies all rows of
+    // cell c for its column vector cv (no row groups, no reduction)
+    const int slot = (int)(seq0 % kRing);
+    if (!wait_issued(issued, seq0)) return false;
+    if (!mbar_wait(&full[slot], (uint32_t)((seq0 / kRing) & 1))) return false;
+    const TM* base = reinterpret_cast<const TM*>(ring + (size_t)slot * kRingChunk);
+    const int c = lane / ncv, cvl = lane - c * ncv;
+    const bool on = c < cnt;
+    acc.zero();
+    if (on) {
+      const TM* K = base + (size_t)c * n * ld + cvl * V;
+      const XV* xc = xv + c * n;
+      int r = 0;
+      for (; r + 3 < n; r += 4) {
+        const XV x0 = xc[r], x1 = xc[r + 1], x2 = xc[r + 2], x3 = xc[r + 3];
+        fma_row(acc, 0, K + (size_t)r * ld, x0);
+        fma_row(acc, 0, K + (size_t)(r + 1) * ld, x1);
+        fma_row(acc, 0, K + (size_t)(r + 2) * ld, x2);
+        fma_row(acc, 0, K + (size_t)(r + 3) * ld, x3);
+      }
+      for (; r < n; ++r) fma_row(acc, 0, K + (size_t)r * ld, xc[r]);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[slot], arrivals);
+    if (on) {
+      const int cell = cs[c];
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const int j = cvl * V + k;
+        if (j < n) Y[(size_t)j * g.ncells + cell] = (TV)acc_value(acc, k);
+      }
+    }
+  } else if (S.cpc == 1) {
     const int slot = (int)(seq0 % kRing);
     if (!wait_issued(issued, seq0)) return false;
     if (!mbar_wait(&full[slot], (uint32_t)((seq0 / kRing) & 1))) return false;
@@ -825,8 +858,8 @@ __global__ void __launch_bounds__(kOpThreads) own_kernel(CellOpArgs<TV> A) {
                    smem_raw, tab);
 }
 
-// Small stored matrices (n <= 16: the Q1 levels, 2D low degree): a group of
-// L lanes per cell (N rounded up to 4, 8 or 16).  Lane j < N loads its own
+// Small stored matrices (n <= 16: the Q1 and p = 1 levels, 2D low degree):
+// a group of L lanes per cell (N rounded up to 4, 8 or 16).  Lane j < N loads its own
 // coefficient x_j and row j of the cell's matrix (row j = column j by
 // symmetry; the cell's rows are one contiguous run across the group), gets
 // the other coefficients by shuffles within the group and accumulates
@@ -854,16 +887,73 @@ struct LaneAcc<float2> {
   __device__ double get() const { return (double)s + (double)c; }
 };
 
+template <int N>
+__host__ __device__ constexpr int lane_group() {
+  return N <= 4 ? 4 : (N <= 8 ? 8 : 16);
+}
+// Cell sizes taken by the lane-group kernels: the Q1 and p = 1 Poisson
+// levels (8 in 3D, 4 in 2D) and p = 2, 3 in 2D (9, 16).  From 24 DOFs a
+// cell per warp writes its products to n scattered sectors and leaves no
+// room beside it for the shared-matrix tiles: at p = 2 in 3D (n = 27) the
+// stored-matrix step took 22.5 us with the tiles after it, against 16.5 us
+// for the TMA ring with the tiles beside it.
+__host__ __device__ constexpr bool lane_group_size(int n) {
+  return n == 4 || n == 8 || n == 9 || n == 16;
+}
+
+// One cell per lane group: lane j < N multiplies row j of the cell's
+// stored matrix (16-byte loads unpacked by value, so krow stays in
+// registers) with the group's coefficients.
 template <int N, typename TV, typename TM>
-__global__ void __launch_bounds__(kOpThreads) small_kernel(LevelGeom g, int n_own,
-                                                           const int* __restrict__ cells,
-                                                           const TM* __restrict__ mats,
-                                                           const TV* __restrict__ x,
-                                                           TV* __restrict__ Y) {
-  constexpr int L = N <= 4 ? 4 : (N <= 8 ? 8 : 16);
-  constexpr int G = 32 / L;                   // cells per warp
+__device__ __forceinline__ void small_cell(const LevelGeom& g, const int* tab, int ci, int n,
+                                           const int* __restrict__ cells,
+                                           const TM* __restrict__ mats,
+                                           const TV* __restrict__ x, TV* __restrict__ Y,
+                                           int j) {
+  constexpr int L = lane_group<N>();
   constexpr int LD = (N + 3) & ~3;
   constexpr int VE = 16 / (int)sizeof(TM);   // entries per 16-byte load
+  const bool live = ci < n && j < N;
+  TM krow[LD];
+  if (live) {
+    const float4* row = reinterpret_cast<const float4*>(mats + ((size_t)ci * N + j) * LD);
+#pragma unroll
+    for (int v = 0; v < LD / VE; ++v) {
+      const float4 t = row[v];
+      if constexpr (std::is_same<TM, float>::value) {
+        krow[4 * v] = t.x;
+        krow[4 * v + 1] = t.y;
+        krow[4 * v + 2] = t.z;
+        krow[4 * v + 3] = t.w;
+      } else if constexpr (std::is_same<TM, float2>::value) {
+        krow[2 * v] = make_float2(t.x, t.y);
+        krow[2 * v + 1] = make_float2(t.z, t.w);
+      } else {
+        krow[2 * v] = __hiloint2double(__float_as_int(t.y), __float_as_int(t.x));
+        krow[2 * v + 1] = __hiloint2double(__float_as_int(t.w), __float_as_int(t.z));
+      }
+    }
+  }
+  const int cell = ci < n ? cells[ci] : 0;
+  const TV xj = live ? x[cell_base_of(g, cell) + tab[j]] : (TV)0;
+  LaneAcc<TM> acc;
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const TV xr = __shfl_sync(0xffffffffu, xj, r, L);
+    if (live) acc.add(krow[r], xr);
+  }
+  if (live) Y[(size_t)j * g.ncells + cell] = (TV)acc.get();
+}
+
+// Two stored sets of one level (the mixed path's FP32 and df32 matrices) in
+// one launch: warps [0, W1) take set 1, the following W2 warps set 2.
+template <int N, typename TV, typename TM1, typename TM2>
+__global__ void __launch_bounds__(kOpThreads) small_kernel(
+    LevelGeom g, int n1, const int* __restrict__ cells1, const TM1* __restrict__ mats1, int n2,
+    const int* __restrict__ cells2, const TM2* __restrict__ mats2, const TV* __restrict__ x,
+    TV* __restrict__ Y) {
+  constexpr int L = lane_group<N>();
+  constexpr int G = 32 / L;  // cells per warp
   __shared__ int tab[128];
   build_local_table(g, tab);
   __syncthreads();
@@ -871,54 +961,113 @@ __global__ void __launch_bounds__(kOpThreads) small_kernel(LevelGeom g, int n_ow
   pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int j = lane % L;
-  const long long ncells = g.ncells;
+  const int W1 = (n1 + G - 1) / G, W = W1 + (n2 + G - 1) / G;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * G < n_own; w += nw) {
-    const int ci = w * G + lane / L;
-    const bool live = ci < n_own && j < N;
-    TM krow[LD];
-    if (live) {
-      const TM* row = mats + ((size_t)ci * N + j) * LD;
-#pragma unroll
-      for (int v = 0; v < LD / VE; ++v)
-        *reinterpret_cast<float4*>(&krow[v * VE]) = *reinterpret_cast<const float4*>(row + v * VE);
-    }
-    const int cell = ci < n_own ? cells[ci] : 0;
-    const TV xj = live ? x[cell_base_of(g, cell) + tab[j]] : (TV)0;
-    LaneAcc<TM> acc;
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-      const TV xr = __shfl_sync(0xffffffffu, xj, r, L);
-      if (live) acc.add(krow[r], xr);
-    }
-    if (live) Y[(size_t)j * ncells + cell] = (TV)acc.get();
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < W; w += nw) {
+    if (w < W1)
+      small_cell<N, TV, TM1>(g, tab, w * G + lane / L, n1, cells1, mats1, x, Y, j);
+    else
+      small_cell<N, TV, TM2>(g, tab, (w - W1) * G + lane / L, n2, cells2, mats2, x, Y, j);
   }
 }
 
-template <int N, typename TV, typename TM>
-void launch_small(const LevelGeom& g, int n_own, const int* cells, const TM* mats, const TV* x,
-                  TV* Y, cudaStream_t s) {
-  constexpr int L = N <= 4 ? 4 : (N <= 8 ? 8 : 16);
-  const long long threads = (long long)n_own * L;
+template <int N, typename TV, typename TM1, typename TM2>
+void launch_small(const LevelGeom& g, int n1, const int* cells1, const TM1* mats1, int n2,
+                  const int* cells2, const TM2* mats2, const TV* x, TV* Y, cudaStream_t s) {
+  constexpr int L = lane_group<N>();
+  const long long threads = ((long long)n1 + n2) * L + 2 * 32;
   int blocks = (int)((threads + kOpThreads - 1) / kOpThreads);
   if (blocks < 1) blocks = 1;
-  launch_pdl(small_kernel<N, TV, TM>, dim3(blocks), dim3(kOpThreads), 0, s, g, n_own, cells, mats,
-             x, Y);
+  launch_pdl(small_kernel<N, TV, TM1, TM2>, dim3(blocks), dim3(kOpThreads), 0, s, g, n1, cells1,
+             mats1, n2, cells2, mats2, x, Y);
 }
 
-// n in {4, 8, 9, 16} with padded rows: lane-group kernel; false: not
-// handled here.
-template <typename TV, typename TM>
-bool dispatch_small(const LevelGeom& g, int ld, int n_own, const int* cells, const void* mats,
-                    const TV* x, TV* Y, cudaStream_t s) {
+// Shared matrices of small cells (n in {4, 8, 9, 16}: the p = 1 level in
+// 3D, p <= 3 in 2D), by the lane-group scheme of small_kernel over the
+// shared-cell tiles: a tile's cells use one canonical n x n matrix (row j =
+// column j) and a per-cell scale, y_c = s_c K x_c.  A block takes
+// kOpThreads / L cells of one tile; lane j of a group loads column j of the
+// tile's matrix (K[r][j] for r = 0 .. n-1: at each r the group reads one
+// contiguous row, the same for every group, from L1) and its own
+// coefficient, and gets the others by shuffles.  Compared with the tile
+// kernel's gather-compute-store rounds per 64-cell tile, every cell is one
+// short chain of independent loads.
+template <int N, typename TV>
+__global__ void __launch_bounds__(kOpThreads) small_shared_kernel(
+    LevelGeom g, const int4* __restrict__ tiles, int parts, const int* __restrict__ cells,
+    const TV* __restrict__ scale, const TV* __restrict__ mats, const TV* __restrict__ x,
+    TV* __restrict__ Y) {
+  constexpr int L = lane_group<N>();
+  constexpr int CPB = kOpThreads / L;  // cells per block
+  __shared__ int tab[128];
+  build_local_table(g, tab);
+  __syncthreads();
+  pdl_wait();
+  pdl_trigger();
+  const int4 t = tiles[blockIdx.x / parts];
+  const int slot = (int)(blockIdx.x % parts) * CPB + (int)threadIdx.x / L;
+  const int j = (int)threadIdx.x % L;
+  const bool has = slot < t.z;
+  const bool live = has && j < N;
+  TV krow[N];
+  if (live) {
+    const TV* col = mats + (size_t)t.x * N * N + j;
+#pragma unroll
+    for (int r = 0; r < N; ++r) krow[r] = col[(size_t)r * N];
+  }
+  const int e = t.y + (has ? slot : 0);
+  const int cell = has ? cells[e] : 0;
+  const TV xj = live ? x[cell_base_of(g, cell) + tab[j]] : (TV)0;
+  TV acc = (TV)0;
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const TV xr = __shfl_sync(0xffffffffu, xj, r, L);
+    if (live) acc = fma(krow[r], xr, acc);
+  }
+  if (live) Y[(size_t)j * g.ncells + cell] = scale[e] * acc;
+}
+
+// Shared cells of small n through small_shared_kernel; false: not handled.
+template <typename TV>
+bool dispatch_small_shared(const CellOpArgs<TV>& A, cudaStream_t s) {
+  auto go = [&](auto kernel, int L) {
+    const int parts = (kTileCells * L + kOpThreads - 1) / kOpThreads;
+    launch_pdl(kernel, dim3(A.ntiles * parts), dim3(kOpThreads), 0, s, A.g, A.tiles, parts,
+               A.sh_cells, A.sh_scale, A.sh_mats, A.x, A.Y);
+  };
+  switch (A.g.nloc) {
+    case 4: go(small_shared_kernel<4, TV>, 4); return true;
+    case 8: go(small_shared_kernel<8, TV>, 8); return true;
+    case 9: go(small_shared_kernel<9, TV>, 16); return true;
+    case 16: go(small_shared_kernel<16, TV>, 16); return true;
+    // from 24 DOFs a warp per cell re-reads the whole matrix per cell, and
+    // the 64-cell tiles are faster (p = 2 in 3D: 8.3 against 13.6 us)
+    default: return false;
+  }
+}
+
+// n of lane_group_size with padded rows: lane-group kernel over the two
+// stored sets (n2 = 0: one set); false: not handled here.
+template <typename TV, typename TM1, typename TM2>
+bool dispatch_small(const LevelGeom& g, int ld, int n1, const int* cells1, const void* mats1,
+                    int n2, const int* cells2, const void* mats2, const TV* x, TV* Y,
+                    cudaStream_t s) {
   const int n = g.nloc;
-  if (ld != padded_ld(n) || (reinterpret_cast<uintptr_t>(mats) & 15)) return false;
-  const TM* m = static_cast<const TM*>(mats);
+  if (ld != padded_ld(n) || (reinterpret_cast<uintptr_t>(mats1) & 15) ||
+      (reinterpret_cast<uintptr_t>(mats2) & 15))
+    return false;
+  const TM1* m1 = static_cast<const TM1*>(mats1);
+  const TM2* m2 = static_cast<const TM2*>(mats2);
   switch (n) {
-    case 4: launch_small<4, TV, TM>(g, n_own, cells, m, x, Y, s); return true;
-    case 8: launch_small<8, TV, TM>(g, n_own, cells, m, x, Y, s); return true;
-    case 9: launch_small<9, TV, TM>(g, n_own, cells, m, x, Y, s); return true;
-    case 16: launch_small<16, TV, TM>(g, n_own, cells, m, x, Y, s); return true;
+#define FCM_SMALL_CASE(NN)                                                                  \
+  case NN:                                                                                  \
+    launch_small<NN, TV, TM1, TM2>(g, n1, cells1, m1, n2, cells2, m2, x, Y, s);             \
+    return true;
+    FCM_SMALL_CASE(4)
+    FCM_SMALL_CASE(8)
+    FCM_SMALL_CASE(9)
+    FCM_SMALL_CASE(16)
+#undef FCM_SMALL_CASE
     default: return false;
   }
 }
@@ -2112,6 +2261,10 @@ StreamSet<TM> make_stream_set(int n, const int* cells, const void* mats, int nlo
   if (cb <= (size_t)kRingChunk) {
     int k = (int)(kRingChunk / cb);
     if (k > kItemVals / nloc) k = kItemVals / nloc;
+    // several cells per item are taken side by side, a lane per (cell,
+    // column vector): at most 32 such pairs
+    const int ncv = ld / Elem<TM>::V;
+    if (k > 1 && k * ncv > 32) k = 32 / ncv > 1 ? 32 / ncv : 1;
     S.k = k < 1 ? 1 : k;
     S.cpc = 1;
     S.rc = nloc;
@@ -2204,7 +2357,7 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   // grid instead.
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   const bool al = (ld & 3) == 0 && al16(op.own.mats) && al16(op.own_x.mats);
-  const bool small = (n == 4 || n == 8 || n == 9 || n == 16) && ld == padded_ld(n) && al;
+  const bool small = lane_group_size(n) && ld == padded_ld(n) && al;
   // FP32 vectors: the shared-matrix products run on the tensor cores
   // (tc_tile_kernel) from kMmaMinN DOFs per cell up, with the operand chunk
   // KC sized so that one block fits beside a streaming block when they run
@@ -2250,12 +2403,12 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   if (fork) cudaEventRecord(side->fork, s);
   if (A.nb_own || A.nb_own_x) {
     if (small) {
-      if (A.nb_own) dispatch_small<TV, TV>(g, ld, op.own.n, op.own.cells, op.own.mats, x, Y, s);
-      if constexpr (std::is_same<TV, float>::value) {
-        if (A.nb_own_x)
-          dispatch_small<float, float2>(g, ld, op.own_x.n, op.own_x.cells, op.own_x.mats, x, Y,
-                                        s);
-      }
+      if constexpr (std::is_same<TV, float>::value)
+        dispatch_small<float, float, float2>(g, ld, op.own.n, op.own.cells, op.own.mats,
+                                             op.own_x.n, op.own_x.cells, op.own_x.mats, x, Y, s);
+      else
+        dispatch_small<double, double, double>(g, ld, op.own.n, op.own.cells, op.own.mats, 0,
+                                               nullptr, nullptr, x, Y, s);
     } else if (al && n <= 128) {
       if constexpr (std::is_same<TV, float>::value) {
         StreamArgs<float, float, float2> S{
@@ -2301,15 +2454,20 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
     // one block per SM only beside stream blocks; the small-cell kernels
     // leave the SMs' shared memory free
     const bool one = fork && !small;
+    bool done = false;
     if constexpr (std::is_same<TV, double>::value) {
       if (op.sh.kron) {
         launch_kron_tile(A, op.sh.kron, one, st);
-        if (fork) {
-          cudaEventRecord(side->join, side->s2);
-          cudaStreamWaitEvent(s, side->join, 0);
-        }
-        return;
+        done = true;
       }
+    }
+    if (!done) done = dispatch_small_shared<TV>(A, st);
+    if (done) {
+      if (fork) {
+        cudaEventRecord(side->join, side->s2);
+        cudaStreamWaitEvent(s, side->join, 0);
+      }
+      return;
     }
     switch (npad / 16) {
       case 1: launch_tile<TV, 1>(A, sm_tile, st, one); break;
@@ -2423,6 +2581,137 @@ __global__ void trunk_mask_vec_kernel(LevelGeom g, int q, double* v) {
     if (sum > q) v[i] = 0.0;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Node-centric level operations (p = 1 and Q1 levels, n = nf 2^d).  On
+// these levels a cell product and its DOF gather are each a few
+// microseconds of dependent loads on small vectors; one pass per half step
+// halves the launches.  A group of 2^d lanes serves one DOF (field f, node
+// i): lane s takes the cell on side s of the node, multiplies row
+// l = f 2^d + k of the cell's matrix (k: the node's corner in the cell; row
+// l = column l by symmetry) with the cell's coefficients read from x (a
+// df32 row with compensated accumulation, a shared row scaled by the
+// cell's factor), and the group sums the 2^d products in lane order.  The
+// arithmetic per product and the summation order across cells are those of
+// the cell kernels and the gather.
+template <int D, int NF, typename TV, typename TM2, int MODE>
+__global__ void __launch_bounds__(256) node_kernel(LevelGeom g, NodeSet<TV> op,
+                                                   const TV* __restrict__ x,
+                                                   const TV* __restrict__ b,
+                                                   TV* __restrict__ out, TV w) {
+  constexpr int NS = 1 << D;  // nodes per cell = lanes per DOF
+  constexpr int N = NF * NS;  // DOFs per cell
+  pdl_wait();
+  pdl_trigger();
+  const int Ntot = (int)g.N, M = (int)g.M;
+  const int m0 = g.m[0], m1 = D == 3 ? g.m[1] : 1;
+  const TV* __restrict__ A1 = static_cast<const TV*>(op.m1);
+  const TM2* __restrict__ A2 = static_cast<const TM2*>(op.m2);
+  const int lane = threadIdx.x & 31;
+  const int sl = lane % NS;  // the cell side: bit a set = the cell above the node on axis a
+  const int stride = (gridDim.x * blockDim.x) / NS;
+  // every lane of a warp runs the same number of iterations (the shuffles)
+  const int total = (Ntot + stride - 1) / stride;
+  int I = (blockIdx.x * blockDim.x + threadIdx.x) / NS;
+  for (int it = 0; it < total; ++it, I += stride) {
+    TV part = (TV)0;
+    if (I < Ntot) {
+      const int f = I / M;
+      const int r = I - f * M;
+      const int ix = r % m0;
+      const int iy = D == 3 ? (r / m0) % m1 : r / m0;
+      const int iz = D == 3 ? r / (m0 * m1) : 0;
+      const int sx = sl & 1, sy = (sl >> 1) & 1, sz = D == 3 ? (sl >> 2) & 1 : 0;
+      const int cx = ix - 1 + sx, cy = iy - 1 + sy, cz = D == 3 ? iz - 1 + sz : 0;
+      if (cx >= 0 && cx < g.C[0] && cy >= 0 && cy < g.C[1] && cz >= 0 && cz < g.C[2]) {
+        const int k = (1 - sx) + 2 * (1 - sy) + 4 * (D == 3 ? 1 - sz : 0);
+        const int l = f * NS + k;
+        const int cell = cx + g.C[0] * (cy + g.C[1] * cz);
+        const int nb = cx + m0 * (cy + m1 * cz);  // the cell's first node
+        TV xc[N];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          const int f2 = q / NS, k2 = q % NS;
+          xc[q] = x[f2 * M + nb + (k2 & 1) + m0 * ((k2 >> 1) & 1) + m0 * m1 * (k2 >> 2)];
+        }
+        const int cd = op.code[cell];
+        if (cd >= 0) {
+          const TV* row = A1 + ((size_t)cd * N + l) * op.ld;
+#pragma unroll
+          for (int q = 0; q < N; ++q) part = fma(row[q], xc[q], part);
+        } else if (cd <= -2) {
+          if constexpr (std::is_same<TM2, float2>::value) {
+            const float2* row = A2 + ((size_t)(-cd - 2) * N + l) * op.ld;
+            float s0 = 0.f, c0 = 0.f;
+#pragma unroll
+            for (int q = 0; q < N; ++q) df_term(s0, c0, row[q].x, row[q].y, xc[q]);
+            part = (TV)((double)s0 + (double)c0);
+          }
+        } else {
+          const TV* row = op.sh + ((size_t)op.mat[cell] * N + l) * N;
+          TV t = (TV)0;
+#pragma unroll
+          for (int q = 0; q < N; ++q) t = fma(row[q], xc[q], t);
+          part = op.scale[cell] * t;
+        }
+      }
+    }
+    // fixed-order sum over the group's lanes
+    TV y = __shfl_sync(0xffffffffu, part, 0, NS);
+#pragma unroll
+    for (int q = 1; q < NS; ++q) y += __shfl_sync(0xffffffffu, part, q, NS);
+    if (I < Ntot && sl == 0) {
+      if (MODE == GATHER_SET)
+        out[I] = y;
+      else if (MODE == GATHER_RESID)
+        out[I] = b[I] - y;
+      else if (MODE == GATHER_ADD)
+        out[I] = out[I] + w * y;
+      else
+        out[I] = w * y;
+    }
+  }
+}
+
+template <int D, int NF, typename TV>
+void launch_node_dn(const LevelGeom& g, const NodeSet<TV>& op, const TV* x, const TV* b, TV* out,
+                    TV w, int mode, cudaStream_t s) {
+  using TM2 = typename std::conditional<std::is_same<TV, float>::value, float2, double>::type;
+  const long long threads = g.N * (1LL << D);
+  const int grid = (int)((threads + 255) / 256);
+  switch (mode) {
+    case GATHER_SET:
+      launch_pdl(node_kernel<D, NF, TV, TM2, GATHER_SET>, dim3(grid), dim3(256), 0, s, g, op, x, b,
+                 out, w);
+      break;
+    case GATHER_RESID:
+      launch_pdl(node_kernel<D, NF, TV, TM2, GATHER_RESID>, dim3(grid), dim3(256), 0, s, g, op, x,
+                 b, out, w);
+      break;
+    case GATHER_ADD:
+      launch_pdl(node_kernel<D, NF, TV, TM2, GATHER_ADD>, dim3(grid), dim3(256), 0, s, g, op, x, b,
+                 out, w);
+      break;
+    default:
+      launch_pdl(node_kernel<D, NF, TV, TM2, GATHER_SCALE>, dim3(grid), dim3(256), 0, s, g, op, x,
+                 b, out, w);
+      break;
+  }
+}
+
+template <typename TV>
+void launch_node(const LevelGeom& g, const NodeSet<TV>& op, const TV* x, const TV* b, TV* out,
+                 double w, int mode, cudaStream_t s) {
+  const TV tw = (TV)w;
+  if (g.dim == 3 && g.nf == 1) launch_node_dn<3, 1, TV>(g, op, x, b, out, tw, mode, s);
+  else if (g.dim == 3 && g.nf == 3) launch_node_dn<3, 3, TV>(g, op, x, b, out, tw, mode, s);
+  else if (g.dim == 2 && g.nf == 1) launch_node_dn<2, 1, TV>(g, op, x, b, out, tw, mode, s);
+  else launch_node_dn<2, 2, TV>(g, op, x, b, out, tw, mode, s);
+}
+template void launch_node<float>(const LevelGeom&, const NodeSet<float>&, const float*,
+                                 const float*, float*, double, int, cudaStream_t);
+template void launch_node<double>(const LevelGeom&, const NodeSet<double>&, const double*,
+                                  const double*, double*, double, int, cudaStream_t);
 
 void launch_trunk_mask_mats(long long count, int dim, int nf, int p, int q, bool unit_diag,
                             double* mats, cudaStream_t s) {

@@ -81,7 +81,7 @@ __device__ void cell_box(const Problem& P, int cx, int cy, int cz, double* x0, d
 
 __global__ void classify_kernel(Problem P, signed char* cls, unsigned char* faces) {
   int ncell = P.C[0] * P.C[1] * P.C[2];
-  Geo G{P.geom_kind, P.dim, P.n_gparams, P.d_gparams};
+  Geo G{P.geom_kind, P.dim, P.n_gparams, P.d_gparams, P.geom_complement};
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
     int cx = c % P.C[0], cy = (c / P.C[0]) % P.C[1], cz = c / (P.C[0] * P.C[1]);
     double x0[3], x1[3];
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kThreads) element_own_kernel(
   const bool elastic = P.pde == FCM_PDE_ELASTICITY;
   const double lam = P.E * P.nu / ((1.0 + P.nu) * (1.0 - 2.0 * P.nu));
   const double mu = P.E / (2.0 * (1.0 + P.nu));
-  Geo G{P.geom_kind, dim, P.n_gparams, P.d_gparams};
+  Geo G{P.geom_kind, dim, P.n_gparams, P.d_gparams, P.geom_complement};
   const int nq1 = P1;  // points per axis
   int Qleaf = 1;
   for (int a = 0; a < dim; ++a) Qleaf *= nq1;

@@ -46,7 +46,8 @@ class fcm_grid(C.Structure):
 
 
 class fcm_geometry(C.Structure):
-    _fields_ = [("kind", C.c_int), ("n_params", C.c_int), ("params", C.POINTER(C.c_double))]
+    _fields_ = [("kind", C.c_int), ("n_params", C.c_int), ("params", C.POINTER(C.c_double)),
+                ("complement", C.c_int)]
 
 
 class fcm_physics(C.Structure):
@@ -274,7 +275,7 @@ def descriptors(prob: dict, build_mixed: bool = True):
     else:
         params = []
     arr = (C.c_double * max(1, len(params)))(*params)
-    gm = fcm_geometry(GEOM[kind], len(params), arr)
+    gm = fcm_geometry(GEOM[kind], len(params), arr, 1 if geo.get("complement") else 0)
     ph = fcm_physics()
     ph.pde = PDE[prob["pde"]]
     ph.kappa = prob["kappa"]

@@ -218,6 +218,9 @@ def test_leaf_transform_is_a_kronecker_product_of_restrictions(make):
     lambda fi: fi.perforated_plate(cells=8, p=2, overlay_levels=3),
     lambda fi: fi.poisson3d_sphere_mlhp(cells=4, p=2, overlay_levels=2),
     lambda fi: dict(fi.poisson2d_circle(cells=4, p=2), overlay_levels=0),
+    # a hole instead of an inclusion: the same leaves, inside and outside swapped
+    lambda fi: dict(fi.poisson2d_circle(cells=8, p=2), overlay_levels=2,
+                    geometry=dict(kind="ball", center=(0.5, 0.5), radius=0.4, complement=True)),
 ])
 def test_overlay_leaf_classes_and_levels_match_the_oracle(make):
     import numpy as np
@@ -257,3 +260,7 @@ def test_descriptors_refuse_what_the_library_lacks():
     assert g.space == fcm.SPACE_TENSOR
     g, _, _, _, _ = fcm.descriptors(fi.popcorn(cells=4, drop_outside=False))
     assert g.space == fcm.SPACE_TRUNK
+    _, gm, _, _, _ = fcm.descriptors(base)
+    assert gm.complement == 0
+    _, gm, _, _, _ = fcm.descriptors(dict(base, geometry=dict(base["geometry"], complement=True)))
+    assert gm.complement == 1

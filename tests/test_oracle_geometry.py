@@ -106,3 +106,66 @@ def test_void_sampler_respects_gaps():
         assert np.all(c - r >= 1 / 64 - 1e-15) and np.all(c + r <= 1 - 1 / 64 + 1e-15)
         for j in range(i):
             assert np.linalg.norm(c - v[j, :3]) >= r + v[j, 3] + 1 / 64 - 1e-12
+
+
+# Complement domains (the geometry's "complement" flag, Omega_phys = {psi >= 0}).
+
+@pytest.mark.parametrize("geom", GEOMS)
+def test_complement_classification_agrees_with_sampling(geom):
+    """A complement box class holds for sampled points of the complement:
+    INSIDE boxes lie in {psi >= 0}, OUTSIDE boxes in {psi < 0}."""
+    gc = dict(geom, complement=True)
+    rng = np.random.default_rng(4)
+    seen = set()
+    for _ in range(300):
+        lo = rng.uniform(0, 0.9, 3)
+        hi = lo + rng.uniform(0.01, 0.2, 3)
+        c = classify_box(gc, lo, hi)
+        seen.add(c)
+        pts = lo + (hi - lo) * rng.uniform(0, 1, (400, 3))
+        psi_kind = levelset(geom, pts)
+        assert np.array_equal(levelset(gc, pts), -psi_kind)
+        if c == INSIDE:
+            assert np.all(psi_kind >= -1e-12)
+        elif c == OUTSIDE:
+            assert np.all(psi_kind < 1e-12)
+    assert CUT in seen and len(seen) == (2 if geom["kind"] == "voids" else 3)
+
+
+def test_complement_circle_area_and_perimeter():
+    """The square with a circular hole: area 1 - pi r^2, the same perimeter."""
+    r = 0.4
+    prob = fi.poisson2d_circle(cells=8, p=2, radius=r, quad_depth=5)
+    prob["geometry"] = dict(prob["geometry"], complement=True)
+    vol, per = _measure(prob)
+    area = 1.0 - math.pi * r * r
+    assert abs(vol - area) / area < 3e-4 * math.pi * r * r / area
+    assert abs(per - 2 * math.pi * r) / (2 * math.pi * r) < 3e-4
+
+
+@pytest.mark.parametrize("pde", ["poisson", "elasticity"])
+def test_complement_cell_matrices_sum_to_the_uncut_ones(pde):
+    """alpha_Omega + alpha_complement = 1 + alpha pointwise, and both sides
+    use the same space tree, so on every cell K(Omega) + K(complement) =
+    (1 + alpha) K(uncut), with the penalty terms of the shared surface
+    counted twice; checked without the penalty (beta = 0) to 1e-12
+    relative, cut cells included."""
+    from oracle.assembly import element_system
+    if pde == "poisson":
+        prob = fi.poisson3d_sphere(cells=4, p=2, radius=0.35, quad_depth=2)
+    else:
+        prob = fi.elasticity3d_voids(cells=4, p=1, n_voids=3, seed=1)
+        prob["quad_depth"] = 2
+    prob = dict(prob, beta=0.0)
+    comp = dict(prob, geometry=dict(prob["geometry"], complement=True))
+    box = dict(prob, geometry=dict(kind="none"))
+    ncut = 0
+    for cell in all_cells(prob["dim"], prob["cells"]):
+        K1, _, c1 = element_system(prob, cell)
+        K2, _, c2 = element_system(comp, cell)
+        K0, _, _ = element_system(box, cell)
+        ncut += c1 == CUT
+        assert (c1 == CUT) == (c2 == CUT) and (c1 == INSIDE) == (c2 == OUTSIDE)
+        ref = (1.0 + prob["alpha"]) * K0
+        assert np.abs(K1 + K2 - ref).max() <= 1e-12 * np.abs(ref).max(), cell
+    assert ncut > 0
