@@ -1394,6 +1394,7 @@ __global__ void __launch_bounds__(kOpThreads) kron_tile_kernel(CellOpArgs<double
 // consecutive addresses.
 constexpr int kMmaCells = 128;
 constexpr int kMmaMinN = 48;  // DOFs per cell from which the tensor-core tiles are used
+constexpr int kMmaMinForked = 24;  // the same beside a streaming block
 constexpr uint32_t kMmaWaitLimit = 1u << 24;
 
 template <int RV>
@@ -2364,10 +2365,18 @@ void launch_cell_op(const LevelGeom& g, const OpData<TV>& op, const TV* x, TV* Y
   // side by side.  Below that the product is a few hundred FMAs per cell and
   // the CUDA-core tiles finish sooner than the tensor-core kernel's fixed
   // latency (tensor-memory allocation, MMA commit and wait: about 5 us).
-  bool mma = std::is_same<TV, float>::value && A.ntiles_mma > 0 && n >= kMmaMinN &&
-             n <= 128 && op.sh.mma_b != nullptr;
+  const bool mma_ok = std::is_same<TV, float>::value && A.ntiles_mma > 0 && n <= 128 &&
+                      op.sh.mma_b != nullptr;
+  bool mma = mma_ok && n >= kMmaMinN;
   int KC = mma ? mma_chunk(n, 200 * 1024) : 0;
   const bool stored = A.nb_own || A.nb_own_x;
+  // beside a streaming block the CUDA-core tiles get one block per SM; from
+  // kMmaMinForked DOFs per cell the tensor-core tiles finish sooner there
+  // (the operator at p = 2 in 3D: 14.4 against 16.5 us per step; not the
+  // smoother's many shared inverses, 22.5 against 20.5 us, see below)
+  if (!mma && mma_ok && n >= kMmaMinForked && side && side->s2 && stored &&
+      !lane_group_size(n))
+    mma = true;
   // shared memory left on an SM beside one streaming block (12 KB: static
   // shared memory of both kernels and the per-block reservations)
   size_t left = 0;
