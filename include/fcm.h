@@ -92,7 +92,7 @@ typedef struct {
 /* Level-set geometry, Omega_phys = {psi <= 0}.  params (host memory, read
  * during fcm_setup only):
  *   BALL       cx cy [cz] r                          psi = |x-c| - r
- *   VOIDS      n_params/4 balls (cx cy cz r)          psi = max_k (r_k - |x-c_k|)
+ *   VOIDS      n_params/4 balls (cx cy cz r; cz unused in 2D)   psi = max_k (r_k - |x-c_k|)
  *   ELLIPSOID  cx cy cz a0 a1 a2 R00 R01 ... R22      psi = |diag(1/a) R^T (x-c)| - 1
  *   POPCORN    r0 A sigma, then bump centres (cx cy cz)...  (3D, Sec. 4.3.2)
  *              psi = |x| - r0 - sum_k A exp(-|x - c_k|^2 / sigma^2)
@@ -292,6 +292,34 @@ fcm_status fcm_mlhp_patches(const fcm_mlhp* m, long long* offsets, long long* fu
 fcm_status fcm_mlhp_leaf_classes(const fcm_mlhp* m, signed char* cls);
 fcm_status fcm_mlhp_levels(const fcm_mlhp* m, int* n_levels, int* coarsest);
 fcm_status fcm_mlhp_restriction_1d(int p, int dk, int pos, double* S);
+
+/* The operator and load of an overlay mesh on the device (refinement by
+ * superposition, Sec. 2.2; the leaf assembly of Eq. (weakform) over the
+ * functions of each leaf).  For every leaf the cell matrix and load of its
+ * box are integrated on the device (the cell kernels of fcm_setup on the
+ * lattice of the leaf's level: space tree on cut leaves, box-face terms on
+ * leaves at the box boundary) and mapped to the leaf's functions,
+ * K_L = T^T K_box T and b_L = T^T b_box, with T the Kronecker product of
+ * the 1D restrictions (fcm_mlhp_restriction_1d) from each function's
+ * ancestor; leaf matrices stay in device memory.
+ * fcm_mlhp_op_create: m the topology built from the same grid and
+ *   geometry; grid, geom, phys as for fcm_setup (grid->overlay_levels as
+ *   for fcm_mlhp_create; tensor-product space only).  `stream` as in
+ *   fcm_setup.  FCM_E_UNSUPPORTED when a leaf carries more than 6144 DOFs.
+ * fcm_mlhp_op_ndofs: nf M, vectors field-major (f M + function id, the
+ *   function order of fcm_mlhp_functions).
+ * fcm_mlhp_op_apply: y = A x: y_L = K_L x_L per leaf, the leaf results
+ *   summed per DOF in a fixed order (reproducible bit for bit).
+ * fcm_mlhp_op_rhs: the assembled load b.
+ * The multigrid hierarchy of overlay meshes (hp-levels, patchwise blocks)
+ * is not built on the device; fcm_setup refuses overlays. */
+typedef struct fcm_mlhp_op fcm_mlhp_op;
+fcm_status fcm_mlhp_op_create(const fcm_mlhp* m, const fcm_grid* grid, const fcm_geometry* geom,
+                              const fcm_physics* phys, void* stream, fcm_mlhp_op** out);
+fcm_status fcm_mlhp_op_ndofs(const fcm_mlhp_op* op, long long* n);
+fcm_status fcm_mlhp_op_apply(fcm_mlhp_op* op, const double* x_dev, double* y_dev);
+fcm_status fcm_mlhp_op_rhs(const fcm_mlhp_op* op, double* b_dev);
+void fcm_mlhp_op_destroy(fcm_mlhp_op* op);
 
 /* Copy the assembled load vector b into b_dev (ndofs doubles). */
 fcm_status fcm_rhs(const fcm_handle* h, double* b_dev);

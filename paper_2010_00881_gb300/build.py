@@ -29,6 +29,7 @@ SOURCES = {
     "noalloc.cu": [],
     "peaks.cu": [],
     "batch.cu": [],
+    "mlhp_ops.cu": [],
     "mlhp.cu": ["-Xcompiler", "-ffp-contract=off"],
 }
 

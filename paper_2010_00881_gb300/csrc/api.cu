@@ -636,8 +636,8 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   if (geom->kind == FCM_GEOM_POPCORN && geom->n_params >= 3 && geom->params &&
       !(geom->params[2] > 0.0))
     throw Error(FCM_E_INVALID, "popcorn sigma must be > 0");
-  if (geom->kind == FCM_GEOM_VOIDS && (geom->n_params < 4 || geom->n_params % 4 || P.dim != 3))
-    throw Error(FCM_E_INVALID, "voids need 3D and 4 parameters per ball");
+  if (geom->kind == FCM_GEOM_VOIDS && (geom->n_params < 4 || geom->n_params % 4))
+    throw Error(FCM_E_INVALID, "voids need 4 parameters per ball (cx cy cz r; cz unused in 2D)");
   if (geom->kind == FCM_GEOM_ELLIPSOID && P.dim != 3)
     throw Error(FCM_E_INVALID, "ellipsoid needs 3D");
   if (geom->n_params < need || (need && !geom->params))
@@ -1905,6 +1905,238 @@ fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, lon
   *bytes = op_bytes(h->levels[level], which, prec);
   return FCM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Multi-level hp operator on the device (see mlhp_ops.cu).
+}  // extern "C"
+
+struct fcm_mlhp_op {
+  std::unique_ptr<fcm_handle> h;  // problem data, stream and device memory
+  long long M = 0;                // scalar functions
+  int nf = 1, nleaf = 0, max_nl = 0;
+  long long* off = nullptr;       // leaf incidence offsets (L + 1)
+  long long* fn = nullptr;        // incidences: function ids
+  long long* koff = nullptr;      // leaf matrix offsets
+  double* KL = nullptr;           // leaf matrices
+  double* Yl = nullptr;           // leaf products (nf per incidence)
+  long long* ioff = nullptr;      // per function: its incidences
+  long long* ibase = nullptr;
+  int* istride = nullptr;
+  double* b = nullptr;            // assembled load
+};
+
+namespace {
+
+void mlhp_op_build(fcm_mlhp_op* op, const fcm_mlhp* m, const fcm_grid* grid,
+                   const fcm_geometry* geom, const fcm_physics* phys) {
+  Handle* h = op->h.get();
+  if (!grid || !geom || !phys) throw Error(FCM_E_INVALID, "null descriptor");
+  fcm_grid g0 = *grid;
+  g0.overlay_levels = 0;
+  if (g0.space != FCM_SPACE_TENSOR)
+    throw Error(FCM_E_UNSUPPORTED, "overlay meshes carry tensor-product elements");
+  fcm_solver_opts opts;
+  std::memset(&opts, 0, sizeof(opts));
+  opts.smoother = FCM_SMOOTHER_ELEMENTWISE;
+  opts.n_pre = opts.n_post = 1;
+  opts.coarse_cells = 1;
+  build_problem(h, &g0, geom, phys, &opts);
+  Problem& P = h->P;
+  const int dim = P.dim, p = P.p, P1 = p + 1, nf = P.nf;
+  int ns = 1;
+  for (int a = 0; a < dim; ++a) ns *= P1;
+  const int n = nf * ns;
+  // topology from the host builder
+  long long M = 0, L = 0, ninc = 0, npatch = 0;
+  auto ok = [](fcm_status st) {
+    if (st != FCM_OK) throw Error(st, fcm_last_error());
+  };
+  ok(fcm_mlhp_sizes(m, &M, &L, &ninc, &npatch));
+  std::vector<int> flev(M), ft(3 * M), fq(3 * M), llev(L), lidx(3 * L);
+  std::vector<long long> loff(L + 1), lfn(ninc);
+  ok(fcm_mlhp_functions(m, flev.data(), ft.data(), fq.data()));
+  ok(fcm_mlhp_leaves(m, llev.data(), lidx.data(), loff.data(), lfn.data()));
+  int depth = 0;
+  for (int k : llev) depth = std::max(depth, k);
+  // 1D restriction tables for every (dk, pos): table (dk, pos) at entry
+  // ((2^dk - 1) + pos) P1^2
+  std::vector<double> S((size_t)((2 << depth) - 1) * P1 * P1);
+  for (int dk = 0; dk <= depth; ++dk)
+    for (int pos = 0; pos < (1 << dk); ++pos)
+      ok(fcm_mlhp_restriction_1d(p, dk, pos, S.data() + (size_t)((1 << dk) - 1 + pos) * P1 * P1));
+  // per incidence: table offsets and local modes per axis
+  std::vector<int> inc(6 * ninc, 0);
+  int max_nl = 0;
+  for (long long l = 0; l < L; ++l) {
+    const int k = llev[l];
+    max_nl = std::max(max_nl, (int)(nf * (loff[l + 1] - loff[l])));
+    for (long long e = loff[l]; e < loff[l + 1]; ++e) {
+      const long long f = lfn[e];
+      const int dk = k - flev[f];
+      if (dk < 0) throw Error(FCM_E_INVALID, "overlay topology: function above its leaf");
+      for (int a = 0; a < dim; ++a) {
+        const int ea = lidx[3 * l + a], ae = ea >> dk, pos = ea - (ae << dk);
+        const int t = ft[3 * f + a];
+        int mode;
+        if (t % 2 == 0)
+          mode = t / 2 == ae ? 0 : 1;
+        else
+          mode = fq[3 * f + a];
+        inc[6 * e + a] = ((1 << dk) - 1 + pos) * P1 * P1;
+        inc[6 * e + 3 + a] = mode;
+      }
+    }
+  }
+  if ((size_t)max_nl * sizeof(double) > 48 * 1024)
+    throw Error(FCM_E_UNSUPPORTED, "more than 6144 DOFs on one leaf");
+  if (mlhp_inc_bytes() != 6 * sizeof(int)) throw Error(FCM_E_CUDA, "incidence layout");
+  // cell matrices and loads of the leaves' boxes, level by level (a leaf of
+  // level k is a cell of the grid with 2^k times the base cells per axis)
+  double* gauss = h->alloc<double>(2 * P1);
+  launch_gauss_table(P1, gauss, h->s);
+  double* Kbox = h->alloc<double>((size_t)L * n * n);
+  double* bbox = h->alloc<double>((size_t)L * n);
+  const int max_nodes = next_pow_nodes(dim, P.quad_depth);
+  long long l0 = 0;
+  for (int k = 0; k <= depth; ++k) {
+    long long l1 = l0;
+    while (l1 < L && llev[l1] == k) ++l1;
+    if (l1 == l0) continue;
+    Problem Pk = P;
+    std::vector<int> cells(l1 - l0);
+    for (int a = 0; a < 3; ++a)
+      if (a < dim) {
+        Pk.C[a] = P.C[a] << k;
+        Pk.h[a] = (Pk.hi[a] - Pk.lo[a]) / Pk.C[a];
+      }
+    for (long long l = l0; l < l1; ++l) {
+      const int* e = &lidx[3 * l];
+      cells[l - l0] = e[0] + Pk.C[0] * (e[1] + Pk.C[1] * e[2]);
+    }
+    const int ne = (int)cells.size();
+    int* d_cells = h->upload(cells);
+    int* scratch = h->alloc<int>((element_scratch_bytes(ne, max_nodes) + 3) / 4);
+    launch_element_own(Pk, gauss, ne, d_cells, Kbox + (size_t)l0 * n * n, bbox + (size_t)l0 * n,
+                       scratch, max_nodes, h->s);
+    CKL();
+    l0 = l1;
+  }
+  if (l0 != L) throw Error(FCM_E_INVALID, "overlay topology: leaves not ordered by level");
+  // leaf matrices and loads
+  std::vector<long long> koff(L + 1, 0), woff(L + 1, 0);
+  for (long long l = 0; l < L; ++l) {
+    const long long nl = nf * (loff[l + 1] - loff[l]);
+    koff[l + 1] = koff[l] + nl * nl;
+    woff[l + 1] = woff[l] + (long long)n * nl;
+  }
+  op->off = h->upload(loff);
+  op->fn = h->upload(lfn);
+  op->koff = h->upload(koff);
+  op->KL = h->alloc<double>((size_t)std::max(1LL, koff[L]));
+  double* W = h->alloc<double>((size_t)std::max(1LL, woff[L]));
+  double* bL = h->alloc<double>((size_t)std::max(1LL, nf * ninc));
+  int* d_inc = h->upload(inc);
+  double* d_S = h->upload(S);
+  long long* d_woff = h->upload(woff);
+  launch_leaf_transform((int)L, dim, P1, nf, op->off, d_inc, d_S, Kbox, bbox, op->koff, d_woff,
+                        W, op->KL, bL, h->s);
+  CKL();
+  // inverse incidence lists: per function, its (leaf, position) pairs in
+  // leaf order; the value of field f sits at nf off[l] + f nfun_l + i
+  std::vector<long long> ioff(M + 1, 0);
+  for (long long e = 0; e < ninc; ++e) ++ioff[lfn[e] + 1];
+  for (long long i = 0; i < M; ++i) ioff[i + 1] += ioff[i];
+  std::vector<long long> ibase(ninc), fill(ioff.begin(), ioff.end() - 1);
+  std::vector<int> istride(ninc);
+  for (long long l = 0; l < L; ++l)
+    for (long long e = loff[l]; e < loff[l + 1]; ++e) {
+      const long long slot = fill[lfn[e]]++;
+      ibase[slot] = nf * loff[l] + (e - loff[l]);
+      istride[slot] = (int)(loff[l + 1] - loff[l]);
+    }
+  op->ioff = h->upload(ioff);
+  op->ibase = h->upload(ibase);
+  op->istride = h->upload(istride);
+  op->Yl = h->alloc<double>((size_t)std::max(1LL, nf * ninc));
+  op->b = h->alloc<double>((size_t)nf * M);
+  launch_leaf_gather(M, nf, op->ioff, op->ibase, op->istride, bL, op->b, h->s);
+  CKL();
+  CK(cudaStreamSynchronize(h->s));
+  op->M = M;
+  op->nf = nf;
+  op->nleaf = (int)L;
+  op->max_nl = max_nl;
+}
+
+}  // namespace
+
+extern "C" {
+
+fcm_status fcm_mlhp_op_create(const fcm_mlhp* m, const fcm_grid* grid, const fcm_geometry* geom,
+                              const fcm_physics* phys, void* stream, fcm_mlhp_op** out) {
+  if (!out || !m) {
+    g_last_error = "fcm_mlhp_op_create: null argument";
+    return FCM_E_INVALID;
+  }
+  *out = nullptr;
+  return guarded([&]() {
+    std::unique_ptr<fcm_mlhp_op> op(new fcm_mlhp_op());
+    op->h.reset(new fcm_handle());
+    Handle* h = op->h.get();
+    h->user = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CallScope cs(h);
+    mlhp_op_build(op.get(), m, grid, geom, phys);
+    cs.finish();
+    *out = op.release();
+    return FCM_OK;
+  });
+}
+
+fcm_status fcm_mlhp_op_ndofs(const fcm_mlhp_op* op, long long* n) {
+  if (!op || !n) {
+    g_last_error = "null argument";
+    return FCM_E_INVALID;
+  }
+  *n = op->M * op->nf;
+  return FCM_OK;
+}
+
+fcm_status fcm_mlhp_op_apply(fcm_mlhp_op* op, const double* x_dev, double* y_dev) {
+  if (!op || !x_dev || !y_dev) {
+    g_last_error = "null argument";
+    return FCM_E_INVALID;
+  }
+  return guarded([&]() {
+    Handle* h = op->h.get();
+    CallScope cs(h);
+    launch_leaf_apply(op->nleaf, op->nf, op->M, op->max_nl, op->off, op->fn, op->koff, op->KL,
+                      x_dev, op->Yl, h->s);
+    launch_leaf_gather(op->M, op->nf, op->ioff, op->ibase, op->istride, op->Yl, y_dev, h->s);
+    CKL();
+    cs.finish();
+    return FCM_OK;
+  });
+}
+
+fcm_status fcm_mlhp_op_rhs(const fcm_mlhp_op* op, double* b_dev) {
+  if (!op || !b_dev) {
+    g_last_error = "null argument";
+    return FCM_E_INVALID;
+  }
+  return guarded([&]() {
+    Handle* h = op->h.get();
+    CallScope cs(h);
+    CK(cudaMemcpyAsync(b_dev, op->b, op->M * op->nf * sizeof(double), cudaMemcpyDeviceToDevice,
+                       h->s));
+    cs.finish();
+    return FCM_OK;
+  });
+}
+
+void fcm_mlhp_op_destroy(fcm_mlhp_op* op) { delete op; }
 
 void fcm_destroy(fcm_handle* h) { delete h; }
 

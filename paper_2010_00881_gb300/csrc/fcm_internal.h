@@ -236,6 +236,21 @@ template <typename TV>
 void launch_node(const LevelGeom& g, const NodeSet<TV>& op, const TV* x, const TV* b, TV* out,
                  double w, int mode, cudaStream_t s);
 
+// Multi-level hp operator (mlhp_ops.cu): per-incidence restriction data
+// (mlhp_inc_bytes() bytes each: table offsets and local modes, 3 + 3 ints),
+// leaf matrices K_L = T^T K_box T and loads b_L = T^T b_box, the leaf-wise
+// apply and the fixed-order DOF gather.
+size_t mlhp_inc_bytes();
+void launch_leaf_transform(int nleaf, int dim, int P1, int nf, const long long* off,
+                           const void* inc, const double* S, const double* Kbox,
+                           const double* bbox, const long long* koff, const long long* woff,
+                           double* W, double* KL, double* bL, cudaStream_t s);
+void launch_leaf_apply(int nleaf, int nf, long long M, int max_nl, const long long* off,
+                       const long long* fn, const long long* koff, const double* KL,
+                       const double* x, double* Yl, cudaStream_t s);
+void launch_leaf_gather(long long M, int nf, const long long* ioff, const long long* ibase,
+                        const int* istride, const double* Yl, double* out, cudaStream_t s);
+
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };
 template <typename TV>

@@ -36,7 +36,8 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
            "fcm_cell_dofs", "fcm_mlhp_create", "fcm_mlhp_destroy", "fcm_mlhp_sizes",
            "fcm_mlhp_functions", "fcm_mlhp_leaves", "fcm_mlhp_patches",
            "fcm_mlhp_leaf_classes", "fcm_mlhp_levels", "fcm_mlhp_restriction_1d",
-           "fcm_measure_fma_peak", "fcm_solve"]
+           "fcm_measure_fma_peak", "fcm_solve", "fcm_mlhp_op_create", "fcm_mlhp_op_ndofs",
+           "fcm_mlhp_op_apply", "fcm_mlhp_op_rhs", "fcm_mlhp_op_destroy"]
 
 
 class fcm_grid(C.Structure):
@@ -143,9 +144,17 @@ def load():
     lib.fcm_mlhp_leaf_classes.argtypes = [P, C.POINTER(C.c_byte)]
     lib.fcm_mlhp_levels.argtypes = [P, IP, IP]
     lib.fcm_mlhp_restriction_1d.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
+    lib.fcm_mlhp_op_create.argtypes = [P, C.POINTER(fcm_grid), C.POINTER(fcm_geometry),
+                                       C.POINTER(fcm_physics), P, C.POINTER(P)]
+    lib.fcm_mlhp_op_ndofs.argtypes = [P, LL]
+    lib.fcm_mlhp_op_apply.argtypes = [P, P, P]
+    lib.fcm_mlhp_op_rhs.argtypes = [P, P]
+    lib.fcm_mlhp_op_destroy.argtypes = [P]
+    lib.fcm_mlhp_op_destroy.restype = None
     lib.fcm_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("fcm_destroy", "fcm_batch_destroy", "fcm_last_error", "fcm_mlhp_destroy"):
+        if name not in ("fcm_destroy", "fcm_batch_destroy", "fcm_last_error", "fcm_mlhp_destroy",
+                        "fcm_mlhp_op_destroy"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -224,6 +233,49 @@ class Overlay:
             lib.fcm_mlhp_destroy(h)
         self.n_functions = M
         self.n_leaves = L
+
+
+class MlhpOperator:
+    """Operator and load of an overlay mesh on the device (fcm_mlhp_op_*):
+    leaf matrices integrated and mapped to the leaves' functions on the GPU;
+    apply(x) = A x for a CUDA float64 tensor of ndofs entries (field-major,
+    the function order of Overlay)."""
+
+    def __init__(self, prob: dict):
+        import torch
+        self._torch = torch
+        g, gm, ph, _, self._keep = descriptors(prob)
+        lib = load()
+        m = C.c_void_p()
+        _check(lib.fcm_mlhp_create(C.byref(g), C.byref(gm), C.byref(m)))
+        try:
+            self.h = C.c_void_p()
+            stream = torch.cuda.current_stream().cuda_stream
+            _check(lib.fcm_mlhp_op_create(m, C.byref(g), C.byref(gm), C.byref(ph),
+                                          C.c_void_p(stream), C.byref(self.h)))
+        finally:
+            lib.fcm_mlhp_destroy(m)
+        n = C.c_longlong()
+        _check(lib.fcm_mlhp_op_ndofs(self.h, C.byref(n)))
+        self.ndofs = n.value
+
+    def _empty(self):
+        return self._torch.empty(self.ndofs, dtype=self._torch.float64, device="cuda")
+
+    def apply(self, x):
+        y = self._empty()
+        _check(load().fcm_mlhp_op_apply(self.h, _ptr(x), _ptr(y)))
+        return y
+
+    def rhs(self):
+        b = self._empty()
+        _check(load().fcm_mlhp_op_rhs(self.h, _ptr(b)))
+        return b
+
+    def close(self):
+        if self.h:
+            load().fcm_mlhp_op_destroy(self.h)
+            self.h = None
 
 
 def measure_fma_peak(prec: int) -> float:
