@@ -77,7 +77,12 @@ enum { FCM_SMOOTHER_ELEMENTWISE = 0, FCM_SMOOTHER_PATCHWISE = 1, FCM_SMOOTHER_JA
  * sum to at most p; the p-levels use the trunk spaces of their degrees).
  * With trunk elements vectors keep the tensor layout: the other modes are
  * removed from the system (zero rows, columns, loads and corrections) and
- * stay zero in every result; fcm_level_info.ndofs_active counts the rest. */
+ * stay zero in every result; fcm_level_info.ndofs_active counts the rest.
+ * drop_outside: 1 removes the cells classified outside the physical domain
+ * together with the DOFs supported only on them (Sec. 4.3 and 4.3.2; trunk
+ * space only): their matrices, loads and blocks are left out, the Q1
+ * h-levels keep the coarse nodes some kept fine node depends on, and the
+ * removed DOFs keep their slots in the vectors like removed trunk modes. */
 enum { FCM_SPACE_TENSOR = 0, FCM_SPACE_TRUNK = 1 };
 typedef struct {
   int dim;
@@ -87,6 +92,7 @@ typedef struct {
   int overlay_levels;
   int overlay_p;
   int space;
+  int drop_outside;
 } fcm_grid;
 
 /* Level-set geometry, Omega_phys = {psi <= 0}.  params (host memory, read

@@ -30,6 +30,7 @@ SOURCES = {
     "peaks.cu": [],
     "batch.cu": [],
     "mlhp_ops.cu": [],
+    "masks.cu": [],
     "mlhp.cu": ["-Xcompiler", "-ffp-contract=off"],
 }
 

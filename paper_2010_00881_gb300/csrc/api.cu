@@ -76,6 +76,11 @@ struct Level {
   double* Kown_c = nullptr;         // canonical n x n own cell matrices (setup only)
   std::vector<int> h_own_index;
   std::vector<double> h_scale_cell;
+  // removed cells and DOFs (trunk modes, fully fictitious cells): h_drop
+  // per cell of a p-level (1: removed), h_keep per scalar DOF (empty: all
+  // kept); d_keep its device copy
+  std::vector<unsigned char> h_drop, h_keep;
+  unsigned char* d_keep = nullptr;
   // work vectors
   double *x = nullptr, *b = nullptr, *r = nullptr, *Y = nullptr;
   float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr, *Y32 = nullptr;
@@ -444,10 +449,14 @@ void record_vcycle(Handle* h, int l, int top64) {
   } else {
     record_vcycle<TV>(h, l - 1, top64);
   }
-  if (Lc.is_h)
+  if (Lc.is_h) {
     launch_h_prolong_add<TV>(Lc.g, L.g, V::x(Lc), x, s);
-  else
+    // interpolation reaches the removed nodes next to kept ones (the
+    // operator's columns there are zero): keep the iterate zero on them
+    if (h->P.drop && L.d_keep) launch_mask_vec<TV>(L.g.N, L.g.M, L.d_keep, x, s);
+  } else {
     launch_p_prolong_add<TV>(Lc.g, L.g, V::x(Lc), x, s);
+  }
   for (int k = 0; k < h->n_post; ++k) {
     apply(false, x, b, r, 1.0, GATHER_RESID);
     if (jac)
@@ -492,11 +501,14 @@ cudaGraphExec_t capture_vcycle(Handle* h, long long* nodes, int top64) {
 
 // ---------------------------------------------------------------------------
 // Levels whose operations run node-centric (launch_node): one mode per node
-// and field (p = 1 and the Q1 h-levels), scalar or vector fields.
+// (p = 1 and the Q1 h-levels) of a scalar field.  With vector fields every
+// lane would load all nf 2^d coefficients of its cell (24 in 3D
+// elasticity), and the cell kernels with the gather are faster (64^3, p = 2
+// elasticity: 11.0 against 11.9 M DOFs/s per solve).
 bool node_level(const Level& L) {
   const LevelGeom& g = L.g;
-  const bool shape = (g.dim == 3 && (g.nf == 1 || g.nf == 3)) || (g.dim == 2 && (g.nf == 1 || g.nf == 2));
-  return (L.is_h || g.p == 1) && shape && g.nloc == (g.nf << g.dim);
+  return (L.is_h || g.p == 1) && g.nf == 1 && (g.dim == 2 || g.dim == 3) &&
+         g.nloc == (1 << g.dim);
 }
 
 // Node set from per-cell codes, shared matrix ids and scales (host arrays).
@@ -543,6 +555,11 @@ std::vector<unsigned char> trunk_keep(const LevelGeom& g) {
 }
 
 long long active_dofs(const Handle* h, const Level& L) {
+  if (!L.h_keep.empty()) {
+    long long m = 0;
+    for (unsigned char k : L.h_keep) m += k;
+    return m * L.g.nf;
+  }
   if (!trunk_level(h, L)) return L.g.N;
   // count by the distribution of bubble-degree sums, axis by axis
   const int p = L.g.p;
@@ -566,13 +583,75 @@ long long active_dofs(const Handle* h, const Level& L) {
 // with the entries of removed trunk modes taken as zero (copied to cb).
 const double* solve_rhs(Handle* h, const double* b_in) {
   if (!b_in) return h->b;
-  if (!h->P.trunk) return b_in;
-  const LevelGeom& g = h->levels.back().g;
+  const Level& T = h->levels.back();
+  if (!T.d_keep) return b_in;
+  const LevelGeom& g = T.g;
   if (b_in != h->cb)
     CK(cudaMemcpyAsync(h->cb, b_in, g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-  launch_trunk_mask_vec(g, g.p, h->cb, h->s);
+  launch_mask_vec(g.N, g.M, T.d_keep, h->cb, h->s);
   CKL();
   return h->cb;
+}
+
+// Kept scalar DOFs of every level (trunk modes; DOFs of kept cells; on the
+// Q1 h-levels the coarse nodes some kept node of the finer level depends
+// on: fine node i lies in the support of coarse nodes ceil((i-1)/2) ..
+// floor((i+1)/2) per axis).  Levels that keep everything get no mask.
+void build_keep_masks(Handle* h) {
+  const Problem& P = h->P;
+  const int top = (int)h->levels.size() - 1;
+  for (int l = top; l >= 0; --l) {
+    Level& L = h->levels[l];
+    const LevelGeom& g = L.g;
+    std::vector<unsigned char> keep((size_t)g.M, 1);
+    if (!L.is_h) {
+      if (trunk_level(h, L)) keep = trunk_keep(g);
+      if (P.drop) {
+        std::vector<unsigned char> sup((size_t)g.M, 0);
+        const int P1 = g.p + 1;
+        for (int c = 0; c < g.ncells; ++c) {
+          if (L.h_drop[c]) continue;
+          const int cc[3] = {c % g.C[0], (c / g.C[0]) % g.C[1], c / (g.C[0] * g.C[1])};
+          for (int s = 0; s < g.nloc_s; ++s) {
+            long long idx = 0, stride = 1;
+            int t = s;
+            for (int a = 0; a < g.dim; ++a) {
+              const int j = t % P1;
+              t /= P1;
+              idx += (long long)dof1(g.C[a], cc[a], j) * stride;
+              stride *= g.m[a];
+            }
+            sup[(size_t)idx] = 1;
+          }
+        }
+        for (size_t i = 0; i < keep.size(); ++i) keep[i] &= sup[i];
+      }
+    } else {
+      const Level& F = h->levels[l + 1];
+      std::fill(keep.begin(), keep.end(), 0);
+      for (long long i = 0; i < F.g.M; ++i) {
+        if (!F.h_keep.empty() && !F.h_keep[(size_t)i]) continue;
+        long long t = i;
+        int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) {
+          const int ia = (int)(t % F.g.m[a]);
+          t /= F.g.m[a];
+          lo[a] = ia / 2;            // ceil((ia - 1) / 2)
+          hi[a] = std::min((ia + 1) / 2, g.m[a] - 1);
+        }
+        for (int kz = lo[2]; kz <= hi[2]; ++kz)
+          for (int ky = lo[1]; ky <= hi[1]; ++ky)
+            for (int kx = lo[0]; kx <= hi[0]; ++kx)
+              keep[(size_t)kx + (size_t)g.m[0] * (ky + (size_t)g.m[1] * kz)] = 1;
+      }
+    }
+    bool all = true;
+    for (unsigned char k : keep) all = all && k;
+    if (!all) {
+      L.h_keep = keep;
+      L.d_keep = h->upload(keep);
+    }
+  }
 }
 
 void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
@@ -589,6 +668,11 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   P.dim = grid->dim;
   P.p = grid->p;
   P.trunk = grid->space == FCM_SPACE_TRUNK ? 1 : 0;
+  if (grid->drop_outside != 0 && grid->drop_outside != 1)
+    throw Error(FCM_E_INVALID, "drop_outside must be 0 or 1");
+  P.drop = grid->drop_outside;
+  if (P.drop && !P.trunk)
+    throw Error(FCM_E_UNSUPPORTED, "fictitious cells are removed with trunk-space elements only");
   P.pde = phys->pde;
   if (P.pde != FCM_PDE_POISSON && P.pde != FCM_PDE_ELASTICITY)
     throw Error(FCM_E_INVALID, "unknown pde");
@@ -678,7 +762,7 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     throw Error(FCM_E_UNSUPPORTED, "patchwise additive Schwarz blocks are not implemented");
   if (opts->smoother != FCM_SMOOTHER_ELEMENTWISE && opts->smoother != FCM_SMOOTHER_JACOBI)
     throw Error(FCM_E_INVALID, "unknown smoother");
-  if (P.trunk && opts->smoother == FCM_SMOOTHER_JACOBI)
+  if ((P.trunk || P.drop) && opts->smoother == FCM_SMOOTHER_JACOBI)
     throw Error(FCM_E_UNSUPPORTED, "the Jacobi smoother is not built for trunk-space elements");
   h->smoother = opts->smoother;
   h->n_pre = opts->n_pre;
@@ -910,6 +994,7 @@ void build_smoother(Handle* h, Level& L) {
     cc[0] = c % g.C[0];
     cc[1] = (c / g.C[0]) % g.C[1];
     cc[2] = c / (g.C[0] * g.C[1]);
+    const bool dropped = !L.h_drop.empty() && L.h_drop[c];
     bool ok = !L.is_h;
     double s0 = 0.0;
     int sig = 0;
@@ -926,7 +1011,7 @@ void build_smoother(Handle* h, Level& L) {
         }
         if (!exists) continue;
         int ncell = nb[0] + g.C[0] * (nb[1] + g.C[1] * nb[2]);
-        if (L.h_own_index[ncell] >= 0) {
+        if (L.h_own_index[ncell] >= 0 || (!L.h_drop.empty() && L.h_drop[ncell])) {
           ok = false;
           break;
         }
@@ -941,7 +1026,12 @@ void build_smoother(Handle* h, Level& L) {
         sig |= sa << (2 * a);
       }
     }
-    if (ok) {
+    if (dropped) {
+      // a removed cell: no block (the shared block of its signature, scaled
+      // by 0, so that its products are written as zeros)
+      shared.push_back({sig, c});
+      shared_s.push_back(0.0);
+    } else if (ok) {
       shared.push_back({sig, c});
       shared_s.push_back(s0);
     } else {
@@ -959,11 +1049,18 @@ void build_smoother(Handle* h, Level& L) {
     launch_block_assemble(g, nown, d_cells, src, inv, h->s);
     CKL();
     if (trunk) launch_trunk_mask_mats(nown, g.dim, g.nf, g.p, g.p, true, inv, h->s);
+    // removed DOFs (fully fictitious cells): empty rows of the blocks
+    unsigned char* empty = nullptr;
+    if (h->P.drop) {
+      empty = h->alloc<unsigned char>((size_t)nown * n);
+      launch_mask_empty_rows(nown, n, 0, inv, empty, h->s);
+    }
     double* d_piv = h->alloc<double>(2 * (size_t)nown);
     int* d_info = h->alloc<int>(nown);
     launch_chol_inverse(nown, n, inv, d_piv, d_info, h->s);
     CKL();
     if (trunk) launch_trunk_mask_mats(nown, g.dim, g.nf, g.p, g.p, false, inv, h->s);
+    if (empty) launch_mask_empty_rows(nown, n, 1, inv, empty, h->s);
     check_status(h, d_info, nown, "additive Schwarz block");
     piv.resize(2 * (size_t)nown);
     CK(cudaMemcpyAsync(piv.data(), d_piv, piv.size() * sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -991,7 +1088,7 @@ void build_smoother(Handle* h, Level& L) {
     if (sigs.empty() || sigs.back() != sg) sigs.push_back(sg);
     mat_of.push_back((int)sigs.size() - 1);
     cells.push_back(shared[k].second);
-    scale.push_back(1.0 / shared_s[k]);
+    scale.push_back(shared_s[k] == 0.0 ? 0.0 : 1.0 / shared_s[k]);
   }
   double* sinv = nullptr;
   if (!sigs.empty()) {
@@ -1108,11 +1205,11 @@ void estimate_omega(Handle* h, Level& L, double omega_paper) {
   double* v = L.x;
   double* Av = L.r;
   double* w = L.b;
-  if (trunk_level(h, L)) {
-    // v_k = sin(k + 1) over the level's trunk DOFs numbered consecutively
-    // (the removed modes zero), the start vector of the tensor case
+  if (!L.h_keep.empty()) {
+    // v_k = sin(k + 1) over the level's kept DOFs numbered consecutively
+    // (the removed ones zero), the start vector of the full space
     std::vector<double> hv((size_t)N, 0.0);
-    std::vector<unsigned char> keep = trunk_keep(L.g);
+    const std::vector<unsigned char>& keep = L.h_keep;
     long long k = 0;
     for (long long i = 0; i < N; ++i)
       if (keep[(size_t)(i % L.g.M)]) hv[(size_t)i] = std::sin((double)(k++) + 1.0);
@@ -1158,9 +1255,19 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   CK(cudaMemcpyAsync(faces.data(), d_faces, ncell, cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
 
-  std::vector<int> own_cells, sh_cells;
+  std::vector<int> own_cells, sh_cells, dropped;
   std::vector<double> sh_scale;
+  // removed cells (drop_outside) keep a place among the shared cells with
+  // scale 0: every cell kernel still writes their (zero) products
+  std::vector<unsigned char> drop_cell(ncell, 0);
   for (int c = 0; c < ncell; ++c) {
+    if (P.drop && h->cls[c] == CLS_OUTSIDE) {
+      drop_cell[c] = 1;
+      dropped.push_back(c);
+      sh_cells.push_back(c);
+      sh_scale.push_back(0.0);
+      continue;
+    }
     bool own = h->cls[c] == CLS_CUT;
     if (P.dirichlet == FCM_DIR_FACES && (faces[c] & P.dir_faces)) own = true;
     if (P.traction_face >= 0 && (faces[c] >> P.traction_face) & 1u) own = true;
@@ -1193,6 +1300,12 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   int* d_sh = sh_cells.empty() ? nullptr : h->upload(sh_cells);
   launch_load_uncut(P, gauss, (int)sh_cells.size(), d_sh, d_cls, Bcells, h->s);
   launch_scatter_rows((int)own_cells.size(), d_elist, bown, n, ncell, Bcells, h->s);
+  if (!dropped.empty()) {
+    // removed cells contribute no load
+    double* zeros = h->alloc<double>(dropped.size() * (size_t)n);
+    CK(cudaMemsetAsync(zeros, 0, dropped.size() * (size_t)n * sizeof(double), h->s));
+    launch_scatter_rows((int)dropped.size(), h->upload(dropped), zeros, n, ncell, Bcells, h->s);
+  }
   h->b = h->alloc<double>(gt.N);
   launch_gather<double>(gt, GATHER_SET, Bcells, nullptr, h->b, 1.0, h->s);
   if (P.trunk && p >= 2) launch_trunk_mask_vec(gt, p, h->b, h->s);
@@ -1204,6 +1317,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   {
     Level L;
     L.g = gt;
+    if (P.drop) L.h_drop = drop_cell;
     build_operator(h, L, own_cells, own_cells.empty() ? nullptr : Ktop, KrefTop, sh_cells,
                    sh_scale);
     prepare_kron(h, L);
@@ -1212,6 +1326,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   for (int pc = p - 1; pc >= 1; --pc) {
     Level L;
     L.g = make_geom(dim, nf, pc, P.C);
+    if (P.drop) L.h_drop = drop_cell;
     int nl = L.g.nloc;
     double* Kown = own_cells.empty() ? nullptr : h->alloc<double>(own_cells.size() * (size_t)nl * nl);
     double* Kref = h->alloc<double>((size_t)nl * nl);
@@ -1247,6 +1362,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   }
   std::reverse(lv.begin(), lv.end());
   h->levels = std::move(lv);
+  if (P.trunk || P.drop) build_keep_masks(h);
 
   g_stage = "coarse factorisation";
   // coarsest level: dense matrix, Cholesky, factor inverse
@@ -1276,6 +1392,11 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     (void)d_all;
     L0.Linv = h->alloc<double>((size_t)N0 * N0);
     launch_dense_assemble(L0.g, Kall, L0.Linv, h->s);
+    if (P.drop) {
+      // coarse nodes no kept node depends on: a unit diagonal
+      unsigned char* flags = h->alloc<unsigned char>(N0);
+      launch_mask_empty_rows(1, (int)N0, 0, L0.Linv, flags, h->s);
+    }
     int* d_info = h->alloc<int>(1);
     launch_chol_factor((int)N0, L0.Linv, d_info, h->s);
     CKL();

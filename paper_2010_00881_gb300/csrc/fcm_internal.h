@@ -102,6 +102,7 @@ struct Problem {
   double traction[3];
   int quad_depth;
   int trunk;                    // 1: trunk-space elements (non-trunk modes removed)
+  int drop;                     // 1: fully fictitious cells removed
 };
 
 // Cell classes.
@@ -250,6 +251,15 @@ void launch_leaf_apply(int nleaf, int nf, long long M, int max_nl, const long lo
                        const double* x, double* Yl, cudaStream_t s);
 void launch_leaf_gather(long long M, int nf, const long long* ioff, const long long* ibase,
                         const int* istride, const double* Yl, double* out, cudaStream_t s);
+
+// Removed DOFs (fully fictitious cells dropped): empty rows of `count`
+// assembled n x n blocks get a unit diagonal (phase 0, flags written) and
+// are zeroed in the inverse (phase 1); a vector's entries of removed scalar
+// DOFs (keep[i % M] == 0) are zeroed.
+void launch_mask_empty_rows(long long count, int n, int phase, double* mats,
+                            unsigned char* flags, cudaStream_t s);
+template <typename T>
+void launch_mask_vec(long long N, long long M, const unsigned char* keep, T* v, cudaStream_t s);
 
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };

@@ -1674,7 +1674,7 @@ __device__ __forceinline__ void gather_store(const TV v[8], const TV* __restrict
 
 // kGatherDofs DOFs per thread (I, I + stride, ...), all their loads in
 // flight before any sum.
-constexpr int kGatherDofs = 2;
+constexpr int kGatherDofs = 1;
 template <typename TV, int MODE>
 __global__ void __launch_bounds__(256) gather_kernel(LevelGeom g, const TV* __restrict__ Y,
                                                      const TV* __restrict__ b,

@@ -43,7 +43,7 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
 class fcm_grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("cells", C.c_int * 3), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("p", C.c_int), ("overlay_levels", C.c_int),
-                ("overlay_p", C.c_int), ("space", C.c_int)]
+                ("overlay_p", C.c_int), ("space", C.c_int), ("drop_outside", C.c_int)]
 
 
 class fcm_geometry(C.Structure):
@@ -298,8 +298,10 @@ def descriptors(prob: dict, build_mixed: bool = True):
     ValueError for problem features the library has no descriptor for
     (trunk-space elements, removal of fictitious cells, geometry kinds or
     smoothers it does not know) instead of dropping them."""
-    if prob.get("space", "tensor") not in ("tensor", "trunk") or prob.get("drop_outside"):
-        raise ValueError("the library discretises all cells with tensor-product or trunk elements")
+    if prob.get("space", "tensor") not in ("tensor", "trunk"):
+        raise ValueError("the library discretises with tensor-product or trunk elements")
+    if prob.get("drop_outside") and prob.get("space", "tensor") != "trunk":
+        raise ValueError("the library removes fictitious cells with trunk elements only")
     if prob["geometry"]["kind"] not in GEOM:
         raise ValueError(f"geometry kind {prob['geometry']['kind']!r} has no library descriptor")
     if prob.get("smoother", "elementwise") not in SMOOTHER:
@@ -314,6 +316,7 @@ def descriptors(prob: dict, build_mixed: bool = True):
     g.p = prob["p"]
     g.overlay_levels = prob.get("overlay_levels", 0)
     g.space = SPACE_TRUNK if prob.get("space", "tensor") == "trunk" else SPACE_TENSOR
+    g.drop_outside = 1 if prob.get("drop_outside") else 0
     geo = prob["geometry"]
     kind = geo["kind"]
     if kind == "ball":

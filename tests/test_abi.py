@@ -242,16 +242,19 @@ def test_overlay_leaf_classes_and_levels_match_the_oracle(make):
 
 def test_descriptors_refuse_what_the_library_lacks():
     """Problem features without a library descriptor raise instead of being
-    dropped silently (removal of fully fictitious cells, spaces other than
-    tensor and trunk); overlays, patchwise blocks and trunk elements with the
-    Jacobi smoother reach the library (which rejects them in fcm_setup)."""
+    dropped silently (spaces other than tensor and trunk, removal of fully
+    fictitious cells without trunk elements); overlays, patchwise blocks and
+    trunk elements with the Jacobi smoother reach the library (which rejects
+    them in fcm_setup)."""
     import fcm_inputs as fi
     from paper_2010_00881_gb300 import fcm
     base = fi.poisson3d_sphere(cells=4, p=2)
     for bad in (dict(base, space="serendipity"), dict(base, drop_outside=True),
-                fi.popcorn(cells=4), dict(base, smoother="gauss_seidel")):
+                fi.popcorn(cells=4, space="tensor"), dict(base, smoother="gauss_seidel")):
         with pytest.raises(ValueError):
             fcm.descriptors(bad)
+    g, _, _, _, _ = fcm.descriptors(fi.popcorn(cells=4))
+    assert g.space == fcm.SPACE_TRUNK and g.drop_outside == 1
     g, _, _, op, _ = fcm.descriptors(fi.poisson3d_sphere_mlhp(cells=4))
     assert g.overlay_levels == 3 and op.smoother == 1
     g, _, _, op, _ = fcm.descriptors(dict(base, space="trunk", smoother="jacobi"))

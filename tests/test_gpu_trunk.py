@@ -1,5 +1,6 @@
-"""Trunk-space elements (Sec. 4.3) on the GPU, through the C ABI, against
-the oracle's trunk hierarchy (oracle.trunk.TrunkHierarchy).
+"""Trunk-space elements (Sec. 4.3) on the GPU, with and without removal of
+the fully fictitious cells (Sec. 4.3.2), through the C ABI, against the
+oracle's trunk hierarchy (oracle.trunk.TrunkHierarchy).
 
 The library keeps the tensor layout and removes the non-trunk modes from the
 system; the oracle numbers the trunk DOFs consecutively.  A library vector
@@ -33,25 +34,35 @@ def _trunk(prob):
     return dict(prob, space="trunk")
 
 
+def _drop(prob):
+    return dict(prob, space="trunk", drop_outside=True)
+
+
 CASES = {
     "sphere4_p3": lambda: _trunk(fi.poisson3d_sphere(cells=4, p=3)),
     "sphere5_p2": lambda: _trunk(fi.poisson3d_sphere(cells=5, p=2)),
     "circle8_p4": lambda: _trunk(fi.poisson2d_circle(cells=8, p=4)),
     "elastic4_p2": lambda: _trunk(fi.elasticity3d_voids(cells=4, p=2, n_voids=3, seed=1)),
+    # fully fictitious cells removed as well (the paper's popcorn setting)
+    "sphere6_p3_drop": lambda: _drop(fi.poisson3d_sphere(cells=6, p=3)),
+    "circle9_p4_drop": lambda: _drop(fi.poisson2d_circle(cells=9, p=4)),
+    "popcorn8_p2_drop": lambda: fi.popcorn(cells=8, p=2),
 }
 
 
 # Energy-norm error of the mixed V-cycle against the oracle's FP64 V-cycle
 # (random residual, seed 2) measured on a GB300; the test bar is 10 x these.
 MIXED_VCYCLE = {"sphere4_p3": 5.5e-7, "sphere5_p2": 1.1e-6, "circle8_p4": 3.7e-5,
-                "elastic4_p2": 3.7e-7}
+                "elastic4_p2": 3.7e-7, "sphere6_p3_drop": 2.0e-5, "circle9_p4_drop": 2.8e-5,
+                "popcorn8_p2_drop": 1.6e-6}
 
 
-def _level_index(prob, nf, pc):
+def _level_index(prob, nf, pc, kept):
     """Library indices (tensor layout of degree pc, fields stacked) of the
-    oracle's DOFs of the trunk p-level of degree pc, in the oracle's order."""
+    oracle's DOFs of the trunk p-level of degree pc, in the oracle's order;
+    kept: the finest level's kept scalar ids (degree-p layout)."""
     d, C, p = prob["dim"], prob["cells"], prob["p"]
-    ts = np.flatnonzero(trunk_global_mask(d, C, p, pc))     # ids in the degree-p layout
+    ts = kept[trunk_global_mask(d, C, p, pc)[kept]]          # ids in the degree-p layout
     out = np.zeros(len(ts), dtype=np.int64)
     rem = ts.copy()
     stride = 1
@@ -71,7 +82,8 @@ class Case:
         self.H = TrunkHierarchy(self.prob)
         self.s = Solver(self.prob)
         self.nf = self.H.space.nf
-        self.idx, self.N = _level_index(self.prob, self.nf, self.prob["p"])
+        self.kept = self.H.space.tensor_index
+        self.idx, self.N = _level_index(self.prob, self.nf, self.prob["p"], self.kept)
 
     def to_lib(self, xo, idx=None, N=None):
         idx = self.idx if idx is None else idx
@@ -113,7 +125,7 @@ def test_levels_and_dofs(case):
         info = s.level_info(l)
         assert info["ndofs_active"] == lv.N, (c.name, l, info["ndofs_active"], lv.N)
         assert info["p"] == lv.p
-        if info["p"] == 1:
+        if info["p"] == 1 and not c.prob.get("drop_outside"):
             assert info["ndofs"] == lv.N
         if l > 0:
             assert abs(info["omega"] - lv.omega) <= 1e-6 * lv.omega, (l, info["omega"], lv.omega)
@@ -147,7 +159,7 @@ def test_level_operators(case):
         info = s.level_info(l)
         if info["is_h_level"] or l == 0:
             continue
-        idx, N = _level_index(c.prob, c.nf, lv.p)
+        idx, N = _level_index(c.prob, c.nf, lv.p, c.kept)
         xo = fi.random_vector(lv.N, seed=10 + l)
         x = c.to_lib(xo, idx, N)
         y = s.level_op(l, F.OP_APPLY, torch.from_numpy(x).cuda(), N).cpu().numpy()
