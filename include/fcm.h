@@ -317,14 +317,37 @@ fcm_status fcm_mlhp_restriction_1d(int p, int dk, int pos, double* S);
  * fcm_mlhp_op_apply: y = A x: y_L = K_L x_L per leaf, the leaf results
  *   summed per DOF in a fixed order (reproducible bit for bit).
  * fcm_mlhp_op_rhs: the assembled load b.
- * The multigrid hierarchy of overlay meshes (hp-levels, patchwise blocks)
- * is not built on the device; fcm_setup refuses overlays. */
+ * fcm_mlhp_op_prepare: the hp-multigrid of Sec. 3.2 on the overlay mesh
+ *   (Fig. hpmultigrid): the hp-levels of fcm_mlhp_levels as masks of the
+ *   full-length vectors (restriction: the coarser level's mask;
+ *   prolongation: an add), additive Schwarz blocks on every level >= 1
+ *   (opts->smoother PATCHWISE: the functions touching the base cells around
+ *   a base node, Sec. 3.3.1; ELEMENTWISE: those touching one base cell),
+ *   inverted densely, omega as in fcm_setup (patchwise paper values 1/6 in
+ *   2D, 1/18 in 3D), the coarsest level (the base grid's hats) solved by its
+ *   dense inverse.  The blocks are assembled and inverted on the host at
+ *   set-up; FCM_E_UNSUPPORTED when the base grid has more than
+ *   opts->coarse_cells cells on an axis (the uniform Q1 h-levels below the
+ *   base grid are not built for overlays) or a block exceeds 6144 DOFs.
+ * fcm_mlhp_op_level: per level (0 = coarsest) its DOFs, omega, number and
+ *   largest size of its blocks.
+ * fcm_mlhp_op_vcycle: z = V(r), Algorithm 1 with zero initial guess, every
+ *   operation on the device.
+ * fcm_mlhp_op_pcg: V-cycle-preconditioned CG in FP64 from x = 0 (b_dev
+ *   NULL: the assembled load), as fcm_pcg_solve.
+ * fcm_setup refuses overlays. */
 typedef struct fcm_mlhp_op fcm_mlhp_op;
 fcm_status fcm_mlhp_op_create(const fcm_mlhp* m, const fcm_grid* grid, const fcm_geometry* geom,
                               const fcm_physics* phys, void* stream, fcm_mlhp_op** out);
 fcm_status fcm_mlhp_op_ndofs(const fcm_mlhp_op* op, long long* n);
 fcm_status fcm_mlhp_op_apply(fcm_mlhp_op* op, const double* x_dev, double* y_dev);
 fcm_status fcm_mlhp_op_rhs(const fcm_mlhp_op* op, double* b_dev);
+fcm_status fcm_mlhp_op_prepare(fcm_mlhp_op* op, const fcm_solver_opts* opts);
+fcm_status fcm_mlhp_op_level(const fcm_mlhp_op* op, int level, long long* ndofs, double* omega,
+                             int* n_blocks, int* max_block);
+fcm_status fcm_mlhp_op_vcycle(fcm_mlhp_op* op, const double* r_dev, double* z_dev);
+fcm_status fcm_mlhp_op_pcg(fcm_mlhp_op* op, const double* b_dev, double* x_dev, double rtol,
+                           int maxit, fcm_info* info);
 void fcm_mlhp_op_destroy(fcm_mlhp_op* op);
 
 /* Copy the assembled load vector b into b_dev (ndofs doubles). */

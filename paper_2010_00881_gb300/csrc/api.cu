@@ -2031,10 +2031,45 @@ fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, lon
 // Multi-level hp operator on the device (see mlhp_ops.cu).
 }  // extern "C"
 
+// One level of the overlay hp-multigrid (full-length vectors, removed
+// functions zero): the level's DOF mask, its additive Schwarz blocks (DOF
+// lists, dense inverses) with their fixed-order gather lists, omega.
+struct MlhpLevel {
+  long long ndofs = 0;
+  unsigned char* mask = nullptr;
+  int nblk = 0, max_m = 0;
+  long long* boff = nullptr;      // block DOF-list offsets
+  long long* bdof = nullptr;      // block DOFs (global, field-major)
+  long long* binv_off = nullptr;  // inverse offsets
+  double* binv = nullptr;         // dense inverses, row-major (symmetric)
+  long long* gioff = nullptr;     // per DOF: its block entries
+  long long* gibase = nullptr;
+  int* gistride = nullptr;
+  double omega = 0.0, lambda = 0.0;
+  double *x = nullptr, *b = nullptr, *r = nullptr;  // work vectors
+};
+
 struct fcm_mlhp_op {
   std::unique_ptr<fcm_handle> h;  // problem data, stream and device memory
   long long M = 0;                // scalar functions
   int nf = 1, nleaf = 0, max_nl = 0;
+  int dim = 0, C[3] = {1, 1, 1};
+  // host copies kept for the hierarchy: leaf incidences, leaf matrix
+  // offsets, patches and the hp-level of every function
+  std::vector<long long> h_loff, h_lfn, h_koff, h_patch_off, h_patch_fn;
+  std::vector<int> h_coarsest, h_llev, h_lidx;
+  int n_levels = 0;
+  std::vector<MlhpLevel> lv;      // 0 = coarsest
+  int n_pre = 5, n_post = 5;
+  double *y = nullptr, *z = nullptr, *Yb = nullptr;  // apply / smoother scratch
+  double *cx = nullptr, *cr = nullptr, *cp = nullptr, *cq = nullptr, *cz = nullptr,
+         *cb = nullptr;
+  double* part = nullptr;
+  double* d_scalar = nullptr;
+  double* h_scalar = nullptr;     // pinned
+  ~fcm_mlhp_op() {
+    if (h_scalar) cudaFreeHost(h_scalar);
+  }
   long long* off = nullptr;       // leaf incidence offsets (L + 1)
   long long* fn = nullptr;        // incidences: function ids
   long long* koff = nullptr;      // leaf matrix offsets
@@ -2187,6 +2222,365 @@ void mlhp_op_build(fcm_mlhp_op* op, const fcm_mlhp* m, const fcm_grid* grid,
   op->nf = nf;
   op->nleaf = (int)L;
   op->max_nl = max_nl;
+  op->dim = dim;
+  for (int a = 0; a < 3; ++a) op->C[a] = P.C[a];
+  op->h_loff = loff;
+  op->h_lfn = lfn;
+  op->h_koff = koff;
+  op->h_llev = llev;
+  op->h_lidx = lidx;
+  long long nodes = 1;
+  for (int a = 0; a < dim; ++a) nodes *= P.C[a] + 1;
+  op->h_patch_off.assign(nodes + 1, 0);
+  op->h_patch_fn.assign(std::max(1LL, npatch), 0);
+  ok(fcm_mlhp_patches(m, op->h_patch_off.data(), op->h_patch_fn.data()));
+  op->h_coarsest.assign(M, 0);
+  ok(fcm_mlhp_levels(m, &op->n_levels, op->h_coarsest.data()));
+}
+
+
+// Host matrix of the overlay operator (setup only): CSR from the leaf
+// matrices.
+struct HostCsr {
+  long long n = 0;
+  std::vector<long long> ptr, col;
+  std::vector<double> val;
+  double at(long long r, long long c) const {
+    auto b = col.begin() + ptr[r], e = col.begin() + ptr[r + 1];
+    auto it = std::lower_bound(b, e, c);
+    return (it != e && *it == c) ? val[it - col.begin()] : 0.0;
+  }
+};
+
+HostCsr mlhp_host_matrix(fcm_mlhp_op* op) {
+  Handle* h = op->h.get();
+  const long long L = op->nleaf, N = op->M * op->nf;
+  std::vector<double> KL((size_t)op->h_koff[L]);
+  if (!KL.empty())
+    CK(cudaMemcpyAsync(KL.data(), op->KL, KL.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->s));
+  CK(cudaStreamSynchronize(h->s));
+  std::vector<std::pair<long long, double>> ent;  // (row * N + col, value)
+  ent.reserve(KL.size());
+  for (long long l = 0; l < L; ++l) {
+    const long long i0 = op->h_loff[l];
+    const int nfun = (int)(op->h_loff[l + 1] - i0), nl = op->nf * nfun;
+    auto dof = [&](int c) { return (c / nfun) * op->M + op->h_lfn[i0 + c % nfun]; };
+    for (int r = 0; r < nl; ++r)
+      for (int c = 0; c < nl; ++c)
+        ent.push_back({dof(r) * N + dof(c), KL[(size_t)op->h_koff[l] + (size_t)r * nl + c]});
+  }
+  std::sort(ent.begin(), ent.end(),
+            [](const auto& a, const auto& b) { return a.first < b.first; });
+  HostCsr A;
+  A.n = N;
+  A.ptr.assign(N + 1, 0);
+  for (size_t i = 0; i < ent.size();) {
+    size_t j = i;
+    double v = 0.0;
+    while (j < ent.size() && ent[j].first == ent[i].first) v += ent[j++].second;
+    const long long r = ent[i].first / N, c = ent[i].first % N;
+    A.col.push_back(c);
+    A.val.push_back(v);
+    ++A.ptr[r + 1];
+    i = j;
+  }
+  for (long long r = 0; r < N; ++r) A.ptr[r + 1] += A.ptr[r];
+  return A;
+}
+
+// Inverse of a dense SPD matrix through its Cholesky factor (setup only):
+// L L^T = B, B^{-1} = L^{-T} L^{-1}.
+void host_spd_inverse(std::vector<double>& B, int n) {
+  std::vector<double> Lf((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = B[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= Lf[(size_t)j * n + k] * Lf[(size_t)j * n + k];
+    if (!(d > 0.0)) throw Error(FCM_E_INVALID, "overlay Schwarz block: not positive definite");
+    const double ljj = std::sqrt(d);
+    Lf[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = B[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= Lf[(size_t)i * n + k] * Lf[(size_t)j * n + k];
+      Lf[(size_t)i * n + j] = t / ljj;
+    }
+  }
+  // W = L^{-1} (lower), then B^{-1} = W^T W
+  std::vector<double> W((size_t)n * n, 0.0);
+  for (int c = 0; c < n; ++c) {
+    for (int i = c; i < n; ++i) {
+      double t = i == c ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) t -= Lf[(size_t)i * n + k] * W[(size_t)k * n + c];
+      W[(size_t)i * n + c] = t / Lf[(size_t)i * n + i];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double t = 0.0;
+      for (int k = i; k < n; ++k) t += W[(size_t)k * n + i] * W[(size_t)k * n + j];
+      B[(size_t)i * n + j] = B[(size_t)j * n + i] = t;
+    }
+}
+
+// y = A x (full-length vectors) on the device.
+void mlhp_apply_dev(fcm_mlhp_op* op, const double* x, double* y) {
+  Handle* h = op->h.get();
+  launch_leaf_apply(op->nleaf, op->nf, op->M, op->max_nl, op->off, op->fn, op->koff, op->KL, x,
+                    op->Yl, h->s);
+  launch_leaf_gather(op->M, op->nf, op->ioff, op->ibase, op->istride, op->Yl, y, h->s);
+  CKL();
+}
+
+// z = sum of the level's block inverses applied to r (all N entries written).
+void mlhp_smooth_dev(fcm_mlhp_op* op, const MlhpLevel& L, const double* r, double* z) {
+  Handle* h = op->h.get();
+  const long long N = op->M * op->nf;
+  launch_leaf_apply(L.nblk, 1, N, L.max_m, L.boff, L.bdof, L.binv_off, L.binv, r, op->Yb, h->s);
+  launch_leaf_gather(N, 1, L.gioff, L.gibase, L.gistride, op->Yb, z, h->s);
+  CKL();
+}
+
+// x = V(b) on level l with zero initial guess (Algorithm 1; restriction =
+// the coarser level's mask, prolongation = add).
+void mlhp_vcycle_dev(fcm_mlhp_op* op, int l, const double* b, double* x) {
+  Handle* h = op->h.get();
+  const long long N = op->M * op->nf;
+  MlhpLevel& L = op->lv[l];
+  if (l == 0) {
+    mlhp_smooth_dev(op, L, b, x);  // the dense inverse of the coarsest level
+    return;
+  }
+  if (op->n_pre == 0) CK(cudaMemsetAsync(x, 0, N * sizeof(double), h->s));
+  for (int k = 0; k < op->n_pre; ++k) {
+    if (k == 0) {
+      mlhp_smooth_dev(op, L, b, op->z);
+      launch_mlhp_vec(N, 2, nullptr, op->z, nullptr, x, L.omega, h->s);
+    } else {
+      mlhp_apply_dev(op, x, op->y);
+      launch_mlhp_vec(N, 0, L.mask, b, op->y, L.r, 0.0, h->s);
+      mlhp_smooth_dev(op, L, L.r, op->z);
+      launch_mlhp_vec(N, 1, nullptr, op->z, nullptr, x, L.omega, h->s);
+    }
+  }
+  mlhp_apply_dev(op, x, op->y);
+  launch_mlhp_vec(N, 0, L.mask, b, op->y, L.r, 0.0, h->s);
+  MlhpLevel& Lc = op->lv[l - 1];
+  launch_mlhp_vec(N, 3, Lc.mask, L.r, nullptr, Lc.b, 0.0, h->s);
+  mlhp_vcycle_dev(op, l - 1, Lc.b, Lc.x);
+  launch_mlhp_vec(N, 4, nullptr, Lc.x, nullptr, x, 0.0, h->s);
+  for (int k = 0; k < op->n_post; ++k) {
+    mlhp_apply_dev(op, x, op->y);
+    launch_mlhp_vec(N, 0, L.mask, b, op->y, L.r, 0.0, h->s);
+    mlhp_smooth_dev(op, L, L.r, op->z);
+    launch_mlhp_vec(N, 1, nullptr, op->z, nullptr, x, L.omega, h->s);
+  }
+  CKL();
+}
+
+// The hierarchy of Sec. 3.2 on the overlay mesh: hp-levels from
+// fcm_mlhp_levels (level l holds the functions with coarsest <= l), on
+// every level l >= 1 additive Schwarz blocks (patchwise: the functions
+// touching the base cells around a base node; elementwise: those touching
+// one base cell) with omega clamped like the uniform path (power method
+// from sin(k + 1) over the level's numbering, omega = min(paper value,
+// 1.75 / lambda)); the coarsest level (the base grid's hats) solved by its
+// dense inverse.  Set-up on the host from the assembled leaf matrices.
+void mlhp_prepare(fcm_mlhp_op* op, const fcm_solver_opts* opts) {
+  Handle* h = op->h.get();
+  if (!opts) throw Error(FCM_E_INVALID, "null solver options");
+  if (opts->smoother != FCM_SMOOTHER_PATCHWISE && opts->smoother != FCM_SMOOTHER_ELEMENTWISE)
+    throw Error(FCM_E_UNSUPPORTED, "overlay meshes take additive Schwarz blocks");
+  if (opts->n_pre < 0 || opts->n_post < 0 || opts->n_pre > 64 || opts->n_post > 64)
+    throw Error(FCM_E_INVALID, "smoothing steps must be in [0, 64]");
+  int cmax = 0;
+  for (int a = 0; a < op->dim; ++a) cmax = std::max(cmax, op->C[a]);
+  if (cmax > opts->coarse_cells)
+    throw Error(FCM_E_UNSUPPORTED,
+                "overlay hierarchies end at the base grid: base cells per axis must not exceed "
+                "coarse_cells");
+  op->n_pre = opts->n_pre;
+  op->n_post = opts->n_post;
+  const long long M = op->M, N = M * op->nf;
+  const int nl = op->n_levels;
+  const bool patch = opts->smoother == FCM_SMOOTHER_PATCHWISE;
+  const double omega_paper =
+      opts->omega > 0.0 ? opts->omega
+                        : (patch ? (op->dim == 2 ? 1.0 / 6.0 : 1.0 / 18.0)
+                                 : (op->dim == 2 ? 1.0 / 3.0 : 2.0 / 15.0));
+  HostCsr A = mlhp_host_matrix(op);
+  // functions touching each base cell (elementwise blocks)
+  long long nbase = 1;
+  for (int a = 0; a < op->dim; ++a) nbase *= op->C[a];
+  std::vector<std::vector<long long>> per_cell;
+  if (!patch) {
+    per_cell.resize(nbase);
+    for (long long l = 0; l < op->nleaf; ++l) {
+      const int k = op->h_llev[l];
+      long long lin = 0, stride = 1;
+      for (int a = 0; a < op->dim; ++a) {
+        lin += (long long)(op->h_lidx[3 * l + a] >> k) * stride;
+        stride *= op->C[a];
+      }
+      for (long long e = op->h_loff[l]; e < op->h_loff[l + 1]; ++e)
+        per_cell[lin].push_back(op->h_lfn[e]);
+    }
+    for (auto& v : per_cell) {
+      std::sort(v.begin(), v.end());
+      v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+  }
+  op->lv.assign(nl, MlhpLevel());
+  size_t max_m = 1;
+  for (int l = 0; l < nl; ++l) {
+    MlhpLevel& L = op->lv[l];
+    std::vector<unsigned char> inl((size_t)M, 0);
+    for (long long i = 0; i < M; ++i) inl[i] = op->h_coarsest[i] <= l;
+    std::vector<unsigned char> mask((size_t)N);
+    for (long long i = 0; i < N; ++i) mask[i] = inl[i % M];
+    long long Ml = 0;
+    for (unsigned char c : inl) Ml += c;
+    L.ndofs = Ml * op->nf;
+    // blocks: DOF lists (fields outer, ascending function ids)
+    std::vector<std::vector<long long>> blocks;
+    auto expand = [&](const std::vector<long long>& ids) {
+      std::vector<long long> d;
+      for (int f = 0; f < op->nf; ++f)
+        for (long long i : ids) d.push_back(f * M + i);
+      return d;
+    };
+    if (l == 0) {
+      std::vector<long long> ids;
+      for (long long i = 0; i < M; ++i)
+        if (inl[i]) ids.push_back(i);
+      blocks.push_back(expand(ids));
+    } else if (patch) {
+      for (size_t v = 0; v + 1 < op->h_patch_off.size(); ++v) {
+        std::vector<long long> ids;
+        for (long long e = op->h_patch_off[v]; e < op->h_patch_off[v + 1]; ++e)
+          if (inl[op->h_patch_fn[e]]) ids.push_back(op->h_patch_fn[e]);
+        if (!ids.empty()) blocks.push_back(expand(ids));
+      }
+    } else {
+      for (const auto& cell : per_cell) {
+        std::vector<long long> ids;
+        for (long long i : cell)
+          if (inl[i]) ids.push_back(i);
+        if (!ids.empty()) blocks.push_back(expand(ids));
+      }
+    }
+    // dense inverses
+    std::vector<long long> boff(1, 0), bdof, binv_off(1, 0);
+    std::vector<double> binv;
+    for (const auto& b : blocks) {
+      const int m = (int)b.size();
+      if ((size_t)m * sizeof(double) > 48 * 1024)
+        throw Error(FCM_E_UNSUPPORTED, "overlay Schwarz block of more than 6144 DOFs");
+      max_m = std::max(max_m, (size_t)m);
+      std::vector<double> B((size_t)m * m);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) B[(size_t)i * m + j] = A.at(b[i], b[j]);
+      host_spd_inverse(B, m);
+      binv.insert(binv.end(), B.begin(), B.end());
+      bdof.insert(bdof.end(), b.begin(), b.end());
+      boff.push_back((long long)bdof.size());
+      binv_off.push_back((long long)binv.size());
+      L.max_m = std::max(L.max_m, m);
+    }
+    L.nblk = (int)blocks.size();
+    // gather lists: per DOF its block entries in block order
+    std::vector<long long> gioff(N + 1, 0);
+    for (long long d : bdof) ++gioff[d + 1];
+    for (long long i = 0; i < N; ++i) gioff[i + 1] += gioff[i];
+    std::vector<long long> gibase(bdof.size()), fill(gioff.begin(), gioff.end() - 1);
+    for (size_t e = 0; e < bdof.size(); ++e) gibase[fill[bdof[e]]++] = (long long)e;
+    std::vector<int> gistride(bdof.size(), 1);
+    L.mask = h->upload(mask);
+    L.boff = h->upload(boff);
+    L.bdof = h->upload(bdof.empty() ? std::vector<long long>(1, 0) : bdof);
+    L.binv_off = h->upload(binv_off);
+    L.binv = h->upload(binv.empty() ? std::vector<double>(1, 0.0) : binv);
+    L.gioff = h->upload(gioff);
+    L.gibase = h->upload(gibase.empty() ? std::vector<long long>(1, 0) : gibase);
+    L.gistride = h->upload(gistride.empty() ? std::vector<int>(1, 1) : gistride);
+    L.x = h->alloc<double>(N);
+    L.b = h->alloc<double>(N);
+    L.r = h->alloc<double>(N);
+    // omega: power method on M^{-1} A_l (host, full-length vectors)
+    if (l > 0) {
+      auto Av = [&](const std::vector<double>& v, std::vector<double>& out) {
+        for (long long r = 0; r < N; ++r) {
+          double t = 0.0;
+          if (mask[r])
+            for (long long e = A.ptr[r]; e < A.ptr[r + 1]; ++e) t += A.val[e] * v[A.col[e]];
+          out[r] = t;
+        }
+      };
+      auto Mv = [&](const std::vector<double>& v, std::vector<double>& out) {
+        std::fill(out.begin(), out.end(), 0.0);
+        for (size_t bi = 0; bi < blocks.size(); ++bi) {
+          const auto& b = blocks[bi];
+          const int m = (int)b.size();
+          const double* Bi = binv.data() + binv_off[bi];
+          for (int i = 0; i < m; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < m; ++j) t += Bi[(size_t)i * m + j] * v[b[j]];
+            out[b[i]] += t;
+          }
+        }
+      };
+      std::vector<double> v((size_t)N, 0.0), av((size_t)N), w((size_t)N);
+      long long k = 0;
+      for (int f = 0; f < op->nf; ++f)
+        for (long long i = 0; i < M; ++i)
+          if (inl[i]) v[(size_t)(f * M + i)] = std::sin((double)(k++) + 1.0);
+      double lam = 0.0;
+      for (int it = 0; it < 40; ++it) {
+        Av(v, av);
+        Mv(av, w);
+        double num = 0.0, den = 0.0, nw = 0.0;
+        for (long long i = 0; i < N; ++i) {
+          num += av[i] * w[i];
+          den += v[i] * av[i];
+          nw += w[i] * w[i];
+        }
+        lam = num / den;
+        nw = std::sqrt(nw);
+        for (long long i = 0; i < N; ++i) v[i] = w[i] / nw;
+      }
+      L.lambda = lam;
+      L.omega = std::min(omega_paper, 1.75 / lam);
+    }
+  }
+  long long ybsize = 1;
+  for (int l = 0; l < nl; ++l) {
+    long long e = 0;
+    CK(cudaMemcpyAsync(&e, op->lv[l].boff + op->lv[l].nblk, sizeof(long long),
+                       cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    ybsize = std::max(ybsize, e);
+  }
+  op->Yb = h->alloc<double>((size_t)ybsize);
+  op->y = h->alloc<double>(N);
+  op->z = h->alloc<double>(N);
+  op->cx = h->alloc<double>(N);
+  op->cr = h->alloc<double>(N);
+  op->cp = h->alloc<double>(N);
+  op->cq = h->alloc<double>(N);
+  op->cz = h->alloc<double>(N);
+  op->cb = h->alloc<double>(N);
+  op->part = h->alloc<double>(kDotBlocks);
+  op->d_scalar = h->alloc<double>(1);
+  if (!op->h_scalar) CK(cudaMallocHost(&op->h_scalar, sizeof(double)));
+}
+
+double mlhp_dot(fcm_mlhp_op* op, const double* a, const double* b) {
+  Handle* h = op->h.get();
+  launch_dot_partials(a, b, op->M * op->nf, op->part, h->s);
+  launch_reduce(op->part, kDotBlocks, op->d_scalar, h->s);
+  CKL();
+  CK(cudaMemcpyAsync(op->h_scalar, op->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return op->h_scalar[0];
 }
 
 }  // namespace
@@ -2254,6 +2648,126 @@ fcm_status fcm_mlhp_op_rhs(const fcm_mlhp_op* op, double* b_dev) {
                        h->s));
     cs.finish();
     return FCM_OK;
+  });
+}
+
+fcm_status fcm_mlhp_op_prepare(fcm_mlhp_op* op, const fcm_solver_opts* opts) {
+  if (!op) {
+    g_last_error = "null argument";
+    return FCM_E_INVALID;
+  }
+  return guarded([&]() {
+    CallScope cs(op->h.get());
+    mlhp_prepare(op, opts);
+    cs.finish();
+    return FCM_OK;
+  });
+}
+
+fcm_status fcm_mlhp_op_level(const fcm_mlhp_op* op, int level, long long* ndofs, double* omega,
+                             int* n_blocks, int* max_block) {
+  if (!op || level < 0 || level >= (int)op->lv.size() || !ndofs || !omega || !n_blocks ||
+      !max_block) {
+    g_last_error = "invalid argument (fcm_mlhp_op_prepare first)";
+    return FCM_E_INVALID;
+  }
+  const MlhpLevel& L = op->lv[level];
+  *ndofs = L.ndofs;
+  *omega = L.omega;
+  *n_blocks = L.nblk;
+  *max_block = L.max_m;
+  return FCM_OK;
+}
+
+fcm_status fcm_mlhp_op_vcycle(fcm_mlhp_op* op, const double* r_dev, double* z_dev) {
+  if (!op || !r_dev || !z_dev || op->lv.empty()) {
+    g_last_error = "invalid argument (fcm_mlhp_op_prepare first)";
+    return FCM_E_INVALID;
+  }
+  return guarded([&]() {
+    CallScope cs(op->h.get());
+    mlhp_vcycle_dev(op, (int)op->lv.size() - 1, r_dev, z_dev);
+    cs.finish();
+    return FCM_OK;
+  });
+}
+
+fcm_status fcm_mlhp_op_pcg(fcm_mlhp_op* op, const double* b_dev, double* x_dev, double rtol,
+                           int maxit, fcm_info* info) {
+  if (!op || !x_dev || op->lv.empty() || !(rtol > 0.0) || maxit < 0) {
+    g_last_error = "invalid argument (fcm_mlhp_op_prepare first)";
+    return FCM_E_INVALID;
+  }
+  return guarded([&]() {
+    Handle* h = op->h.get();
+    CallScope cs(h);
+    const double t0 = now_ms();
+    const long long N = op->M * op->nf;
+    const int top = (int)op->lv.size() - 1;
+    const unsigned char* all = op->lv[top].mask;
+    const double* b = b_dev ? b_dev : op->b;
+    double *r = op->cr, *z = op->cz, *p = op->cp, *q = op->cq;
+    CK(cudaMemsetAsync(x_dev, 0, N * sizeof(double), h->s));
+    CK(cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    const double nb = std::sqrt(mlhp_dot(op, b, b));
+    if (!std::isfinite(nb)) throw Error(FCM_E_INVALID, "right-hand side is not finite");
+    fcm_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    inf.ndofs = N;
+    fcm_status st = FCM_E_NOT_CONVERGED;
+    int k = 0;
+    double rel = 1.0;
+    if (nb == 0.0) {
+      st = FCM_OK;
+      rel = 0.0;
+    } else {
+      mlhp_vcycle_dev(op, top, r, z);
+      CK(cudaMemcpyAsync(p, z, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+      double rz = mlhp_dot(op, r, z);
+      while (k < maxit) {
+        ++k;
+        mlhp_apply_dev(op, p, q);
+        const double pq = mlhp_dot(op, p, q);
+        if (!(pq > 0.0) || !std::isfinite(rz)) {
+          st = FCM_E_BREAKDOWN;
+          break;
+        }
+        const double a = rz / pq;
+        launch_mlhp_vec(N, 1, nullptr, p, nullptr, x_dev, a, h->s);
+        launch_mlhp_vec(N, 1, nullptr, q, nullptr, r, -a, h->s);
+        rel = std::sqrt(mlhp_dot(op, r, r)) / nb;
+        if (rel <= rtol) {
+          mlhp_apply_dev(op, x_dev, op->y);
+          launch_mlhp_vec(N, 0, all, b, op->y, op->cb, 0.0, h->s);
+          const double rt = std::sqrt(mlhp_dot(op, op->cb, op->cb)) / nb;
+          if (rt <= rtol) {
+            st = FCM_OK;
+            inf.relres_true = rt;
+            break;
+          }
+          CK(cudaMemcpyAsync(r, op->cb, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+        }
+        mlhp_vcycle_dev(op, top, r, z);
+        const double rzn = mlhp_dot(op, r, z);
+        const double beta = rzn / rz;
+        rz = rzn;
+        launch_mlhp_vec(N, 5, nullptr, z, nullptr, p, beta, h->s);
+      }
+    }
+    if (st != FCM_OK && nb > 0.0) {
+      mlhp_apply_dev(op, x_dev, op->y);
+      launch_mlhp_vec(N, 0, all, b, op->y, op->cb, 0.0, h->s);
+      inf.relres_true = std::sqrt(mlhp_dot(op, op->cb, op->cb)) / nb;
+    }
+    CKL();
+    cs.finish();
+    inf.iters = k;
+    inf.relres_recursive = rel;
+    inf.solve_ms = now_ms() - t0;
+    if (info) *info = inf;
+    if (st == FCM_E_NOT_CONVERGED) g_last_error = "maximum number of iterations reached";
+    if (st == FCM_E_BREAKDOWN) g_last_error = "CG breakdown";
+    return st;
   });
 }
 

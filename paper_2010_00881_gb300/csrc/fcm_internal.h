@@ -261,6 +261,12 @@ void launch_mask_empty_rows(long long count, int n, int phase, double* mats,
 template <typename T>
 void launch_mask_vec(long long N, long long M, const unsigned char* keep, T* v, cudaStream_t s);
 
+// Level vector operations of the overlay hp-multigrid (mode 0: out = mask
+// (a - b), 1: out += w a, 2: out = w a, 3: out = mask a, 4: out += a,
+// 5: out = a + w out).
+void launch_mlhp_vec(long long N, int mode, const unsigned char* mask, const double* a,
+                     const double* b, double* out, double w, cudaStream_t s);
+
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };
 template <typename TV>

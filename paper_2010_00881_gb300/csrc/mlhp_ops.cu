@@ -175,3 +175,41 @@ void launch_leaf_gather(long long M, int nf, const long long* ioff, const long l
 }
 
 }  // namespace fcm
+
+// ---------------------------------------------------------------------------
+// hp-multigrid of overlay meshes: the level vectors are full-length
+// (removed functions zero), so restriction is a mask, prolongation an add.
+namespace fcm {
+namespace {
+
+enum { MV_RESID = 0, MV_AXPY = 1, MV_SCALE = 2, MV_MASK = 3, MV_ADD = 4, MV_XPBY = 5 };
+
+// RESID: out = mask (a - b); AXPY: out += w a; SCALE: out = w a;
+// MASK: out = mask a; ADD: out += a; XPBY: out = a + w out.
+__global__ void mlhp_vec_kernel(long long N, int mode, const unsigned char* __restrict__ mask,
+                                const double* __restrict__ a, const double* __restrict__ b,
+                                double* __restrict__ out, double w) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    switch (mode) {
+      case MV_RESID: out[i] = mask[i] ? a[i] - b[i] : 0.0; break;
+      case MV_AXPY: out[i] += w * a[i]; break;
+      case MV_SCALE: out[i] = w * a[i]; break;
+      case MV_MASK: out[i] = mask[i] ? a[i] : 0.0; break;
+      case MV_ADD: out[i] += a[i]; break;
+      default: out[i] = a[i] + w * out[i]; break;  // MV_XPBY
+    }
+  }
+}
+
+}  // namespace
+
+void launch_mlhp_vec(long long N, int mode, const unsigned char* mask, const double* a,
+                     const double* b, double* out, double w, cudaStream_t s) {
+  long long blocks = (N + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  mlhp_vec_kernel<<<(int)blocks, 256, 0, s>>>(N, mode, mask, a, b, out, w);
+}
+
+}  // namespace fcm

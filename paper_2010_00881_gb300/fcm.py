@@ -37,7 +37,8 @@ EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_
            "fcm_mlhp_functions", "fcm_mlhp_leaves", "fcm_mlhp_patches",
            "fcm_mlhp_leaf_classes", "fcm_mlhp_levels", "fcm_mlhp_restriction_1d",
            "fcm_measure_fma_peak", "fcm_solve", "fcm_mlhp_op_create", "fcm_mlhp_op_ndofs",
-           "fcm_mlhp_op_apply", "fcm_mlhp_op_rhs", "fcm_mlhp_op_destroy"]
+           "fcm_mlhp_op_apply", "fcm_mlhp_op_rhs", "fcm_mlhp_op_destroy", "fcm_mlhp_op_prepare",
+           "fcm_mlhp_op_level", "fcm_mlhp_op_vcycle", "fcm_mlhp_op_pcg"]
 
 
 class fcm_grid(C.Structure):
@@ -151,6 +152,10 @@ def load():
     lib.fcm_mlhp_op_rhs.argtypes = [P, P]
     lib.fcm_mlhp_op_destroy.argtypes = [P]
     lib.fcm_mlhp_op_destroy.restype = None
+    lib.fcm_mlhp_op_prepare.argtypes = [P, C.POINTER(fcm_solver_opts)]
+    lib.fcm_mlhp_op_level.argtypes = [P, C.c_int, LL, C.POINTER(C.c_double), IP, IP]
+    lib.fcm_mlhp_op_vcycle.argtypes = [P, P, P]
+    lib.fcm_mlhp_op_pcg.argtypes = [P, P, P, C.c_double, C.c_int, C.POINTER(fcm_info)]
     lib.fcm_last_error.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("fcm_destroy", "fcm_batch_destroy", "fcm_last_error", "fcm_mlhp_destroy",
@@ -244,7 +249,7 @@ class MlhpOperator:
     def __init__(self, prob: dict):
         import torch
         self._torch = torch
-        g, gm, ph, _, self._keep = descriptors(prob)
+        g, gm, ph, self._opts, self._keep = descriptors(prob)
         lib = load()
         m = C.c_void_p()
         _check(lib.fcm_mlhp_create(C.byref(g), C.byref(gm), C.byref(m)))
@@ -271,6 +276,39 @@ class MlhpOperator:
         b = self._empty()
         _check(load().fcm_mlhp_op_rhs(self.h, _ptr(b)))
         return b
+
+    def prepare(self):
+        """Build the hp-multigrid (fcm_mlhp_op_prepare) with the problem's
+        smoother options; returns the number of levels."""
+        _check(load().fcm_mlhp_op_prepare(self.h, C.byref(self._opts)))
+        self.levels = []
+        l = 0
+        while True:
+            nd, om = C.c_longlong(), C.c_double()
+            nb, mb = C.c_int(), C.c_int()
+            st = load().fcm_mlhp_op_level(self.h, l, C.byref(nd), C.byref(om), C.byref(nb),
+                                          C.byref(mb))
+            if st != FCM_OK:
+                break
+            self.levels.append({"ndofs": nd.value, "omega": om.value, "n_blocks": nb.value,
+                                "max_block": mb.value})
+            l += 1
+        return len(self.levels)
+
+    def vcycle(self, r):
+        z = self._empty()
+        _check(load().fcm_mlhp_op_vcycle(self.h, _ptr(r), _ptr(z)))
+        return z
+
+    def pcg(self, b=None, rtol=1e-8, maxit=500, allow_fail=False):
+        x = self._empty()
+        inf = fcm_info()
+        st = load().fcm_mlhp_op_pcg(self.h, _ptr(b) if b is not None else None, _ptr(x), rtol,
+                                    maxit, C.byref(inf))
+        _check(st, allow=(FCM_E_NOT_CONVERGED, FCM_E_BREAKDOWN) if allow_fail else ())
+        d = inf.as_dict()
+        d["status"] = st
+        return x, d
 
     def close(self):
         if self.h:

@@ -74,3 +74,70 @@ def test_apply_is_symmetric(case):
     Au = op.apply(torch.from_numpy(u).cuda()).cpu().numpy()
     Av = op.apply(torch.from_numpy(v).cuda()).cpu().numpy()
     assert abs(v @ Au - u @ Av) <= 1e-12 * (np.abs(v) @ np.abs(Au) + 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# The hp-multigrid of overlay meshes (Sec. 3.2, Fig. hpmultigrid) against
+# oracle.mlhp.MlhpHierarchy: level sizes exact, omega 1e-6, the V-cycle
+# within 1e-12 + 50 x the LU-inverse noise floor (energy norm), PCG
+# iteration counts +-1 and the oracle's true residual.
+
+from oracle import multigrid as mg  # noqa: E402
+from oracle.mlhp import MlhpHierarchy  # noqa: E402
+from parity_helpers import Noise  # noqa: E402
+
+SOLVER_CASES = {
+    "circle4_p2_k3_patch": lambda: dict(fi.poisson2d_circle(cells=4, p=2), overlay_levels=3,
+                                        smoother="patchwise"),
+    "circle4_p3_k2_elem": lambda: dict(fi.poisson2d_circle(cells=4, p=3), overlay_levels=2,
+                                       smoother="elementwise"),
+    "plate8_p2_k2_patch": lambda: dict(fi.perforated_plate(cells=8, p=2, overlay_levels=2),
+                                       coarse_cells=8, smoother="patchwise"),
+    "sphere4_p1_k2_patch": lambda: fi.poisson3d_sphere_mlhp(cells=4, p=1, overlay_levels=2),
+}
+
+
+@pytest.fixture(scope="module", params=list(SOLVER_CASES))
+def solver_case(request):
+    prob = SOLVER_CASES[request.param]()
+    H = MlhpHierarchy(prob)
+    op = F.MlhpOperator(prob)
+    op.prepare()
+    yield request.param, prob, H, op
+    op.close()
+
+
+def _rel_a(A, a, b):
+    e = a - b
+    return np.sqrt(max(e @ (A @ e), 0.0)) / np.sqrt(b @ (A @ b))
+
+
+def test_hierarchy_levels(solver_case):
+    name, prob, H, op = solver_case
+    assert len(op.levels) == len(H.levels)
+    for l, (info, lv) in enumerate(zip(op.levels, H.levels)):
+        assert info["ndofs"] == lv.N, (name, l)
+        if l > 0:
+            assert abs(info["omega"] - lv.omega) <= 1e-6 * lv.omega, (name, l, info, lv.omega)
+            assert info["n_blocks"] == sum(1 for b in lv.blocks if len(b)), (name, l)
+
+
+def test_vcycle(solver_case):
+    name, prob, H, op = solver_case
+    r = fi.random_vector(op.ndofs, seed=2)
+    z = op.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+    zr = H.vcycle(r)
+    bar = 1e-12 + 50.0 * _rel_a(H.A, Noise(H).vcycle(r), zr)
+    err = _rel_a(H.A, z, zr)
+    print(f"overlay V-cycle {name}: {err:.2e} (bar {bar:.2e})")
+    assert err <= bar, (name, err, bar)
+
+
+def test_pcg(solver_case):
+    name, prob, H, op = solver_case
+    _, ko, _ = mg.pcg(H.A, H.b, H.vcycle, rtol=1e-8)
+    x, info = op.pcg(rtol=1e-8)
+    x = x.cpu().numpy()
+    assert info["relres_true"] <= 1e-8
+    assert np.linalg.norm(H.b - H.A @ x) / np.linalg.norm(H.b) <= 1.01e-8
+    assert abs(info["iters"] - ko) <= 1, (name, info["iters"], ko)
