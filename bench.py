@@ -278,13 +278,16 @@ def run_batch(args, rank, world, local):
         torch.cuda.synchronize()
 
     out = {}
-    for prec, name in ((FCM_MIXED, "mixed"), (FCM_FP64, "fp64")):
+    # lockstep (threads 0: every instance in flight, one host thread) is the
+    # batched solve; the host worker pool is reported beside it
+    for prec, name, threads in ((FCM_MIXED, "mixed", 0), (FCM_FP64, "fp64", 0),
+                                (FCM_MIXED, "mixed_pool16", 16)):
         for _ in range(args.warmup):
-            b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec)
+            b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec, threads=threads)
         barrier()
         t = time.perf_counter()
         for _ in range(args.steps):
-            _, infos = b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec)
+            _, infos = b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec, threads=threads)
         barrier()
         (tot,), (value,) = aggregate([1e3 * (time.perf_counter() - t)], world, ndofs, args.steps,
                                      dev)
@@ -300,8 +303,10 @@ def run_batch(args, rank, world, local):
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                           "dtype": "f32+f64", "data": "synthetic",
                           "config": {"workload": "batch256_ellipsoids", "instances": len(probs),
-                                     "ndofs_total": ndofs, "setup_s": setup_s, "threads": 16},
-                          "mixed": out["mixed"], "fp64": out["fp64"]}))
+                                     "ndofs_total": ndofs, "setup_s": setup_s,
+                                     "setup_threads": 16, "solve": "lockstep, one host thread"},
+                          "mixed": out["mixed"], "fp64": out["fp64"],
+                          "mixed_pool16": out["mixed_pool16"]}))
     b.close()
 
 

@@ -1489,37 +1489,65 @@ void precondition(Handle* h, const double* r, double* z, int prec, int method) {
   run_vcycle(h, r, z, prec);
 }
 
-fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int maxit, int prec,
-                    fcm_info* info, int method = FCM_METHOD_CG_MG) {
+// V-cycle-preconditioned CG (Sec. 4) as steps, so that one solve (pcg_impl)
+// and a batch of independent solves in lockstep (pcg_batch_impl) run the
+// same device work in the same order: pcg_begin up to the first search
+// direction; per iteration pcg_phase_a (q = A p, the x / r updates and
+// r.r to pinned host memory, no synchronisation), pcg_check on the host
+// after the stream is synchronised (the convergence test, with the true
+// residual), pcg_phase_b (the next preconditioned residual and direction);
+// pcg_end.
+struct PcgRun {
+  Handle* h = nullptr;
+  double* x = nullptr;
+  const double* b = nullptr;
+  int prec = FCM_FP64, method = FCM_METHOD_CG_MG, maxit = 0, k = 0;
+  double rtol = 0.0, nb = 0.0, rel = 1.0, t0 = 0.0;
+  bool flexible = false, done = false;
+  fcm_status st = FCM_E_NOT_CONVERGED;
+  fcm_info inf;
+};
+
+void pcg_begin(PcgRun& R, Handle* h, const double* b_in, double* x, double rtol, int maxit,
+               int prec, int method) {
   g_stage = "solve";
-  double t0 = now_ms();
+  R.h = h;
+  R.x = x;
+  R.rtol = rtol;
+  R.maxit = maxit;
+  R.prec = prec;
+  R.method = method;
+  R.t0 = now_ms();
+  R.k = 0;
+  R.rel = 1.0;
+  R.done = false;
+  R.st = FCM_E_NOT_CONVERGED;
   h->launches = 0;
   h->bytes = 0;
   Level& T = h->levels.back();
   const long long N = T.g.N;
-  const double* b = solve_rhs(h, b_in);
-  const bool flexible = prec == FCM_MIXED;
+  R.b = solve_rhs(h, b_in);
+  R.flexible = prec == FCM_MIXED;
   if (prec == FCM_MIXED && !h->mixed)
     throw Error(FCM_E_INVALID, "mixed precision data not built (build_mixed = 0)");
   if (!(rtol > 0.0) || maxit < 0) throw Error(FCM_E_INVALID, "rtol must be > 0, maxit >= 0");
   double* r = T.b;  // the residual is the V-cycle's input buffer
   double* z = h->ctmp;
   double* p = h->cp;
-  double* q = h->cq;
   CK(cudaMemsetAsync(x, 0, N * sizeof(double), h->s));
-  CK(cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  CK(cudaMemcpyAsync(r, R.b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
   h->bytes += 3 * N * 8;
-  double bb = host_dot(h, b, b, N);
+  double bb = host_dot(h, R.b, R.b, N);
   if (!std::isfinite(bb)) throw Error(FCM_E_INVALID, "right-hand side is not finite");
-  double nb = std::sqrt(bb);
-  fcm_info inf;
-  std::memset(&inf, 0, sizeof(inf));
-  inf.ndofs = N;
-  inf.setup_ms = h->setup_ms;
-  if (nb == 0.0) {
-    inf.solve_ms = now_ms() - t0;
-    if (info) *info = inf;
-    return FCM_OK;
+  R.nb = std::sqrt(bb);
+  std::memset(&R.inf, 0, sizeof(R.inf));
+  R.inf.ndofs = N;
+  R.inf.setup_ms = h->setup_ms;
+  if (R.nb == 0.0) {
+    R.st = FCM_OK;
+    R.done = true;
+    R.rel = 0.0;
+    return;
   }
   precondition(h, r, z, prec, method);
   launch_dot_partials(r, z, N, h->part, h->s);
@@ -1527,70 +1555,183 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   CKL();
   h->launches += 2;
   h->bytes += 5 * N * 8;
-  int k = 0;
-  double rel = 1.0;
-  fcm_status st = FCM_E_NOT_CONVERGED;
-  while (k < maxit) {
-    ++k;
-    apply_A64(h, T, p, q, GATHER_SET, nullptr);
-    launch_dot_partials(p, q, N, h->part, h->s);
-    launch_cg_update_xr(x, r, p, q, N, h->part, h->sc, h->part + kDotBlocks, h->s);
-    launch_reduce(h->part + kDotBlocks, kDotBlocks, h->d_scalar, h->s);
-    CKL();
-    h->launches += 3;
-    h->bytes += 8 * N * 8;  // p.q; x, r updated from p, q
-    CK(cudaMemcpyAsync(h->h_scalar, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+}
+
+void pcg_phase_a(PcgRun& R) {
+  Handle* h = R.h;
+  Level& T = h->levels.back();
+  const long long N = T.g.N;
+  ++R.k;
+  apply_A64(h, T, h->cp, h->cq, GATHER_SET, nullptr);
+  launch_dot_partials(h->cp, h->cq, N, h->part, h->s);
+  launch_cg_update_xr(R.x, T.b, h->cp, h->cq, N, h->part, h->sc, h->part + kDotBlocks, h->s);
+  launch_reduce(h->part + kDotBlocks, kDotBlocks, h->d_scalar, h->s);
+  CKL();
+  h->launches += 3;
+  h->bytes += 8 * N * 8;  // p.q; x, r updated from p, q
+  CK(cudaMemcpyAsync(h->h_scalar, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+}
+
+// After the stream has finished phase a: false when the solve ends here.
+bool pcg_check(PcgRun& R) {
+  Handle* h = R.h;
+  Level& T = h->levels.back();
+  const long long N = T.g.N;
+  const double rr = h->h_scalar[0];
+  if (!std::isfinite(rr)) {
+    R.st = FCM_E_BREAKDOWN;
+    R.done = true;
+    return false;
+  }
+  R.rel = std::sqrt(rr) / R.nb;
+  if (R.rel <= R.rtol) {
+    // confirm with the true residual b - A x
+    apply_A64(h, T, R.x, h->cz_old, GATHER_RESID, R.b);
+    double rt = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / R.nb;
+    if (rt <= R.rtol) {
+      R.st = FCM_OK;
+      R.inf.relres_true = rt;
+      R.done = true;
+      return false;
+    }
+    CK(cudaMemcpyAsync(T.b, h->cz_old, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    h->bytes += 2 * N * 8;
+  }
+  if (R.k >= R.maxit) {
+    R.done = true;
+    return false;
+  }
+  return true;
+}
+
+void pcg_phase_b(PcgRun& R) {
+  Handle* h = R.h;
+  Level& T = h->levels.back();
+  const long long N = T.g.N;
+  double* r = T.b;
+  double* z = h->ctmp;
+  if (R.flexible) {
+    CK(cudaMemcpyAsync(h->cz_old, z, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    h->bytes += 2 * N * 8;
+  }
+  precondition(h, r, z, R.prec, R.method);
+  if (R.flexible)
+    launch_dot2_partials(r, z, h->cz_old, N, h->part, h->s);
+  else
+    launch_dot_partials(r, z, N, h->part, h->s);
+  launch_cg_update_p(h->cp, z, N, h->part, R.flexible ? 1 : 0, h->sc, h->s);
+  CKL();
+  h->launches += 3;
+  h->bytes += (R.flexible ? 6 : 5) * N * 8;  // r.z (and r.z_old); p from z
+}
+
+fcm_status pcg_end(PcgRun& R, fcm_info* info) {
+  Handle* h = R.h;
+  Level& T = h->levels.back();
+  const long long N = T.g.N;
+  if (R.nb > 0.0) {
+    CGScalars sc;
+    CK(cudaMemcpyAsync(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
-    double rr = h->h_scalar[0];
-    if (!std::isfinite(rr)) {
-      st = FCM_E_BREAKDOWN;
-      break;
+    check_timeout(h);
+    if (sc.flag && R.st != FCM_OK) R.st = FCM_E_BREAKDOWN;
+    if (R.st != FCM_OK) {
+      apply_A64(h, T, R.x, h->cz_old, GATHER_RESID, R.b);
+      R.inf.relres_true = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / R.nb;
     }
-    rel = std::sqrt(rr) / nb;
-    if (rel <= rtol) {
-      // confirm with the true residual b - A x
-      apply_A64(h, T, x, h->cz_old, GATHER_RESID, b);
-      double rt = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / nb;
-      if (rt <= rtol) {
-        st = FCM_OK;
-        inf.relres_true = rt;
-        break;
+  }
+  R.inf.iters = R.k;
+  R.inf.kernel_launches = h->launches;
+  R.inf.bytes_moved_est = h->bytes;
+  R.inf.relres_recursive = R.rel;
+  R.inf.solve_ms = now_ms() - R.t0;
+  if (info) *info = R.inf;
+  if (R.st == FCM_E_NOT_CONVERGED) g_last_error = "maximum number of iterations reached";
+  if (R.st == FCM_E_BREAKDOWN)
+    g_last_error = "CG breakdown (p^T A p <= 0 or non-finite scalar)";
+  return R.st;
+}
+
+fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int maxit, int prec,
+                    fcm_info* info, int method = FCM_METHOD_CG_MG) {
+  PcgRun R;
+  pcg_begin(R, h, b_in, x, rtol, maxit, prec, method);
+  while (!R.done && R.k < R.maxit) {
+    pcg_phase_a(R);
+    CK(cudaStreamSynchronize(h->s));
+    if (!pcg_check(R)) break;
+    pcg_phase_b(R);
+  }
+  return pcg_end(R, info);
+}
+
+// Independent solves in lockstep from one host thread (the batch of Sec.
+// 8 a13): every iteration enqueues phase a of all running instances on
+// their streams, synchronises each once, runs the host checks, then
+// enqueues phase b of those still running.  Each instance does exactly the
+// work of pcg_impl, in the same order on its own stream, so the results are
+// bit for bit those of single solves.  Returns the first failing status in
+// instance order.
+fcm_status pcg_batch_impl(Handle* const* hs, int n, double* const* x, double rtol, int maxit,
+                          int prec, fcm_info* infos, std::string* msg) {
+  std::vector<PcgRun> R(n);
+  std::vector<fcm_status> st(n, FCM_OK);
+  std::vector<std::string> err(n);
+  std::vector<char> alive(n, 1);
+  auto fail = [&](int i, fcm_status s, const char* m) {
+    st[i] = s;
+    err[i] = m;
+    alive[i] = 0;
+  };
+  auto step = [&](int i, auto&& f) {
+    if (!alive[i]) return;
+    try {
+      f();
+    } catch (const Error& e) {
+      fail(i, e.st, e.what());
+    } catch (const std::bad_alloc&) {
+      fail(i, FCM_E_OOM, "host out of memory");
+    } catch (const std::exception& e) {
+      fail(i, FCM_E_CUDA, e.what());
+    }
+  };
+  std::vector<std::unique_ptr<CallScope>> scope(n);
+  for (int i = 0; i < n; ++i)
+    step(i, [&] {
+      scope[i].reset(new CallScope(hs[i]));
+      pcg_begin(R[i], hs[i], nullptr, x[i], rtol, maxit, prec, FCM_METHOD_CG_MG);
+    });
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < n; ++i)
+      step(i, [&] {
+        if (R[i].done) return;
+        pcg_phase_a(R[i]);
+        any = true;
+      });
+    if (!any) break;
+    for (int i = 0; i < n; ++i)
+      step(i, [&] {
+        if (R[i].done) return;
+        CK(cudaStreamSynchronize(hs[i]->s));
+        if (pcg_check(R[i])) pcg_phase_b(R[i]);
+      });
+  }
+  for (int i = 0; i < n; ++i)
+    step(i, [&] {
+      const fcm_status s = pcg_end(R[i], infos ? &infos[i] : nullptr);
+      if (scope[i]) scope[i]->finish();
+      if (s != FCM_OK) {
+        st[i] = s;
+        err[i] = g_last_error;
       }
-      CK(cudaMemcpyAsync(r, h->cz_old, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-      h->bytes += 2 * N * 8;
+    });
+  for (int i = 0; i < n; ++i)
+    if (st[i] != FCM_OK) {
+      *msg = "instance " + std::to_string(i) + ": " + err[i];
+      return st[i];
     }
-    if (flexible) {
-      CK(cudaMemcpyAsync(h->cz_old, z, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
-      h->bytes += 2 * N * 8;
-    }
-    precondition(h, r, z, prec, method);
-    if (flexible)
-      launch_dot2_partials(r, z, h->cz_old, N, h->part, h->s);
-    else
-      launch_dot_partials(r, z, N, h->part, h->s);
-    launch_cg_update_p(p, z, N, h->part, flexible ? 1 : 0, h->sc, h->s);
-    CKL();
-    h->launches += 3;
-    h->bytes += (flexible ? 6 : 5) * N * 8;  // r.z (and r.z_old); p from z
-  }
-  CGScalars sc;
-  CK(cudaMemcpyAsync(&sc, h->sc, sizeof(sc), cudaMemcpyDeviceToHost, h->s));
-  CK(cudaStreamSynchronize(h->s));
-  check_timeout(h);
-  if (sc.flag && st != FCM_OK) st = FCM_E_BREAKDOWN;
-  if (st != FCM_OK) {
-    apply_A64(h, T, x, h->cz_old, GATHER_RESID, b);
-    inf.relres_true = std::sqrt(host_dot(h, h->cz_old, h->cz_old, N)) / nb;
-  }
-  inf.iters = k;
-  inf.kernel_launches = h->launches;
-  inf.bytes_moved_est = h->bytes;
-  inf.relres_recursive = rel;
-  inf.solve_ms = now_ms() - t0;
-  if (info) *info = inf;
-  if (st == FCM_E_NOT_CONVERGED) g_last_error = "maximum number of iterations reached";
-  if (st == FCM_E_BREAKDOWN) g_last_error = "CG breakdown (p^T A p <= 0 or non-finite scalar)";
-  return st;
+  return FCM_OK;
 }
 
 // Multigrid as a stand-alone solver (Sec. 4, Eq. contraction):
@@ -2774,6 +2915,24 @@ fcm_status fcm_mlhp_op_pcg(fcm_mlhp_op* op, const double* b_dev, double* x_dev, 
 void fcm_mlhp_op_destroy(fcm_mlhp_op* op) { delete op; }
 
 void fcm_destroy(fcm_handle* h) { delete h; }
+
+}  // extern "C"
+
+namespace fcm {
+fcm_status pcg_solve_lockstep(fcm_handle* const* hs, int n, double* const* x, double rtol,
+                              int maxit, int prec, fcm_info* infos) {
+  if (prec != FCM_FP64 && prec != FCM_MIXED) {
+    g_last_error = "invalid precision";
+    return FCM_E_INVALID;
+  }
+  std::string msg;
+  fcm_status st = pcg_batch_impl(hs, n, x, rtol, maxit, prec, infos, &msg);
+  if (st != FCM_OK) g_last_error = msg;
+  return st;
+}
+}  // namespace fcm
+
+extern "C" {
 
 const char* fcm_last_error(void) { return g_last_error.c_str(); }
 

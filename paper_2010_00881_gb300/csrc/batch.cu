@@ -112,6 +112,8 @@ fcm_status fcm_pcg_solve_batch(fcm_batch* b, double* const* x_dev, double rtol, 
       fcm::set_last_error("fcm_pcg_solve_batch: x_dev has a NULL entry");
       return FCM_E_INVALID;
     }
+  if (threads <= 0)  // lockstep: all instances in flight, driven by this thread
+    return fcm::pcg_solve_lockstep(b->h.data(), n, x_dev, rtol, maxit, prec, infos);
   std::string msg;
   fcm_status st = run_pool(
       n, threads,

@@ -567,12 +567,15 @@ class Batch:
         except Exception:
             pass
 
-    def pcg(self, xs=None, rtol=1e-8, maxit=500, prec=FCM_FP64):
+    def pcg(self, xs=None, rtol=1e-8, maxit=500, prec=FCM_FP64, threads=None):
+        """threads 0: all instances in lockstep from this thread; > 0: a pool
+        of that many host workers (default: the set-up's thread count)."""
         import torch
         n = len(self.ndofs)
         if xs is None:
             xs = [torch.empty(nd, dtype=torch.float64, device="cuda") for nd in self.ndofs]
         ptrs = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
         infos = (fcm_info * n)()
-        _check(load().fcm_pcg_solve_batch(self.h, ptrs, rtol, maxit, prec, self.threads, infos))
+        t = self.threads if threads is None else threads
+        _check(load().fcm_pcg_solve_batch(self.h, ptrs, rtol, maxit, prec, t, infos))
         return xs, [i.as_dict() for i in infos]

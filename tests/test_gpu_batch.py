@@ -35,10 +35,13 @@ def batch():
     b.close()
 
 
+@pytest.mark.parametrize("threads", [0, 3])
 @pytest.mark.parametrize("prec", [FCM_FP64, FCM_MIXED])
-def test_batch_equals_individual_solves(batch, prec):
+def test_batch_equals_individual_solves(batch, prec, threads):
+    """threads 0: all instances in lockstep from one host thread; 3: a pool
+    of host workers.  Both run each instance's work exactly as alone."""
     probs, b = batch
-    xs, infos = b.pcg(rtol=1e-8, prec=prec)
+    xs, infos = b.pcg(rtol=1e-8, prec=prec, threads=threads)
     for prob, x, info in zip(probs, xs, infos):
         s = F.Solver(prob)
         xi, ii = s.pcg(rtol=1e-8, prec=prec)
@@ -78,7 +81,7 @@ def test_batch_matches_oracle(oracle_batch, prec):
     +-1 and meets the tolerance in the oracle's own residual b - A x."""
     import scipy.sparse.linalg as spla
     probs, Hs, sols, b = oracle_batch
-    xs, infos = b.pcg(rtol=1e-8, prec=prec)
+    xs, infos = b.pcg(rtol=1e-8, prec=prec, threads=0)
     for i, (H, (xo, ko, _), x, info) in enumerate(zip(Hs, sols, xs, infos)):
         x = x.cpu().numpy()
         assert abs(info["iters"] - ko) <= 1, (i, prec, info["iters"], ko)
