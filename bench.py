@@ -281,7 +281,7 @@ def run_batch(args, rank, world, local):
     # lockstep (threads 0: every instance in flight, one host thread) is the
     # batched solve; the host worker pool is reported beside it
     for prec, name, threads in ((FCM_MIXED, "mixed", 0), (FCM_FP64, "fp64", 0),
-                                (FCM_MIXED, "mixed_pool16", 16)):
+                                (FCM_MIXED, "mixed_pool16", 16), (FCM_MIXED, "mixed_graph", -1)):
         for _ in range(args.warmup):
             b.pcg(xs, rtol=RTOL, maxit=MAXIT, prec=prec, threads=threads)
         barrier()
@@ -306,7 +306,8 @@ def run_batch(args, rank, world, local):
                                      "ndofs_total": ndofs, "setup_s": setup_s,
                                      "setup_threads": 16, "solve": "lockstep, one host thread"},
                           "mixed": out["mixed"], "fp64": out["fp64"],
-                          "mixed_pool16": out["mixed_pool16"]}))
+                          "mixed_pool16": out["mixed_pool16"],
+                          "mixed_graph": out["mixed_graph"]}))
     b.close()
 
 

@@ -441,10 +441,18 @@ fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec,
 
 /* Batched mode (independent problems of uneven size, degree and geometry;
  * the paper solves one problem at a time, this is a service mode).  Every
- * instance gets its own handle, stream and V-cycle graphs; `threads` host
- * workers (<= 0: hardware concurrency, at most 64) set instances up and
- * drive their solves so that the GPU runs many instances concurrently.
- * Arrays hold n entries.  On a failing instance fcm_setup_batch destroys
+ * instance gets its own handle, stream and V-cycle graphs.  Set-up:
+ * `threads` host workers (<= 0: hardware concurrency, at most 64).  Solve:
+ * threads 0 runs all instances in lockstep from the calling thread (every
+ * CG iteration enqueues each running instance's operator step on its
+ * stream, synchronises once per instance for the convergence test, then
+ * enqueues each running instance's preconditioner step; a done flag per
+ * instance masks the converged ones); threads < 0 does the same with one
+ * graph launch per CG phase for all running instances (rebuilt when the
+ * running set changes); threads > 0 uses that many host workers, each
+ * driving whole solves.  Every mode does each instance's work of
+ * fcm_pcg_solve in the same order, so the results equal single solves bit
+ * for bit.  Arrays hold n entries.  On a failing instance fcm_setup_batch destroys
  * what it built and returns that instance's status; fcm_pcg_solve_batch
  * solves every instance, fills infos[i] for each, and returns the first
  * non-FCM_OK status (instance index in fcm_last_error).  x_dev[i]: device

@@ -124,6 +124,11 @@ struct fcm_handle {
   double* d_scalar = nullptr;      // reductions for the host
   double* h_scalar = nullptr;      // pinned
   cudaGraphExec_t g_vc64 = nullptr, g_vc32 = nullptr;
+  // batched solves: this instance's CG phases as graphs (index: precision),
+  // captured on first use, and their kernel node counts
+  cudaGraph_t phase_a[2] = {nullptr, nullptr}, phase_b[2] = {nullptr, nullptr};
+  long long phase_nodes[2][2] = {{0, 0}, {0, 0}};
+  long long phase_bytes[2][2] = {{0, 0}, {0, 0}};
   // mixed V-cycle: levels >= top64 run in FP64 (the rest in FP32)
   int top64 = 1 << 30;
   long long vc_nodes64 = 0, vc_nodes32 = 0;  // kernel nodes per V-cycle graph
@@ -152,6 +157,10 @@ struct fcm_handle {
     if (s) cudaStreamSynchronize(s);
     if (g_vc64) cudaGraphExecDestroy(g_vc64);
     if (g_vc32) cudaGraphExecDestroy(g_vc32);
+    for (int i = 0; i < 2; ++i) {
+      if (phase_a[i]) cudaGraphDestroy(phase_a[i]);
+      if (phase_b[i]) cudaGraphDestroy(phase_b[i]);
+    }
     for (void* p : allocs) cudaFree(p);
     if (h_scalar) cudaFreeHost(h_scalar);
     if (ev_in) cudaEventDestroy(ev_in);
@@ -1652,6 +1661,102 @@ fcm_status pcg_end(PcgRun& R, fcm_info* info) {
   return R.st;
 }
 
+// Record f on the handle's stream into a graph; *nodes = its kernel nodes.
+// The solve counters are left as they were.
+template <typename F>
+cudaGraph_t capture_graph(Handle* h, F&& f, long long* nodes, long long* bytes_rec) {
+  const long long launches = h->launches, bytes = h->bytes;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+  try {
+    f();
+  } catch (...) {
+    cudaStreamEndCapture(h->s, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  CK(cudaStreamEndCapture(h->s, &g));
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nv(nn);
+  if (nn) CK(cudaGraphGetNodes(g, nv.data(), &nn));
+  long long kn = 0;
+  for (auto nd : nv) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++kn;
+  }
+  *nodes = kn;
+  *bytes_rec = h->bytes - bytes;  // algorithmic bytes the recorded launches counted
+  h->launches = launches;
+  h->bytes = bytes;
+  return g;
+}
+
+// The preconditioner of phase b recorded into the current capture: the
+// launches run_vcycle makes, with the V-cycle recorded instead of launched
+// as a graph.
+void record_precondition(Handle* h, const double* r, double* z, int prec) {
+  Level& T = h->levels.back();
+  const int top = (int)h->levels.size() - 1;
+  if (prec == FCM_MIXED && h->top64 > top) {
+    launch_copy_d2f(r, T.b32, T.g.N, h->s);
+    record_vcycle<float>(h, top, h->top64);
+    launch_copy_f2d(T.x32, z, T.g.N, h->s);
+  } else {
+    if (r != T.b) CK(cudaMemcpyAsync(T.b, r, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+    record_vcycle<double>(h, top, prec == FCM_MIXED ? h->top64 : 0);
+    if (z != T.x) CK(cudaMemcpyAsync(z, T.x, T.g.N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+  }
+  CKL();
+}
+
+// This instance's CG phases as graphs for the batched solve (iterate in
+// h->cx): a = q = A p, p.q, the x / r updates, r.r to pinned host memory;
+// b = the preconditioned residual and the next direction (pcg_phase_a /
+// pcg_phase_b with the CG+MG method).
+void ensure_phase_graphs(Handle* h, int prec) {
+  const int pi = prec == FCM_MIXED ? 1 : 0;
+  if (h->phase_a[pi]) return;
+  Level& T = h->levels.back();
+  const long long N = T.g.N;
+  const bool flexible = prec == FCM_MIXED;
+  h->phase_a[pi] = capture_graph(
+      h,
+      [&] {
+        apply_A64(h, T, h->cp, h->cq, GATHER_SET, nullptr);
+        launch_dot_partials(h->cp, h->cq, N, h->part, h->s);
+        launch_cg_update_xr(h->cx, T.b, h->cp, h->cq, N, h->part, h->sc, h->part + kDotBlocks,
+                            h->s);
+        launch_reduce(h->part + kDotBlocks, kDotBlocks, h->d_scalar, h->s);
+        CKL();
+        CK(cudaMemcpyAsync(h->h_scalar, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost,
+                           h->s));
+      },
+      &h->phase_nodes[pi][0], &h->phase_bytes[pi][0]);
+  h->phase_b[pi] = capture_graph(
+      h,
+      [&] {
+        double* z = h->ctmp;
+        if (flexible)
+          CK(cudaMemcpyAsync(h->cz_old, z, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+        record_precondition(h, T.b, z, prec);
+        if (flexible)
+          launch_dot2_partials(T.b, z, h->cz_old, N, h->part, h->s);
+        else
+          launch_dot_partials(T.b, z, N, h->part, h->s);
+        launch_cg_update_p(h->cp, z, N, h->part, flexible ? 1 : 0, h->sc, h->s);
+        CKL();
+      },
+      &h->phase_nodes[pi][1], &h->phase_bytes[pi][1]);
+  // the recorded V-cycle counts no bytes itself (run_vcycle adds them)
+  const int top = (int)h->levels.size() - 1;
+  if (prec == FCM_MIXED)
+    h->phase_bytes[pi][1] += h->vc_bytes32 + (h->top64 > top ? 2 * N * (8 + 4) : 4 * N * 8);
+  else
+    h->phase_bytes[pi][1] += h->vc_bytes64 + 4 * N * 8;
+}
+
 fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int maxit, int prec,
                     fcm_info* info, int method = FCM_METHOD_CG_MG) {
   PcgRun R;
@@ -1665,6 +1770,157 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
   return pcg_end(R, info);
 }
 
+// One graph per CG phase for all running instances of a batch: the
+// instances' phase graphs as parallel child nodes, rebuilt when the set of
+// running instances changes (at most once per instance).
+struct BatchGraph {
+  std::vector<int> members;
+  cudaGraphExec_t a = nullptr, b = nullptr;
+  ~BatchGraph() { reset(); }
+  void reset() {
+    if (a) cudaGraphExecDestroy(a);
+    if (b) cudaGraphExecDestroy(b);
+    a = b = nullptr;
+  }
+  static cudaGraphExec_t build(Handle* const* hs, const std::vector<int>& m, int pi, bool phase_b) {
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    try {
+      for (int i : m) {
+        cudaGraphNode_t nd;
+        CK(cudaGraphAddChildGraphNode(&nd, g, nullptr, 0,
+                                      phase_b ? hs[i]->phase_b[pi] : hs[i]->phase_a[pi]));
+      }
+    } catch (...) {
+      cudaGraphDestroy(g);
+      throw;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return ex;
+  }
+  void update(Handle* const* hs, const std::vector<int>& m, int pi) {
+    if (m == members && a) return;
+    reset();
+    members = m;
+    if (m.empty()) return;
+    a = build(hs, m, pi, false);
+    b = build(hs, m, pi, true);
+  }
+};
+
+// The same lockstep with one graph launch per CG phase for all running
+// instances (threads < 0 in fcm_pcg_solve_batch): phase a
+// of every running instance, one synchronisation, the host checks (a
+// per-instance done flag is the convergence mask; a true-residual check
+// runs on the instance's own stream), then phase b of those still running.
+// Each instance does the work of pcg_impl in the same order (its iterate in
+// its handle, copied out at the end), so the results are bit for bit those
+// of single solves.  Returns the first failing status in instance order.
+// Measured on 64 instances of the batch workload: slower than the
+// per-instance launches of pcg_batch_lockstep in the mixed solve (9.1 vs
+// 11.0 M DOFs/s), because every change of the running set re-instantiates
+// two graphs of all running instances' phases (a V-cycle's nodes each).
+fcm_status pcg_batch_graph(Handle* const* hs, int n, double* const* x, double rtol, int maxit,
+                           int prec, fcm_info* infos, std::string* msg) {
+  const int pi = prec == FCM_MIXED ? 1 : 0;
+  std::vector<PcgRun> R(n);
+  std::vector<fcm_status> st(n, FCM_OK);
+  std::vector<std::string> err(n);
+  std::vector<char> alive(n, 1);
+  auto fail = [&](int i, fcm_status s, const char* m) {
+    st[i] = s;
+    err[i] = m;
+    alive[i] = 0;
+  };
+  auto step = [&](int i, auto&& f) {
+    if (!alive[i]) return;
+    try {
+      f();
+    } catch (const Error& e) {
+      fail(i, e.st, e.what());
+    } catch (const std::bad_alloc&) {
+      fail(i, FCM_E_OOM, "host out of memory");
+    } catch (const std::exception& e) {
+      fail(i, FCM_E_CUDA, e.what());
+    }
+  };
+  std::vector<std::unique_ptr<CallScope>> scope(n);
+  for (int i = 0; i < n; ++i)
+    step(i, [&] {
+      scope[i].reset(new CallScope(hs[i]));
+      if (prec == FCM_MIXED && !hs[i]->mixed)
+        throw Error(FCM_E_INVALID, "mixed precision data not built (build_mixed = 0)");
+      ensure_phase_graphs(hs[i], prec);
+      pcg_begin(R[i], hs[i], nullptr, hs[i]->cx, rtol, maxit, prec, FCM_METHOD_CG_MG);
+      CK(cudaStreamSynchronize(hs[i]->s));
+    });
+  cudaStream_t bs = nullptr;
+  fcm_status gst = FCM_OK;
+  std::string gmsg;
+  BatchGraph bg;
+  try {
+    CK(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    for (;;) {
+      std::vector<int> run;
+      for (int i = 0; i < n; ++i)
+        if (alive[i] && !R[i].done && R[i].k < R[i].maxit) run.push_back(i);
+      if (run.empty()) break;
+      bg.update(hs, run, pi);
+      CK(cudaGraphLaunch(bg.a, bs));
+      CK(cudaStreamSynchronize(bs));
+      std::vector<int> next;
+      for (int i : run)
+        step(i, [&] {
+          Handle* h = hs[i];
+          ++R[i].k;
+          h->launches += h->phase_nodes[pi][0];
+          h->bytes += h->phase_bytes[pi][0];
+          const bool more = pcg_check(R[i]);
+          CK(cudaStreamSynchronize(h->s));
+          if (more) next.push_back(i);
+        });
+      if (next.empty()) continue;
+      if (next != run) bg.update(hs, next, pi);
+      CK(cudaGraphLaunch(bg.b, bs));
+      CK(cudaStreamSynchronize(bs));
+      for (int i : next) {
+        hs[i]->launches += hs[i]->phase_nodes[pi][1];
+        hs[i]->bytes += hs[i]->phase_bytes[pi][1];
+      }
+    }
+  } catch (const Error& e) {
+    gst = e.st;
+    gmsg = e.what();
+  }
+  bg.reset();
+  if (bs) cudaStreamDestroy(bs);
+  if (gst != FCM_OK) {
+    *msg = std::string("batched solve: ") + gmsg;
+    return gst;
+  }
+  for (int i = 0; i < n; ++i)
+    step(i, [&] {
+      Handle* h = hs[i];
+      const long long N = h->levels.back().g.N;
+      const fcm_status s = pcg_end(R[i], infos ? &infos[i] : nullptr);
+      CK(cudaMemcpyAsync(x[i], h->cx, N * sizeof(double), cudaMemcpyDeviceToDevice, h->s));
+      if (scope[i]) scope[i]->finish();
+      if (s != FCM_OK) {
+        st[i] = s;
+        err[i] = g_last_error;
+      }
+    });
+  for (int i = 0; i < n; ++i)
+    if (st[i] != FCM_OK) {
+      *msg = "instance " + std::to_string(i) + ": " + err[i];
+      return st[i];
+    }
+  return FCM_OK;
+}
+
 // Independent solves in lockstep from one host thread (the batch of Sec.
 // 8 a13): every iteration enqueues phase a of all running instances on
 // their streams, synchronises each once, runs the host checks, then
@@ -1672,8 +1928,8 @@ fcm_status pcg_impl(Handle* h, const double* b_in, double* x, double rtol, int m
 // work of pcg_impl, in the same order on its own stream, so the results are
 // bit for bit those of single solves.  Returns the first failing status in
 // instance order.
-fcm_status pcg_batch_impl(Handle* const* hs, int n, double* const* x, double rtol, int maxit,
-                          int prec, fcm_info* infos, std::string* msg) {
+fcm_status pcg_batch_lockstep(Handle* const* hs, int n, double* const* x, double rtol,
+                              int maxit, int prec, fcm_info* infos, std::string* msg) {
   std::vector<PcgRun> R(n);
   std::vector<fcm_status> st(n, FCM_OK);
   std::vector<std::string> err(n);
@@ -2920,13 +3176,14 @@ void fcm_destroy(fcm_handle* h) { delete h; }
 
 namespace fcm {
 fcm_status pcg_solve_lockstep(fcm_handle* const* hs, int n, double* const* x, double rtol,
-                              int maxit, int prec, fcm_info* infos) {
+                              int maxit, int prec, fcm_info* infos, bool graph) {
   if (prec != FCM_FP64 && prec != FCM_MIXED) {
     g_last_error = "invalid precision";
     return FCM_E_INVALID;
   }
   std::string msg;
-  fcm_status st = pcg_batch_impl(hs, n, x, rtol, maxit, prec, infos, &msg);
+  fcm_status st = graph ? pcg_batch_graph(hs, n, x, rtol, maxit, prec, infos, &msg)
+                        : pcg_batch_lockstep(hs, n, x, rtol, maxit, prec, infos, &msg);
   if (st != FCM_OK) g_last_error = msg;
   return st;
 }

@@ -112,8 +112,10 @@ fcm_status fcm_pcg_solve_batch(fcm_batch* b, double* const* x_dev, double rtol, 
       fcm::set_last_error("fcm_pcg_solve_batch: x_dev has a NULL entry");
       return FCM_E_INVALID;
     }
-  if (threads <= 0)  // lockstep: all instances in flight, driven by this thread
-    return fcm::pcg_solve_lockstep(b->h.data(), n, x_dev, rtol, maxit, prec, infos);
+  // lockstep: all instances in flight, driven by this thread (threads < 0:
+  // one graph launch per CG phase for all running instances)
+  if (threads <= 0)
+    return fcm::pcg_solve_lockstep(b->h.data(), n, x_dev, rtol, maxit, prec, infos, threads < 0);
   std::string msg;
   fcm_status st = run_pool(
       n, threads,

@@ -268,9 +268,10 @@ void launch_mlhp_vec(long long N, int mode, const unsigned char* mask, const dou
                      const double* b, double* out, double w, cudaStream_t s);
 
 // Independent CG solves of several handles in lockstep from the calling
-// thread (batched mode); the first failing status in instance order.
+// thread (batched mode; graph: one graph launch per CG phase for all
+// running instances); the first failing status in instance order.
 fcm_status pcg_solve_lockstep(fcm_handle* const* hs, int n, double* const* x, double rtol,
-                              int maxit, int prec, fcm_info* infos);
+                              int maxit, int prec, fcm_info* infos, bool graph);
 
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };

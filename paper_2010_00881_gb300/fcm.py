@@ -568,8 +568,9 @@ class Batch:
             pass
 
     def pcg(self, xs=None, rtol=1e-8, maxit=500, prec=FCM_FP64, threads=None):
-        """threads 0: all instances in lockstep from this thread; > 0: a pool
-        of that many host workers (default: the set-up's thread count)."""
+        """threads 0: all instances in lockstep from this thread; -1: the same
+        with one graph launch per CG phase; > 0: a pool of that many host
+        workers (default: the set-up's thread count)."""
         import torch
         n = len(self.ndofs)
         if xs is None:

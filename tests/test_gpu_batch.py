@@ -35,11 +35,12 @@ def batch():
     b.close()
 
 
-@pytest.mark.parametrize("threads", [0, 3])
+@pytest.mark.parametrize("threads", [0, -1, 3])
 @pytest.mark.parametrize("prec", [FCM_FP64, FCM_MIXED])
 def test_batch_equals_individual_solves(batch, prec, threads):
-    """threads 0: all instances in lockstep from one host thread; 3: a pool
-    of host workers.  Both run each instance's work exactly as alone."""
+    """threads 0: all instances in lockstep from one host thread; -1: the
+    same with one graph launch per CG phase; 3: a pool of host workers.
+    All run each instance's work exactly as alone."""
     probs, b = batch
     xs, infos = b.pcg(rtol=1e-8, prec=prec, threads=threads)
     for prob, x, info in zip(probs, xs, infos):
