@@ -324,11 +324,12 @@ fcm_status fcm_mlhp_restriction_1d(int p, int dk, int pos, double* S);
  *   (opts->smoother PATCHWISE: the functions touching the base cells around
  *   a base node, Sec. 3.3.1; ELEMENTWISE: those touching one base cell),
  *   inverted densely, omega as in fcm_setup (patchwise paper values 1/6 in
- *   2D, 1/18 in 3D), the coarsest level (the base grid's hats) solved by its
- *   dense inverse.  The blocks are assembled and inverted on the host at
- *   set-up; FCM_E_UNSUPPORTED when the base grid has more than
- *   opts->coarse_cells cells on an axis (the uniform Q1 h-levels below the
- *   base grid are not built for overlays) or a block exceeds 6144 DOFs.
+ *   2D, 1/18 in 3D); below the base grid's hats, while the grid has more
+ *   than opts->coarse_cells cells on an axis, Q1 h-levels by Galerkin
+ *   P^T A P with multilinear interpolation (the Remark of Sec. 3.2; node
+ *   blocks of the same kind); the coarsest level solved by its dense
+ *   inverse.  The blocks and Q1 operators are assembled and inverted on the
+ *   host at set-up; FCM_E_UNSUPPORTED when a block exceeds 6144 DOFs.
  * fcm_mlhp_op_level: per level (0 = coarsest) its DOFs, omega, number and
  *   largest size of its blocks.
  * fcm_mlhp_op_vcycle: z = V(r), Algorithm 1 with zero initial guess, every

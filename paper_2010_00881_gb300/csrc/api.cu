@@ -2432,8 +2432,16 @@ fcm_status fcm_op_bytes(const fcm_handle* h, int level, int which, int prec, lon
 // functions zero): the level's DOF mask, its additive Schwarz blocks (DOF
 // lists, dense inverses) with their fixed-order gather lists, omega.
 struct MlhpLevel {
+  bool q1 = false;                // a Q1 level below the base grid (own vectors)
+  long long N = 0;                // vector length (all functions on hp-levels)
   long long ndofs = 0;
   unsigned char* mask = nullptr;
+  long long *aptr = nullptr, *acol = nullptr;  // Q1 levels: CSR operator
+  double* aval = nullptr;
+  // transfer to the next coarser level when that is a Q1 level: R (its
+  // rows) and P (this level's rows), CSR; otherwise the coarser level's mask
+  long long *rptr = nullptr, *rcol = nullptr, *pptr = nullptr, *pcol = nullptr;
+  double *rval = nullptr, *pval = nullptr;
   int nblk = 0, max_m = 0;
   long long* boff = nullptr;      // block DOF-list offsets
   long long* bdof = nullptr;      // block DOFs (global, field-major)
@@ -2454,7 +2462,7 @@ struct fcm_mlhp_op {
   // host copies kept for the hierarchy: leaf incidences, leaf matrix
   // offsets, patches and the hp-level of every function
   std::vector<long long> h_loff, h_lfn, h_koff, h_patch_off, h_patch_fn;
-  std::vector<int> h_coarsest, h_llev, h_lidx;
+  std::vector<int> h_coarsest, h_llev, h_lidx, h_ft;
   int n_levels = 0;
   std::vector<MlhpLevel> lv;      // 0 = coarsest
   int n_pre = 5, n_post = 5;
@@ -2625,6 +2633,7 @@ void mlhp_op_build(fcm_mlhp_op* op, const fcm_mlhp* m, const fcm_grid* grid,
   op->h_lfn = lfn;
   op->h_koff = koff;
   op->h_llev = llev;
+  op->h_ft = ft;
   op->h_lidx = lidx;
   long long nodes = 1;
   for (int a = 0; a < dim; ++a) nodes *= P.C[a] + 1;
@@ -2731,18 +2740,28 @@ void mlhp_apply_dev(fcm_mlhp_op* op, const double* x, double* y) {
 // z = sum of the level's block inverses applied to r (all N entries written).
 void mlhp_smooth_dev(fcm_mlhp_op* op, const MlhpLevel& L, const double* r, double* z) {
   Handle* h = op->h.get();
-  const long long N = op->M * op->nf;
-  launch_leaf_apply(L.nblk, 1, N, L.max_m, L.boff, L.bdof, L.binv_off, L.binv, r, op->Yb, h->s);
-  launch_leaf_gather(N, 1, L.gioff, L.gibase, L.gistride, op->Yb, z, h->s);
+  launch_leaf_apply(L.nblk, 1, L.N, L.max_m, L.boff, L.bdof, L.binv_off, L.binv, r, op->Yb, h->s);
+  launch_leaf_gather(L.N, 1, L.gioff, L.gibase, L.gistride, op->Yb, z, h->s);
   CKL();
 }
 
-// x = V(b) on level l with zero initial guess (Algorithm 1; restriction =
-// the coarser level's mask, prolongation = add).
+// y = A_l x: the leaf operator on hp-levels (x is zero off the level; the
+// caller masks the result), the CSR matrix on Q1 levels.
+void mlhp_level_apply(fcm_mlhp_op* op, const MlhpLevel& L, const double* x, double* y) {
+  if (L.q1)
+    launch_csr_spmv(L.N, L.aptr, L.acol, L.aval, x, y, op->h->s);
+  else
+    mlhp_apply_dev(op, x, y);
+  CKL();
+}
+
+// x = V(b) on level l with zero initial guess (Algorithm 1; restriction to
+// a coarser hp-level is its mask and prolongation an add, to a Q1 level the
+// CSR transfers).
 void mlhp_vcycle_dev(fcm_mlhp_op* op, int l, const double* b, double* x) {
   Handle* h = op->h.get();
-  const long long N = op->M * op->nf;
   MlhpLevel& L = op->lv[l];
+  const long long N = L.N;
   if (l == 0) {
     mlhp_smooth_dev(op, L, b, x);  // the dense inverse of the coarsest level
     return;
@@ -2753,20 +2772,28 @@ void mlhp_vcycle_dev(fcm_mlhp_op* op, int l, const double* b, double* x) {
       mlhp_smooth_dev(op, L, b, op->z);
       launch_mlhp_vec(N, 2, nullptr, op->z, nullptr, x, L.omega, h->s);
     } else {
-      mlhp_apply_dev(op, x, op->y);
+      mlhp_level_apply(op, L, x, op->y);
       launch_mlhp_vec(N, 0, L.mask, b, op->y, L.r, 0.0, h->s);
       mlhp_smooth_dev(op, L, L.r, op->z);
       launch_mlhp_vec(N, 1, nullptr, op->z, nullptr, x, L.omega, h->s);
     }
   }
-  mlhp_apply_dev(op, x, op->y);
+  mlhp_level_apply(op, L, x, op->y);
   launch_mlhp_vec(N, 0, L.mask, b, op->y, L.r, 0.0, h->s);
   MlhpLevel& Lc = op->lv[l - 1];
-  launch_mlhp_vec(N, 3, Lc.mask, L.r, nullptr, Lc.b, 0.0, h->s);
+  if (Lc.q1)
+    launch_csr_spmv(Lc.N, L.rptr, L.rcol, L.rval, L.r, Lc.b, h->s);
+  else
+    launch_mlhp_vec(N, 3, Lc.mask, L.r, nullptr, Lc.b, 0.0, h->s);
   mlhp_vcycle_dev(op, l - 1, Lc.b, Lc.x);
-  launch_mlhp_vec(N, 4, nullptr, Lc.x, nullptr, x, 0.0, h->s);
+  if (Lc.q1) {
+    launch_csr_spmv(N, L.pptr, L.pcol, L.pval, Lc.x, op->y, h->s);
+    launch_mlhp_vec(N, 4, nullptr, op->y, nullptr, x, 0.0, h->s);
+  } else {
+    launch_mlhp_vec(N, 4, nullptr, Lc.x, nullptr, x, 0.0, h->s);
+  }
   for (int k = 0; k < op->n_post; ++k) {
-    mlhp_apply_dev(op, x, op->y);
+    mlhp_level_apply(op, L, x, op->y);
     launch_mlhp_vec(N, 0, L.mask, b, op->y, L.r, 0.0, h->s);
     mlhp_smooth_dev(op, L, L.r, op->z);
     launch_mlhp_vec(N, 1, nullptr, op->z, nullptr, x, L.omega, h->s);
@@ -2774,14 +2801,247 @@ void mlhp_vcycle_dev(fcm_mlhp_op* op, int l, const double* b, double* x) {
   CKL();
 }
 
+// Host sparse matrices of the overlay hierarchy set-up.
+HostCsr csr_from_rows(long long nrows, std::vector<std::map<long long, double>>& rows) {
+  HostCsr A;
+  A.n = nrows;
+  A.ptr.assign(nrows + 1, 0);
+  for (long long r = 0; r < nrows; ++r) {
+    for (const auto& kv : rows[r]) {
+      A.col.push_back(kv.first);
+      A.val.push_back(kv.second);
+    }
+    A.ptr[r + 1] = (long long)A.col.size();
+  }
+  return A;
+}
+
+// C = A B (A: rows x k, B: k x cols).
+HostCsr csr_mul(const HostCsr& A, const HostCsr& B) {
+  std::vector<std::map<long long, double>> rows(A.n);
+  for (long long r = 0; r < A.n; ++r)
+    for (long long e = A.ptr[r]; e < A.ptr[r + 1]; ++e) {
+      const long long k = A.col[e];
+      for (long long f = B.ptr[k]; f < B.ptr[k + 1]; ++f) rows[r][B.col[f]] += A.val[e] * B.val[f];
+    }
+  return csr_from_rows(A.n, rows);
+}
+
+HostCsr csr_transpose(const HostCsr& A, long long ncols) {
+  std::vector<std::map<long long, double>> rows(ncols);
+  for (long long r = 0; r < A.n; ++r)
+    for (long long e = A.ptr[r]; e < A.ptr[r + 1]; ++e) rows[A.col[e]][r] += A.val[e];
+  return csr_from_rows(ncols, rows);
+}
+
+// Tensor-product Q1 prolongation of a grid with C cells per axis from the
+// grid with ceil(C / 2) (x fastest, fields block diagonal): even node 2k =
+// coarse node k, odd node 2k + 1 = average of coarse nodes k and k + 1.
+HostCsr q1_prolongation_host(int dim, const int* Cf, int nf) {
+  int mf[3] = {1, 1, 1}, mc[3] = {1, 1, 1};
+  for (int a = 0; a < dim; ++a) {
+    mf[a] = Cf[a] + 1;
+    mc[a] = (Cf[a] + 1) / 2 + 1;
+  }
+  const long long nvf = (long long)mf[0] * mf[1] * mf[2], nvc = (long long)mc[0] * mc[1] * mc[2];
+  std::vector<std::map<long long, double>> rows(nf * nvf);
+  for (long long v = 0; v < nvf; ++v) {
+    int i[3] = {(int)(v % mf[0]), (int)((v / mf[0]) % mf[1]), (int)(v / ((long long)mf[0] * mf[1]))};
+    int lo[3], hi[3];
+    double wl[3], wh[3];
+    for (int a = 0; a < 3; ++a) {
+      if (i[a] % 2 == 0) {
+        lo[a] = hi[a] = i[a] / 2;
+        wl[a] = 1.0;
+        wh[a] = 0.0;
+      } else {
+        lo[a] = i[a] / 2;
+        hi[a] = i[a] / 2 + 1;
+        wl[a] = wh[a] = 0.5;
+      }
+    }
+    for (int cz = 0; cz < 2; ++cz)
+      for (int cy = 0; cy < 2; ++cy)
+        for (int cx = 0; cx < 2; ++cx) {
+          const int c[3] = {cx, cy, cz};
+          double w = 1.0;
+          long long cv = 0, stride = 1;
+          bool ok = true;
+          for (int a = 0; a < 3; ++a) {
+            const double wa = c[a] ? wh[a] : wl[a];
+            if (wa == 0.0) {
+              ok = false;
+              break;
+            }
+            w *= wa;
+            cv += (long long)(c[a] ? hi[a] : lo[a]) * stride;
+            stride *= mc[a];
+          }
+          if (!ok) continue;
+          for (int f = 0; f < nf; ++f) rows[f * nvf + v][f * nvc + cv] += w;
+        }
+  }
+  return csr_from_rows(nf * nvf, rows);
+}
+
+// Schwarz blocks of a Q1 grid level (nodes x fastest, fields stacked):
+// patchwise, the nodes of the cells around each node; elementwise, the
+// nodes of each cell.
+std::vector<std::vector<long long>> q1_blocks(int dim, const int* Cq, int nf, bool patch) {
+  int m[3] = {1, 1, 1}, C3[3] = {1, 1, 1};
+  for (int a = 0; a < dim; ++a) {
+    m[a] = Cq[a] + 1;
+    C3[a] = Cq[a];
+  }
+  const long long nv = (long long)m[0] * m[1] * m[2];
+  auto cell_nodes = [&](const int* c, std::vector<long long>& out) {
+    for (int oz = 0; oz < (dim == 3 ? 2 : 1); ++oz)
+      for (int oy = 0; oy < 2; ++oy)
+        for (int ox = 0; ox < 2; ++ox)
+          out.push_back((c[0] + ox) + (long long)m[0] * ((c[1] + oy) + (long long)m[1] * (c[2] + oz)));
+  };
+  std::vector<std::vector<long long>> blocks;
+  auto fields = [&](std::vector<long long>& ids) {
+    std::sort(ids.begin(), ids.end());
+    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    std::vector<long long> d;
+    for (int f = 0; f < nf; ++f)
+      for (long long i : ids) d.push_back(f * nv + i);
+    blocks.push_back(d);
+  };
+  if (!patch) {
+    for (int cz = 0; cz < C3[2]; ++cz)
+      for (int cy = 0; cy < C3[1]; ++cy)
+        for (int cx = 0; cx < C3[0]; ++cx) {
+          const int c[3] = {cx, cy, cz};
+          std::vector<long long> ids;
+          cell_nodes(c, ids);
+          fields(ids);
+        }
+    return blocks;
+  }
+  for (int vz = 0; vz < m[2]; ++vz)
+    for (int vy = 0; vy < m[1]; ++vy)
+      for (int vx = 0; vx < m[0]; ++vx) {
+        std::vector<long long> ids;
+        for (int oz = 0; oz < (dim == 3 ? 2 : 1); ++oz)
+          for (int oy = 0; oy < 2; ++oy)
+            for (int ox = 0; ox < 2; ++ox) {
+              const int c[3] = {vx - ox, vy - oy, dim == 3 ? vz - oz : 0};
+              if (c[0] < 0 || c[0] >= C3[0] || c[1] < 0 || c[1] >= C3[1] || c[2] < 0 ||
+                  c[2] >= C3[2])
+                continue;
+              cell_nodes(c, ids);
+            }
+        fields(ids);
+      }
+  return blocks;
+}
+
+// Blocks, dense inverses, gather lists and omega of one level (host), then
+// uploaded: blocks over DOFs 0 .. N-1, A the level's host operator (the
+// rows and columns of the level), coarsest: one dense inverse, no omega.
+void mlhp_level_blocks(fcm_mlhp_op* op, MlhpLevel& L, const HostCsr& A,
+                       const std::vector<std::vector<long long>>& blocks,
+                       const std::vector<unsigned char>& mask, double omega_paper,
+                       bool coarsest, const std::vector<long long>& order) {
+  Handle* h = op->h.get();
+  const long long N = L.N;
+  std::vector<long long> boff(1, 0), bdof, binv_off(1, 0);
+  std::vector<double> binv;
+  for (const auto& b : blocks) {
+    const int m = (int)b.size();
+    if ((size_t)m * sizeof(double) > 48 * 1024)
+      throw Error(FCM_E_UNSUPPORTED, "overlay Schwarz block of more than 6144 DOFs");
+    std::vector<double> B((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) B[(size_t)i * m + j] = A.at(b[i], b[j]);
+    host_spd_inverse(B, m);
+    binv.insert(binv.end(), B.begin(), B.end());
+    bdof.insert(bdof.end(), b.begin(), b.end());
+    boff.push_back((long long)bdof.size());
+    binv_off.push_back((long long)binv.size());
+    L.max_m = std::max(L.max_m, m);
+  }
+  L.nblk = (int)blocks.size();
+  std::vector<long long> gioff(N + 1, 0);
+  for (long long d : bdof) ++gioff[d + 1];
+  for (long long i = 0; i < N; ++i) gioff[i + 1] += gioff[i];
+  std::vector<long long> gibase(bdof.size()), fill(gioff.begin(), gioff.end() - 1);
+  for (size_t e = 0; e < bdof.size(); ++e) gibase[fill[bdof[e]]++] = (long long)e;
+  std::vector<int> gistride(bdof.size(), 1);
+  L.mask = h->upload(mask);
+  L.boff = h->upload(boff);
+  L.bdof = h->upload(bdof.empty() ? std::vector<long long>(1, 0) : bdof);
+  L.binv_off = h->upload(binv_off);
+  L.binv = h->upload(binv.empty() ? std::vector<double>(1, 0.0) : binv);
+  L.gioff = h->upload(gioff);
+  L.gibase = h->upload(gibase.empty() ? std::vector<long long>(1, 0) : gibase);
+  L.gistride = h->upload(gistride.empty() ? std::vector<int>(1, 1) : gistride);
+  L.x = h->alloc<double>(N);
+  L.b = h->alloc<double>(N);
+  L.r = h->alloc<double>(N);
+  if (coarsest) return;
+  // omega: power method on M^{-1} A_l from sin(k + 1) over the level's
+  // numbering (`order`: the level's DOFs in that numbering)
+  auto Av = [&](const std::vector<double>& v, std::vector<double>& out) {
+    for (long long r = 0; r < N; ++r) {
+      double t = 0.0;
+      if (mask[r])
+        for (long long e = A.ptr[r]; e < A.ptr[r + 1]; ++e) t += A.val[e] * v[A.col[e]];
+      out[r] = t;
+    }
+  };
+  auto Mv = [&](const std::vector<double>& v, std::vector<double>& out) {
+    std::fill(out.begin(), out.end(), 0.0);
+    for (size_t bi = 0; bi < blocks.size(); ++bi) {
+      const auto& b = blocks[bi];
+      const int m = (int)b.size();
+      const double* Bi = binv.data() + binv_off[bi];
+      for (int i = 0; i < m; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < m; ++j) t += Bi[(size_t)i * m + j] * v[b[j]];
+        out[b[i]] += t;
+      }
+    }
+  };
+  std::vector<double> v((size_t)N, 0.0), av((size_t)N), w((size_t)N);
+  for (size_t k = 0; k < order.size(); ++k) v[(size_t)order[k]] = std::sin((double)k + 1.0);
+  double lam = 0.0;
+  for (int it = 0; it < 40; ++it) {
+    Av(v, av);
+    Mv(av, w);
+    double num = 0.0, den = 0.0, nw = 0.0;
+    for (long long i = 0; i < N; ++i) {
+      num += av[i] * w[i];
+      den += v[i] * av[i];
+      nw += w[i] * w[i];
+    }
+    lam = num / den;
+    nw = std::sqrt(nw);
+    for (long long i = 0; i < N; ++i) v[i] = w[i] / nw;
+  }
+  L.lambda = lam;
+  L.omega = std::min(omega_paper, 1.75 / lam);
+}
+
+void upload_csr(Handle* h, const HostCsr& A, long long*& ptr, long long*& col, double*& val) {
+  ptr = h->upload(A.ptr);
+  col = h->upload(A.col.empty() ? std::vector<long long>(1, 0) : A.col);
+  val = h->upload(A.val.empty() ? std::vector<double>(1, 0.0) : A.val);
+}
+
 // The hierarchy of Sec. 3.2 on the overlay mesh: hp-levels from
-// fcm_mlhp_levels (level l holds the functions with coarsest <= l), on
-// every level l >= 1 additive Schwarz blocks (patchwise: the functions
-// touching the base cells around a base node; elementwise: those touching
-// one base cell) with omega clamped like the uniform path (power method
-// from sin(k + 1) over the level's numbering, omega = min(paper value,
-// 1.75 / lambda)); the coarsest level (the base grid's hats) solved by its
-// dense inverse.  Set-up on the host from the assembled leaf matrices.
+// fcm_mlhp_levels (level l holds the functions with coarsest <= l), on every
+// smoothing level additive Schwarz blocks (patchwise: the functions touching
+// the base cells around a base node; elementwise: those touching one base
+// cell) with omega clamped like the uniform path (power method from
+// sin(k + 1) over the level's numbering, omega = min(paper value,
+// 1.75 / lambda)); below the base grid's hats, while the grid has more than
+// coarse_cells cells on an axis, Q1 h-levels by Galerkin P^T A P with the
+// multilinear prolongation (the Remark of Sec. 3.2), with node blocks of the
+// same kind; the coarsest level solved by its dense inverse.  Set-up on the
+// host from the assembled leaf matrices.
 void mlhp_prepare(fcm_mlhp_op* op, const fcm_solver_opts* opts) {
   Handle* h = op->h.get();
   if (!opts) throw Error(FCM_E_INVALID, "null solver options");
@@ -2789,32 +3049,31 @@ void mlhp_prepare(fcm_mlhp_op* op, const fcm_solver_opts* opts) {
     throw Error(FCM_E_UNSUPPORTED, "overlay meshes take additive Schwarz blocks");
   if (opts->n_pre < 0 || opts->n_post < 0 || opts->n_pre > 64 || opts->n_post > 64)
     throw Error(FCM_E_INVALID, "smoothing steps must be in [0, 64]");
-  int cmax = 0;
-  for (int a = 0; a < op->dim; ++a) cmax = std::max(cmax, op->C[a]);
-  if (cmax > opts->coarse_cells)
-    throw Error(FCM_E_UNSUPPORTED,
-                "overlay hierarchies end at the base grid: base cells per axis must not exceed "
-                "coarse_cells");
+  if (opts->coarse_cells < 1) throw Error(FCM_E_INVALID, "coarse_cells must be >= 1");
   op->n_pre = opts->n_pre;
   op->n_post = opts->n_post;
   const long long M = op->M, N = M * op->nf;
+  const int nf = op->nf, dim = op->dim;
   const int nl = op->n_levels;
   const bool patch = opts->smoother == FCM_SMOOTHER_PATCHWISE;
   const double omega_paper =
       opts->omega > 0.0 ? opts->omega
-                        : (patch ? (op->dim == 2 ? 1.0 / 6.0 : 1.0 / 18.0)
-                                 : (op->dim == 2 ? 1.0 / 3.0 : 2.0 / 15.0));
+                        : (patch ? (dim == 2 ? 1.0 / 6.0 : 1.0 / 18.0)
+                                 : (dim == 2 ? 1.0 / 3.0 : 2.0 / 15.0));
+  int cmax = 0;
+  for (int a = 0; a < dim; ++a) cmax = std::max(cmax, op->C[a]);
+  const bool has_q1 = cmax > opts->coarse_cells;
   HostCsr A = mlhp_host_matrix(op);
   // functions touching each base cell (elementwise blocks)
   long long nbase = 1;
-  for (int a = 0; a < op->dim; ++a) nbase *= op->C[a];
+  for (int a = 0; a < dim; ++a) nbase *= op->C[a];
   std::vector<std::vector<long long>> per_cell;
   if (!patch) {
     per_cell.resize(nbase);
     for (long long l = 0; l < op->nleaf; ++l) {
       const int k = op->h_llev[l];
       long long lin = 0, stride = 1;
-      for (int a = 0; a < op->dim; ++a) {
+      for (int a = 0; a < dim; ++a) {
         lin += (long long)(op->h_lidx[3 * l + a] >> k) * stride;
         stride *= op->C[a];
       }
@@ -2826,30 +3085,30 @@ void mlhp_prepare(fcm_mlhp_op* op, const fcm_solver_opts* opts) {
       v.erase(std::unique(v.begin(), v.end()), v.end());
     }
   }
-  op->lv.assign(nl, MlhpLevel());
-  size_t max_m = 1;
+  // hp-levels
+  std::vector<MlhpLevel> hp(nl);
   for (int l = 0; l < nl; ++l) {
-    MlhpLevel& L = op->lv[l];
+    MlhpLevel& L = hp[l];
+    L.N = N;
     std::vector<unsigned char> inl((size_t)M, 0);
     for (long long i = 0; i < M; ++i) inl[i] = op->h_coarsest[i] <= l;
     std::vector<unsigned char> mask((size_t)N);
     for (long long i = 0; i < N; ++i) mask[i] = inl[i % M];
-    long long Ml = 0;
-    for (unsigned char c : inl) Ml += c;
-    L.ndofs = Ml * op->nf;
-    // blocks: DOF lists (fields outer, ascending function ids)
-    std::vector<std::vector<long long>> blocks;
+    std::vector<long long> order;  // the level's DOFs: fields outer, ascending ids
+    for (int f = 0; f < nf; ++f)
+      for (long long i = 0; i < M; ++i)
+        if (inl[i]) order.push_back(f * M + i);
+    L.ndofs = (long long)order.size();
     auto expand = [&](const std::vector<long long>& ids) {
       std::vector<long long> d;
-      for (int f = 0; f < op->nf; ++f)
+      for (int f = 0; f < nf; ++f)
         for (long long i : ids) d.push_back(f * M + i);
       return d;
     };
-    if (l == 0) {
-      std::vector<long long> ids;
-      for (long long i = 0; i < M; ++i)
-        if (inl[i]) ids.push_back(i);
-      blocks.push_back(expand(ids));
+    std::vector<std::vector<long long>> blocks;
+    const bool coarsest = l == 0 && !has_q1;
+    if (coarsest) {
+      blocks.push_back(order);
     } else if (patch) {
       for (size_t v = 0; v + 1 < op->h_patch_off.size(); ++v) {
         std::vector<long long> ids;
@@ -2865,94 +3124,115 @@ void mlhp_prepare(fcm_mlhp_op* op, const fcm_solver_opts* opts) {
         if (!ids.empty()) blocks.push_back(expand(ids));
       }
     }
-    // dense inverses
-    std::vector<long long> boff(1, 0), bdof, binv_off(1, 0);
-    std::vector<double> binv;
-    for (const auto& b : blocks) {
-      const int m = (int)b.size();
-      if ((size_t)m * sizeof(double) > 48 * 1024)
-        throw Error(FCM_E_UNSUPPORTED, "overlay Schwarz block of more than 6144 DOFs");
-      max_m = std::max(max_m, (size_t)m);
-      std::vector<double> B((size_t)m * m);
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) B[(size_t)i * m + j] = A.at(b[i], b[j]);
-      host_spd_inverse(B, m);
-      binv.insert(binv.end(), B.begin(), B.end());
-      bdof.insert(bdof.end(), b.begin(), b.end());
-      boff.push_back((long long)bdof.size());
-      binv_off.push_back((long long)binv.size());
-      L.max_m = std::max(L.max_m, m);
+    mlhp_level_blocks(op, L, A, blocks, mask, omega_paper, coarsest, order);
+  }
+  // Q1 h-levels below the base grid's hats
+  std::vector<MlhpLevel> q1;  // fine to coarse
+  if (has_q1) {
+    // the hats: functions of hp-level 0, in grid order (x fastest)
+    std::vector<long long> hats;
+    for (long long i = 0; i < M; ++i)
+      if (op->h_coarsest[i] == 0) hats.push_back(i);
+    long long nv = 1;
+    int m0[3] = {1, 1, 1};
+    for (int a = 0; a < dim; ++a) {
+      m0[a] = op->C[a] + 1;
+      nv *= m0[a];
     }
-    L.nblk = (int)blocks.size();
-    // gather lists: per DOF its block entries in block order
-    std::vector<long long> gioff(N + 1, 0);
-    for (long long d : bdof) ++gioff[d + 1];
-    for (long long i = 0; i < N; ++i) gioff[i + 1] += gioff[i];
-    std::vector<long long> gibase(bdof.size()), fill(gioff.begin(), gioff.end() - 1);
-    for (size_t e = 0; e < bdof.size(); ++e) gibase[fill[bdof[e]]++] = (long long)e;
-    std::vector<int> gistride(bdof.size(), 1);
-    L.mask = h->upload(mask);
-    L.boff = h->upload(boff);
-    L.bdof = h->upload(bdof.empty() ? std::vector<long long>(1, 0) : bdof);
-    L.binv_off = h->upload(binv_off);
-    L.binv = h->upload(binv.empty() ? std::vector<double>(1, 0.0) : binv);
-    L.gioff = h->upload(gioff);
-    L.gibase = h->upload(gibase.empty() ? std::vector<long long>(1, 0) : gibase);
-    L.gistride = h->upload(gistride.empty() ? std::vector<int>(1, 1) : gistride);
-    L.x = h->alloc<double>(N);
-    L.b = h->alloc<double>(N);
-    L.r = h->alloc<double>(N);
-    // omega: power method on M^{-1} A_l (host, full-length vectors)
-    if (l > 0) {
-      auto Av = [&](const std::vector<double>& v, std::vector<double>& out) {
-        for (long long r = 0; r < N; ++r) {
-          double t = 0.0;
-          if (mask[r])
-            for (long long e = A.ptr[r]; e < A.ptr[r + 1]; ++e) t += A.val[e] * v[A.col[e]];
-          out[r] = t;
-        }
-      };
-      auto Mv = [&](const std::vector<double>& v, std::vector<double>& out) {
-        std::fill(out.begin(), out.end(), 0.0);
-        for (size_t bi = 0; bi < blocks.size(); ++bi) {
-          const auto& b = blocks[bi];
-          const int m = (int)b.size();
-          const double* Bi = binv.data() + binv_off[bi];
-          for (int i = 0; i < m; ++i) {
-            double t = 0.0;
-            for (int j = 0; j < m; ++j) t += Bi[(size_t)i * m + j] * v[b[j]];
-            out[b[i]] += t;
-          }
-        }
-      };
-      std::vector<double> v((size_t)N, 0.0), av((size_t)N), w((size_t)N);
-      long long k = 0;
-      for (int f = 0; f < op->nf; ++f)
-        for (long long i = 0; i < M; ++i)
-          if (inl[i]) v[(size_t)(f * M + i)] = std::sin((double)(k++) + 1.0);
-      double lam = 0.0;
-      for (int it = 0; it < 40; ++it) {
-        Av(v, av);
-        Mv(av, w);
-        double num = 0.0, den = 0.0, nw = 0.0;
-        for (long long i = 0; i < N; ++i) {
-          num += av[i] * w[i];
-          den += v[i] * av[i];
-          nw += w[i] * w[i];
-        }
-        lam = num / den;
-        nw = std::sqrt(nw);
-        for (long long i = 0; i < N; ++i) v[i] = w[i] / nw;
+    if ((long long)hats.size() != nv)
+      throw Error(FCM_E_INVALID, "overlay hierarchy: the coarsest hp-level is not the base grid's hats");
+    for (long long v = 0; v < nv; ++v) {
+      const long long f = hats[v];
+      long long node = 0, stride = 1;
+      for (int a = 0; a < dim; ++a) {
+        node += (long long)(op->h_ft[3 * f + a] / 2) * stride;
+        stride *= m0[a];
       }
-      L.lambda = lam;
-      L.omega = std::min(omega_paper, 1.75 / lam);
+      if (node != v || op->h_ft[3 * f] % 2)
+        throw Error(FCM_E_INVALID, "overlay hierarchy: hats out of grid order");
+    }
+    // A on the hats (rows f nv + v)
+    std::vector<long long> pos(N, -1);
+    for (int f = 0; f < nf; ++f)
+      for (long long v = 0; v < nv; ++v) pos[f * M + hats[v]] = f * nv + v;
+    std::vector<std::map<long long, double>> rows(nf * nv);
+    for (long long r = 0; r < N; ++r) {
+      if (pos[r] < 0) continue;
+      for (long long e = A.ptr[r]; e < A.ptr[r + 1]; ++e)
+        if (pos[A.col[e]] >= 0) rows[pos[r]][pos[A.col[e]]] += A.val[e];
+    }
+    HostCsr Af = csr_from_rows(nf * nv, rows);
+    int cells[3] = {1, 1, 1};
+    for (int a = 0; a < dim; ++a) cells[a] = op->C[a];
+    bool first = true;
+    MlhpLevel* fine = &hp[0];
+    for (;;) {
+      int cm = 0;
+      for (int a = 0; a < dim; ++a) cm = std::max(cm, cells[a]);
+      if (cm <= opts->coarse_cells) break;
+      HostCsr P = q1_prolongation_host(dim, cells, nf);  // fine Q1 DOFs x coarse
+      int cc[3] = {1, 1, 1};
+      long long nvc = 1;
+      for (int a = 0; a < dim; ++a) {
+        cc[a] = (cells[a] + 1) / 2;
+        nvc *= cc[a] + 1;
+      }
+      const long long Nc = nf * nvc;
+      HostCsr Pt = csr_transpose(P, Nc);
+      HostCsr Ac = csr_mul(Pt, csr_mul(Af, P));
+      // transfers of the finer level: its rows are the hats' full-length
+      // DOFs on the first transfer
+      HostCsr Pf = P, Rf = Pt;
+      if (first) {
+        std::vector<std::map<long long, double>> prow(N), rrow(Nc);
+        for (int f = 0; f < nf; ++f)
+          for (long long v = 0; v < nv; ++v) {
+            const long long fr = f * nv + v, full = f * M + hats[v];
+            for (long long e = P.ptr[fr]; e < P.ptr[fr + 1]; ++e) prow[full][P.col[e]] += P.val[e];
+          }
+        for (long long r = 0; r < Nc; ++r)
+          for (long long e = Pt.ptr[r]; e < Pt.ptr[r + 1]; ++e) {
+            const long long fr = Pt.col[e];
+            rrow[r][(fr / nv) * M + hats[fr % nv]] += Pt.val[e];
+          }
+        Pf = csr_from_rows(N, prow);
+        Rf = csr_from_rows(Nc, rrow);
+      }
+      upload_csr(h, Pf, fine->pptr, fine->pcol, fine->pval);
+      upload_csr(h, Rf, fine->rptr, fine->rcol, fine->rval);
+      for (int a = 0; a < 3; ++a) cells[a] = cc[a];
+      q1.emplace_back();
+      MlhpLevel& Lq = q1.back();
+      Lq.q1 = true;
+      Lq.N = Nc;
+      Lq.ndofs = Nc;
+      upload_csr(h, Ac, Lq.aptr, Lq.acol, Lq.aval);
+      int cmn = 0;
+      for (int a = 0; a < dim; ++a) cmn = std::max(cmn, cells[a]);
+      const bool coarsest = cmn <= opts->coarse_cells;
+      std::vector<std::vector<long long>> blocks;
+      std::vector<long long> order(Nc);
+      for (long long i = 0; i < Nc; ++i) order[i] = i;
+      if (coarsest)
+        blocks.push_back(order);
+      else
+        blocks = q1_blocks(dim, cells, nf, patch);
+      std::vector<unsigned char> ones((size_t)Nc, 1);
+      mlhp_level_blocks(op, Lq, Ac, blocks, ones, omega_paper, coarsest, order);
+      Af = Ac;
+      nv = nvc;
+      first = false;
+      fine = &q1.back();
     }
   }
+  // levels, coarsest first: Q1 levels (coarse to fine), then hp-levels
+  op->lv.clear();
+  for (auto it = q1.rbegin(); it != q1.rend(); ++it) op->lv.push_back(*it);
+  for (auto& L : hp) op->lv.push_back(L);
   long long ybsize = 1;
-  for (int l = 0; l < nl; ++l) {
+  for (const MlhpLevel& L : op->lv) {
     long long e = 0;
-    CK(cudaMemcpyAsync(&e, op->lv[l].boff + op->lv[l].nblk, sizeof(long long),
-                       cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(&e, L.boff + L.nblk, sizeof(long long), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
     ybsize = std::max(ybsize, e);
   }

@@ -273,6 +273,10 @@ void launch_mlhp_vec(long long N, int mode, const unsigned char* mask, const dou
 fcm_status pcg_solve_lockstep(fcm_handle* const* hs, int n, double* const* x, double rtol,
                               int maxit, int prec, fcm_info* infos, bool graph);
 
+// y = A x for a CSR matrix (rows x any), one thread per row.
+void launch_csr_spmv(long long rows, const long long* ptr, const long long* col,
+                     const double* val, const double* x, double* y, cudaStream_t s);
+
 // DOF gather modes: out = sum | out = b - sum | out += w sum | out = w sum
 enum { GATHER_SET = 0, GATHER_RESID = 1, GATHER_ADD = 2, GATHER_SCALE = 3 };
 template <typename TV>

@@ -213,3 +213,33 @@ void launch_mlhp_vec(long long N, int mode, const unsigned char* mask, const dou
 }
 
 }  // namespace fcm
+
+// y = A x for a CSR matrix (the Q1 levels below an overlay mesh's base
+// grid and the transfers to them), one thread per row, entries summed in
+// column order.
+namespace fcm {
+namespace {
+
+__global__ void csr_spmv_kernel(long long rows, const long long* __restrict__ ptr,
+                                const long long* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ x,
+                                double* __restrict__ y) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+       r += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (long long e = ptr[r]; e < ptr[r + 1]; ++e) s = fma(val[e], x[col[e]], s);
+    y[r] = s;
+  }
+}
+
+}  // namespace
+
+void launch_csr_spmv(long long rows, const long long* ptr, const long long* col,
+                     const double* val, const double* x, double* y, cudaStream_t s) {
+  long long blocks = (rows + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  csr_spmv_kernel<<<(int)blocks, 256, 0, s>>>(rows, ptr, col, val, x, y);
+}
+
+}  // namespace fcm

@@ -77,7 +77,8 @@ def test_apply_is_symmetric(case):
 
 
 # ---------------------------------------------------------------------------
-# The hp-multigrid of overlay meshes (Sec. 3.2, Fig. hpmultigrid) against
+# The hp-multigrid of overlay meshes (Sec. 3.2, Fig. hpmultigrid; the Q1
+# h-levels of the Remark of Sec. 3.2 below the base grid) against
 # oracle.mlhp.MlhpHierarchy: level sizes exact, omega 1e-6, the V-cycle
 # within 1e-12 + 50 x the LU-inverse noise floor (energy norm), PCG
 # iteration counts +-1 and the oracle's true residual.
@@ -87,13 +88,20 @@ from oracle.mlhp import MlhpHierarchy  # noqa: E402
 from parity_helpers import Noise  # noqa: E402
 
 SOLVER_CASES = {
+    # hierarchies ending at the base grid (base cells <= coarse_cells)
     "circle4_p2_k3_patch": lambda: dict(fi.poisson2d_circle(cells=4, p=2), overlay_levels=3,
                                         smoother="patchwise"),
     "circle4_p3_k2_elem": lambda: dict(fi.poisson2d_circle(cells=4, p=3), overlay_levels=2,
                                        smoother="elementwise"),
-    "plate8_p2_k2_patch": lambda: dict(fi.perforated_plate(cells=8, p=2, overlay_levels=2),
-                                       coarse_cells=8, smoother="patchwise"),
     "sphere4_p1_k2_patch": lambda: fi.poisson3d_sphere_mlhp(cells=4, p=1, overlay_levels=2),
+    # Q1 h-levels below the base grid (Galerkin, ragged halving 10 -> 5 -> 3)
+    "circle8_p2_k2_patch": lambda: dict(fi.poisson2d_circle(cells=8, p=2), overlay_levels=2,
+                                        smoother="patchwise"),
+    "circle10_p2_k1_elem": lambda: dict(fi.poisson2d_circle(cells=10, p=2), overlay_levels=1,
+                                        smoother="elementwise"),
+    "plate8_p2_k2_patch": lambda: dict(fi.perforated_plate(cells=8, p=2, overlay_levels=2),
+                                       smoother="patchwise"),
+    "sphere6_p1_k1_patch": lambda: fi.poisson3d_sphere_mlhp(cells=6, p=1, overlay_levels=1),
 }
 
 
@@ -119,7 +127,7 @@ def test_hierarchy_levels(solver_case):
         assert info["ndofs"] == lv.N, (name, l)
         if l > 0:
             assert abs(info["omega"] - lv.omega) <= 1e-6 * lv.omega, (name, l, info, lv.omega)
-            assert info["n_blocks"] == sum(1 for b in lv.blocks if len(b)), (name, l)
+            assert info["n_blocks"] == sum(len(IDX) for IDX, _ in lv.groups), (name, l)
 
 
 def test_vcycle(solver_case):
