@@ -311,6 +311,76 @@ def run_batch(args, rank, world, local):
     b.close()
 
 
+def run_mlhp(args, rank, world, local):
+    """Overlay meshes (Sec. 2.2) with the hp-multigrid of Sec. 3.2 through
+    fcm_mlhp_op_*: the 3D sphere r = 0.3 on a C^3 base grid, p = 2, k
+    overlay levels toward the surface (k = 0: a uniform grid, where the
+    same path is the patchwise additive Schwarz smoother of Sec. 3.3.1);
+    FP64 PCG from x = 0 to RTOL, timed with CUDA events on the operator's
+    stream, L2 flushed between solves."""
+    import torch
+    from paper_2010_00881_gb300 import fcm as F
+    cells, k = args.cells or 16, args.overlays
+    if k > 0:
+        prob = fi.poisson3d_sphere_mlhp(cells=cells, p=2, overlay_levels=k)
+    else:
+        prob = dict(fi.poisson3d_sphere(cells=cells, p=2, radius=0.3), overlay_levels=0)
+    prob = dict(prob, smoother=args.smoother)
+    wl_name = f"poisson3d_sphere_mlhp_{cells}^3_p2_k{k}_{args.smoother}"
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    op = F.MlhpOperator(prob)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    op.prepare()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    N = op.ndofs
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    b = op.rhs()
+    x = torch.zeros(N, dtype=torch.float64, device=dev)
+
+    def timed(steps, fn):
+        ms = []
+        for _ in range(steps):
+            flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, out
+
+    for _ in range(args.warmup):
+        op.pcg(b, rtol=RTOL, maxit=MAXIT)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, (_, info) = timed(args.steps, lambda: op.pcg(b, rtol=RTOL, maxit=MAXIT))
+    ms_apply, _ = timed(max(args.steps, 5), lambda: op.apply(x))
+    ms_v, _ = timed(max(args.steps, 5), lambda: op.vcycle(b))
+    (tot,), (value,) = aggregate([sum(ms)], world, N, args.steps, dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC.replace("mixed-prec vs FP64", "FP64")
+            + " (overlay hp-multigrid path)",
+            "value": value, "unit": "DOFs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl_name, "ndofs": N, "rtol": RTOL,
+                       "l2": "256 MB flushed between solves",
+                       "setup_s": {"operator": t1 - t0, "hierarchy": t2 - t1}},
+            "iterations": info["iters"], "relres_true": info["relres_true"],
+            "levels": op.levels, "apply_ms": sum(ms_apply) / len(ms_apply),
+            "vcycle_ms": sum(ms_v) / len(ms_v)}))
+    op.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -319,14 +389,21 @@ def main():
     ap.add_argument("--impl", default="fcm", choices=["fcm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="sphere",
-                    choices=["sphere", "batch256", "elasticity64", "circle16", "popcorn"],
+                    choices=["sphere", "batch256", "elasticity64", "circle16", "popcorn",
+                             "mlhp"],
                     help="sphere: 32^3 p=3 sphere (default); batch256: independent instances; "
                          "elasticity64: 64^3 block with 64 voids, p = 2; circle16: 2D circle, "
-                         "16^2 cells, p = 2")
+                         "16^2 cells, p = 2; mlhp: sphere r = 0.3 on a --cells^3 base grid "
+                         "(default 16), p = 2, --overlays levels (0: patchwise blocks on a "
+                         "uniform grid)")
     ap.add_argument("--batch-n", type=int, default=256,
                     help="instances of the batch workload (the first n of the seeded 256)")
     ap.add_argument("--cells", type=int, default=0,
                     help="cells per axis of the popcorn workload (default 96)")
+    ap.add_argument("--overlays", type=int, default=1,
+                    help="overlay levels of the mlhp workload")
+    ap.add_argument("--smoother", default="patchwise", choices=["patchwise", "elementwise"],
+                    help="additive Schwarz blocks of the mlhp workload")
     ap.add_argument("--profile-run", action="store_true",
                     help="setup, W warm-up and K timed mixed solves only (for profilers)")
     args = ap.parse_args()
@@ -348,8 +425,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     fbuild.build()
-    if args.workload == "batch256":
-        run_batch(args, rank, world, local)
+    if args.workload in ("batch256", "mlhp"):
+        (run_batch if args.workload == "batch256" else run_mlhp)(args, rank, world, local)
         if world > 1:
             dist.destroy_process_group()
         return

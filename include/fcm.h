@@ -145,7 +145,9 @@ typedef struct {
 
 /* Solver options.  smoother: ELEMENTWISE additive Schwarz (Sec. 3.3.1), or
  * JACOBI, the pointwise comparison smoother of Sec. 4.1 (x += omega D^{-1} r,
- * D = diag(A_l); omega <= 0 selects 2/3); PATCHWISE is FCM_E_UNSUPPORTED.
+ * D = diag(A_l); omega <= 0 selects 2/3); PATCHWISE is FCM_E_UNSUPPORTED
+ * here (patchwise blocks run through fcm_mlhp_op_prepare, on uniform grids
+ * with grid->overlay_levels = 0).
  * For ELEMENTWISE omega <= 0 selects the paper's values (Sec. 3.3.2),
  * clamped per level to 1.75 / lambda_max(M^{-1} A) where that value would
  * break the stability condition rho(I - omega M^{-1} A) < 1.  n_pre, n_post:
@@ -330,6 +332,8 @@ fcm_status fcm_mlhp_restriction_1d(int p, int dk, int pos, double* S);
  *   blocks of the same kind); the coarsest level solved by its dense
  *   inverse.  The blocks and Q1 operators are assembled and inverted on the
  *   host at set-up; FCM_E_UNSUPPORTED when a block exceeds 6144 DOFs.
+ *   With grid->overlay_levels = 0 this is the uniform-grid hierarchy of
+ *   fcm_setup (p-levels, Q1 h-levels, coarse solve) with either block kind.
  * fcm_mlhp_op_level: per level (0 = coarsest) its DOFs, omega, number and
  *   largest size of its blocks.
  * fcm_mlhp_op_vcycle: z = V(r), Algorithm 1 with zero initial guess, every

@@ -4,13 +4,17 @@
 // every number of the discretisation and of the solve is computed by the
 // device kernels of setup_geom.cu, setup_levels.cu and ops.cu.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fcm_internal.h"
@@ -768,7 +772,8 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     throw Error(FCM_E_INVALID, "smoothing steps must be in [0, 64]");
   if (opts->coarse_cells < 1) throw Error(FCM_E_INVALID, "coarse_cells must be >= 1");
   if (opts->smoother == FCM_SMOOTHER_PATCHWISE)
-    throw Error(FCM_E_UNSUPPORTED, "patchwise additive Schwarz blocks are not implemented");
+    throw Error(FCM_E_UNSUPPORTED, "patchwise additive Schwarz blocks: use fcm_mlhp_op_prepare "
+                                  "(overlay_levels 0 on uniform grids)");
   if (opts->smoother != FCM_SMOOTHER_ELEMENTWISE && opts->smoother != FCM_SMOOTHER_JACOBI)
     throw Error(FCM_E_INVALID, "unknown smoother");
   if ((P.trunk || P.drop) && opts->smoother == FCM_SMOOTHER_JACOBI)
@@ -2711,21 +2716,59 @@ void host_spd_inverse(std::vector<double>& B, int n) {
       Lf[(size_t)i * n + j] = t / ljj;
     }
   }
-  // W = L^{-1} (lower), then B^{-1} = W^T W
-  std::vector<double> W((size_t)n * n, 0.0);
+  // W = L^{-1} (lower), held transposed (Wt[c][i] = W[i][c], rows contiguous
+  // in the summation index), then B^{-1} = W^T W
+  std::vector<double> Wt((size_t)n * n, 0.0);
   for (int c = 0; c < n; ++c) {
+    double* w = Wt.data() + (size_t)c * n;
     for (int i = c; i < n; ++i) {
+      const double* l = Lf.data() + (size_t)i * n;
       double t = i == c ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) t -= Lf[(size_t)i * n + k] * W[(size_t)k * n + c];
-      W[(size_t)i * n + c] = t / Lf[(size_t)i * n + i];
+      for (int k = c; k < i; ++k) t -= l[k] * w[k];
+      w[i] = t / l[i];
     }
   }
   for (int i = 0; i < n; ++i)
     for (int j = 0; j <= i; ++j) {
+      const double* wi = Wt.data() + (size_t)i * n;
+      const double* wj = Wt.data() + (size_t)j * n;
       double t = 0.0;
-      for (int k = i; k < n; ++k) t += W[(size_t)k * n + i] * W[(size_t)k * n + j];
+      for (int k = i; k < n; ++k) t += wi[k] * wj[k];
       B[(size_t)i * n + j] = B[(size_t)j * n + i] = t;
     }
+}
+
+// body(i) for i in [0, n) on up to hardware_concurrency host threads (each
+// index once; results must not depend on which thread runs it); the first
+// exception thrown is rethrown after all threads have joined.
+template <class F>
+void host_parallel_for(long long n, F&& body) {
+  int nt = (int)std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  if ((long long)nt > n) nt = (int)std::max(1LL, n);
+  std::atomic<long long> next(0);
+  std::exception_ptr err;
+  std::mutex mu;
+  auto work = [&]() {
+    for (;;) {
+      const long long i = next.fetch_add(1);
+      if (i >= n) return;
+      try {
+        body(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mu);
+        if (!err) err = std::current_exception();
+        next.store(n);
+        return;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  if (err) std::rethrow_exception(err);
 }
 
 // y = A x (full-length vectors) on the device.
@@ -2948,21 +2991,27 @@ void mlhp_level_blocks(fcm_mlhp_op* op, MlhpLevel& L, const HostCsr& A,
   Handle* h = op->h.get();
   const long long N = L.N;
   std::vector<long long> boff(1, 0), bdof, binv_off(1, 0);
-  std::vector<double> binv;
   for (const auto& b : blocks) {
     const int m = (int)b.size();
     if ((size_t)m * sizeof(double) > 48 * 1024)
       throw Error(FCM_E_UNSUPPORTED, "overlay Schwarz block of more than 6144 DOFs");
+    bdof.insert(bdof.end(), b.begin(), b.end());
+    boff.push_back((long long)bdof.size());
+    binv_off.push_back(binv_off.back() + (long long)m * m);
+    L.max_m = std::max(L.max_m, m);
+  }
+  // the blocks are independent: assembled and inverted on host threads,
+  // each written to its own slot
+  std::vector<double> binv((size_t)binv_off.back());
+  host_parallel_for((long long)blocks.size(), [&](long long bi) {
+    const auto& b = blocks[bi];
+    const int m = (int)b.size();
     std::vector<double> B((size_t)m * m);
     for (int i = 0; i < m; ++i)
       for (int j = 0; j < m; ++j) B[(size_t)i * m + j] = A.at(b[i], b[j]);
     host_spd_inverse(B, m);
-    binv.insert(binv.end(), B.begin(), B.end());
-    bdof.insert(bdof.end(), b.begin(), b.end());
-    boff.push_back((long long)bdof.size());
-    binv_off.push_back((long long)binv.size());
-    L.max_m = std::max(L.max_m, m);
-  }
+    std::copy(B.begin(), B.end(), binv.begin() + binv_off[bi]);
+  });
   L.nblk = (int)blocks.size();
   std::vector<long long> gioff(N + 1, 0);
   for (long long d : bdof) ++gioff[d + 1];
@@ -2992,18 +3041,22 @@ void mlhp_level_blocks(fcm_mlhp_op* op, MlhpLevel& L, const HostCsr& A,
       out[r] = t;
     }
   };
+  // block products on host threads, then summed per DOF in block order
+  std::vector<double> yb(bdof.size());
   auto Mv = [&](const std::vector<double>& v, std::vector<double>& out) {
-    std::fill(out.begin(), out.end(), 0.0);
-    for (size_t bi = 0; bi < blocks.size(); ++bi) {
+    host_parallel_for((long long)blocks.size(), [&](long long bi) {
       const auto& b = blocks[bi];
       const int m = (int)b.size();
       const double* Bi = binv.data() + binv_off[bi];
+      double* y = yb.data() + boff[bi];
       for (int i = 0; i < m; ++i) {
         double t = 0.0;
         for (int j = 0; j < m; ++j) t += Bi[(size_t)i * m + j] * v[b[j]];
-        out[b[i]] += t;
+        y[i] = t;
       }
-    }
+    });
+    std::fill(out.begin(), out.end(), 0.0);
+    for (size_t e = 0; e < bdof.size(); ++e) out[bdof[e]] += yb[e];
   };
   std::vector<double> v((size_t)N, 0.0), av((size_t)N), w((size_t)N);
   for (size_t k = 0; k < order.size(); ++k) v[(size_t)order[k]] = std::sin((double)k + 1.0);

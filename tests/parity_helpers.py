@@ -6,13 +6,15 @@ use the oracle only).
 * Noise: the oracle's V-cycle and smoothers with every block inverse taken
   from an LU factorisation instead of Cholesky, the noise floor of two
   backward-stable FP64 computations of the same ill-conditioned operators.
+* uniform_index: the uniform-grid number of every function of an
+  overlay-free multi-level hp space.
 """
 import numpy as np
 import scipy.sparse as sp
 
 from oracle.assembly import nfields, shape_functions
 from oracle.geometry import INSIDE, OUTSIDE, classify_box
-from oracle.grid import all_cells, cell_box, cell_dofs, ndofs
+from oracle.grid import all_cells, cell_box, cell_dofs, m_1d, ndofs
 from oracle.quadrature import cell_rules, leaf_rule
 
 
@@ -98,3 +100,26 @@ class Noise:
             return self.H.levels[l].smoother(x)
         finally:
             self._swap()
+
+
+def uniform_index(space):
+    """Uniform-grid scalar index of every function of an overlay-free
+    multi-level hp space (oracle.mlhp.MlhpSpace): vertex hats first on the
+    (C + 1)-lattice, then per axis the edge modes of degree q grouped by q,
+    as oracle.grid numbers the 1D functions."""
+    mesh, p = space.mesh, space.p
+    C = mesh.cells
+    out = []
+    for k, t, qs in space.funcs:
+        assert k == 0
+        g, stride, qi = 0, 1, 0
+        for a in range(mesh.dim):
+            if t[a] % 2 == 0:
+                i = t[a] // 2
+            else:
+                i = (C[a] + 1) + (qs[qi] - 2) * C[a] + (t[a] - 1) // 2
+                qi += 1
+            g += i * stride
+            stride *= m_1d(C[a], p)
+        out.append(g)
+    return np.array(out)

@@ -11,6 +11,9 @@ FP64 bar.  Cases: 2D Poisson with three overlays on a cut circle, the 3D
 sphere with two overlays (p = 2), the elastic perforated plate (box-face
 Dirichlet and traction terms on refined leaves), a 3D elastic block with
 voids and one overlay, and a hole (complement domain) with two overlays.
+
+Without overlays the same path is the patchwise additive Schwarz smoother
+on uniform grids, checked against the uniform oracle hierarchy as well.
 """
 import numpy as np
 import pytest
@@ -102,7 +105,15 @@ SOLVER_CASES = {
     "plate8_p2_k2_patch": lambda: dict(fi.perforated_plate(cells=8, p=2, overlay_levels=2),
                                        smoother="patchwise"),
     "sphere6_p1_k1_patch": lambda: fi.poisson3d_sphere_mlhp(cells=6, p=1, overlay_levels=1),
+    # no overlays: patchwise blocks on uniform grids (12 -> 6 -> 3 Q1 levels)
+    "circle8_p3_k0_patch": lambda: dict(fi.poisson2d_circle(cells=8, p=3), overlay_levels=0,
+                                        smoother="patchwise"),
+    "circle12_p2_k0_patch": lambda: dict(fi.poisson2d_circle(cells=12, p=2), overlay_levels=0,
+                                         smoother="patchwise"),
+    "sphere4_p2_k0_patch": lambda: dict(fi.poisson3d_sphere(cells=4, p=2, radius=0.3),
+                                        overlay_levels=0, smoother="patchwise"),
 }
+UNIFORM_CASES = [k for k in SOLVER_CASES if "_k0_" in k]
 
 
 @pytest.fixture(scope="module", params=list(SOLVER_CASES))
@@ -149,3 +160,45 @@ def test_pcg(solver_case):
     assert info["relres_true"] <= 1e-8
     assert np.linalg.norm(H.b - H.A @ x) / np.linalg.norm(H.b) <= 1.01e-8
     assert abs(info["iters"] - ko) <= 1, (name, info["iters"], ko)
+
+
+@pytest.mark.parametrize("name", UNIFORM_CASES)
+def test_uniform_grid_patchwise_equals_uniform_hierarchy(name):
+    """Without overlays the device's hp-multigrid is the uniform-grid
+    hierarchy of Sec. 3.1 with the patchwise blocks of Sec. 3.3.1: its
+    V-cycle equals the uniform oracle's (oracle.multigrid.Hierarchy, grid
+    numbering, the omega per level taken from the device, whose power-method
+    start vector follows the overlay numbering) within 1e-12 + 50 x the
+    LU-inverse noise floor, and PCG takes the uniform oracle's iteration
+    count +-1."""
+    from oracle.mlhp import MlhpSpace, mesh_for
+    from oracle.multigrid import Hierarchy
+    from parity_helpers import uniform_index
+    prob = SOLVER_CASES[name]()
+    U = Hierarchy(prob)
+    op = F.MlhpOperator(prob)
+    try:
+        op.prepare()
+        assert [info["ndofs"] for info in op.levels] == [lv.N for lv in U.levels]
+        for info, lv in zip(op.levels[1:], U.levels[1:]):
+            assert abs(info["omega"] - lv.omega) <= 0.03 * lv.omega
+            lv.omega = info["omega"]
+        perm = uniform_index(MlhpSpace(mesh_for(prob), prob["p"], 1))
+        r = fi.random_vector(op.ndofs, seed=2)
+        ru = np.zeros_like(r)
+        ru[perm] = r
+        z = np.zeros_like(r)
+        z[perm] = op.vcycle(torch.from_numpy(r).cuda()).cpu().numpy()
+        zu = U.vcycle(ru)
+        bar = 1e-12 + 50.0 * _rel_a(U.A, Noise(U).vcycle(ru), zu)
+        err = _rel_a(U.A, z, zu)
+        print(f"uniform patchwise V-cycle {name}: {err:.2e} (bar {bar:.2e})")
+        assert err <= bar, (name, err, bar)
+        _, ku, _ = mg.pcg(U.A, U.b, U.vcycle, rtol=1e-8)
+        x, info = op.pcg(rtol=1e-8)
+        assert abs(info["iters"] - ku) <= 1, (name, info["iters"], ku)
+        xu = np.zeros_like(r)
+        xu[perm] = x.cpu().numpy()
+        assert np.linalg.norm(U.b - U.A @ xu) / np.linalg.norm(U.b) <= 1.01e-8
+    finally:
+        op.close()
