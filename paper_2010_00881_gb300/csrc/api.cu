@@ -2447,7 +2447,8 @@ struct MlhpLevel {
   // rows) and P (this level's rows), CSR; otherwise the coarser level's mask
   long long *rptr = nullptr, *rcol = nullptr, *pptr = nullptr, *pcol = nullptr;
   double *rval = nullptr, *pval = nullptr;
-  int nblk = 0, max_m = 0;
+  int nblk = 0, max_m = 0, nitem = 0;
+  int2* items = nullptr;          // row tiles of the blocks (launch_leaf_apply)
   long long* boff = nullptr;      // block DOF-list offsets
   long long* bdof = nullptr;      // block DOFs (global, field-major)
   long long* binv_off = nullptr;  // inverse offsets
@@ -2462,7 +2463,8 @@ struct MlhpLevel {
 struct fcm_mlhp_op {
   std::unique_ptr<fcm_handle> h;  // problem data, stream and device memory
   long long M = 0;                // scalar functions
-  int nf = 1, nleaf = 0, max_nl = 0;
+  int nf = 1, nleaf = 0, max_nl = 0, nitem = 0;
+  int2* items = nullptr;          // row tiles of the leaves (launch_leaf_apply)
   int dim = 0, C[3] = {1, 1, 1};
   // host copies kept for the hierarchy: leaf incidences, leaf matrix
   // offsets, patches and the hp-level of every function
@@ -2492,6 +2494,26 @@ struct fcm_mlhp_op {
 };
 
 namespace {
+
+// Work items of launch_leaf_apply for leaves (or blocks) with DOF-list
+// offsets off (nf fields each): (leaf, first row) for every kLeafRows rows,
+// flattened as int pairs.
+std::vector<int> leaf_row_tiles(const std::vector<long long>& off, int nf) {
+  std::vector<int> items;
+  for (size_t l = 0; l + 1 < off.size(); ++l) {
+    const long long nl = nf * (off[l + 1] - off[l]);
+    for (long long r0 = 0; r0 < nl; r0 += kLeafRows) {
+      items.push_back((int)l);
+      items.push_back((int)r0);
+    }
+  }
+  return items;
+}
+
+int2* upload_items(Handle* h, const std::vector<int>& items, int* nitem) {
+  *nitem = (int)(items.size() / 2);
+  return reinterpret_cast<int2*>(h->upload(items.empty() ? std::vector<int>(2, 0) : items));
+}
 
 void mlhp_op_build(fcm_mlhp_op* op, const fcm_mlhp* m, const fcm_grid* grid,
                    const fcm_geometry* geom, const fcm_physics* phys) {
@@ -2596,6 +2618,7 @@ void mlhp_op_build(fcm_mlhp_op* op, const fcm_mlhp* m, const fcm_grid* grid,
     woff[l + 1] = woff[l] + (long long)n * nl;
   }
   op->off = h->upload(loff);
+  op->items = upload_items(h, leaf_row_tiles(loff, nf), &op->nitem);
   op->fn = h->upload(lfn);
   op->koff = h->upload(koff);
   op->KL = h->alloc<double>((size_t)std::max(1LL, koff[L]));
@@ -2774,8 +2797,8 @@ void host_parallel_for(long long n, F&& body) {
 // y = A x (full-length vectors) on the device.
 void mlhp_apply_dev(fcm_mlhp_op* op, const double* x, double* y) {
   Handle* h = op->h.get();
-  launch_leaf_apply(op->nleaf, op->nf, op->M, op->max_nl, op->off, op->fn, op->koff, op->KL, x,
-                    op->Yl, h->s);
+  launch_leaf_apply(op->nitem, op->items, op->nf, op->M, op->max_nl, op->off, op->fn, op->koff,
+                    op->KL, x, op->Yl, h->s);
   launch_leaf_gather(op->M, op->nf, op->ioff, op->ibase, op->istride, op->Yl, y, h->s);
   CKL();
 }
@@ -2783,7 +2806,8 @@ void mlhp_apply_dev(fcm_mlhp_op* op, const double* x, double* y) {
 // z = sum of the level's block inverses applied to r (all N entries written).
 void mlhp_smooth_dev(fcm_mlhp_op* op, const MlhpLevel& L, const double* r, double* z) {
   Handle* h = op->h.get();
-  launch_leaf_apply(L.nblk, 1, L.N, L.max_m, L.boff, L.bdof, L.binv_off, L.binv, r, op->Yb, h->s);
+  launch_leaf_apply(L.nitem, L.items, 1, L.N, L.max_m, L.boff, L.bdof, L.binv_off, L.binv, r,
+                    op->Yb, h->s);
   launch_leaf_gather(L.N, 1, L.gioff, L.gibase, L.gistride, op->Yb, z, h->s);
   CKL();
 }
@@ -3021,6 +3045,7 @@ void mlhp_level_blocks(fcm_mlhp_op* op, MlhpLevel& L, const HostCsr& A,
   std::vector<int> gistride(bdof.size(), 1);
   L.mask = h->upload(mask);
   L.boff = h->upload(boff);
+  L.items = upload_items(h, leaf_row_tiles(boff, 1), &L.nitem);
   L.bdof = h->upload(bdof.empty() ? std::vector<long long>(1, 0) : bdof);
   L.binv_off = h->upload(binv_off);
   L.binv = h->upload(binv.empty() ? std::vector<double>(1, 0.0) : binv);
@@ -3357,10 +3382,7 @@ fcm_status fcm_mlhp_op_apply(fcm_mlhp_op* op, const double* x_dev, double* y_dev
   return guarded([&]() {
     Handle* h = op->h.get();
     CallScope cs(h);
-    launch_leaf_apply(op->nleaf, op->nf, op->M, op->max_nl, op->off, op->fn, op->koff, op->KL,
-                      x_dev, op->Yl, h->s);
-    launch_leaf_gather(op->M, op->nf, op->ioff, op->ibase, op->istride, op->Yl, y_dev, h->s);
-    CKL();
+    mlhp_apply_dev(op, x_dev, y_dev);
     cs.finish();
     return FCM_OK;
   });

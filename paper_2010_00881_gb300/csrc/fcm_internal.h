@@ -246,9 +246,12 @@ void launch_leaf_transform(int nleaf, int dim, int P1, int nf, const long long* 
                            const void* inc, const double* S, const double* Kbox,
                            const double* bbox, const long long* koff, const long long* woff,
                            double* W, double* KL, double* bL, cudaStream_t s);
-void launch_leaf_apply(int nleaf, int nf, long long M, int max_nl, const long long* off,
-                       const long long* fn, const long long* koff, const double* KL,
-                       const double* x, double* Yl, cudaStream_t s);
+// Rows per work item of launch_leaf_apply (its block size): items are
+// (leaf or block, first row), one per kLeafRows rows of each leaf.
+constexpr int kLeafRows = 128;
+void launch_leaf_apply(int nitem, const int2* items, int nf, long long M, int max_nl,
+                       const long long* off, const long long* fn, const long long* koff,
+                       const double* KL, const double* x, double* Yl, cudaStream_t s);
 void launch_leaf_gather(long long M, int nf, const long long* ioff, const long long* ibase,
                         const int* istride, const double* Yl, double* out, cudaStream_t s);
 

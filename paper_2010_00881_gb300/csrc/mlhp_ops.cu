@@ -97,31 +97,42 @@ __global__ void leaf_transform_kernel(int nleaf, int dim, int P1, int nf,
   }
 }
 
-// y_L = K_L x_L per leaf (x_L gathered through the leaf's function list,
-// field-major DOFs f M + id); K_L is symmetric, so thread r reads column r
-// (row c, consecutive across threads).
-__global__ void __launch_bounds__(128) leaf_apply_kernel(int nleaf, int nf, long long M,
-                                                         const long long* __restrict__ off,
-                                                         const long long* __restrict__ fn,
-                                                         const long long* __restrict__ koff,
-                                                         const double* __restrict__ KL,
-                                                         const double* __restrict__ x,
-                                                         double* __restrict__ Yl) {
+// y_L = K_L x_L, one row tile per work item: item (l, r0) computes rows
+// r0 .. r0 + kLeafRows - 1 of leaf l (x_L gathered through the leaf's
+// function list, field-major DOFs f M + id), so a large block spreads over
+// several SMs.  K_L is symmetric, so thread r reads column r (row c,
+// consecutive across threads); four partial sums over c = 0, 1, 2, 3 mod 4
+// keep four loads in flight per thread and are added in a fixed order.
+__global__ void __launch_bounds__(kLeafRows) leaf_apply_kernel(
+    int nitem, const int2* __restrict__ items, int nf, long long M,
+    const long long* __restrict__ off, const long long* __restrict__ fn,
+    const long long* __restrict__ koff, const double* __restrict__ KL,
+    const double* __restrict__ x, double* __restrict__ Yl) {
   extern __shared__ double xs[];
-  for (int l = blockIdx.x; l < nleaf; l += gridDim.x) {
-    const long long i0 = off[l];
-    const int nfun = (int)(off[l + 1] - i0);
+  for (int w = blockIdx.x; w < nitem; w += gridDim.x) {
+    const int2 it = items[w];
+    const long long i0 = off[it.x];
+    const int nfun = (int)(off[it.x + 1] - i0);
     const int nl = nf * nfun;
     for (int c = threadIdx.x; c < nl; c += blockDim.x) {
       const int f = c / nfun, i = c % nfun;
       xs[c] = x[f * M + fn[i0 + i]];
     }
     __syncthreads();
-    const double* Kl = KL + koff[l];
-    for (int r = threadIdx.x; r < nl; r += blockDim.x) {
-      double s = 0.0;
-      for (int c = 0; c < nl; ++c) s = fma(Kl[(size_t)c * nl + r], xs[c], s);
-      Yl[nf * i0 + r] = s;
+    const double* Kl = KL + koff[it.x];
+    const int r = it.y + (int)threadIdx.x;
+    if (r < nl) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      const double* k = Kl + r;
+      int c = 0;
+      for (; c + 4 <= nl; c += 4) {
+        s0 = fma(k[(size_t)c * nl], xs[c], s0);
+        s1 = fma(k[(size_t)(c + 1) * nl], xs[c + 1], s1);
+        s2 = fma(k[(size_t)(c + 2) * nl], xs[c + 2], s2);
+        s3 = fma(k[(size_t)(c + 3) * nl], xs[c + 3], s3);
+      }
+      for (; c < nl; ++c) s0 = fma(k[(size_t)c * nl], xs[c], s0);
+      Yl[nf * i0 + r] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
   }
@@ -158,13 +169,13 @@ void launch_leaf_transform(int nleaf, int dim, int P1, int nf, const long long* 
                                             woff, W, KL, bL);
 }
 
-void launch_leaf_apply(int nleaf, int nf, long long M, int max_nl, const long long* off,
-                       const long long* fn, const long long* koff, const double* KL,
-                       const double* x, double* Yl, cudaStream_t s) {
-  if (nleaf == 0) return;
-  const int grid = nleaf < 8192 ? nleaf : 8192;
-  leaf_apply_kernel<<<grid, 128, (size_t)max_nl * sizeof(double), s>>>(nleaf, nf, M, off, fn,
-                                                                       koff, KL, x, Yl);
+void launch_leaf_apply(int nitem, const int2* items, int nf, long long M, int max_nl,
+                       const long long* off, const long long* fn, const long long* koff,
+                       const double* KL, const double* x, double* Yl, cudaStream_t s) {
+  if (nitem == 0) return;
+  const int grid = nitem < 16384 ? nitem : 16384;
+  leaf_apply_kernel<<<grid, kLeafRows, (size_t)max_nl * sizeof(double), s>>>(
+      nitem, items, nf, M, off, fn, koff, KL, x, Yl);
 }
 
 void launch_leaf_gather(long long M, int nf, const long long* ioff, const long long* ibase,
