@@ -573,6 +573,8 @@ def main():
             "speedup_mixed_vs_fp64": value / value64,
             "vcycles_per_s": (inf_mixed[-1]["iters"] + 1) * args.steps / (tot / 1e3),
             "setup_ms": inf_mixed[-1]["setup_ms"],
+            "setup_phases_ms": dict(zip(("geometry", "levels", "coarse", "smoothers",
+                                         "graphs"), inf_mixed[-1]["setup_phase_ms"])),
             "e2e": {"value": value_e2e, "unit": "DOFs/s", "h2d_bytes_per_step": 8 * N,
                     "d2h_bytes_per_step": 8 * N},
             "gpu_launches": int(sum(i["kernel_launches"] for i in inf_mixed)),

@@ -175,6 +175,13 @@ typedef struct {
                                 per-kernel byte model of fcm_op_bytes), summed over the
                                 launches made; divided by solve_ms, the solve's
                                 effective bandwidth */
+  double setup_phase_ms[5];  /* fcm_setup by phase, timed by CUDA events on the handle's
+                                stream (host work between launches included): [0] geometry
+                                (classification, space-tree integration of the cut cells,
+                                load), [1] level hierarchy (p-levels, Galerkin h-levels),
+                                [2] coarse factorisation, [3] smoothers (block
+                                factorisation and inversion, omega estimates), [4] V-cycle
+                                graph capture; zero for handles not made by fcm_setup */
 } fcm_info;
 
 /* Per-level description (test and benchmark introspection). */

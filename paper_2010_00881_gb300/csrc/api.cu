@@ -118,6 +118,11 @@ struct fcm_handle {
   int smoother = FCM_SMOOTHER_ELEMENTWISE;
   bool mixed = false;
   double setup_ms = 0.0;
+  // fcm_setup phases: events recorded on s at the phase boundaries, the
+  // durations read once the setup has synchronised
+  static constexpr int kSetupPhases = 5;
+  cudaEvent_t phase_ev[kSetupPhases + 1] = {};
+  double phase_ms[kSetupPhases] = {};
   std::vector<signed char> cls;
   double* b = nullptr;             // assembled load (top)
   // CG work (FP64)
@@ -171,6 +176,8 @@ struct fcm_handle {
     if (ev_out) cudaEventDestroy(ev_out);
     if (side.fork) cudaEventDestroy(side.fork);
     if (side.join) cudaEventDestroy(side.join);
+    for (cudaEvent_t e : phase_ev)
+      if (e) cudaEventDestroy(e);
     if (side.s2) cudaStreamDestroy(side.s2);
     if (s) cudaStreamDestroy(s);
   }
@@ -1248,6 +1255,12 @@ void estimate_omega(Handle* h, Level& L, double omega_paper) {
   L.omega = std::min(omega_paper, 1.75 / lam);
 }
 
+// Boundary k of the setup phases (fcm_info.setup_phase_ms); never called
+// while the stream is capturing.
+void phase_mark(Handle* h, int k) {
+  if (h->phase_ev[k]) CK(cudaEventRecord(h->phase_ev[k], h->s));
+}
+
 void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
                 const fcm_physics* phys, const fcm_solver_opts* opts) {
   build_problem(h, grid, geom, phys, opts);
@@ -1257,6 +1270,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   const int ncell = gt.ncells, n = gt.nloc;
 
   g_stage = "classification";
+  phase_mark(h, 0);
   double* gauss = h->alloc<double>(2 * (p + 1));
   launch_gauss_table(p + 1, gauss, h->s);
   signed char* d_cls = h->alloc<signed char>(ncell);
@@ -1326,6 +1340,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   CKL();
 
   g_stage = "level hierarchy";
+  phase_mark(h, 1);
   // ---- level hierarchy, finest first
   std::vector<Level> lv;
   {
@@ -1379,6 +1394,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
   if (P.trunk || P.drop) build_keep_masks(h);
 
   g_stage = "coarse factorisation";
+  phase_mark(h, 2);
   // coarsest level: dense matrix, Cholesky, factor inverse
   {
     Level& L0 = h->levels[0];
@@ -1416,6 +1432,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     CKL();
     check_status(h, d_info, 1, "coarsest level");
   }
+  phase_mark(h, 3);
   // CG work
   h->cx = h->alloc<double>(gt.N);
   h->cb = h->alloc<double>(gt.N);
@@ -1444,6 +1461,7 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     g_stage = "omega estimate";
     estimate_omega(h, L, omega_paper);
   }
+  phase_mark(h, 4);
   CK(cudaStreamSynchronize(h->s));
   check_timeout(h);
   g_stage = "graph capture";
@@ -1461,7 +1479,14 @@ void setup_impl(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     h->g_vc32 = capture_vcycle<float>(h, &h->vc_nodes32, h->top64);
     h->vc_bytes32 = vcycle_bytes(h, top, h->top64, top >= h->top64);
   }
+  phase_mark(h, 5);
   CK(cudaStreamSynchronize(h->s));
+  if (h->phase_ev[0])
+    for (int k = 0; k < Handle::kSetupPhases; ++k) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, h->phase_ev[k], h->phase_ev[k + 1]));
+      h->phase_ms[k] = ms;
+    }
 }
 
 // z = V(r) on the finest level in the requested precision (r, z FP64).
@@ -1557,6 +1582,7 @@ void pcg_begin(PcgRun& R, Handle* h, const double* b_in, double* x, double rtol,
   std::memset(&R.inf, 0, sizeof(R.inf));
   R.inf.ndofs = N;
   R.inf.setup_ms = h->setup_ms;
+  for (int k = 0; k < Handle::kSetupPhases; ++k) R.inf.setup_phase_ms[k] = h->phase_ms[k];
   if (R.nb == 0.0) {
     R.st = FCM_OK;
     R.done = true;
@@ -2022,6 +2048,7 @@ fcm_status mg_impl(Handle* h, const double* b_in, double* x, double rtol, int ma
   std::memset(&inf, 0, sizeof(inf));
   inf.ndofs = N;
   inf.setup_ms = h->setup_ms;
+  for (int k = 0; k < Handle::kSetupPhases; ++k) inf.setup_phase_ms[k] = h->phase_ms[k];
   double nr = nb;
   int k = 0;
   fcm_status st = FCM_OK;
@@ -2098,6 +2125,7 @@ fcm_status fcm_setup(const fcm_grid* grid, const fcm_geometry* geom, const fcm_p
     CK(cudaStreamCreateWithFlags(&h->side.s2, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->side.fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->side.join, cudaEventDisableTiming));
+    for (cudaEvent_t& e : h->phase_ev) CK(cudaEventCreate(&e));
     CallScope cs(h.get());
     setup_impl(h.get(), grid, geom, phys, opts);
     cs.finish();

@@ -69,10 +69,13 @@ class fcm_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("relres_recursive", C.c_double),
                 ("relres_true", C.c_double), ("setup_ms", C.c_double),
                 ("solve_ms", C.c_double), ("ndofs", C.c_longlong),
-                ("kernel_launches", C.c_longlong), ("bytes_moved_est", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("bytes_moved_est", C.c_longlong),
+                ("setup_phase_ms", C.c_double * 5)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["setup_phase_ms"] = list(self.setup_phase_ms)
+        return d
 
 
 class fcm_level_info(C.Structure):

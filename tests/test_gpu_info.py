@@ -6,7 +6,8 @@ same amount every time: the increments between solves stopped after k,
 k + 1 and k + 2 iterations are equal.  Each iteration runs one V-cycle
 (n_pre + n_post smoothing steps on every level >= 1) and one FP64 operator
 apply, so its bytes are at least those of the finest level's cell
-operations in those steps (fcm_op_bytes).
+operations in those steps (fcm_op_bytes).  The set-up phases add up within
+the set-up's wall time.
 """
 import pytest
 
@@ -55,3 +56,14 @@ def test_bytes_of_a_converged_solve(solver):
     assert info["bytes_moved_est"] > 0
     print(f"bytes per solve {info['bytes_moved_est'] / 1e9:.3f} GB, "
           f"{info['bytes_moved_est'] / (info['solve_ms'] * 1e-3) / 1e9:.0f} GB/s (host clock)")
+
+
+def test_setup_phases_add_up_within_the_setup_time(solver):
+    """fcm_info.setup_phase_ms: five non-negative phase durations (CUDA
+    events on the handle's stream) that together stay within the wall time
+    of fcm_setup, the geometry phase (space-tree integration) non-zero."""
+    _, info = solver.pcg(rtol=1e-8)
+    ph = info["setup_phase_ms"]
+    assert len(ph) == 5 and min(ph) >= 0.0
+    assert ph[0] > 0.0
+    assert sum(ph) <= info["setup_ms"] * 1.001 + 0.05
