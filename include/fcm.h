@@ -127,7 +127,13 @@ typedef struct {
  * dirichlet: LEVELSET (penalty on {psi = 0}) or FACES (bit 2a+s of
  * dirichlet_faces: face of axis a, lower s = 0 / upper s = 1); g selects
  * g_D.  traction_face (-1: none) carries the constant traction vector.
- * quad_depth: space-tree depth on cut cells (0..4). */
+ * quad_depth: space-tree depth on cut cells (0..4).  quadrature: how the
+ * cell matrices are summed on each space-tree leaf (the same Gauss points
+ * either way, results equal up to rounding): FCM_QUAD_POINTS (0) point by
+ * point; FCM_QUAD_SUMFACT (1) by sum factorisation over the leaf's tensor
+ * grid of points, one axis at a time (leaves of at most 128 points, i.e.
+ * p <= 4 in 3D; others point by point). */
+enum { FCM_QUAD_POINTS = 0, FCM_QUAD_SUMFACT = 1 };
 typedef struct {
   int pde;
   double kappa, E, nu;
@@ -141,6 +147,7 @@ typedef struct {
   int traction_face;
   double traction[3];
   int quad_depth;
+  int quadrature;
 } fcm_physics;
 
 /* Solver options.  smoother: ELEMENTWISE additive Schwarz (Sec. 3.3.1), or

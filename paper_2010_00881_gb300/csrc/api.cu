@@ -775,6 +775,9 @@ void build_problem(Handle* h, const fcm_grid* grid, const fcm_geometry* geom,
     throw Error(FCM_E_INVALID, "quad_depth must be in [0, 4]");
   if (P.dim == 3 && P.quad_depth > 3)
     throw Error(FCM_E_UNSUPPORTED, "quad_depth > 3 in 3D");
+  if (phys->quadrature != FCM_QUAD_POINTS && phys->quadrature != FCM_QUAD_SUMFACT)
+    throw Error(FCM_E_INVALID, "quadrature must be FCM_QUAD_POINTS or FCM_QUAD_SUMFACT");
+  P.sumfact = phys->quadrature == FCM_QUAD_SUMFACT ? 1 : 0;
   if (opts->n_pre < 0 || opts->n_post < 0 || opts->n_pre > 64 || opts->n_post > 64)
     throw Error(FCM_E_INVALID, "smoothing steps must be in [0, 64]");
   if (opts->coarse_cells < 1) throw Error(FCM_E_INVALID, "coarse_cells must be >= 1");

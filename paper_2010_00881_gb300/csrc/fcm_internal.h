@@ -101,6 +101,7 @@ struct Problem {
   int traction_face;
   double traction[3];
   int quad_depth;
+  int sumfact;                  // 1: leaf sums by sum factorisation (FCM_QUAD_SUMFACT)
   int trunk;                    // 1: trunk-space elements (non-trunk modes removed)
   int drop;                     // 1: fully fictitious cells removed
 };

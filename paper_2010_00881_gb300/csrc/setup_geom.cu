@@ -6,6 +6,7 @@
 // values at corners, lattice points and quadrature points) is computed with
 // separately rounded multiplies and adds in a fixed order, so the decisions
 // are reproducible by any IEEE-754 implementation of the same formulas.
+#include <algorithm>
 #include <cmath>
 
 #include "fcm_internal.h"
@@ -275,6 +276,116 @@ __device__ void accumulate_elastic(const PointBatch& B, int np, int dim, int P1,
   }
 }
 
+// Sum factorisation of the leaf sums (FCM_QUAD_SUMFACT).  The points of a
+// leaf are its tensor grid q = q0 + P q1 + P^2 q2 (P = p + 1 per axis, x
+// fastest) with weights W_q = B.w[q], so every product of 1D factors in the
+// pair sums contracts one axis at a time:
+//   Z[v][q0 + P q1][i2, j2] = sum_q2 W_q A2(si, q2, i2) A2(sj, q2, j2),
+//   Y[u][q0][(i1, i2), (j1, j2)] = sum_q1 Z[..][q0 + P q1][i2, j2] A1(.., q1, i1) A1(.., q1, j1),
+//   K_IJ += sum_q0 Y[..][q0][(i1, i2), (j1, j2)] A0(.., q0, i0) A0(.., q0, j0),
+// with A_a(s, q, m) the mode m (s = 1: its derivative) at the axis-a
+// coordinate of the leaf's q-th Gauss point (read from B.T).  A 2D problem
+// has one point and one mode (value 1, derivative 0) on axis 2.  Poisson
+// needs Y for no derivative on axes 1 and 2 and for one derivative on either;
+// elasticity one Y per (f, g) for the integrals of d_f N_i d_g N_j.  Every
+// thread of the block calls this (it synchronises).
+__host__ __device__ inline int sf_doubles(int dim, int P, bool elastic) {
+  const int P2 = dim == 3 ? P : 1, M12 = P * P2;
+  return 6 * P * P + 4 * P * P * P2 * P2 + (elastic ? dim * dim : 2) * P * M12 * M12;
+}
+
+__device__ void sf_accumulate(const PointBatch& B, double* sfx, int dim, int P, int ns,
+                              bool elastic, double lam, double mu, double kappa, PairSet& ps) {
+  const int P2 = dim == 3 ? P : 1;  // points and modes on axis 2
+  const int M12 = P * P2;           // modes on axes 1 and 2: r = i1 + P i2
+  const int PP = P * P, Z2 = P2 * P2;
+  double* A = sfx;                  // [axis][s][q][m]: 3 x 2 x P x P
+  double* Z = A + 6 * PP;           // [v = si + 2 sj][q0 + P q1][i2 + P2 j2]
+  double* Y = Z + 4 * PP * Z2;      // [u][q0][r][c]
+  const int ny = P * M12 * M12;
+  for (int t = threadIdx.x; t < 6 * PP; t += blockDim.x) {
+    const int m = t % P, q = (t / P) % P, sd = (t / PP) % 2, a = t / (2 * PP);
+    double v;
+    if (a < dim)
+      v = B.T[a == 0 ? q : (a == 1 ? q * P : q * PP)][a][sd][m];
+    else
+      v = (sd == 0 && q == 0 && m == 0) ? 1.0 : 0.0;
+    A[t] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 4 * PP * Z2; t += blockDim.x) {
+    const int e = t % Z2, q01 = (t / Z2) % PP, v = t / (Z2 * PP);
+    const int i2 = e % P2, j2 = e / P2;
+    const double* ai = A + (4 + (v & 1)) * PP;
+    const double* aj = A + (4 + (v >> 1)) * PP;
+    double z = 0.0;
+    for (int q2 = 0; q2 < P2; ++q2) z += B.w[q01 + PP * q2] * ai[q2 * P + i2] * aj[q2 * P + j2];
+    Z[t] = z;
+  }
+  __syncthreads();
+  const int nu = elastic ? dim * dim : 2;
+  for (int t = threadIdx.x; t < nu * ny; t += blockDim.x) {
+    const int w = t % ny, u = t / ny;
+    const int c = w % M12, r = (w / M12) % M12, q0 = w / (M12 * M12);
+    const int i1 = r % P, i2 = r / P, j1 = c % P, j2 = c / P;
+    const int e = i2 + P2 * j2;
+    double y = 0.0;
+    if (!elastic) {
+      // u = 0: no derivative on axes 1, 2; u = 1: one derivative on axis 1 or 2
+      const double* a10 = A + 2 * PP;
+      const double* a11 = A + 3 * PP;
+      for (int q1 = 0; q1 < P; ++q1) {
+        const double z0 = Z[(q0 + P * q1) * Z2 + e];
+        const double v0 = a10[q1 * P + i1] * a10[q1 * P + j1];
+        if (u == 0) {
+          y += z0 * v0;
+        } else {
+          const double z1 = Z[(3 * PP + q0 + P * q1) * Z2 + e];
+          y += z0 * (a11[q1 * P + i1] * a11[q1 * P + j1]) + z1 * v0;
+        }
+      }
+    } else {
+      const int f = u / dim, g = u % dim;
+      const int v = (f == 2 ? 1 : 0) + 2 * (g == 2 ? 1 : 0);
+      const double* ai = A + (2 + (f == 1 ? 1 : 0)) * PP;
+      const double* aj = A + (2 + (g == 1 ? 1 : 0)) * PP;
+      for (int q1 = 0; q1 < P; ++q1)
+        y += Z[(v * PP + q0 + P * q1) * Z2 + e] * ai[q1 * P + i1] * aj[q1 * P + j1];
+    }
+    Y[t] = y;
+  }
+  __syncthreads();
+  for (int k = 0; k < ps.cnt; ++k) {
+    const int I = ps.i[k], J = ps.j[k];
+    double s = 0.0;
+    if (!elastic) {
+      const int i0 = I % P, r = I / P, j0 = J % P, c = J / P;
+      for (int q0 = 0; q0 < P; ++q0) {
+        const int o = (q0 * M12 + r) * M12 + c;
+        s += Y[o] * (A[PP + q0 * P + i0] * A[PP + q0 * P + j0]) +
+             Y[ny + o] * (A[q0 * P + i0] * A[q0 * P + j0]);
+      }
+      ps.acc[k] += kappa * s;
+    } else {
+      const int f = I / ns, g = J / ns, i = I % ns, j = J % ns;
+      const int i0 = i % P, r = i / P, j0 = j % P, c = j / P;
+      const int sf0 = f == 0 ? 1 : 0, sg0 = g == 0 ? 1 : 0;
+      for (int q0 = 0; q0 < P; ++q0) {
+        const int o = (q0 * M12 + r) * M12 + c;
+        double t = lam * Y[(f * dim + g) * ny + o] * (A[sf0 * PP + q0 * P + i0] * A[sg0 * PP + q0 * P + j0]) +
+                   mu * Y[(g * dim + f) * ny + o] * (A[sg0 * PP + q0 * P + i0] * A[sf0 * PP + q0 * P + j0]);
+        if (f == g)
+          for (int a = 0; a < dim; ++a) {
+            const int sa = a == 0 ? 1 : 0;
+            t += mu * Y[(a * dim + a) * ny + o] * (A[sa * PP + q0 * P + i0] * A[sa * PP + q0 * P + j0]);
+          }
+        s += t;
+      }
+      ps.acc[k] += s;
+    }
+  }
+}
+
 // b_i += sum_q w_q fg_q N_i
 __device__ void accumulate_load(const PointBatch& B, int np, int dim, int P1, int n,
                                 double* bacc) {
@@ -377,15 +488,19 @@ struct ElemShared {
   double gauss[2 * (kMaxP + 1)];
 };
 
+// Start of the sum-factorisation scratch behind ElemShared (16-byte aligned).
+__host__ __device__ constexpr size_t sf_offset() { return (sizeof(ElemShared) + 15) / 16 * 16; }
+
 // One CTA per own cell: volume terms on the space-tree leaves, penalty on
 // the marching-simplex surface of cut leaves, box-face penalty and traction.
 // Poisson (n = (p+1)^d) or isotropic elasticity (n = d (p+1)^d, fields
 // stacked).
 __global__ void __launch_bounds__(kThreads) element_own_kernel(
     Problem P, const double* gauss, int ncell, const int* cells, double* Kout, double* bout,
-    Node* scratch, int max_nodes) {
+    Node* scratch, int max_nodes, int sf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ElemShared& S = *reinterpret_cast<ElemShared*>(smem_raw);
+  double* sfx = reinterpret_cast<double*>(smem_raw + sf_offset());  // sum factorisation
   const int dim = P.dim, p = P.p, P1 = p + 1;
   int ns = 1;
   for (int a = 0; a < dim; ++a) ns *= P1;
@@ -536,7 +651,9 @@ __global__ void __launch_bounds__(kThreads) element_own_kernel(
         __syncthreads();
         batch_tables(S.B, np, dim, p, S.x0, S.x1);
         __syncthreads();
-        if (elastic)
+        if (sf)  // the leaf's points are one batch (np == Qleaf)
+          sf_accumulate(S.B, sfx, dim, P1, ns, elastic, lam, mu, P.kappa, ps);
+        else if (elastic)
           accumulate_elastic(S.B, np, dim, P1, ns, lam, mu, ps);
         else
           accumulate_stiffness(S.B, np, dim, P1, P.kappa, ps);
@@ -769,16 +886,33 @@ void launch_element_own(const Problem& P, const double* gauss, int ncell, const 
                         cudaStream_t s) {
   if (ncell == 0) return;
   int grid = ncell < 2048 ? ncell : 2048;
-  size_t smem = sizeof(ElemShared);
-  static const bool attr = [smem] {
+  // sum factorisation when a leaf's (p+1)^d points are one batch
+  int ns = 1;
+  for (int a = 0; a < P.dim; ++a) ns *= P.p + 1;
+  const bool elastic = P.pde == FCM_PDE_ELASTICITY;
+  const int sf = P.sumfact && ns <= kMaxPts ? 1 : 0;
+  size_t smem = sf ? sf_offset() + sizeof(double) * sf_doubles(P.dim, P.p + 1, elastic)
+                   : sizeof(ElemShared);
+  static const bool attr = [] {
+    // the largest scratch of the supported cases: (p+1)^d <= kMaxPts points
+    // and at most 128 DOFs per cell
+    int most = 0;
+    for (int dim = 2; dim <= 3; ++dim)
+      for (int P1 = 2; P1 <= kMaxP + 1; ++P1) {
+        int q = 1;
+        for (int a = 0; a < dim; ++a) q *= P1;
+        if (q > kMaxPts) continue;
+        most = std::max(most, sf_doubles(dim, P1, false));
+        if (dim * q <= 128) most = std::max(most, sf_doubles(dim, P1, true));
+      }
     cudaFuncSetAttribute(element_own_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+                         (int)(sf_offset() + sizeof(double) * most));
     return true;
   }();
   (void)attr;
   element_own_kernel<<<grid, kThreads, smem, s>>>(P, gauss, ncell, cells, K, bvec,
                                                   reinterpret_cast<Node*>(leaf_scratch),
-                                                  max_nodes);
+                                                  max_nodes, sf);
 }
 
 size_t element_scratch_bytes(int ncell, int max_nodes) {

@@ -27,6 +27,7 @@ OP_APPLY, OP_SMOOTHER, OP_RESTRICT, OP_PROLONG, OP_COARSE = 0, 1, 2, 3, 4
 SMOOTHER = {"elementwise": 0, "patchwise": 1, "jacobi": 2}
 METHOD_CG_MG, METHOD_MG, METHOD_CG_AS = 0, 1, 2
 SPACE_TENSOR, SPACE_TRUNK = 0, 1
+QUAD_POINTS, QUAD_SUMFACT = 0, 1
 
 EXPORTS = ["fcm_setup", "fcm_ndofs", "fcm_rhs", "fcm_apply", "fcm_vcycle", "fcm_num_levels",
            "fcm_level_info_get", "fcm_level_op", "fcm_cell_classes", "fcm_pcg_solve",
@@ -57,7 +58,8 @@ class fcm_physics(C.Structure):
                 ("alpha", C.c_double), ("beta", C.c_double), ("source", C.c_int),
                 ("f0", C.c_double), ("src_a", C.c_double), ("dirichlet", C.c_int),
                 ("g", C.c_int), ("dirichlet_faces", C.c_uint), ("traction_face", C.c_int),
-                ("traction", C.c_double * 3), ("quad_depth", C.c_int)]
+                ("traction", C.c_double * 3), ("quad_depth", C.c_int),
+                ("quadrature", C.c_int)]
 
 
 class fcm_solver_opts(C.Structure):
@@ -396,6 +398,10 @@ def descriptors(prob: dict, build_mixed: bool = True):
         for a in range(3):
             ph.traction[a] = tr["t"][a] if a < len(tr["t"]) else 0.0
     ph.quad_depth = prob["quad_depth"]
+    quads = {"points": QUAD_POINTS, "sumfact": QUAD_SUMFACT}
+    if prob.get("quadrature", "points") not in quads:
+        raise ValueError(f"quadrature {prob['quadrature']!r}: one of {sorted(quads)}")
+    ph.quadrature = quads[prob.get("quadrature", "points")]
     op = fcm_solver_opts()
     op.smoother = SMOOTHER[prob.get("smoother", "elementwise")]
     op.omega = prob["omega"] if prob.get("omega") else 0.0

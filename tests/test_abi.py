@@ -267,3 +267,18 @@ def test_descriptors_refuse_what_the_library_lacks():
     assert gm.complement == 0
     _, gm, _, _, _ = fcm.descriptors(dict(base, geometry=dict(base["geometry"], complement=True)))
     assert gm.complement == 1
+
+
+def test_quadrature_descriptor():
+    """The leaf-sum scheme of the cell integration reaches fcm_physics:
+    point sums by default, sum factorisation on request, anything else
+    refused before the library is called."""
+    import fcm_inputs as fi
+    from paper_2010_00881_gb300 import fcm
+    base = fi.poisson3d_sphere(cells=4, p=3)
+    _, _, ph, _, _ = fcm.descriptors(base)
+    assert ph.quadrature == fcm.QUAD_POINTS == 0
+    _, _, ph, _, _ = fcm.descriptors(dict(base, quadrature="sumfact"))
+    assert ph.quadrature == fcm.QUAD_SUMFACT == 1
+    with pytest.raises(ValueError):
+        fcm.descriptors(dict(base, quadrature="gauss"))
