@@ -263,7 +263,8 @@ def run_batch(args, rank, world, local):
     import torch
     from paper_2010_00881_gb300 import FCM_FP64, FCM_MIXED
     from paper_2010_00881_gb300 import fcm as F
-    probs = fi.batch(256, base_seed=0)[: args.batch_n]
+    probs = [dict(q, quadrature=args.quadrature)
+             for q in fi.batch(256, base_seed=0)[: args.batch_n]]
     t0 = time.perf_counter()
     b = F.Batch(probs, threads=16)
     setup_s = time.perf_counter() - t0
@@ -325,7 +326,7 @@ def run_mlhp(args, rank, world, local):
         prob = fi.poisson3d_sphere_mlhp(cells=cells, p=2, overlay_levels=k)
     else:
         prob = dict(fi.poisson3d_sphere(cells=cells, p=2, radius=0.3), overlay_levels=0)
-    prob = dict(prob, smoother=args.smoother)
+    prob = dict(prob, smoother=args.smoother, quadrature=args.quadrature)
     wl_name = f"poisson3d_sphere_mlhp_{cells}^3_p2_k{k}_{args.smoother}"
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
@@ -400,6 +401,9 @@ def main():
                     help="instances of the batch workload (the first n of the seeded 256)")
     ap.add_argument("--cells", type=int, default=0,
                     help="cells per axis of the popcorn workload (default 96)")
+    ap.add_argument("--quadrature", default="points", choices=["points", "sumfact"],
+                    help="leaf sums of the cut-cell integration (set-up): point by point, or "
+                         "sum factorisation over each leaf's tensor grid of points")
     ap.add_argument("--overlays", type=int, default=1,
                     help="overlay levels of the mlhp workload")
     ap.add_argument("--smoother", default="patchwise", choices=["patchwise", "elementwise"],
@@ -439,6 +443,8 @@ def main():
         wl_name = f"popcorn_{args.cells or 96}^3_p3_tensor"
     else:
         prob, wl_name = fi.elasticity3d_voids(cells=64, p=2), "elasticity3d_voids_64^3_p2"
+    if args.quadrature != "points":
+        prob, wl_name = dict(prob, quadrature=args.quadrature), wl_name + "_" + args.quadrature
     s = Solver(prob, build_mixed=True)
     N = s.ndofs
     dev = torch.device("cuda", local)
