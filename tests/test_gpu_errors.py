@@ -36,6 +36,7 @@ def _setup(prob, **over):
     ({"op.coarse_cells": 0}, F.FCM_E_INVALID),
     ({"g.overlay_levels": 2}, F.FCM_E_UNSUPPORTED),
     ({"op.smoother": 1}, F.FCM_E_UNSUPPORTED),
+    ({"ph.quadrature": 7}, F.FCM_E_INVALID),
 ])
 def test_invalid_setup(over, status):
     st, h = _setup(fi.poisson2d_circle(cells=4), **over)
